@@ -1,0 +1,167 @@
+/*
+ * bsd.h -- C ABI of the GB300 beam search decoder for quantum LDPC codes.
+ *
+ * The decoding problem is the triple (H in F2^{M x N}, A in F2^{K x N},
+ * p in (0,1)^N) of the paper's App. A: columns are error sources, rows of H
+ * are detectors, rows of A are logical observables.  Given a syndrome
+ * s = H e the decoder returns a correction e^ with (when it converges)
+ * H e^ = s, and the observable flips A e^.  The method is BP-guided beam
+ * search: min-sum belief propagation (App. A, Eqs. 1-4), masked BP (Alg. 2)
+ * and the beam search controller (Alg. 3 with App. B), run on the GPU for
+ * every beam candidate of every syndrome.
+ *
+ * Conventions
+ *   - Every function returns BSD_OK (0) or a negative BSD_ERR_* code; no
+ *     function aborts the process.  bsd_error_string() names a code.
+ *   - Bit vectors are little-endian uint32 words: bit i of a length-L vector
+ *     is bit (i % 32) of word i / 32; a vector takes ceil(L/32) words and
+ *     padding bits above L must be zero on input and are written as zero.
+ *   - Buffers marked "device" are CUDA device pointers on the decoder's
+ *     device; buffers marked "host" are ordinary (preferably pinned) host
+ *     memory.  The caller owns every input and output buffer; the decoder
+ *     owns only its internal copies of (H, A, p) and its workspace.
+ *   - Decoding is asynchronous and stream-ordered, like a CUDA call on the
+ *     given stream (NULL = the legacy default stream), except where stated.
+ *   - A decoder handle is not thread-safe: one call at a time per handle.
+ *   - Arithmetic: edge messages are stored in single precision and every sum
+ *     is formed in single precision in the order fixed by the readings below,
+ *     so results do not depend on launch configuration or scheduling.
+ *
+ * Readings of points the paper leaves open (shared with the test oracle):
+ *   min-sum scale alpha on D (ms_scale, 1 = Eq. 1 as printed); sign(x) = -1
+ *   iff x < 0; a minimum over no other unmasked neighbour is llr_clamp; every
+ *   stored E_{j->i} is clamped to [-llr_clamp, llr_clamp]; the sums of
+ *   Eqs. 2-3 start at Lambda_j and add the detector messages in ascending
+ *   order of value; sum_LLR covers the iterations actually run in that call;
+ *   argmin ties go to the lowest index; pruning keeps the top beam_width under
+ *   (score descending, canonical index ascending) where the canonical index
+ *   of a child is 2 * (rank of its parent) + val; scores and weights are
+ *   summed exactly on the fixed-point grid 2^-16.
+ */
+#ifndef BSD_H
+#define BSD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BSD_PARAMS_VERSION 1u
+
+/* return codes */
+#define BSD_OK               0
+#define BSD_ERR_INVALID_ARG (-1)   /* bad pointer, size, index, prior or parameter */
+#define BSD_ERR_CUDA        (-2)   /* a CUDA runtime call failed */
+#define BSD_ERR_OOM         (-3)   /* device or host allocation failed */
+#define BSD_ERR_TIMEOUT     (-4)   /* a bounded device-side wait gave up */
+#define BSD_ERR_UNSUPPORTED (-5)   /* valid input outside what this build handles */
+#define BSD_ERR_DEVICE      (-6)   /* a device-side check recorded an error */
+
+/* message storage precision (bsd_params.msg_precision) */
+#define BSD_FP32 0
+
+/* per-shot status words written by bsd_decode */
+#define BSD_STATUS_CONVERGED_SEED 1u  /* returned e^ comes from the seed BP (Alg. 3, first BP run) */
+#define BSD_STATUS_CONVERGED_BEAM 2u  /* returned e^ comes from a masked BP round (Alg. 2/3)    */
+#define BSD_STATUS_FAILED         4u  /* no e^ with H e^ = s was found: e^ is the hard decision
+                                         of the best path of the final set, fixed values filled */
+
+typedef struct bsd_decoder bsd_decoder;
+
+/* Decoder parameters.  max_rounds .. num_results are the five parameters of
+   Alg. 3 (Table I lists the paper's presets). */
+typedef struct {
+    uint32_t struct_version;   /* must be BSD_PARAMS_VERSION */
+    int32_t  max_rounds;       /* rounds of branching, >= 0 */
+    int32_t  beam_width;       /* paths kept per round, 1..64 */
+    int32_t  initial_iters;    /* seed BP iterations, >= 1 */
+    int32_t  iters_per_round;  /* masked BP iterations per child, >= 1 */
+    int32_t  num_results;      /* valid solutions to collect before returning, 1..64 */
+    float    ms_scale;         /* alpha in D = alpha * (-1)^s * prod sign * min; (0, 1] */
+    float    llr_clamp;        /* L_MAX > 0 */
+    int32_t  msg_precision;    /* BSD_FP32 */
+    int32_t  reserved0;
+    int64_t  workspace_bytes;  /* device workspace budget; 0 = library default (4 GiB) */
+} bsd_params;
+
+/* Fill *out with the library defaults: beam8_230iters, ms_scale 1,
+   llr_clamp 1e4, FP32.  Returns BSD_ERR_INVALID_ARG if out is NULL. */
+int bsd_params_default(bsd_params *out);
+
+/* Fill *out with a Table I preset ("beam8_230iters", "beam32_340iters",
+   "beam64_640iters", "beam64_32res_640iters"); other fields take the
+   defaults.  Returns BSD_ERR_INVALID_ARG for an unknown name or NULL. */
+int bsd_params_preset(const char *name, bsd_params *out);
+
+/* Create a decoder for (H, A, p) on CUDA device `device`.
+ *   H_row_ptr[M+1], H_col_idx[nnz]  host CSR of H; column indices of a row
+ *                                    strictly ascending, each in [0, N)
+ *   A_row_ptr[K+1], A_col_idx[nnzA] host CSR of A (K may be 0)
+ *   priors[N]                        host, each strictly inside (0, 1);
+ *                                    Lambda_j = log((1 - p_j) / p_j) (App. A)
+ *   params                           see bsd_params
+ * The inputs are copied; the caller may free them after the call.  Device
+ * memory for the graph and the workspace is allocated here (synchronously).
+ * Errors: BSD_ERR_INVALID_ARG (sizes, indices, priors, parameters),
+ * BSD_ERR_UNSUPPORTED (a size beyond this build's limits), BSD_ERR_OOM,
+ * BSD_ERR_CUDA.  On error *out is set to NULL. */
+int bsd_create(int32_t M, int32_t N, int32_t K,
+               const int32_t *H_row_ptr, const int32_t *H_col_idx,
+               const int32_t *A_row_ptr, const int32_t *A_col_idx,
+               const double *priors, const bsd_params *params,
+               int device, bsd_decoder **out);
+
+/* Decode B syndromes with the beam search decoder (Alg. 3).
+ *   d_syndromes    device, B x ceil(M/32) words, read only
+ *   d_corrections  device, B x ceil(N/32) words, e^ per shot
+ *   d_obs_flips    device, B x ceil(K/32) words, A e^ per shot (may be NULL if K = 0)
+ *   d_status       device, B words, one BSD_STATUS_* value per shot
+ *   d_iters        device, B words or NULL: BP iterations the sequential
+ *                  algorithm runs up to its return (seed plus every visited
+ *                  child), capped at 2^32 - 1
+ *   cuda_stream    cudaStream_t or NULL
+ * Shots are independent; results do not depend on B or on how the batch is
+ * split.  Returns BSD_ERR_INVALID_ARG for NULL buffers or B < 0, else the
+ * launch status (BSD_ERR_CUDA).  Device-side errors are reported by
+ * bsd_sync_error. */
+int bsd_decode(bsd_decoder *dec, const uint32_t *d_syndromes, int64_t B,
+               uint32_t *d_corrections, uint32_t *d_obs_flips,
+               uint32_t *d_status, uint32_t *d_iters, void *cuda_stream);
+
+/* bsd_decode on host buffers (same layouts): copies the syndromes in,
+ * decodes and copies the results back, synchronising the stream before it
+ * returns.  h_iters may be NULL.  Pinned host memory gives asynchronous
+ * copies; pageable memory works but copies synchronously. */
+int bsd_decode_host(bsd_decoder *dec, const uint32_t *h_syndromes, int64_t B,
+                    uint32_t *h_corrections, uint32_t *h_obs_flips,
+                    uint32_t *h_status, uint32_t *h_iters, void *cuda_stream);
+
+/* Plain min-sum BP (App. A, Eqs. 1-3) from E(0) = Lambda for exactly T
+ * iterations per syndrome, with no stopping rule; writes the posterior LLRs
+ * Lambda_j(T) (device, B x N floats) and, if d_sum_llr is not NULL, the sums
+ * over t = 1..T of Lambda_j(t) (device, B x N floats).  Used to measure the
+ * LLRs against a double-precision reference.  T in [1, 100000]. */
+int bsd_bp_llr(bsd_decoder *dec, const uint32_t *d_syndromes, int64_t B, int32_t T,
+               float *d_llr, float *d_sum_llr, void *cuda_stream);
+
+/* Synchronise the decoder's last stream, read and clear the device-side
+ * error word: BSD_OK, BSD_ERR_TIMEOUT or BSD_ERR_DEVICE. */
+int bsd_sync_error(bsd_decoder *dec);
+
+/* Sizes and launch shape: any pointer may be NULL.  chunk_shots is the
+ * number of shots decoded per internal pass (bounded by the workspace). */
+int bsd_get_info(const bsd_decoder *dec, int32_t *M, int32_t *N, int32_t *K, int32_t *n_edges,
+                 int64_t *chunk_shots, int64_t *workspace_bytes);
+
+/* Static text for a return code. */
+const char *bsd_error_string(int code);
+
+/* Release the decoder's device memory.  NULL is ignored. */
+void bsd_destroy(bsd_decoder *dec);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSD_H */

@@ -83,8 +83,8 @@ def _lib(precision: str) -> C.CDLL:
     lib.oracle_graph_create.restype = P
     lib.oracle_graph_create.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P]
     lib.oracle_graph_destroy.argtypes = [P]
-    lib.oracle_decode.argtypes = [P, C.POINTER(_Params), P, P, P, P, P, C.POINTER(_Trace)]
-    lib.oracle_decode_batch.argtypes = [P, C.POINTER(_Params), P, C.c_int64, P, P, P, P, P, C.c_int]
+    lib.oracle_decode.argtypes = [P, C.POINTER(_Params), P, P, P, P, P, P, C.POINTER(_Trace)]
+    lib.oracle_decode_batch.argtypes = [P, C.POINTER(_Params), P, C.c_int64, P, P, P, P, P, P, C.c_int]
     lib.oracle_masked_bp.argtypes = [P, C.POINTER(_Params), P, P, P, P, C.c_int, C.c_int,
                                      P, P, P, P, P, P]
     lib.oracle_masked_bp.restype = C.c_int
@@ -143,10 +143,11 @@ class Graph:
         status = np.zeros(B, np.uint32)
         iters = np.zeros(B, np.uint32)
         gap = np.zeros(B, np.float64)
+        ties = np.zeros(B, np.int32)
         p = params._c()
         self.lib.oracle_decode_batch(self.h, C.byref(p), _ptr(synd), B, _ptr(corr), _ptr(obs),
-                                     _ptr(status), _ptr(iters), _ptr(gap), int(nthreads))
-        return dict(corrections=corr, obs=obs, status=status, iters=iters, min_gap=gap)
+                                     _ptr(status), _ptr(iters), _ptr(gap), _ptr(ties), int(nthreads))
+        return dict(corrections=corr, obs=obs, status=status, iters=iters, min_gap=gap, ties=ties)
 
     def decode_one(self, s_bits: np.ndarray, params: Params, trace_cap: int = 4096) -> dict:
         """One syndrome given as M bytes; returns ehat (N bytes), status, iters, gap, trace."""
@@ -155,6 +156,7 @@ class Graph:
         st = np.zeros(1, np.int32)
         it = np.zeros(1, np.int64)
         gap = np.zeros(1, np.float64)
+        nt = np.zeros(1, np.int32)
         arrs = {nm: np.zeros(trace_cap, np.int32) for nm in
                 ("round", "canon", "parent_rank", "val", "pos", "success", "iters", "next_pos", "kept")}
         score = np.zeros(trace_cap, np.float64)
@@ -165,13 +167,14 @@ class Graph:
         tr.score = score.ctypes.data_as(C.POINTER(C.c_double))
         p = params._c()
         self.lib.oracle_decode(self.h, C.byref(p), _ptr(s), _ptr(e), _ptr(st), _ptr(it), _ptr(gap),
-                               C.byref(tr))
+                               _ptr(nt), C.byref(tr))
         n = tr.n
         trace = {nm: a[:n].copy() for nm, a in arrs.items()}
         trace["score"] = score[:n].copy()
         trace.update(seed_iters=tr.seed_iters, seed_success=tr.seed_success,
                      seed_next_pos=tr.seed_next_pos, ret_round=tr.ret_round, ret_canon=tr.ret_canon)
-        return dict(ehat=e, status=int(st[0]), iters=int(it[0]), min_gap=float(gap[0]), trace=trace)
+        return dict(ehat=e, status=int(st[0]), iters=int(it[0]), min_gap=float(gap[0]), ties=int(nt[0]),
+                    trace=trace)
 
     # ------------------------------------------------------------- masked BP
     def masked_bp(self, E_in, masked, val, s_bits, max_iters: int, params: Params,

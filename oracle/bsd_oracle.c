@@ -185,15 +185,20 @@ typedef struct {
     int *ebuf;
 } bp_work;
 
-/* Near-tie log: the smallest nonzero relative margin of a decision taken in
-   floating point (a sign, an argmin, a score order, a weight order).  Exact
-   ties (margin 0) are not near-ties: R5 and R7 settle them the same way in
-   any precision. */
+/* Near-tie log of the decisions taken in floating point (a sign, an argmin,
+   a score order, a weight order): the smallest nonzero relative margin, and
+   the number of exact ties (margin 0).  R5 and R7 settle an exact tie the
+   same way in any precision only when both precisions compute equal values;
+   a lower precision can also split an exact tie of this build. */
+static int g_ties_tls_dummy;
+static _Thread_local int *g_tie_counter = &g_ties_tls_dummy;
+
 static void gap_update(double *g, double value, double scale)
 {
     double s = scale > 1.0 ? scale : 1.0;
     double r = fabs(value) / s;
-    if (r > 0 && r < *g) *g = r;
+    if (r == 0) { ++*g_tie_counter; return; }
+    if (r < *g) *g = r;
 }
 
 static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *c, bp_work *w)
@@ -537,8 +542,10 @@ static void trace_child(oracle_trace *tr, int round, int canon, int prank, int v
    (1 = converged in the seed BP, 2 = converged in a masked BP round, 4 = failed),
    iters = BP iterations run by the sequential algorithm up to its return. */
 static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *status,
-                       int64_t *iters_total, double *min_gap, oracle_trace *tr)
+                       int64_t *iters_total, double *min_gap, int32_t *n_ties, oracle_trace *tr)
 {
+    int ties = 0;
+    g_tie_counter = &ties;
     const oracle_graph *g = x->g;
     const oracle_params *prm = x->prm;
     const int N = g->N, E = g->E;
@@ -569,7 +576,8 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
     total += c->iters;
     double agap;
     seed->next_pos = least_reliable(g, x->sum_llr, x->cmask, &agap);
-    if (agap > 0 && agap < gap) gap = agap;
+    if (agap == 0) ++*g_tie_counter;
+    else if (agap < gap) gap = agap;
     seed->score = 0;
     seed->canon = 0;
     memset(seed->masked, 0, (size_t)N);
@@ -608,7 +616,8 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
                 memcpy(ch->masked, x->cmask, (size_t)N);
                 memcpy(ch->val, x->cval, (size_t)N);
                 ch->next_pos = least_reliable(g, x->sum_llr, x->cmask, &agap);
-                if (ch->next_pos >= 0 && agap > 0 && agap < gap) gap = agap;
+                if (ch->next_pos >= 0 && agap == 0) ++*g_tie_counter;
+                else if (ch->next_pos >= 0 && agap < gap) gap = agap;
                 ch->score = path_score(g, x->sum_llr, x->cmask, c->iters, x->tmp);
                 ch->canon = canon;
                 trace_child(tr, r, canon, pr, v, par->next_pos, succ, c->iters, ch->next_pos,
@@ -663,6 +672,8 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
     *status = st;
     *iters_total = total;
     if (min_gap) *min_gap = gap;
+    if (n_ties) *n_ties = ties;
+    g_tie_counter = &g_ties_tls_dummy;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -673,10 +684,10 @@ int oracle_real_bytes(void) { return (int)sizeof(real); }
 /* One syndrome, unpacked bytes.  Returns 0. */
 int oracle_decode(const oracle_graph *g, const oracle_params *prm, const uint8_t *s,
                   uint8_t *ehat, int32_t *status, int64_t *iters, double *min_gap,
-                  oracle_trace *tr)
+                  int32_t *n_ties, oracle_trace *tr)
 {
     dec_ctx *x = ctx_new(g, prm);
-    decode_one(x, s, ehat, status, iters, min_gap, tr);
+    decode_one(x, s, ehat, status, iters, min_gap, n_ties, tr);
     ctx_free(x);
     return 0;
 }
@@ -688,6 +699,7 @@ typedef struct {
     int64_t b0, b1;
     uint32_t *corr, *obs, *status, *iters;
     double *min_gap;
+    int32_t *ties;
 } batch_job;
 
 static void *batch_worker(void *arg)
@@ -701,8 +713,8 @@ static void *batch_worker(void *arg)
     uint8_t *e = (uint8_t *)malloc((size_t)(N > 0 ? N : 1));
     for (int64_t b = jb->b0; b < jb->b1; ++b) {
         for (int i = 0; i < M; ++i) s[i] = (uint8_t)((jb->synd[b * WM + i / 32] >> (i % 32)) & 1u);
-        int32_t st; int64_t it; double gp;
-        decode_one(x, s, e, &st, &it, &gp, NULL);
+        int32_t st, nt; int64_t it; double gp;
+        decode_one(x, s, e, &st, &it, &gp, &nt, NULL);
         if (jb->corr) {
             uint32_t *o = jb->corr + b * WN;
             for (int k = 0; k < WN; ++k) o[k] = 0;
@@ -720,6 +732,7 @@ static void *batch_worker(void *arg)
         if (jb->status) jb->status[b] = (uint32_t)st;
         if (jb->iters) jb->iters[b] = (uint32_t)it;
         if (jb->min_gap) jb->min_gap[b] = gp;
+        if (jb->ties) jb->ties[b] = nt;
     }
     free(s); free(e);
     ctx_free(x);
@@ -733,7 +746,7 @@ static void *batch_worker(void *arg)
 int oracle_decode_batch(const oracle_graph *g, const oracle_params *prm,
                         const uint32_t *synd, int64_t B,
                         uint32_t *corr, uint32_t *obs, uint32_t *status, uint32_t *iters,
-                        double *min_gap, int nthreads)
+                        double *min_gap, int32_t *ties, int nthreads)
 {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > B) nthreads = (int)(B > 0 ? B : 1);
@@ -744,6 +757,7 @@ int oracle_decode_batch(const oracle_graph *g, const oracle_params *prm,
         jobs[k].b0 = B * k / nthreads; jobs[k].b1 = B * (k + 1) / nthreads;
         jobs[k].corr = corr; jobs[k].obs = obs; jobs[k].status = status; jobs[k].iters = iters;
         jobs[k].min_gap = min_gap;
+        jobs[k].ties = ties;
     }
     for (int k = 1; k < nthreads; ++k) pthread_create(&th[k], NULL, batch_worker, &jobs[k]);
     batch_worker(&jobs[0]);

@@ -1,0 +1,140 @@
+"""ctypes binding of libbsd.so: the C ABI of include/bsd.h under the same names.
+
+Argument marshalling only; every step of decoding runs in the CUDA library.
+There is no CPU fallback: if the library is missing or fails to load, the
+import of this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbsd.so")
+
+BSD_PARAMS_VERSION = 1
+BSD_OK = 0
+BSD_ERR_INVALID_ARG = -1
+BSD_ERR_CUDA = -2
+BSD_ERR_OOM = -3
+BSD_ERR_TIMEOUT = -4
+BSD_ERR_UNSUPPORTED = -5
+BSD_ERR_DEVICE = -6
+BSD_FP32 = 0
+BSD_STATUS_CONVERGED_SEED = 1
+BSD_STATUS_CONVERGED_BEAM = 2
+BSD_STATUS_FAILED = 4
+
+# every symbol include/bsd.h declares
+EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
+           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_error_string", "bsd_destroy")
+
+
+class bsd_params(C.Structure):
+    _fields_ = [("struct_version", C.c_uint32), ("max_rounds", C.c_int32), ("beam_width", C.c_int32),
+                ("initial_iters", C.c_int32), ("iters_per_round", C.c_int32), ("num_results", C.c_int32),
+                ("ms_scale", C.c_float), ("llr_clamp", C.c_float), ("msg_precision", C.c_int32),
+                ("reserved0", C.c_int32), ("workspace_bytes", C.c_int64)]
+
+
+class BsdError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {bsd_error_string(code)} ({code})")
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load libbsd.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        from . import _build
+        path = _build.build()
+    if not os.path.exists(path):
+        raise OSError(f"CUDA library not found: {path}")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.bsd_params_default.argtypes = [C.POINTER(bsd_params)]
+    lib.bsd_params_preset.argtypes = [C.c_char_p, C.POINTER(bsd_params)]
+    lib.bsd_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, C.POINTER(bsd_params), C.c_int,
+                               C.POINTER(P)]
+    lib.bsd_decode.argtypes = [P, P, C.c_int64, P, P, P, P, P]
+    lib.bsd_decode_host.argtypes = [P, P, C.c_int64, P, P, P, P, P]
+    lib.bsd_bp_llr.argtypes = [P, P, C.c_int64, C.c_int32, P, P, P]
+    lib.bsd_sync_error.argtypes = [P]
+    lib.bsd_get_info.argtypes = [P] + [C.POINTER(C.c_int32)] * 4 + [C.POINTER(C.c_int64)] * 2
+    lib.bsd_error_string.argtypes = [C.c_int]
+    lib.bsd_error_string.restype = C.c_char_p
+    lib.bsd_destroy.argtypes = [P]
+    lib.bsd_destroy.restype = None
+    for nm in EXPORTS:
+        if nm not in ("bsd_error_string", "bsd_destroy"):
+            getattr(lib, nm).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def check(code: int, what: str) -> None:
+    if code != BSD_OK:
+        raise BsdError(code, what)
+
+
+# ---- the C ABI, same names ---------------------------------------------------
+def bsd_error_string(code: int) -> str:
+    return load().bsd_error_string(int(code)).decode()
+
+
+def bsd_params_default() -> bsd_params:
+    p = bsd_params()
+    check(load().bsd_params_default(C.byref(p)), "bsd_params_default")
+    return p
+
+
+def bsd_params_preset(name: str) -> bsd_params:
+    p = bsd_params()
+    check(load().bsd_params_preset(name.encode(), C.byref(p)), f"bsd_params_preset({name})")
+    return p
+
+
+def bsd_create(M, N, K, H_row_ptr, H_col_idx, A_row_ptr, A_col_idx, priors, params: bsd_params,
+               device: int = 0) -> int:
+    """Pointers are host addresses (ints) of int32 / float64 arrays."""
+    h = C.c_void_p()
+    check(load().bsd_create(int(M), int(N), int(K), H_row_ptr, H_col_idx, A_row_ptr, A_col_idx, priors,
+                            C.byref(params), int(device), C.byref(h)), "bsd_create")
+    return h.value
+
+
+def bsd_decode(dec, d_syndromes, B, d_corrections, d_obs_flips, d_status, d_iters, stream) -> None:
+    check(load().bsd_decode(dec, d_syndromes, int(B), d_corrections, d_obs_flips, d_status, d_iters, stream),
+          "bsd_decode")
+
+
+def bsd_decode_host(dec, h_syndromes, B, h_corrections, h_obs_flips, h_status, h_iters, stream) -> None:
+    check(load().bsd_decode_host(dec, h_syndromes, int(B), h_corrections, h_obs_flips, h_status, h_iters, stream),
+          "bsd_decode_host")
+
+
+def bsd_bp_llr(dec, d_syndromes, B, T, d_llr, d_sum_llr, stream) -> None:
+    check(load().bsd_bp_llr(dec, d_syndromes, int(B), int(T), d_llr, d_sum_llr, stream), "bsd_bp_llr")
+
+
+def bsd_sync_error(dec) -> int:
+    return int(load().bsd_sync_error(dec))
+
+
+def bsd_get_info(dec) -> dict:
+    M, N, K, E = (C.c_int32() for _ in range(4))
+    cs, wb = C.c_int64(), C.c_int64()
+    check(load().bsd_get_info(dec, C.byref(M), C.byref(N), C.byref(K), C.byref(E), C.byref(cs), C.byref(wb)),
+          "bsd_get_info")
+    return dict(M=M.value, N=N.value, K=K.value, n_edges=E.value, chunk_shots=cs.value, workspace_bytes=wb.value)
+
+
+def bsd_destroy(dec) -> None:
+    if dec:
+        load().bsd_destroy(dec)

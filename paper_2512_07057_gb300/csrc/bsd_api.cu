@@ -1,0 +1,449 @@
+// bsd_api.cu -- host side of the C ABI declared in include/bsd.h.
+//
+// bsd_create validates (H, A, p) and the Alg. 3 parameters, builds the
+// device graph tables (CSR, per-column edge lists, column bitsets of H and A,
+// prior LLRs) and sizes the beam workspace; bsd_decode splits a batch into
+// chunks that fit the workspace and launches, per chunk, the seed kernel and
+// two kernels per beam round, all on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bsd.h"
+#include "bsd_internal.cuh"
+
+using namespace bsd;
+
+struct bsd_decoder {
+    int device = 0;
+    bsd_params prm{};
+    DevGraph g{};
+    DecCfg cfg{};
+    LaunchShape ls{};
+    void* graph_mem = nullptr;
+    size_t graph_bytes = 0;
+    void* work_mem = nullptr;
+    size_t work_bytes = 0;
+    size_t ctr_bytes = 0;
+    Work w{};
+    void* io_mem = nullptr;        // device staging for bsd_decode_host
+    size_t io_bytes = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+inline int words_of(long long bits) { return (int)((bits + 31) / 32); }
+
+const char* kPresetNames[] = {"beam8_230iters", "beam32_340iters", "beam64_640iters", "beam64_32res_640iters"};
+// Table I: max_rounds, beam_width, initial_iters, iters_per_round, num_results
+const int kPresetVals[][5] = {{10, 8, 30, 20, 1}, {10, 32, 40, 30, 1}, {20, 64, 40, 30, 1}, {20, 64, 40, 30, 32}};
+
+int validate_params(const bsd_params* p)
+{
+    if (!p) return BSD_ERR_INVALID_ARG;
+    if (p->struct_version != BSD_PARAMS_VERSION) return BSD_ERR_INVALID_ARG;
+    if (p->max_rounds < 0 || p->max_rounds > 10000) return BSD_ERR_INVALID_ARG;
+    if (p->beam_width < 1 || p->beam_width > kMaxBeam) return BSD_ERR_INVALID_ARG;
+    if (p->initial_iters < 1 || p->initial_iters > 1000000) return BSD_ERR_INVALID_ARG;
+    if (p->iters_per_round < 1 || p->iters_per_round > 1000000) return BSD_ERR_INVALID_ARG;
+    if (p->num_results < 1 || p->num_results > kMaxResults) return BSD_ERR_INVALID_ARG;
+    if (!(p->ms_scale > 0.f) || !(p->ms_scale <= 4.f)) return BSD_ERR_INVALID_ARG;
+    if (!(p->llr_clamp > 0.f) || !std::isfinite(p->llr_clamp)) return BSD_ERR_INVALID_ARG;
+    if (p->msg_precision != BSD_FP32) return BSD_ERR_UNSUPPORTED;
+    if (p->workspace_bytes < 0) return BSD_ERR_INVALID_ARG;
+    return BSD_OK;
+}
+
+template <class T>
+T* carve(char*& p, size_t count)
+{
+    T* r = reinterpret_cast<T*>(p);
+    p += align256(sizeof(T) * (count > 0 ? count : 1));
+    return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bsd_error_string(int code)
+{
+    switch (code) {
+        case BSD_OK: return "ok";
+        case BSD_ERR_INVALID_ARG: return "invalid argument";
+        case BSD_ERR_CUDA: return "CUDA runtime error";
+        case BSD_ERR_OOM: return "out of memory";
+        case BSD_ERR_TIMEOUT: return "device-side wait timed out";
+        case BSD_ERR_UNSUPPORTED: return "unsupported size or option";
+        case BSD_ERR_DEVICE: return "device-side check failed";
+        default: return "unknown error";
+    }
+}
+
+int bsd_params_default(bsd_params* out)
+{
+    if (!out) return BSD_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->struct_version = BSD_PARAMS_VERSION;
+    out->max_rounds = 10;
+    out->beam_width = 8;
+    out->initial_iters = 30;
+    out->iters_per_round = 20;
+    out->num_results = 1;
+    out->ms_scale = 1.0f;
+    out->llr_clamp = 1.0e4f;
+    out->msg_precision = BSD_FP32;
+    out->workspace_bytes = 0;
+    return BSD_OK;
+}
+
+int bsd_params_preset(const char* name, bsd_params* out)
+{
+    if (!name || !out) return BSD_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) {
+        if (std::strcmp(name, kPresetNames[k]) == 0) {
+            bsd_params_default(out);
+            out->max_rounds = kPresetVals[k][0];
+            out->beam_width = kPresetVals[k][1];
+            out->initial_iters = kPresetVals[k][2];
+            out->iters_per_round = kPresetVals[k][3];
+            out->num_results = kPresetVals[k][4];
+            return BSD_OK;
+        }
+    }
+    return BSD_ERR_INVALID_ARG;
+}
+
+void bsd_destroy(bsd_decoder* dec)
+{
+    if (!dec) return;
+    {
+        DeviceGuard dg(dec->device);
+        if (dec->graph_mem) cudaFree(dec->graph_mem);
+        if (dec->work_mem) cudaFree(dec->work_mem);
+        if (dec->io_mem) cudaFree(dec->io_mem);
+    }
+    delete dec;
+}
+
+int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const int32_t* H_col_idx,
+               const int32_t* A_row_ptr, const int32_t* A_col_idx, const double* priors, const bsd_params* params,
+               int device, bsd_decoder** out)
+{
+    if (!out) return BSD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (M < 1 || N < 1 || K < 0 || !H_row_ptr || !H_col_idx || !priors) return BSD_ERR_INVALID_ARG;
+    if (K > 0 && (!A_row_ptr || !A_col_idx)) return BSD_ERR_INVALID_ARG;
+    int rc = validate_params(params);
+    if (rc) return rc;
+    // ---- validate H and A
+    if (H_row_ptr[0] != 0) return BSD_ERR_INVALID_ARG;
+    for (int i = 0; i < M; ++i) {
+        if (H_row_ptr[i + 1] < H_row_ptr[i]) return BSD_ERR_INVALID_ARG;
+        for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e) {
+            if (H_col_idx[e] < 0 || H_col_idx[e] >= N) return BSD_ERR_INVALID_ARG;
+            if (e > H_row_ptr[i] && H_col_idx[e] <= H_col_idx[e - 1]) return BSD_ERR_INVALID_ARG;
+        }
+    }
+    const long long E = H_row_ptr[M];
+    if (E < 1 || E > (1ll << 30)) return E < 1 ? BSD_ERR_INVALID_ARG : BSD_ERR_UNSUPPORTED;
+    if (K > 0) {
+        if (A_row_ptr[0] != 0) return BSD_ERR_INVALID_ARG;
+        for (int i = 0; i < K; ++i) {
+            if (A_row_ptr[i + 1] < A_row_ptr[i]) return BSD_ERR_INVALID_ARG;
+            for (int e = A_row_ptr[i]; e < A_row_ptr[i + 1]; ++e)
+                if (A_col_idx[e] < 0 || A_col_idx[e] >= N) return BSD_ERR_INVALID_ARG;
+        }
+    }
+    for (int j = 0; j < N; ++j)
+        if (!(priors[j] > 0.0 && priors[j] < 1.0)) return BSD_ERR_INVALID_ARG;
+
+    bsd_decoder* dec = new (std::nothrow) bsd_decoder();
+    if (!dec) return BSD_ERR_OOM;
+    dec->device = device;
+    dec->prm = *params;
+    DeviceGuard dg(device);
+    if (!dg.ok) { delete dec; return BSD_ERR_CUDA; }
+
+    // ---- host tables
+    const int WM = words_of(M), WN = words_of(N), WK = words_of(K);
+    const int Epad = (int)((E + 3) / 4 * 4), Npad = (N + 3) / 4 * 4;
+    std::vector<int> col_ptr(N + 1, 0), col_edge(E), col_row(E);
+    for (long long e = 0; e < E; ++e) col_ptr[H_col_idx[e] + 1]++;
+    for (int j = 0; j < N; ++j) col_ptr[j + 1] += col_ptr[j];
+    {
+        std::vector<int> fill(N, 0);
+        for (int i = 0; i < M; ++i)
+            for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e) {
+                const int j = H_col_idx[e];
+                const int k = col_ptr[j] + fill[j]++;
+                col_edge[k] = e;
+                col_row[k] = i;
+            }
+    }
+    int max_col = 0, max_row = 0;
+    for (int j = 0; j < N; ++j) max_col = std::max(max_col, col_ptr[j + 1] - col_ptr[j]);
+    for (int i = 0; i < M; ++i) max_row = std::max(max_row, H_row_ptr[i + 1] - H_row_ptr[i]);
+    const float L = params->llr_clamp;
+    std::vector<float> lam(Npad, 0.f), lamE(Epad, 0.f);
+    std::vector<long long> lamq(N);
+    int all_pos = 1;
+    for (int j = 0; j < N; ++j) {
+        // prior LLR (App. A): Lambda_j = log((1 - p_j) / p_j)
+        lam[j] = (float)std::log((1.0 - priors[j]) / priors[j]);
+        lamq[j] = (long long)std::llrint((double)lam[j] * kFixScale);
+        if (!(lam[j] > 0.f)) all_pos = 0;
+    }
+    for (long long e = 0; e < E; ++e) lamE[e] = std::fmin(std::fmax(lam[H_col_idx[e]], -L), L);
+    std::vector<uint32_t> hcol((size_t)N * WM, 0u), acol((size_t)N * (WK > 0 ? WK : 1), 0u);
+    for (int i = 0; i < M; ++i)
+        for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e)
+            hcol[(size_t)H_col_idx[e] * WM + (i >> 5)] |= 1u << (i & 31);
+    for (int i = 0; i < K; ++i)
+        for (int e = A_row_ptr[i]; e < A_row_ptr[i + 1]; ++e)
+            acol[(size_t)A_col_idx[e] * WK + (i >> 5)] ^= 1u << (i & 31);
+
+    // ---- device graph
+    size_t gb = 0;
+    gb += align256(sizeof(int) * (M + 1));
+    gb += align256(sizeof(int) * (N + 1));
+    gb += 2 * align256(sizeof(int) * E);
+    gb += align256(sizeof(float) * Npad);
+    gb += align256(sizeof(float) * Epad);
+    gb += align256(sizeof(uint32_t) * hcol.size());
+    gb += align256(sizeof(uint32_t) * acol.size());
+    gb += align256(sizeof(long long) * N);
+    if (cudaMalloc(&dec->graph_mem, gb) != cudaSuccess) { bsd_destroy(dec); return BSD_ERR_OOM; }
+    dec->graph_bytes = gb;
+    char* p = (char*)dec->graph_mem;
+    int* d_row_ptr = carve<int>(p, M + 1);
+    int* d_col_ptr = carve<int>(p, N + 1);
+    int* d_col_edge = carve<int>(p, E);
+    int* d_col_row = carve<int>(p, E);
+    float* d_lam = carve<float>(p, Npad);
+    float* d_lamE = carve<float>(p, Epad);
+    uint32_t* d_hcol = carve<uint32_t>(p, hcol.size());
+    uint32_t* d_acol = carve<uint32_t>(p, acol.size());
+    long long* d_lamq = carve<long long>(p, N);
+    bool ok = cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(d_col_edge, col_edge.data(), sizeof(int) * E, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(d_col_row, col_row.data(), sizeof(int) * E, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(d_lam, lam.data(), sizeof(float) * Npad, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(d_lamE, lamE.data(), sizeof(float) * Epad, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(d_hcol, hcol.data(), sizeof(uint32_t) * hcol.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(d_acol, acol.data(), sizeof(uint32_t) * acol.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(d_lamq, lamq.data(), sizeof(long long) * N, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) { bsd_destroy(dec); return BSD_ERR_CUDA; }
+
+    DevGraph& g = dec->g;
+    g.M = M; g.N = N; g.K = K; g.E = (int)E;
+    g.WM = WM; g.WN = WN; g.WK = WK;
+    g.Epad = Epad; g.Npad = Npad;
+    g.max_col_deg = max_col; g.max_row_deg = max_row;
+    g.all_lam_pos = all_pos;
+    g.row_ptr = d_row_ptr; g.col_ptr = d_col_ptr; g.col_edge = d_col_edge; g.col_row = d_col_row;
+    g.lam = d_lam; g.lamE = d_lamE; g.hcol = d_hcol; g.acol = d_acol; g.lamq = d_lamq;
+
+    DecCfg& cfg = dec->cfg;
+    cfg.max_rounds = params->max_rounds;
+    cfg.w = params->beam_width;
+    cfg.initial_iters = params->initial_iters;
+    cfg.iters_per_round = params->iters_per_round;
+    cfg.num_results = params->num_results;
+    cfg.alpha = params->ms_scale;
+    cfg.L = params->llr_clamp;
+
+    rc = configure_kernels(g, cfg, device, &dec->ls);
+    if (rc) { bsd_destroy(dec); return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA; }
+
+    // ---- workspace: two banks of 2w child slots per shot of a chunk
+    const int W2 = 2 * cfg.w;
+    const int SB = WM + 3 * WN;
+    const int NR = cfg.num_results;
+    const size_t per_shot = 2ull * W2 * (sizeof(float) * Epad + sizeof(uint32_t) * SB + sizeof(SlotMeta)) +
+                            sizeof(int) * 3 + cfg.w + sizeof(unsigned long long) +
+                            (size_t)NR * (sizeof(uint32_t) * WN + sizeof(long long) + sizeof(int)) + sizeof(int) +
+                            2ull * W2 * sizeof(int2);
+    const long long budget = params->workspace_bytes > 0 ? params->workspace_bytes : (4ll << 30);
+    long long C = (long long)(budget / (long long)(per_shot + 64));
+    if (C > (1ll << 22)) C = 1ll << 22;
+    if (C < 1) C = 1;
+    dec->ctr_bytes = align256(sizeof(Counters) + sizeof(int) * 3 * (size_t)(cfg.max_rounds + 2));
+    for (;;) {
+        size_t wb = dec->ctr_bytes;
+        wb += align256(sizeof(float) * 2ull * C * W2 * Epad);
+        wb += align256(sizeof(uint32_t) * 2ull * C * W2 * SB);
+        wb += align256(sizeof(SlotMeta) * 2ull * C * W2);
+        wb += 3 * align256(sizeof(int) * C) + align256((size_t)C * cfg.w) + align256(sizeof(unsigned long long) * C);
+        wb += align256(sizeof(uint32_t) * (size_t)C * NR * WN) + align256(sizeof(long long) * (size_t)C * NR) +
+              align256(sizeof(int) * (size_t)C * NR) + align256(sizeof(int) * C);
+        wb += align256(sizeof(int2) * 2ull * C * W2);
+        if (cudaMalloc(&dec->work_mem, wb) == cudaSuccess) { dec->work_bytes = wb; break; }
+        cudaGetLastError();
+        dec->work_mem = nullptr;
+        if (C == 1) { bsd_destroy(dec); return BSD_ERR_OOM; }
+        C = C / 2;
+    }
+    Work& w = dec->w;
+    char* q = (char*)dec->work_mem;
+    w.ctr = reinterpret_cast<Counters*>(q);
+    w.round_ctr = reinterpret_cast<int*>(q + sizeof(Counters));
+    q += dec->ctr_bytes;
+    w.C = C;
+    w.SB = SB;
+    w.slotE = carve<float>(q, 2ull * C * W2 * Epad);
+    w.slotBits = carve<uint32_t>(q, 2ull * C * W2 * SB);
+    w.slotMeta = carve<SlotMeta>(q, 2ull * C * W2);
+    w.shot_of = carve<int>(q, C);
+    w.set_size = carve<int>(q, C);
+    w.done = carve<int>(q, C);
+    w.set_idx = carve<uint8_t>(q, (size_t)C * cfg.w);
+    w.iters_acc = carve<unsigned long long>(q, C);
+    w.res_bits = carve<uint32_t>(q, (size_t)C * NR * WN);
+    w.res_w = carve<long long>(q, (size_t)C * NR);
+    w.res_origin = carve<int>(q, (size_t)C * NR);
+    w.res_n = carve<int>(q, C);
+    w.items = carve<int2>(q, 2ull * C * W2);
+    if (cudaMemset(dec->work_mem, 0, dec->ctr_bytes) != cudaSuccess) { bsd_destroy(dec); return BSD_ERR_CUDA; }
+    *out = dec;
+    return BSD_OK;
+}
+
+static int decode_impl(bsd_decoder* dec, const uint32_t* d_synd, long long base, long long n, const Outputs& o,
+                       cudaStream_t s)
+{
+    if (cudaMemsetAsync(dec->work_mem, 0, dec->ctr_bytes, s) != cudaSuccess) return BSD_ERR_CUDA;
+    return launch_chunk(dec->g, dec->cfg, dec->w, dec->ls, d_synd, base, n, o, s) ? BSD_ERR_CUDA : BSD_OK;
+}
+
+int bsd_decode(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, uint32_t* d_corrections,
+               uint32_t* d_obs_flips, uint32_t* d_status, uint32_t* d_iters, void* cuda_stream)
+{
+    if (!dec || B < 0) return BSD_ERR_INVALID_ARG;
+    if (B == 0) return BSD_OK;
+    if (!d_syndromes || !d_corrections || !d_status || (dec->g.K > 0 && !d_obs_flips)) return BSD_ERR_INVALID_ARG;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    dec->last_stream = s;
+    Outputs o{d_corrections, dec->g.K > 0 ? d_obs_flips : nullptr, d_status, d_iters};
+    for (long long base = 0; base < B; base += dec->w.C) {
+        const long long n = (B - base) < dec->w.C ? (B - base) : dec->w.C;
+        const int rc = decode_impl(dec, d_syndromes, base, n, o, s);
+        if (rc) return rc;
+    }
+    return BSD_OK;
+}
+
+int bsd_decode_host(bsd_decoder* dec, const uint32_t* h_syndromes, int64_t B, uint32_t* h_corrections,
+                    uint32_t* h_obs_flips, uint32_t* h_status, uint32_t* h_iters, void* cuda_stream)
+{
+    if (!dec || B < 0) return BSD_ERR_INVALID_ARG;
+    if (B == 0) return BSD_OK;
+    if (!h_syndromes || !h_corrections || !h_status || (dec->g.K > 0 && !h_obs_flips)) return BSD_ERR_INVALID_ARG;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    dec->last_stream = s;
+    const DevGraph& g = dec->g;
+    const long long C = dec->w.C;
+    const size_t need = align256(sizeof(uint32_t) * C * g.WM) + align256(sizeof(uint32_t) * C * g.WN) +
+                        align256(sizeof(uint32_t) * C * (g.WK > 0 ? g.WK : 1)) + 2 * align256(sizeof(uint32_t) * C);
+    if (dec->io_bytes < need) {
+        if (dec->io_mem) cudaFree(dec->io_mem);
+        dec->io_mem = nullptr;
+        dec->io_bytes = 0;
+        if (cudaMalloc(&dec->io_mem, need) != cudaSuccess) { cudaGetLastError(); return BSD_ERR_OOM; }
+        dec->io_bytes = need;
+    }
+    char* p = (char*)dec->io_mem;
+    uint32_t* d_s = carve<uint32_t>(p, C * g.WM);
+    uint32_t* d_c = carve<uint32_t>(p, C * g.WN);
+    uint32_t* d_o = carve<uint32_t>(p, C * (g.WK > 0 ? g.WK : 1));
+    uint32_t* d_st = carve<uint32_t>(p, C);
+    uint32_t* d_it = carve<uint32_t>(p, C);
+    Outputs o{d_c, g.K > 0 ? d_o : nullptr, d_st, h_iters ? d_it : nullptr};
+    for (long long base = 0; base < B; base += C) {
+        const long long n = (B - base) < C ? (B - base) : C;
+        if (cudaMemcpyAsync(d_s, h_syndromes + base * g.WM, sizeof(uint32_t) * n * g.WM, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return BSD_ERR_CUDA;
+        int rc = decode_impl(dec, d_s, 0, n, o, s);
+        if (rc) return rc;
+        bool ok = cudaMemcpyAsync(h_corrections + base * g.WN, d_c, sizeof(uint32_t) * n * g.WN,
+                                  cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                  cudaMemcpyAsync(h_status + base, d_st, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        if (ok && g.K > 0)
+            ok = cudaMemcpyAsync(h_obs_flips + base * g.WK, d_o, sizeof(uint32_t) * n * g.WK, cudaMemcpyDeviceToHost,
+                                 s) == cudaSuccess;
+        if (ok && h_iters)
+            ok = cudaMemcpyAsync(h_iters + base, d_it, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        if (!ok) return BSD_ERR_CUDA;
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? BSD_OK : BSD_ERR_CUDA;
+}
+
+int bsd_bp_llr(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, int32_t T, float* d_llr, float* d_sum_llr,
+               void* cuda_stream)
+{
+    if (!dec || B < 0 || T < 1 || T > 100000) return BSD_ERR_INVALID_ARG;
+    if (B == 0) return BSD_OK;
+    if (!d_syndromes || !d_llr) return BSD_ERR_INVALID_ARG;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    dec->last_stream = (cudaStream_t)cuda_stream;
+    return launch_bp_llr(dec->g, dec->cfg, dec->ls, d_syndromes, B, T, d_llr, d_sum_llr, cuda_stream) ? BSD_ERR_CUDA
+                                                                                                      : BSD_OK;
+}
+
+int bsd_sync_error(bsd_decoder* dec)
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    if (cudaStreamSynchronize(dec->last_stream) != cudaSuccess) return BSD_ERR_CUDA;
+    Counters c;
+    if (cudaMemcpy(&c, dec->w.ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return BSD_ERR_CUDA;
+    if (c.err != 0) {
+        const int zero = 0;
+        cudaMemcpy(&dec->w.ctr->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return c.err == 1 ? BSD_ERR_TIMEOUT : BSD_ERR_DEVICE;
+    }
+    return BSD_OK;
+}
+
+int bsd_get_info(const bsd_decoder* dec, int32_t* M, int32_t* N, int32_t* K, int32_t* n_edges, int64_t* chunk_shots,
+                 int64_t* workspace_bytes)
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    if (M) *M = dec->g.M;
+    if (N) *N = dec->g.N;
+    if (K) *K = dec->g.K;
+    if (n_edges) *n_edges = dec->g.E;
+    if (chunk_shots) *chunk_shots = dec->w.C;
+    if (workspace_bytes) *workspace_bytes = (int64_t)dec->work_bytes;
+    return BSD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,773 @@
+// bsd_kernels.cu -- sm_103a kernels of the BP-guided beam search decoder.
+//
+// One warp owns one BP candidate (the seed path of a shot, or one child of a
+// beam round) and keeps its whole state in shared memory: the edge messages
+// E_{j->i}, a compact per-detector record (min1, min2, argmin edge, sign
+// parity) standing in for the detector-to-error messages D_{i->j}, sum_LLR,
+// and the bit vectors s', mask, vals, e^ and the running syndrome parity.
+//
+// Kernels (all persistent: warps claim work with one atomic per item and
+// exit when the item counter runs out, so uneven iteration counts balance):
+//   k_seed<DV>    the seed BP of every shot in a chunk (Alg. 3, first BP run)
+//   k_round<DV>   expand + masked BP for every child of round r (Alg. 2)
+//   k_select      per shot: first success in visit order, results, top-w
+//                 pruning and the work list of round r + 1 (Alg. 3, App. B)
+//   k_bp_llr<DV>  plain BP for a fixed number of iterations (LLR measurement)
+//
+// Arithmetic follows the readings stated in include/bsd.h: D = alpha * sign *
+// min with the minimum over no other unmasked neighbour equal to L_MAX;
+// E clamped to [-L_MAX, L_MAX]; the sums of Eqs. 2-3 start at Lambda_j and
+// add the incoming messages in ascending order; every add and multiply is a
+// single IEEE round-to-nearest operation (__fadd_rn / __fmul_rn, so no FMA
+// contraction); scores and weights are summed exactly on a 2^-16 grid.
+//
+// Masked nodes: the messages of a masked error node are set to +L_MAX when it
+// is masked.  A +L_MAX input never lowers a minimum below that of the other
+// inputs and never flips a sign, so the check pass needs no mask test; the
+// error-node pass skips masked nodes, whose messages therefore stay +L_MAX.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+
+#include "bsd_internal.cuh"
+
+namespace bsd {
+
+#define FULLMASK 0xffffffffu
+
+enum : uint32_t { ST_SEED = 1u, ST_BEAM = 2u, ST_FAILED = 4u };
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// per-warp shared-memory footprint of one BP candidate
+__host__ __device__ inline size_t warp_smem_bytes(const DevGraph& g)
+{
+    return align16(sizeof(float) * (size_t)g.Epad) + sizeof(float4) * (size_t)g.M +
+           align16(sizeof(float) * (size_t)g.Npad) + align16(sizeof(uint32_t) * (size_t)(2 * g.WM + 3 * g.WN));
+}
+
+struct WarpState {
+    float* E;          // [Epad] E_{j->i}, CSR edge order
+    float4* rs;        // [M]    (min1, min2, argmin edge id, s'_i xor parity of negatives)
+    float* sumllr;     // [Npad]
+    uint32_t* sp;      // [WM] s' = s with the columns of nodes fixed to 1 folded in
+    uint32_t* par;     // [WM] s' xor H e^ (zero iff converged)
+    uint32_t* mask;    // [WN]
+    uint32_t* vals;    // [WN]
+    uint32_t* ehat;    // [WN]
+};
+
+__device__ inline WarpState carve(char* base, const DevGraph& g)
+{
+    WarpState s;
+    char* p = base;
+    s.E = reinterpret_cast<float*>(p);       p += align16(sizeof(float) * (size_t)g.Epad);
+    s.rs = reinterpret_cast<float4*>(p);     p += sizeof(float4) * (size_t)g.M;
+    s.sumllr = reinterpret_cast<float*>(p);  p += align16(sizeof(float) * (size_t)g.Npad);
+    uint32_t* b = reinterpret_cast<uint32_t*>(p);
+    s.sp = b;
+    s.par = b + g.WM;
+    s.mask = b + 2 * g.WM;
+    s.vals = b + 2 * g.WM + g.WN;
+    s.ehat = b + 2 * g.WM + 2 * g.WN;
+    return s;
+}
+
+__device__ inline unsigned long long fixq(float x)
+{
+    return (unsigned long long)__double2ll_rn((double)x * kFixScale);
+}
+
+// ----------------------------------------------------------------------------
+// BP iterations on one candidate (Eqs. 1-4 with the masking of Alg. 2)
+// ----------------------------------------------------------------------------
+// Runs up to max_iters flooding iterations from the messages in st.E.  With
+// stop = true it returns at the first t with H e^(t) = s' (Alg. 2).  On return
+// st.ehat holds e^(t) of the last iteration (masked positions 0), st.sumllr
+// holds the sum over the iterations run of Lambda_j(t).  If post_out is not
+// null, Lambda_j(max_iters) is written there.
+template <int DV>
+__device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
+                          bool stop, int* success, float* post_out)
+{
+    const int lane = threadIdx.x & 31;
+    const float alpha = cfg.alpha;
+    const float L = cfg.L;
+    int iters = 0;
+    int ok = 0;
+    for (int t = 1; t <= max_iters; ++t) {
+        for (int q = lane; q < g.WM; q += 32) st.par[q] = st.sp[q];
+
+        // ---- detector pass (Eq. 1): min1, min2, argmin and sign parity per row
+        for (int i = lane; i < g.M; i += 32) {
+            const int rb = __ldg(g.row_ptr + i), re = __ldg(g.row_ptr + i + 1);
+            float m1 = L, m2 = L;
+            int id = -1;
+            uint32_t neg = (st.sp[i >> 5] >> (i & 31)) & 1u;
+            for (int e = rb; e < re; ++e) {
+                const float x = st.E[e];
+                const float a = fabsf(x);
+                if (a < m1) { m2 = m1; m1 = a; id = e; }
+                else if (a < m2) { m2 = a; }
+                neg ^= (x < 0.f) ? 1u : 0u;
+            }
+            st.rs[i] = make_float4(m1, m2, __int_as_float(id), __uint_as_float(neg));
+        }
+        __syncwarp();
+
+        // ---- error-node pass (Eqs. 2-4) and syndrome parity
+        for (int jb = 0; jb < g.N; jb += 32) {
+            const int j = jb + lane;
+            uint32_t ebit = 0;
+            const bool act = (j < g.N) && !((st.mask[jb >> 5] >> lane) & 1u);
+            if (act) {
+                const int kb = __ldg(g.col_ptr + j);
+                const int deg = __ldg(g.col_ptr + j + 1) - kb;
+                float v[DV];
+                int ed[DV];
+#pragma unroll
+                for (int k = 0; k < DV; ++k) {
+                    if (k < deg) {
+                        const int e = __ldg(g.col_edge + kb + k);
+                        const int r = __ldg(g.col_row + kb + k);
+                        const float4 s4 = st.rs[r];
+                        const float xo = st.E[e];
+                        const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
+                        const uint32_t sg = __float_as_uint(s4.w) ^ ((xo < 0.f) ? 1u : 0u);
+                        const float d = __fmul_rn(alpha, m);
+                        v[k] = sg ? -d : d;
+                        ed[k] = e;
+                    } else {
+                        v[k] = INFINITY;
+                        ed[k] = -1;
+                    }
+                }
+                // ascending order of value (exchange network; padding +inf stays last)
+#pragma unroll
+                for (int a = 0; a < DV; ++a) {
+#pragma unroll
+                    for (int k = 0; k + 1 < DV - a; ++k) {
+                        if (v[k] > v[k + 1]) {
+                            const float tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv;
+                            const int te = ed[k]; ed[k] = ed[k + 1]; ed[k + 1] = te;
+                        }
+                    }
+                }
+                const float lj = __ldg(g.lam + j);
+                float post = lj;                                  // Eq. 3
+#pragma unroll
+                for (int k = 0; k < DV; ++k)
+                    if (k < deg) post = __fadd_rn(post, v[k]);
+#pragma unroll
+                for (int k = 0; k < DV; ++k) {                    // Eq. 2: leave d_i out
+                    if (k < deg) {
+                        float acc = lj;
+#pragma unroll
+                        for (int k2 = 0; k2 < DV; ++k2)
+                            if (k2 != k && k2 < deg) acc = __fadd_rn(acc, v[k2]);
+                        st.E[ed[k]] = fminf(fmaxf(acc, -L), L);
+                    }
+                }
+                st.sumllr[j] = __fadd_rn(st.sumllr[j], post);
+                if (post_out != nullptr && t == max_iters) post_out[j] = post;
+                ebit = (post <= 0.f) ? 1u : 0u;                   // Eq. 4
+                if (ebit) {
+                    for (int k = 0; k < deg; ++k) {
+                        const int r = __ldg(g.col_row + kb + k);
+                        atomicXor(&st.par[r >> 5], 1u << (r & 31));
+                    }
+                }
+            }
+            const uint32_t bal = __ballot_sync(FULLMASK, ebit);
+            if (lane == 0) st.ehat[jb >> 5] = bal;
+        }
+        __syncwarp();
+
+        // ---- stopping rule: H e^(t) = s'
+        uint32_t nz = 0;
+        for (int q = lane; q < g.WM; q += 32) nz |= st.par[q];
+        ok = !__any_sync(FULLMASK, nz != 0u);
+        iters = t;
+        __syncwarp();
+        if (ok && stop) break;
+    }
+    *success = ok;
+    return iters;
+}
+
+// least reliable unmasked node (lowest index on ties) and the score numerator
+__device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, int* next_pos,
+                                        long long* S)
+{
+    const int lane = threadIdx.x & 31;
+    float best = INFINITY;
+    int bj = -1;
+    unsigned long long s = 0;
+    for (int j = lane; j < g.N; j += 32) {
+        if ((st.mask[j >> 5] >> (j & 31)) & 1u) continue;
+        const float a = fabsf(st.sumllr[j]);
+        if (bj < 0 || a < best) { best = a; bj = j; }
+        s += fixq(a);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(FULLMASK, best, o);
+        const int oj = __shfl_xor_sync(FULLMASK, bj, o);
+        if (oj >= 0 && (bj < 0 || ob < best || (ob == best && oj < bj))) { best = ob; bj = oj; }
+        s += __shfl_xor_sync(FULLMASK, s, o);
+    }
+    *next_pos = bj;
+    *S = (long long)s;
+}
+
+// write one shot's outputs: e^, A e^, status, iteration count
+__device__ void finalize_shot(const DevGraph& g, const Outputs& out, long long gb, const uint32_t* ehat,
+                              uint32_t status, unsigned long long iters)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t* corr = out.corr + gb * g.WN;
+    for (int q = lane; q < g.WN; q += 32) corr[q] = ehat[q];
+    if (out.obs != nullptr) {
+        for (int wq = 0; wq < g.WK; ++wq) {
+            uint32_t acc = 0;
+            for (int j = lane; j < g.N; j += 32)
+                if ((ehat[j >> 5] >> (j & 31)) & 1u) acc ^= __ldg(g.acol + (size_t)j * g.WK + wq);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(FULLMASK, acc, o);
+            if (lane == 0) out.obs[gb * g.WK + wq] = acc;
+        }
+    }
+    if (lane == 0) {
+        out.status[gb] = status;
+        if (out.iters != nullptr) out.iters[gb] = iters > 0xffffffffull ? 0xffffffffu : (uint32_t)iters;
+    }
+}
+
+// weight of a bit vector on the 2^-16 grid: sum of q(Lambda_j) over its support
+__device__ inline long long vector_weight(const DevGraph& g, const uint32_t* bits)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long s = 0;
+    for (int j = lane; j < g.N; j += 32)
+        if ((bits[j >> 5] >> (j & 31)) & 1u) s += (unsigned long long)__ldg(g.lamq + j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULLMASK, s, o);
+    return (long long)s;
+}
+
+__device__ inline int* round_ctr(const Work& w, int r) { return w.round_ctr + 3 * r; }
+
+__device__ inline size_t slot_index(const Work& w, int bank, int a, int c, int W2)
+{
+    return ((size_t)bank * (size_t)w.C + (size_t)a) * (size_t)W2 + (size_t)c;
+}
+
+// ----------------------------------------------------------------------------
+// seed BP
+// ----------------------------------------------------------------------------
+template <int DV>
+__global__ void __launch_bounds__(256) k_seed(DevGraph g, DecCfg cfg, Work w, const uint32_t* __restrict__ synd,
+                                              long long base, long long n, Outputs out)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
+    const int W2 = 2 * cfg.w;
+    for (;;) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(&w.ctr->claim_seed, 1);
+        b = __shfl_sync(FULLMASK, b, 0);
+        if (b >= n) break;
+        const long long gb = base + b;
+        const uint32_t* s = synd + gb * g.WM;
+        uint32_t nz = 0;
+        for (int q = lane; q < g.WM; q += 32) {
+            const uint32_t x = s[q];
+            st.sp[q] = x;
+            nz |= x;
+        }
+        for (int q = lane; q < g.WN; q += 32) { st.mask[q] = 0u; st.vals[q] = 0u; st.ehat[q] = 0u; }
+        __syncwarp();
+        // s = 0 with every Lambda_j > 0: D > 0 at t = 1, so e^(1) = 0 and the
+        // seed converges after one iteration (exact, no BP needed)
+        if (!__any_sync(FULLMASK, nz != 0u) && cfg.num_results == 1 && g.all_lam_pos) {
+            finalize_shot(g, out, gb, st.ehat, ST_SEED, 1ull);
+            __syncwarp();
+            continue;
+        }
+        const float4* src = reinterpret_cast<const float4*>(g.lamE);
+        float4* dst = reinterpret_cast<float4*>(st.E);
+        for (int q = lane; q < g.Epad / 4; q += 32) dst[q] = __ldg(src + q);
+        for (int j = lane; j < g.N; j += 32) st.sumllr[j] = 0.f;
+        __syncwarp();
+        int succ = 0;
+        const int it = bp_iterate<DV>(g, cfg, st, cfg.initial_iters, true, &succ, nullptr);
+        __syncwarp();
+        if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
+            finalize_shot(g, out, gb, st.ehat, succ ? ST_SEED : ST_FAILED, (unsigned long long)it);
+            __syncwarp();
+            continue;
+        }
+        int np;
+        long long S;
+        argmin_and_score(g, st, &np, &S);
+        int a = 0;
+        if (lane == 0) a = atomicAdd(&w.ctr->n_active, 1);
+        a = __shfl_sync(FULLMASK, a, 0);
+        // the seed path: bank 0, child index 0
+        const size_t slot = slot_index(w, 0, a, 0, W2);
+        float4* dE = reinterpret_cast<float4*>(w.slotE + slot * (size_t)g.Epad);
+        for (int q = lane; q < g.Epad / 4; q += 32) dE[q] = dst[q];
+        uint32_t* bits = w.slotBits + slot * (size_t)w.SB;
+        for (int q = lane; q < g.WM; q += 32) bits[q] = st.sp[q];
+        for (int q = lane; q < g.WN; q += 32) {
+            bits[g.WM + q] = 0u;
+            bits[g.WM + g.WN + q] = 0u;
+            bits[g.WM + 2 * g.WN + q] = st.ehat[q];
+        }
+        long long W = 0;
+        if (succ) {                       // num_results > 1: the seed result opens `results`
+            uint32_t* rb = w.res_bits + (size_t)a * cfg.num_results * g.WN;
+            for (int q = lane; q < g.WN; q += 32) rb[q] = st.ehat[q];
+            W = vector_weight(g, st.ehat);
+        }
+        if (lane == 0) {
+            SlotMeta m;
+            m.S = 0; m.iters = it; m.next_pos = np; m.success = succ; m.pad = 0;
+            w.slotMeta[slot] = m;
+            w.shot_of[a] = b;
+            w.set_size[a] = 1;
+            w.set_idx[(size_t)a * cfg.w] = 0;
+            w.iters_acc[a] = (unsigned long long)it;
+            w.done[a] = 0;
+            w.res_n[a] = succ ? 1 : 0;
+            if (succ) {
+                w.res_w[(size_t)a * cfg.num_results] = W;
+                w.res_origin[(size_t)a * cfg.num_results] = 0;
+            }
+            if (np >= 0) {
+                const int wb = atomicAdd(&round_ctr(w, 1)[2], 2);
+                int2* items = w.items + (size_t)1 * (size_t)w.C * (size_t)W2;
+                items[wb] = make_int2(a, 0);
+                items[wb + 1] = make_int2(a, 1);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// one beam round: expand every child and run masked BP (Alg. 2)
+// ----------------------------------------------------------------------------
+template <int DV>
+__global__ void __launch_bounds__(256) k_round(DevGraph g, DecCfg cfg, Work w, int r)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
+    const int W2 = 2 * cfg.w;
+    int* rc = round_ctr(w, r);
+    const int nitems = *((volatile int*)(rc + 2));
+    const int2* items = w.items + (size_t)(r & 1) * (size_t)w.C * (size_t)W2;
+    const int pb = (r - 1) & 1, cb = r & 1;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&rc[0], 1);
+        it = __shfl_sync(FULLMASK, it, 0);
+        if (it >= nitems) break;
+        const int2 item = items[it];
+        const int a = item.x, c = item.y;
+        const int k = c >> 1, v = c & 1;
+        const int pc = w.set_idx[(size_t)a * cfg.w + k];
+        const size_t pslot = slot_index(w, pb, a, pc, W2);
+        const size_t cslot = slot_index(w, cb, a, c, W2);
+        const int pos = w.slotMeta[pslot].next_pos;
+        const uint32_t* pbits = w.slotBits + pslot * (size_t)w.SB;
+        // s' of the child: flip the detectors of pos when it is fixed to 1
+        for (int q = lane; q < g.WM; q += 32) {
+            uint32_t x = pbits[q];
+            if (v) x ^= __ldg(g.hcol + (size_t)pos * g.WM + q);
+            st.sp[q] = x;
+        }
+        for (int q = lane; q < g.WN; q += 32) {
+            uint32_t m = pbits[g.WM + q];
+            uint32_t vv = pbits[g.WM + g.WN + q];
+            if (q == (pos >> 5)) {
+                m |= 1u << (pos & 31);
+                if (v) vv |= 1u << (pos & 31);
+            }
+            st.mask[q] = m;
+            st.vals[q] = vv;
+        }
+        // warm start from the parent's snapshot
+        const float4* pE = reinterpret_cast<const float4*>(w.slotE + pslot * (size_t)g.Epad);
+        float4* sE = reinterpret_cast<float4*>(st.E);
+        for (int q = lane; q < g.Epad / 4; q += 32) sE[q] = pE[q];
+        for (int j = lane; j < g.N; j += 32) st.sumllr[j] = 0.f;
+        __syncwarp();
+        for (int q = __ldg(g.col_ptr + pos) + lane; q < __ldg(g.col_ptr + pos + 1); q += 32)
+            st.E[__ldg(g.col_edge + q)] = cfg.L;
+        __syncwarp();
+        int succ = 0;
+        const int iters = bp_iterate<DV>(g, cfg, st, cfg.iters_per_round, true, &succ, nullptr);
+        __syncwarp();
+        for (int q = lane; q < g.WN; q += 32) st.ehat[q] = (st.ehat[q] & ~st.mask[q]) | st.vals[q];
+        __syncwarp();
+        int np;
+        long long S;
+        argmin_and_score(g, st, &np, &S);
+        float4* cE = reinterpret_cast<float4*>(w.slotE + cslot * (size_t)g.Epad);
+        for (int q = lane; q < g.Epad / 4; q += 32) cE[q] = sE[q];
+        uint32_t* cbits = w.slotBits + cslot * (size_t)w.SB;
+        for (int q = lane; q < g.WM; q += 32) cbits[q] = st.sp[q];
+        for (int q = lane; q < g.WN; q += 32) {
+            cbits[g.WM + q] = st.mask[q];
+            cbits[g.WM + g.WN + q] = st.vals[q];
+            cbits[g.WM + 2 * g.WN + q] = st.ehat[q];
+        }
+        if (lane == 0) {
+            SlotMeta m;
+            m.S = S; m.iters = iters; m.next_pos = np; m.success = succ; m.pad = 0;
+            w.slotMeta[cslot] = m;
+        }
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// per-shot selection after round r
+// ----------------------------------------------------------------------------
+struct SelScratch {
+    double score[2 * kMaxBeam];
+    int iters[2 * kMaxBeam];
+    int flags[2 * kMaxBeam];     // bit0 exists, bit1 success
+};
+
+__device__ void finalize_results(const DevGraph& g, const DecCfg& cfg, const Work& w, const Outputs& out,
+                                 int a, long long gb, unsigned long long total)
+{
+    const int n = w.res_n[a];
+    const long long* rw = w.res_w + (size_t)a * cfg.num_results;
+    int bi = 0;
+    for (int q = 1; q < n; ++q)
+        if (rw[q] < rw[bi]) bi = q;
+    const uint32_t st = (w.res_origin[(size_t)a * cfg.num_results + bi] == 0) ? ST_SEED : ST_BEAM;
+    finalize_shot(g, out, gb, w.res_bits + ((size_t)a * cfg.num_results + bi) * g.WN, st, total);
+}
+
+__global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, int r, long long base, Outputs out)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    SelScratch* sc = reinterpret_cast<SelScratch*>(smem) + wid;
+    const int W2 = 2 * cfg.w;
+    const int n_active = *((volatile int*)&w.ctr->n_active);
+    int* rc = round_ctr(w, r);
+    const int pb = (r - 1) & 1, cb = r & 1;
+    for (;;) {
+        int a = 0;
+        if (lane == 0) a = atomicAdd(&rc[1], 1);
+        a = __shfl_sync(FULLMASK, a, 0);
+        if (a >= n_active) break;
+        if (w.done[a]) continue;
+        const long long gb = base + w.shot_of[a];
+        const int npar = w.set_size[a];
+        const int nch = 2 * npar;
+        // gather the children of this round in canonical order c = 2 * rank + val
+        for (int c = lane; c < nch; c += 32) {
+            const int pc = w.set_idx[(size_t)a * cfg.w + (c >> 1)];
+            const int pnp = w.slotMeta[slot_index(w, pb, a, pc, W2)].next_pos;
+            int fl = 0, it = 0;
+            double scv = 0.0;
+            if (pnp >= 0) {
+                const SlotMeta m = w.slotMeta[slot_index(w, cb, a, c, W2)];
+                fl = 1 | (m.success ? 2 : 0);
+                it = m.iters;
+                scv = ((double)m.S / kFixScale) / (double)m.iters;
+            }
+            sc->flags[c] = fl;
+            sc->iters[c] = it;
+            sc->score[c] = scv;
+        }
+        __syncwarp();
+        unsigned long long acc = w.iters_acc[a];
+        bool done = false;
+        if (cfg.num_results == 1) {
+            // Alg. 3: the first successful child in visit order ends the search
+            int first = 0x7fffffff;
+            for (int c = lane; c < nch; c += 32)
+                if ((sc->flags[c] & 3) == 3 && c < first) first = c;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(FULLMASK, first, o));
+            if (first != 0x7fffffff) {
+                unsigned long long sum = 0;
+                for (int c = lane; c <= first; c += 32)
+                    if (sc->flags[c] & 1) sum += (unsigned long long)sc->iters[c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULLMASK, sum, o);
+                const uint32_t* eb = w.slotBits + slot_index(w, cb, a, first, W2) * (size_t)w.SB + g.WM + 2 * g.WN;
+                finalize_shot(g, out, gb, eb, ST_BEAM, acc + sum);
+                done = true;
+            }
+        } else {
+            // results collection in visit order (dedupe by equality, App. B)
+            unsigned long long sum = 0;
+            for (int c = 0; c < nch && !done; ++c) {
+                const int fl = sc->flags[c];
+                if (!(fl & 1)) continue;
+                sum += (unsigned long long)sc->iters[c];
+                if (!(fl & 2)) continue;
+                const uint32_t* eb = w.slotBits + slot_index(w, cb, a, c, W2) * (size_t)w.SB + g.WM + 2 * g.WN;
+                const int nres = w.res_n[a];
+                bool dup = false;
+                for (int q = 0; q < nres && !dup; ++q) {
+                    const uint32_t* rb = w.res_bits + ((size_t)a * cfg.num_results + q) * g.WN;
+                    bool eq = true;
+                    for (int x = lane; x < g.WN; x += 32) eq = eq && (rb[x] == eb[x]);
+                    dup = __all_sync(FULLMASK, eq);
+                }
+                if (!dup) {
+                    uint32_t* rb = w.res_bits + ((size_t)a * cfg.num_results + nres) * g.WN;
+                    for (int x = lane; x < g.WN; x += 32) rb[x] = eb[x];
+                    const long long W = vector_weight(g, eb);
+                    __syncwarp();
+                    if (lane == 0) {
+                        w.res_w[(size_t)a * cfg.num_results + nres] = W;
+                        w.res_origin[(size_t)a * cfg.num_results + nres] = 1;
+                        w.res_n[a] = nres + 1;
+                    }
+                    __syncwarp();
+                    if (nres + 1 >= cfg.num_results) {
+                        finalize_results(g, cfg, w, out, a, gb, acc + sum);
+                        done = true;
+                    }
+                }
+            }
+        }
+        if (!done) {
+            unsigned long long sum = 0;
+            int nex = 0;
+            for (int c = lane; c < nch; c += 32) {
+                if (sc->flags[c] & 1) { sum += (unsigned long long)sc->iters[c]; ++nex; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sum += __shfl_xor_sync(FULLMASK, sum, o);
+                nex += __shfl_xor_sync(FULLMASK, nex, o);
+            }
+            acc += sum;
+            // rank of each existing child under (score desc, canonical index asc)
+            int myrank[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = lane + 32 * q;
+                myrank[q] = -1;
+                if (c < nch && (sc->flags[c] & 1)) {
+                    const double s0 = sc->score[c];
+                    int rk = 0;
+                    for (int c2 = 0; c2 < nch; ++c2) {
+                        if (!(sc->flags[c2] & 1)) continue;
+                        const double s2 = sc->score[c2];
+                        rk += (s2 > s0 || (s2 == s0 && c2 < c)) ? 1 : 0;
+                    }
+                    myrank[q] = rk;
+                }
+            }
+            if (r >= cfg.max_rounds || nex == 0) {
+                if (cfg.num_results > 1 && w.res_n[a] > 0) {
+                    finalize_results(g, cfg, w, out, a, gb, acc);
+                } else {
+                    // no valid solution: the best path of the final set
+                    int best = 0x7fffffff;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (myrank[q] == 0) best = lane + 32 * q;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(FULLMASK, best, o));
+                    const uint32_t* eb;
+                    if (best != 0x7fffffff)
+                        eb = w.slotBits + slot_index(w, cb, a, best, W2) * (size_t)w.SB + g.WM + 2 * g.WN;
+                    else
+                        eb = w.slotBits + slot_index(w, pb, a, w.set_idx[(size_t)a * cfg.w], W2) * (size_t)w.SB +
+                             g.WM + 2 * g.WN;
+                    finalize_shot(g, out, gb, eb, ST_FAILED, acc);
+                }
+                done = true;
+            } else {
+                // keep the top beam_width; their slots become the next round's parents
+                __syncwarp();
+                const int keep = nex < cfg.w ? nex : cfg.w;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (myrank[q] >= 0 && myrank[q] < keep)
+                        w.set_idx[(size_t)a * cfg.w + myrank[q]] = (uint8_t)(lane + 32 * q);
+                __syncwarp();
+                // children of round r + 1: two per kept path that has a next_pos
+                int cnt = 0;
+                for (int k = lane; k < keep; k += 32) {
+                    const int c = w.set_idx[(size_t)a * cfg.w + k];
+                    cnt += (w.slotMeta[slot_index(w, cb, a, c, W2)].next_pos >= 0) ? 1 : 0;
+                }
+                int tot = cnt;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULLMASK, tot, o);
+                int wbase = 0;
+                if (lane == 0) {
+                    w.set_size[a] = keep;
+                    w.iters_acc[a] = acc;
+                    if (tot > 0) wbase = atomicAdd(&round_ctr(w, r + 1)[2], 2 * tot);
+                }
+                wbase = __shfl_sync(FULLMASK, wbase, 0);
+                if (tot > 0 && lane == 0) {
+                    int2* items = w.items + (size_t)((r + 1) & 1) * (size_t)w.C * (size_t)W2;
+                    int o = 0;
+                    for (int k = 0; k < keep; ++k) {
+                        const int c = w.set_idx[(size_t)a * cfg.w + k];
+                        if (w.slotMeta[slot_index(w, cb, a, c, W2)].next_pos >= 0) {
+                            items[wbase + o] = make_int2(a, 2 * k);
+                            items[wbase + o + 1] = make_int2(a, 2 * k + 1);
+                            o += 2;
+                        }
+                    }
+                }
+            }
+        }
+        if (done && lane == 0) w.done[a] = 1;
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// plain BP for a fixed number of iterations (LLR measurement)
+// ----------------------------------------------------------------------------
+template <int DV>
+__global__ void __launch_bounds__(256) k_bp_llr(DevGraph g, DecCfg cfg, const uint32_t* __restrict__ synd, long long B,
+                                                int T, float* llr, float* sum_llr)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long b = (long long)blockIdx.x * (blockDim.x >> 5) + wid; b < B; b += nw) {
+        for (int q = lane; q < g.WM; q += 32) st.sp[q] = synd[b * g.WM + q];
+        for (int q = lane; q < g.WN; q += 32) { st.mask[q] = 0u; st.vals[q] = 0u; }
+        const float4* src = reinterpret_cast<const float4*>(g.lamE);
+        float4* dst = reinterpret_cast<float4*>(st.E);
+        for (int q = lane; q < g.Epad / 4; q += 32) dst[q] = __ldg(src + q);
+        for (int j = lane; j < g.N; j += 32) st.sumllr[j] = 0.f;
+        __syncwarp();
+        int succ;
+        bp_iterate<DV>(g, cfg, st, T, false, &succ, llr + b * g.N);
+        __syncwarp();
+        if (sum_llr != nullptr)
+            for (int j = lane; j < g.N; j += 32) sum_llr[b * g.N + j] = st.sumllr[j];
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// host-side launch helpers
+// ----------------------------------------------------------------------------
+template <int DV>
+static int set_attrs(size_t smem_bp, size_t smem_sel)
+{
+    if (cudaFuncSetAttribute(k_seed<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
+        cudaFuncSetAttribute(k_round<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
+        cudaFuncSetAttribute(k_bp_llr<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
+        cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sel) != cudaSuccess)
+        return -2;
+    return 0;
+}
+
+template <int DV>
+static int occupancy(int threads, size_t smem_bp, size_t smem_sel, int* bps_bp, int* bps_sel)
+{
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_bp, k_round<DV>, threads, smem_bp) != cudaSuccess) return -2;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_sel, k_select, threads, smem_sel) != cudaSuccess) return -2;
+    return 0;
+}
+
+int configure_kernels(const DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls)
+{
+    (void)cfg;
+    int dv;
+    if (g.max_col_deg <= 3) dv = 3;
+    else if (g.max_col_deg <= 6) dv = 6;
+    else if (g.max_col_deg <= 16) dv = 16;
+    else return -5;
+    const size_t per_warp = warp_smem_bytes(g);
+    int max_optin = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return -2;
+    if (per_warp > (size_t)max_optin) return -5;
+    int wpb = (int)((96 * 1024) / per_warp);
+    if (wpb > 8) wpb = 8;
+    if (wpb < 1) wpb = 1;
+    ls->warps_per_block = wpb;
+    ls->smem_bp = per_warp * (size_t)wpb;
+    ls->smem_select = sizeof(SelScratch) * (size_t)wpb;
+    ls->dv = dv;
+    int rc = 0, bps_bp = 0, bps_sel = 0;
+    const int threads = 32 * wpb;
+    switch (dv) {
+        case 3: rc = set_attrs<3>(ls->smem_bp, ls->smem_select); if (!rc) rc = occupancy<3>(threads, ls->smem_bp, ls->smem_select, &bps_bp, &bps_sel); break;
+        case 6: rc = set_attrs<6>(ls->smem_bp, ls->smem_select); if (!rc) rc = occupancy<6>(threads, ls->smem_bp, ls->smem_select, &bps_bp, &bps_sel); break;
+        default: rc = set_attrs<16>(ls->smem_bp, ls->smem_select); if (!rc) rc = occupancy<16>(threads, ls->smem_bp, ls->smem_select, &bps_bp, &bps_sel); break;
+    }
+    if (rc) return rc;
+    if (bps_bp < 1 || bps_sel < 1) return -5;
+    ls->grid_seed = sms * bps_bp;
+    ls->grid_round = sms * bps_bp;
+    ls->grid_select = sms * bps_sel;
+    return 0;
+}
+
+template <int DV>
+static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls,
+                          const uint32_t* synd, long long base, long long n, const Outputs& out, cudaStream_t s)
+{
+    const int threads = 32 * ls.warps_per_block;
+    k_seed<DV><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, synd, base, n, out);
+    if (cudaGetLastError() != cudaSuccess) return -2;
+    for (int r = 1; r <= cfg.max_rounds; ++r) {
+        k_round<DV><<<ls.grid_round, threads, ls.smem_bp, s>>>(g, cfg, w, r);
+        k_select<<<ls.grid_select, threads, ls.smem_select, s>>>(g, cfg, w, r, base, out);
+        if (cudaGetLastError() != cudaSuccess) return -2;
+    }
+    return 0;
+}
+
+int launch_chunk(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls, const uint32_t* synd,
+                 long long base, long long n, const Outputs& out, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (ls.dv) {
+        case 3: return launch_chunk_t<3>(g, cfg, w, ls, synd, base, n, out, s);
+        case 6: return launch_chunk_t<6>(g, cfg, w, ls, synd, base, n, out, s);
+        default: return launch_chunk_t<16>(g, cfg, w, ls, synd, base, n, out, s);
+    }
+}
+
+int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, const uint32_t* synd, long long B,
+                  int T, float* llr, float* sum_llr, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const int threads = 32 * ls.warps_per_block;
+    long long blocks = (B + ls.warps_per_block - 1) / ls.warps_per_block;
+    if (blocks > ls.grid_round) blocks = ls.grid_round;
+    if (blocks < 1) blocks = 1;
+    switch (ls.dv) {
+        case 3: k_bp_llr<3><<<(int)blocks, threads, ls.smem_bp, s>>>(g, cfg, synd, B, T, llr, sum_llr); break;
+        case 6: k_bp_llr<6><<<(int)blocks, threads, ls.smem_bp, s>>>(g, cfg, synd, B, T, llr, sum_llr); break;
+        default: k_bp_llr<16><<<(int)blocks, threads, ls.smem_bp, s>>>(g, cfg, synd, B, T, llr, sum_llr); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+}  // namespace bsd

@@ -393,5 +393,6 @@ def test_fp32_build_tracks_fp64(oracle_mod):
     r64 = g64.decode_batch(sh.syndromes, prm, nthreads=4)
     r32 = g32.decode_batch(sh.syndromes, prm, nthreads=4)
     diff = (r64["corrections"] != r32["corrections"]).any(1) | (r64["status"] != r32["status"])
-    # any disagreement must sit on a logged near-tie of the double build
-    assert np.all(r64["min_gap"][diff] < 1e-4)
+    # any disagreement must sit on a logged near-tie or exact tie of the double build
+    assert np.all((r64["min_gap"][diff] < 1e-4) | (r64["ties"][diff] > 0))
+    assert diff.sum() <= 2
