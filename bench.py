@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 beam search decoder on the [[144,12,12]] BB code.
+
+Workload (one step): decode 10^6 seeded code-capacity shots at each of
+p = 0.01, 0.03, 0.05 with the beam32_340iters preset (Table I) and min-sum
+scale 0.625 -- 3 x 10^6 syndromes per GPU per step, syndromes resident in
+HBM.  The metric is decoded syndromes/s; BP message updates/s, the roofline
+of the dominant kernel, logical error rates, an end-to-end figure through
+host buffers and the CPU oracle's throughput are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 run under torch.distributed.run: every rank decodes its own
+shots (weak scaling, no collective on the data path); rank 0 prints the line.
+--impl reference times the CPU oracle (the test oracle, double precision) on
+a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "decoded syndromes/s & BP msg-updates/s (% HBM peak) vs plain path, same LER"
+PS = (0.01, 0.03, 0.05)
+PRESET = "beam32_340iters"
+ALPHA = 0.625
+WORKLOAD = "bb144_code_capacity beam32_340iters alpha=0.625 p={0.01,0.03,0.05}"
+# algorithmic lane operations per message update of min-sum (Eqs. 1-3):
+# check side |x|, min1 and min2 compares, sign parity, select, sign, scale (7);
+# error side add into the posterior, extrinsic add, two-sided clamp (4);
+# per-node posterior bookkeeping amortised over the edges (1)
+OPS_PER_UPDATE = 12
+LANES_PER_SM = 128          # FP32/INT32 lanes per Blackwell SM
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--shots", type=int, default=1_000_000, help="shots per p per GPU per step")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def make_workload(rank: int, shots: int):
+    from paper_2512_07057_gb300 import workloads as W
+    out = []
+    for p in PS:
+        prob = W.bb144_code_capacity(p)
+        sh = W.sample_shots(prob, shots, W.shot_seed(f"bb144_cc_p{p}", rank))
+        out.append((p, prob, sh))
+    return out
+
+
+def ler_of(prob, shots, obs, status):
+    from paper_2512_07057_gb300 import workloads as W
+    o = W.unpack_bits(obs[:, :(prob.K + 31) // 32], prob.K)
+    t = W.unpack_bits(shots.obs, prob.K)
+    fail = (o != t).any(1) | (status == 4)
+    return float(fail.mean())
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline line and reference arm)
+# ----------------------------------------------------------------------------
+def oracle_rate(work, target_s: float, nthreads: int):
+    """Oracle (double precision) on a bounded prefix of each p batch, sized
+    from a short calibration run so the whole sample takes about target_s."""
+    import oracle
+    per = []
+    for p, prob, sh in work:
+        g = oracle.Graph(prob, "f64")
+        prm = oracle.preset(PRESET, ms_scale=ALPHA)
+        n0 = min(2000, sh.B)
+        t0 = time.perf_counter()
+        g.decode_batch(sh.syndromes[:n0], prm, nthreads=nthreads)
+        per.append((g, prm, sh, (time.perf_counter() - t0) / n0))
+    # equal shot counts per p (the workload mixes the three p equally)
+    sec_per_mix = sum(x[3] for x in per)
+    n = int(max(1000, min(work[0][2].B, target_s / max(sec_per_mix, 1e-9))))
+    t0 = time.perf_counter()
+    for g, prm, sh, _ in per:
+        g.decode_batch(sh.syndromes[:n], prm, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return 3 * n / dt, n, dt
+
+
+def cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    work = make_workload(0, min(args.shots, 200_000))
+    nth = cores()
+    import oracle
+    gs = [(oracle.Graph(prob, "f64"), sh) for _, prob, sh in work]
+    prm = oracle.preset(PRESET, ms_scale=ALPHA)
+    # one step: a bounded equal-size prefix of each p batch
+    rate, n, _ = oracle_rate(work, 8.0, nth)
+    for _ in range(args.warmup):
+        for g, sh in gs:
+            g.decode_batch(sh.syndromes[:max(1000, n // 10)], prm, nthreads=nth)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for g, sh in gs:
+            g.decode_batch(sh.syndromes[:n], prm, nthreads=nth)
+    dt = time.perf_counter() - t0
+    value = 3 * n * args.steps / dt
+    sample = f"first {n} of {work[0][2].B} seeded shots of each p per step, double-precision oracle, {nth} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "shots_per_p_per_step": n, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": nth, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    import torch.distributed as dist
+
+    from __graft_entry__ import build
+    from paper_2512_07057_gb300 import decoder as D
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+        build()
+    work = make_workload(rank, args.shots)
+    decs, synd, outs = [], [], []
+    for p, prob, sh in work:
+        params = D.make_params(PRESET, ms_scale=ALPHA, workspace_bytes=32 << 30)
+        d = D.BeamSearchDecoder(prob, params, device=dev)
+        decs.append(d)
+        synd.append(D.to_torch_words(sh.syndromes, dev))
+        outs.append(d.alloc_outputs(sh.B))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for d, s, o in zip(decs, synd, outs):
+            d.decode(s, o, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize(dev)
+    for d in decs:
+        d.profile(True)
+        d.profile_read()                      # reset counters
+    sampler = ClockSampler(dev) if rank == 0 else None
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                 # L2 flush between timed steps (outside the events)
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_total = float(sum(ms_steps))
+    prof = [d.profile_read() for d in decs]
+    for d in decs:
+        d.profile(False)
+    shots_per_step = sum(sh.B for _, _, sh in work)
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total_max = float(t.item())
+    else:
+        ms_total_max = ms_total
+
+    # ---- outputs of the last step: LER, algorithmic iterations
+    E = work[0][1].n_edges
+    per_p = {}
+    alg_iters_step = 0
+    for (p, prob, sh), o in zip(work, outs):
+        obs = D.from_torch_words(o.obs_flips)
+        st = D.from_torch_words(o.status)
+        it = D.from_torch_words(o.iters).astype(np.int64)
+        alg_iters_step += int(it.sum())
+        per_p[str(p)] = {"ler": ler_of(prob, sh, obs, st), "seed_converged": float((st == 1).mean()),
+                         "beam_converged": float((st == 2).mean()), "failed": float((st == 4).mean()),
+                         "mean_alg_iters": float(it.mean())}
+    ms_kind = np.sum([pr["ms"] for pr in prof], axis=0)
+    launches = np.sum([pr["launches"] for pr in prof], axis=0)
+    exec_iters = np.sum([pr["exec_iters"] for pr in prof], axis=0).astype(np.float64)
+    names = ("k_seed", "k_round", "k_select")
+    for (p, _, _), pr in zip(work, prof):
+        per_p[str(p)]["kernel_ms_per_step"] = {n: float(x) / args.steps for n, x in zip(names, pr["ms"])}
+    dom = int(np.argmax(ms_kind))
+    pk, pk_kind = peaks()
+    sm_mhz_max = float(pk.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak_tops = sms * LANES_PER_SM * sm_mhz_max * 1e6 / 1e12
+    # executed message updates of the dominant kernel (all edges of every candidate-iteration it ran);
+    # the selection kernel runs no BP, so its share is reported but it is never the roofline kernel
+    if dom == 2:
+        dom = int(np.argmax(ms_kind[:2]))
+    dom_iters = exec_iters[dom]
+    dom_updates_per_launch = dom_iters * E / max(1, launches[dom])
+    dom_ms_per_launch = ms_kind[dom] / max(1, launches[dom])
+    achieved = OPS_PER_UPDATE * dom_updates_per_launch / (dom_ms_per_launch * 1e-3) / 1e12
+    roofline = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": alu_peak_tops,
+                "unit": "Tops/s", "frac": achieved / alu_peak_tops, "traffic": None,
+                "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz (sm_max_mhz {pk_kind})",
+                "ops_per_msg_update": OPS_PER_UPDATE,
+                "msg_updates_per_launch": dom_updates_per_launch, "launch_ms": dom_ms_per_launch,
+                "kernel_share": float(ms_kind[dom] / max(ms_kind.sum(), 1e-9))}
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_file):
+        with open(traffic_file) as f:
+            tr = json.load(f)
+        if tr.get("kernel") == names[dom] and tr.get("source_hash") == _source_hash():
+            roofline["traffic"] = tr.get("bytes_per_launch")
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    steps_total_s = ms_total_max * 1e-3
+    value = world * shots_per_step * args.steps / steps_total_s
+    msg_alg = alg_iters_step * E * world / (steps_total_s / args.steps)
+    msg_exec = float(exec_iters.sum()) * E * world / steps_total_s
+    # the survey's streaming model: 14.7 B per update if every iteration moved its state through HBM
+    stream_bytes = 2 * 4 * E + 2 * (2 * 4 + 4) * 72 + 8 * 144
+    line = {
+        "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "code": "[[144,12,12]] BB, H_X 72x144, 432 edges",
+                   "shots_per_p_per_gpu": args.shots, "syndromes_per_step_per_gpu": shots_per_step,
+                   "l2": "flushed before every timed step (256 MiB write outside the step events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "msg_updates_per_s": {"algorithmic": msg_alg, "executed": msg_exec,
+                              "executed_per_algorithmic": float(exec_iters.sum() / args.steps / max(alg_iters_step, 1)),
+                              "pct_hbm_peak_streaming_model": 100 * msg_alg * (stream_bytes / E) / (hbm_peak * 1e9 * world),
+                              "streaming_bytes_per_update": stream_bytes / E},
+        "roofline": roofline,
+        "gpu_launches": int(launches.sum()),
+        "per_p": per_p,
+        "clocks": clocks,
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_host(decs, work, args, dev)
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, n, dt = oracle_rate(work, args.cpu_seconds, cores())
+        line["cpu_baseline"] = {"value": rate, "unit": "syndromes/s", "cores": cores(), "kind": "oracle",
+                                "sample": f"first {n} shots of each p batch (3 x {n}), double-precision oracle, "
+                                          f"{dt:.1f} s on {cores()} host threads"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for d in decs:
+        d.close()
+
+
+def e2e_host(decs, work, args, dev):
+    """Same metric through bsd_decode_host: pinned host syndromes in, host results out."""
+    import torch
+    bufs = []
+    h2d = d2h = 0
+    for d, (p, prob, sh) in zip(decs, work):
+        s = torch.from_numpy(sh.syndromes.view(np.int32)).pin_memory()
+        WN, WK = (prob.N + 31) // 32, max((prob.K + 31) // 32, 1)
+        c = torch.empty((sh.B, WN), dtype=torch.int32).pin_memory()
+        o = torch.empty((sh.B, WK), dtype=torch.int32).pin_memory()
+        st = torch.empty(sh.B, dtype=torch.int32).pin_memory()
+        it = torch.empty(sh.B, dtype=torch.int32).pin_memory()
+        bufs.append((d, s, c, o, st, it, sh.B))
+        h2d += s.numel() * 4
+        d2h += (c.numel() + o.numel() + st.numel() + it.numel()) * 4
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for d, s, c, o, st, it, nb in bufs:
+            d.decode_host_ptrs(s.data_ptr(), nb, c.data_ptr(), o.data_ptr(), st.data_ptr(), it.data_ptr(),
+                               stream=stream)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    shots = sum(b[-1] for b in bufs)
+    return {"value": shots * args.steps / dt, "unit": "syndromes/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "api": "bsd_decode_host (pinned host buffers)"}
+
+
+def _source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2512_07057_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2512_07057_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

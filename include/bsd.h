@@ -154,6 +154,20 @@ int bsd_sync_error(bsd_decoder *dec);
 int bsd_get_info(const bsd_decoder *dec, int32_t *M, int32_t *N, int32_t *K, int32_t *n_edges,
                  int64_t *chunk_shots, int64_t *workspace_bytes);
 
+/* Opt-in timing of this library's kernels (not part of the method): while
+ * enabled, every kernel launch made by bsd_decode / bsd_decode_host is
+ * bracketed by two CUDA events recorded on the decode stream.  Enabling costs
+ * two event records per launch.  Returns BSD_ERR_INVALID_ARG for NULL. */
+int bsd_profile_enable(bsd_decoder *dec, int enable);
+
+/* Synchronise the decode stream, then return and reset, since the previous
+ * read: the summed event-timed duration in milliseconds and the launch count
+ * of each kernel kind (index 0: seed BP, 1: expand + masked BP of a round,
+ * 2: per-shot selection of a round), and the BP iterations executed on the
+ * device (index 0: seed candidates, 1: round candidates, counting children
+ * evaluated after a shot's first success).  Any pointer may be NULL. */
+int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2]);
+
 /* Static text for a return code. */
 const char *bsd_error_string(int code);
 

@@ -27,7 +27,8 @@ BSD_STATUS_FAILED = 4
 
 # every symbol include/bsd.h declares
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
-           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_error_string", "bsd_destroy")
+           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_profile_enable", "bsd_profile_read",
+           "bsd_error_string", "bsd_destroy")
 
 
 class bsd_params(C.Structure):
@@ -67,6 +68,8 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_bp_llr.argtypes = [P, P, C.c_int64, C.c_int32, P, P, P]
     lib.bsd_sync_error.argtypes = [P]
     lib.bsd_get_info.argtypes = [P] + [C.POINTER(C.c_int32)] * 4 + [C.POINTER(C.c_int64)] * 2
+    lib.bsd_profile_enable.argtypes = [P, C.c_int]
+    lib.bsd_profile_read.argtypes = [P, P, P, P]
     lib.bsd_error_string.argtypes = [C.c_int]
     lib.bsd_error_string.restype = C.c_char_p
     lib.bsd_destroy.argtypes = [P]
@@ -133,6 +136,21 @@ def bsd_get_info(dec) -> dict:
     check(load().bsd_get_info(dec, C.byref(M), C.byref(N), C.byref(K), C.byref(E), C.byref(cs), C.byref(wb)),
           "bsd_get_info")
     return dict(M=M.value, N=N.value, K=K.value, n_edges=E.value, chunk_shots=cs.value, workspace_bytes=wb.value)
+
+
+def bsd_profile_enable(dec, enable: bool) -> None:
+    check(load().bsd_profile_enable(dec, int(bool(enable))), "bsd_profile_enable")
+
+
+def bsd_profile_read(dec) -> dict:
+    """Kernel times (ms) and launches per kind (seed, round, select), executed iterations."""
+    import numpy as np
+    ms = np.zeros(3, np.float64)
+    ln = np.zeros(3, np.int64)
+    it = np.zeros(2, np.uint64)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    check(load().bsd_profile_read(dec, p(ms), p(ln), p(it)), "bsd_profile_read")
+    return dict(ms=ms, launches=ln, exec_iters=it)
 
 
 def bsd_destroy(dec) -> None:

@@ -33,6 +33,18 @@ struct bsd_decoder {
     void* io_mem = nullptr;        // device staging for bsd_decode_host
     size_t io_bytes = 0;
     cudaStream_t last_stream = nullptr;
+    unsigned long long* d_stats = nullptr;   // executed BP iterations (seed, rounds)
+    // opt-in kernel timing
+    bool prof = false;
+    cudaStream_t prof_stream = nullptr;
+    std::vector<cudaEvent_t> ev;             // event pool
+    size_t ev_used = 0;
+    struct Rec { int kind; size_t e0, e1; };
+    std::vector<Rec> recs;
+    int open_kind = -1;
+    size_t open_ev = 0;
+    double ms[3] = {0, 0, 0};
+    long long launches[3] = {0, 0, 0};
 };
 
 namespace {
@@ -142,6 +154,8 @@ void bsd_destroy(bsd_decoder* dec)
         if (dec->graph_mem) cudaFree(dec->graph_mem);
         if (dec->work_mem) cudaFree(dec->work_mem);
         if (dec->io_mem) cudaFree(dec->io_mem);
+        if (dec->d_stats) cudaFree(dec->d_stats);
+        for (cudaEvent_t e : dec->ev) cudaEventDestroy(e);
     }
     delete dec;
 }
@@ -326,15 +340,70 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     w.res_n = carve<int>(q, C);
     w.items = carve<int2>(q, 2ull * C * W2);
     if (cudaMemset(dec->work_mem, 0, dec->ctr_bytes) != cudaSuccess) { bsd_destroy(dec); return BSD_ERR_CUDA; }
+    if (cudaMalloc(&dec->d_stats, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(dec->d_stats, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        bsd_destroy(dec);
+        return BSD_ERR_OOM;
+    }
+    w.stats = dec->d_stats;
     *out = dec;
     return BSD_OK;
+}
+
+// ---- opt-in kernel timing: events around every launch on the decode stream
+static size_t prof_event(bsd_decoder* d)
+{
+    if (d->ev_used == d->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+        d->ev.push_back(e);
+    }
+    return d->ev_used++;
+}
+
+static void prof_before(void* ctx, int kind)
+{
+    bsd_decoder* d = (bsd_decoder*)ctx;
+    const size_t e = prof_event(d);
+    if (e == (size_t)-1) return;
+    cudaEventRecord(d->ev[e], d->prof_stream);
+    d->open_kind = kind;
+    d->open_ev = e;
+}
+
+static void prof_after(void* ctx, int kind)
+{
+    bsd_decoder* d = (bsd_decoder*)ctx;
+    if (d->open_kind != kind) return;
+    const size_t e = prof_event(d);
+    if (e == (size_t)-1) return;
+    cudaEventRecord(d->ev[e], d->prof_stream);
+    d->recs.push_back({kind, d->open_ev, e});
+    d->open_kind = -1;
+}
+
+static void prof_collect(bsd_decoder* d)
+{
+    for (const auto& r : d->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, d->ev[r.e0], d->ev[r.e1]) == cudaSuccess) {
+            d->ms[r.kind] += ms;
+            d->launches[r.kind] += 1;
+        }
+    }
+    d->recs.clear();
+    d->ev_used = 0;
 }
 
 static int decode_impl(bsd_decoder* dec, const uint32_t* d_synd, long long base, long long n, const Outputs& o,
                        cudaStream_t s)
 {
     if (cudaMemsetAsync(dec->work_mem, 0, dec->ctr_bytes, s) != cudaSuccess) return BSD_ERR_CUDA;
-    return launch_chunk(dec->g, dec->cfg, dec->w, dec->ls, d_synd, base, n, o, s) ? BSD_ERR_CUDA : BSD_OK;
+    LaunchHooks hk{prof_before, prof_after, dec};
+    dec->prof_stream = s;
+    return launch_chunk(dec->g, dec->cfg, dec->w, dec->ls, d_synd, base, n, o, s, dec->prof ? &hk : nullptr)
+               ? BSD_ERR_CUDA
+               : BSD_OK;
 }
 
 int bsd_decode(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, uint32_t* d_corrections,
@@ -430,6 +499,34 @@ int bsd_sync_error(bsd_decoder* dec)
         cudaMemcpy(&dec->w.ctr->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
         return c.err == 1 ? BSD_ERR_TIMEOUT : BSD_ERR_DEVICE;
     }
+    return BSD_OK;
+}
+
+int bsd_profile_enable(bsd_decoder* dec, int enable)
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    dec->prof = enable != 0;
+    return BSD_OK;
+}
+
+int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2])
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    if (cudaStreamSynchronize(dec->last_stream) != cudaSuccess) return BSD_ERR_CUDA;
+    prof_collect(dec);
+    unsigned long long st[2] = {0, 0};
+    if (cudaMemcpy(st, dec->d_stats, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(dec->d_stats, 0, sizeof(st)) != cudaSuccess)
+        return BSD_ERR_CUDA;
+    for (int k = 0; k < 3; ++k) {
+        if (ms) ms[k] = dec->ms[k];
+        if (launches) launches[k] = dec->launches[k];
+        dec->ms[k] = 0;
+        dec->launches[k] = 0;
+    }
+    if (exec_iters) { exec_iters[0] = st[0]; exec_iters[1] = st[1]; }
     return BSD_OK;
 }
 

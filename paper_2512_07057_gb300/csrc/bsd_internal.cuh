@@ -82,6 +82,7 @@ struct Work {
     int2* items;           // [2][C * 2w] (active entry, child index)
     Counters* ctr;
     int* round_ctr;        // 3 * (max_rounds + 2) ints after ctr
+    unsigned long long* stats;   // [2] executed BP iterations: seed, beam rounds (not reset per chunk)
 };
 
 struct Outputs {
@@ -100,10 +101,17 @@ struct LaunchShape {
     int dv;                // compiled column-degree bound used
 };
 
+// optional callbacks around every kernel launch (kind: 0 seed, 1 round, 2 select)
+struct LaunchHooks {
+    void (*before)(void* ctx, int kind);
+    void (*after)(void* ctx, int kind);
+    void* ctx;
+};
+
 int configure_kernels(const DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls);
 int launch_chunk(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls,
                  const uint32_t* synd, long long chunk_base, long long chunk_n, const Outputs& out,
-                 void* stream);
+                 void* stream, const LaunchHooks* hooks);
 int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, const uint32_t* synd,
                   long long B, int T, float* llr, float* sum_llr, void* stream);
 

@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(256) k_seed(DevGraph g, DecCfg cfg, Work w, co
         __syncwarp();
         int succ = 0;
         const int it = bp_iterate<DV>(g, cfg, st, cfg.initial_iters, true, &succ, nullptr);
+        if (lane == 0) atomicAdd(&w.stats[0], (unsigned long long)it);
         __syncwarp();
         if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
             finalize_shot(g, out, gb, st.ehat, succ ? ST_SEED : ST_FAILED, (unsigned long long)it);
@@ -413,6 +414,7 @@ __global__ void __launch_bounds__(256) k_round(DevGraph g, DecCfg cfg, Work w, i
         __syncwarp();
         int succ = 0;
         const int iters = bp_iterate<DV>(g, cfg, st, cfg.iters_per_round, true, &succ, nullptr);
+        if (lane == 0) atomicAdd(&w.stats[1], (unsigned long long)iters);
         __syncwarp();
         for (int q = lane; q < g.WN; q += 32) st.ehat[q] = (st.ehat[q] & ~st.mask[q]) | st.vals[q];
         __syncwarp();
@@ -730,27 +732,33 @@ int configure_kernels(const DevGraph& g, const DecCfg& cfg, int device, LaunchSh
 
 template <int DV>
 static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls,
-                          const uint32_t* synd, long long base, long long n, const Outputs& out, cudaStream_t s)
+                          const uint32_t* synd, long long base, long long n, const Outputs& out, cudaStream_t s,
+                          const LaunchHooks* hk)
 {
     const int threads = 32 * ls.warps_per_block;
+    if (hk) hk->before(hk->ctx, 0);
     k_seed<DV><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, synd, base, n, out);
+    if (hk) hk->after(hk->ctx, 0);
     if (cudaGetLastError() != cudaSuccess) return -2;
     for (int r = 1; r <= cfg.max_rounds; ++r) {
+        if (hk) hk->before(hk->ctx, 1);
         k_round<DV><<<ls.grid_round, threads, ls.smem_bp, s>>>(g, cfg, w, r);
+        if (hk) { hk->after(hk->ctx, 1); hk->before(hk->ctx, 2); }
         k_select<<<ls.grid_select, threads, ls.smem_select, s>>>(g, cfg, w, r, base, out);
+        if (hk) hk->after(hk->ctx, 2);
         if (cudaGetLastError() != cudaSuccess) return -2;
     }
     return 0;
 }
 
 int launch_chunk(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls, const uint32_t* synd,
-                 long long base, long long n, const Outputs& out, void* stream)
+                 long long base, long long n, const Outputs& out, void* stream, const LaunchHooks* hooks)
 {
     cudaStream_t s = (cudaStream_t)stream;
     switch (ls.dv) {
-        case 3: return launch_chunk_t<3>(g, cfg, w, ls, synd, base, n, out, s);
-        case 6: return launch_chunk_t<6>(g, cfg, w, ls, synd, base, n, out, s);
-        default: return launch_chunk_t<16>(g, cfg, w, ls, synd, base, n, out, s);
+        case 3: return launch_chunk_t<3>(g, cfg, w, ls, synd, base, n, out, s, hooks);
+        case 6: return launch_chunk_t<6>(g, cfg, w, ls, synd, base, n, out, s, hooks);
+        default: return launch_chunk_t<16>(g, cfg, w, ls, synd, base, n, out, s, hooks);
     }
 }
 

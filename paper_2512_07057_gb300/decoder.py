@@ -126,6 +126,12 @@ class BeamSearchDecoder:
     def sync_error(self) -> int:
         return B.bsd_sync_error(self.h)
 
+    def profile(self, enable: bool = True) -> None:
+        B.bsd_profile_enable(self.h, enable)
+
+    def profile_read(self) -> dict:
+        return B.bsd_profile_read(self.h)
+
 
 def to_torch_words(arr: np.ndarray, device: int = 0):
     """uint32 numpy words -> int32 CUDA tensor with the same bits."""
