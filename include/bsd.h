@@ -57,6 +57,7 @@ extern "C" {
 #define BSD_ERR_TIMEOUT     (-4)   /* a bounded device-side wait gave up */
 #define BSD_ERR_UNSUPPORTED (-5)   /* valid input outside what this build handles */
 #define BSD_ERR_DEVICE      (-6)   /* a device-side check recorded an error */
+#define BSD_ERR_SCRATCH     (-7)   /* bsd_decode_noalloc: one shot needs more than the static scratch */
 
 /* message storage precision (bsd_params.msg_precision) */
 #define BSD_FP32 0
@@ -136,6 +137,37 @@ int bsd_decode(bsd_decoder *dec, const uint32_t *d_syndromes, int64_t B,
 int bsd_decode_host(bsd_decoder *dec, const uint32_t *h_syndromes, int64_t B,
                     uint32_t *h_corrections, uint32_t *h_obs_flips,
                     uint32_t *h_status, uint32_t *h_iters, void *cuda_stream);
+
+/* Allocation-free variant of bsd_decode.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory when
+ * they decode -- for example code whose device memory is owned by another
+ * allocator (a framework's caching allocator), or a latency-critical loop
+ * that may not take the driver's allocation locks or risk an allocation
+ * failure mid-run.  Such a caller creates the decoder once at set-up
+ * (bsd_create allocates there) and then decodes through this function, which
+ * calls no cudaMalloc, cudaFree or other allocating routine.  Instead of the
+ * decoder's own workspace it uses one file-scope static device array of
+ * BSD_NOALLOC_SCRATCH_BYTES that every device loading the library holds
+ * until the process exits.
+ *   Arguments, layouts and results are those of bsd_decode; the results are
+ *   identical to bsd_decode's.  Batches of any size are decoded in chunks
+ *   that fit the array.
+ *   The first call on a device looks up the array's device address on that
+ *   device (cudaGetSymbolAddress); make that first call before any stream
+ *   capture on the device.
+ *   All calls on a device share the one array, and it keeps the contents the
+ *   last call left: each call clears the counters it needs zeroed, but calls
+ *   whose work overlaps on the GPU (two streams, two host threads, two
+ *   decoders at once) race on the array and corrupt each other's results.
+ *   Serialise them.
+ *   Returns BSD_ERR_SCRATCH when the beam state of a single shot (two banks
+ *   of 2 * beam_width edge-message snapshots plus bookkeeping) exceeds the
+ *   array, BSD_ERR_INVALID_ARG as bsd_decode does, and BSD_ERR_CUDA when the
+ *   address lookup or a launch fails.  Opt-in kernel timing does not apply. */
+#define BSD_NOALLOC_SCRATCH_BYTES (32u << 20)
+int bsd_decode_noalloc(const bsd_decoder *dec, const uint32_t *d_syndromes, int64_t B,
+                       uint32_t *d_corrections, uint32_t *d_obs_flips,
+                       uint32_t *d_status, uint32_t *d_iters, void *cuda_stream);
 
 /* Plain min-sum BP (App. A, Eqs. 1-3) from E(0) = Lambda for exactly T
  * iterations per syndrome, with no stopping rule; writes the posterior LLRs

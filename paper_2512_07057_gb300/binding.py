@@ -28,7 +28,8 @@ BSD_STATUS_FAILED = 4
 # every symbol include/bsd.h declares
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
            "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_profile_enable", "bsd_profile_read",
-           "bsd_error_string", "bsd_destroy")
+           "bsd_decode_noalloc", "bsd_error_string", "bsd_destroy")
+BSD_ERR_SCRATCH = -7
 
 
 class bsd_params(C.Structure):
@@ -68,6 +69,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_bp_llr.argtypes = [P, P, C.c_int64, C.c_int32, P, P, P]
     lib.bsd_sync_error.argtypes = [P]
     lib.bsd_get_info.argtypes = [P] + [C.POINTER(C.c_int32)] * 4 + [C.POINTER(C.c_int64)] * 2
+    lib.bsd_decode_noalloc.argtypes = [P, P, C.c_int64, P, P, P, P, P]
     lib.bsd_profile_enable.argtypes = [P, C.c_int]
     lib.bsd_profile_read.argtypes = [P, P, P, P]
     lib.bsd_error_string.argtypes = [C.c_int]
@@ -115,6 +117,12 @@ def bsd_create(M, N, K, H_row_ptr, H_col_idx, A_row_ptr, A_col_idx, priors, para
 def bsd_decode(dec, d_syndromes, B, d_corrections, d_obs_flips, d_status, d_iters, stream) -> None:
     check(load().bsd_decode(dec, d_syndromes, int(B), d_corrections, d_obs_flips, d_status, d_iters, stream),
           "bsd_decode")
+
+
+def bsd_decode_noalloc(dec, d_syndromes, B, d_corrections, d_obs_flips, d_status, d_iters, stream) -> int:
+    """Allocation-free decode; returns the code (BSD_ERR_SCRATCH is an expected outcome)."""
+    return int(load().bsd_decode_noalloc(dec, d_syndromes, int(B), d_corrections, d_obs_flips, d_status,
+                                         d_iters, stream))
 
 
 def bsd_decode_host(dec, h_syndromes, B, h_corrections, h_obs_flips, h_status, h_iters, stream) -> None:

@@ -108,6 +108,7 @@ const char* bsd_error_string(int code)
         case BSD_ERR_TIMEOUT: return "device-side wait timed out";
         case BSD_ERR_UNSUPPORTED: return "unsupported size or option";
         case BSD_ERR_DEVICE: return "device-side check failed";
+        case BSD_ERR_SCRATCH: return "one shot needs more scratch than the static array holds";
         default: return "unknown error";
     }
 }
@@ -529,6 +530,24 @@ int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64
     if (exec_iters) { exec_iters[0] = st[0]; exec_iters[1] = st[1]; }
     return BSD_OK;
 }
+
+}  // extern "C"
+
+namespace bsd {
+// read-only view of a decoder for the allocation-free entry point (bsd_noalloc.cu)
+int decoder_view(const bsd_decoder* dec, const DevGraph** g, const DecCfg** cfg, const LaunchShape** ls,
+                 int* device)
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    *g = &dec->g;
+    *cfg = &dec->cfg;
+    *ls = &dec->ls;
+    *device = dec->device;
+    return BSD_OK;
+}
+}  // namespace bsd
+
+extern "C" {
 
 int bsd_get_info(const bsd_decoder* dec, int32_t* M, int32_t* N, int32_t* K, int32_t* n_edges, int64_t* chunk_shots,
                  int64_t* workspace_bytes)

@@ -95,6 +95,14 @@ class BeamSearchDecoder:
                      C.c_void_p(out.iters.data_ptr()) if with_iters else None, self._stream(stream))
         return out
 
+    def decode_noalloc(self, syndromes, out: DecodeResult, stream=None) -> int:
+        """bsd_decode_noalloc into caller-allocated outputs; returns the C return code."""
+        assert syndromes.is_cuda and syndromes.is_contiguous() and syndromes.element_size() == 4
+        return B.bsd_decode_noalloc(self.h, C.c_void_p(syndromes.data_ptr()), syndromes.shape[0],
+                                    C.c_void_p(out.corrections.data_ptr()), C.c_void_p(out.obs_flips.data_ptr()),
+                                    C.c_void_p(out.status.data_ptr()), C.c_void_p(out.iters.data_ptr()),
+                                    self._stream(stream))
+
     def decode_host(self, syndromes: np.ndarray, stream=None) -> dict:
         """Host arrays in and out (the copies run inside the call)."""
         synd = np.ascontiguousarray(syndromes, np.uint32)
