@@ -55,7 +55,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--ps", default="0.01,0.03,0.05", help="physical error rates (a smaller case for profiling)")
+    ap.add_argument("--workspace-gb", type=float, default=32.0, help="device workspace per decoder")
+    a = ap.parse_args()
+    a.ps = tuple(float(x) for x in a.ps.split(","))
+    return a
 
 
 def peaks():
@@ -126,10 +130,10 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def make_workload(rank: int, shots: int):
+def make_workload(rank: int, shots: int, ps=PS):
     from paper_2512_07057_gb300 import workloads as W
     out = []
-    for p in PS:
+    for p in ps:
         prob = W.bb144_code_capacity(p)
         sh = W.sample_shots(prob, shots, W.shot_seed(f"bb144_cc_p{p}", rank))
         out.append((p, prob, sh))
@@ -166,7 +170,7 @@ def oracle_rate(work, target_s: float, nthreads: int):
     for g, prm, sh, _ in per:
         g.decode_batch(sh.syndromes[:n], prm, nthreads=nthreads)
     dt = time.perf_counter() - t0
-    return 3 * n / dt, n, dt
+    return len(work) * n / dt, n, dt
 
 
 def cores() -> int:
@@ -179,7 +183,7 @@ def cores() -> int:
 def run_reference(args, rank: int):
     if rank != 0:
         return
-    work = make_workload(0, min(args.shots, 200_000))
+    work = make_workload(0, min(args.shots, 200_000), args.ps)
     nth = cores()
     import oracle
     gs = [(oracle.Graph(prob, "f64"), sh) for _, prob, sh in work]
@@ -194,7 +198,7 @@ def run_reference(args, rank: int):
         for g, sh in gs:
             g.decode_batch(sh.syndromes[:n], prm, nthreads=nth)
     dt = time.perf_counter() - t0
-    value = 3 * n * args.steps / dt
+    value = len(work) * n * args.steps / dt
     sample = f"first {n} of {work[0][2].B} seeded shots of each p per step, double-precision oracle, {nth} threads"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
@@ -222,10 +226,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if world > 1:
         dist.barrier()
         build()
-    work = make_workload(rank, args.shots)
+    work = make_workload(rank, args.shots, args.ps)
     decs, synd, outs = [], [], []
     for p, prob, sh in work:
-        params = D.make_params(PRESET, ms_scale=ALPHA, workspace_bytes=32 << 30)
+        params = D.make_params(PRESET, ms_scale=ALPHA, workspace_bytes=int(args.workspace_gb * (1 << 30)))
         d = D.BeamSearchDecoder(prob, params, device=dev)
         decs.append(d)
         synd.append(D.to_torch_words(sh.syndromes, dev))

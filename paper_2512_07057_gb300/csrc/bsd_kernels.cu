@@ -196,6 +196,21 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
     return iters;
 }
 
+// warp reduction of per-lane (min |sum_LLR|, its node, sum of q(|sum_LLR|)):
+// the smaller value wins, equal values go to the lower node index
+__device__ inline void reduce_argmin_score(float best, int bj, unsigned long long s, int* next_pos, long long* S)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(FULLMASK, best, o);
+        const int oj = __shfl_xor_sync(FULLMASK, bj, o);
+        if (oj >= 0 && (bj < 0 || ob < best || (ob == best && oj < bj))) { best = ob; bj = oj; }
+        s += __shfl_xor_sync(FULLMASK, s, o);
+    }
+    *next_pos = bj;
+    *S = (long long)s;
+}
+
 // least reliable unmasked node (lowest index on ties) and the score numerator
 __device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, int* next_pos,
                                         long long* S)
@@ -210,16 +225,197 @@ __device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, 
         if (bj < 0 || a < best) { best = a; bj = j; }
         s += fixq(a);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(FULLMASK, best, o);
-        const int oj = __shfl_xor_sync(FULLMASK, bj, o);
-        if (oj >= 0 && (bj < 0 || ob < best || (ob == best && oj < bj))) { best = ob; bj = oj; }
-        s += __shfl_xor_sync(FULLMASK, s, o);
-    }
-    *next_pos = bj;
-    *S = (long long)s;
+    reduce_argmin_score(best, bj, s, next_pos, S);
 }
+
+// ----------------------------------------------------------------------------
+// BP engines: how one warp runs the iterations of one candidate
+// ----------------------------------------------------------------------------
+// GenericEngine: any code whose column degree is at most DV; graph tables
+// are read from global memory (L1-resident) and sum_LLR lives in shared memory.
+template <int DV>
+struct GenericEngine {
+    __device__ void load_graph(const DevGraph&) {}
+    __device__ void clear_sums(const DevGraph& g, const WarpState& st)
+    {
+        for (int j = (threadIdx.x & 31); j < g.N; j += 32) st.sumllr[j] = 0.f;
+    }
+    __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
+                       int* success, float* post_out)
+    {
+        return bp_iterate<DV>(g, cfg, st, max_iters, stop, success, post_out);
+    }
+    __device__ void argmin_score(const DevGraph& g, const WarpState& st, int* np, long long* S)
+    {
+        argmin_and_score(g, st, np, S);
+    }
+    __device__ void write_sums(const DevGraph& g, const WarpState& st, float* dst)
+    {
+        for (int j = (threadIdx.x & 31); j < g.N; j += 32) dst[j] = st.sumllr[j];
+    }
+};
+
+// SmallEngine: codes with every column of degree exactly 3, every row of
+// degree exactly RD (row i's edges at RD*i .. RD*i+RD-1), N <= 32*CPL,
+// M <= 32*RPL and fewer than 65536 edges -- the bivariate bicycle codes.
+// Each lane keeps its columns' edge and row indices, priors, sum_LLR and
+// mask bits in registers for the warp's lifetime, detector records carry
+// alpha * min1 and alpha * min2 already scaled, and the ascending-order sums
+// of three messages are formed from min / max / median directly.  Every value
+// it produces is the one GenericEngine produces (same operations, same order).
+template <int CPL, int RPL, int RD>
+struct SmallEngine {
+    uint32_t ci[CPL][3];   // (CSR edge id << 16) | row, for column lane + 32 c
+    float lam[CPL];
+    float sum[CPL];
+    uint32_t mb;           // bit c: column lane + 32 c is masked or beyond N
+
+    __device__ void load_graph(const DevGraph& g)
+    {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int j = lane + 32 * c;
+            lam[c] = 0.f;
+            ci[c][0] = ci[c][1] = ci[c][2] = 0u;
+            if (j < g.N) {
+                const int kb = __ldg(g.col_ptr + j);
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    ci[c][k] = ((uint32_t)__ldg(g.col_edge + kb + k) << 16) | (uint32_t)__ldg(g.col_row + kb + k);
+                lam[c] = __ldg(g.lam + j);
+            }
+        }
+    }
+    __device__ void clear_sums(const DevGraph&, const WarpState&)
+    {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) sum[c] = 0.f;
+    }
+    __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
+                       int* success, float* post_out)
+    {
+        const int lane = threadIdx.x & 31;
+        const float alpha = cfg.alpha;
+        const float L = cfg.L;
+        mb = 0u;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int j = lane + 32 * c;
+            if (j >= g.N || ((st.mask[c] >> lane) & 1u)) mb |= 1u << c;
+        }
+        int iters = 0;
+        int ok = 0;
+        for (int t = 1; t <= max_iters; ++t) {
+            for (int q = lane; q < g.WM; q += 32) st.par[q] = st.sp[q];
+            // ---- detector pass (Eq. 1)
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int i = lane + 32 * r;
+                if (i < g.M) {
+                    const float2* er = reinterpret_cast<const float2*>(st.E + RD * i);
+                    float m1 = L, m2 = L;
+                    int pos = -1;
+                    uint32_t neg = (st.sp[i >> 5] >> (i & 31)) & 1u;
+#pragma unroll
+                    for (int h = 0; h < RD / 2; ++h) {
+                        const float2 x2 = er[h];
+                        const float xs[2] = {x2.x, x2.y};
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const float a = fabsf(xs[u]);
+                            if (a < m1) { m2 = m1; m1 = a; pos = 2 * h + u; }
+                            else if (a < m2) { m2 = a; }
+                            neg ^= (xs[u] < 0.f) ? 1u : 0u;
+                        }
+                    }
+                    const int id = pos < 0 ? -1 : RD * i + pos;
+                    st.rs[i] = make_float4(__fmul_rn(alpha, m1), __fmul_rn(alpha, m2), __int_as_float(id),
+                                           __uint_as_float(neg));
+                }
+            }
+            __syncwarp();
+            // ---- error-node pass (Eqs. 2-4)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                uint32_t ebit = 0;
+                if (!((mb >> c) & 1u)) {
+                    float v[3];
+                    int ed[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int e = (int)(ci[c][k] >> 16);
+                        const int r = (int)(ci[c][k] & 0xffffu);
+                        const float4 s4 = st.rs[r];
+                        const float xo = st.E[e];
+                        const float d = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
+                        const uint32_t sg = __float_as_uint(s4.w) ^ ((xo < 0.f) ? 1u : 0u);
+                        v[k] = sg ? -d : d;
+                        ed[k] = e;
+                    }
+                    const float l = lam[c];
+                    // Eq. 2: each message leaves its own detector out; the other
+                    // two are added in ascending order
+                    const float e0 = __fadd_rn(__fadd_rn(l, fminf(v[1], v[2])), fmaxf(v[1], v[2]));
+                    const float e1 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[2])), fmaxf(v[0], v[2]));
+                    const float e2 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[1])), fmaxf(v[0], v[1]));
+                    st.E[ed[0]] = fminf(fmaxf(e0, -L), L);
+                    st.E[ed[1]] = fminf(fmaxf(e1, -L), L);
+                    st.E[ed[2]] = fminf(fmaxf(e2, -L), L);
+                    // Eq. 3 in ascending order: smallest, median, largest
+                    const float lo01 = fminf(v[0], v[1]), hi01 = fmaxf(v[0], v[1]);
+                    const float a0 = fminf(lo01, v[2]);
+                    const float a2 = fmaxf(hi01, v[2]);
+                    const float a1 = fmaxf(lo01, fminf(hi01, v[2]));
+                    const float post = __fadd_rn(__fadd_rn(__fadd_rn(l, a0), a1), a2);
+                    sum[c] = __fadd_rn(sum[c], post);
+                    if (post_out != nullptr && t == max_iters) post_out[lane + 32 * c] = post;
+                    ebit = (post <= 0.f) ? 1u : 0u;                                   // Eq. 4
+                    if (ebit) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const int r = (int)(ci[c][k] & 0xffffu);
+                            atomicXor(&st.par[r >> 5], 1u << (r & 31));
+                        }
+                    }
+                }
+                const uint32_t bal = __ballot_sync(FULLMASK, ebit);
+                if (lane == 0) st.ehat[c] = bal;
+            }
+            __syncwarp();
+            uint32_t nz = 0;
+            for (int q = lane; q < g.WM; q += 32) nz |= st.par[q];
+            ok = !__any_sync(FULLMASK, nz != 0u);
+            iters = t;
+            __syncwarp();
+            if (ok && stop) break;
+        }
+        *success = ok;
+        return iters;
+    }
+    __device__ void argmin_score(const DevGraph&, const WarpState&, int* np, long long* S)
+    {
+        const int lane = threadIdx.x & 31;
+        float best = INFINITY;
+        int bj = -1;
+        unsigned long long s = 0;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            if ((mb >> c) & 1u) continue;
+            const float a = fabsf(sum[c]);
+            if (bj < 0 || a < best) { best = a; bj = lane + 32 * c; }
+            s += fixq(a);
+        }
+        reduce_argmin_score(best, bj, s, np, S);
+    }
+    __device__ void write_sums(const DevGraph& g, const WarpState&, float* dst)
+    {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+            if (lane + 32 * c < g.N) dst[lane + 32 * c] = sum[c];
+    }
+};
 
 // write one shot's outputs: e^, A e^, status, iteration count
 __device__ void finalize_shot(const DevGraph& g, const Outputs& out, long long gb, const uint32_t* ehat,
@@ -266,7 +462,7 @@ __device__ inline size_t slot_index(const Work& w, int bank, int a, int c, int W
 // ----------------------------------------------------------------------------
 // seed BP
 // ----------------------------------------------------------------------------
-template <int DV>
+template <class Eng>
 __global__ void __launch_bounds__(256) k_seed(DevGraph g, DecCfg cfg, Work w, const uint32_t* __restrict__ synd,
                                               long long base, long long n, Outputs out)
 {
@@ -275,6 +471,8 @@ __global__ void __launch_bounds__(256) k_seed(DevGraph g, DecCfg cfg, Work w, co
     const int wid = threadIdx.x >> 5;
     const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
     const int W2 = 2 * cfg.w;
+    Eng eng;
+    eng.load_graph(g);
     for (;;) {
         int b = 0;
         if (lane == 0) b = atomicAdd(&w.ctr->claim_seed, 1);
@@ -300,10 +498,10 @@ __global__ void __launch_bounds__(256) k_seed(DevGraph g, DecCfg cfg, Work w, co
         const float4* src = reinterpret_cast<const float4*>(g.lamE);
         float4* dst = reinterpret_cast<float4*>(st.E);
         for (int q = lane; q < g.Epad / 4; q += 32) dst[q] = __ldg(src + q);
-        for (int j = lane; j < g.N; j += 32) st.sumllr[j] = 0.f;
+        eng.clear_sums(g, st);
         __syncwarp();
         int succ = 0;
-        const int it = bp_iterate<DV>(g, cfg, st, cfg.initial_iters, true, &succ, nullptr);
+        const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr);
         if (lane == 0) atomicAdd(&w.stats[0], (unsigned long long)it);
         __syncwarp();
         if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
@@ -313,7 +511,7 @@ __global__ void __launch_bounds__(256) k_seed(DevGraph g, DecCfg cfg, Work w, co
         }
         int np;
         long long S;
-        argmin_and_score(g, st, &np, &S);
+        eng.argmin_score(g, st, &np, &S);
         int a = 0;
         if (lane == 0) a = atomicAdd(&w.ctr->n_active, 1);
         a = __shfl_sync(FULLMASK, a, 0);
@@ -362,7 +560,7 @@ __global__ void __launch_bounds__(256) k_seed(DevGraph g, DecCfg cfg, Work w, co
 // ----------------------------------------------------------------------------
 // one beam round: expand every child and run masked BP (Alg. 2)
 // ----------------------------------------------------------------------------
-template <int DV>
+template <class Eng>
 __global__ void __launch_bounds__(256) k_round(DevGraph g, DecCfg cfg, Work w, int r)
 {
     extern __shared__ __align__(16) char smem[];
@@ -370,6 +568,8 @@ __global__ void __launch_bounds__(256) k_round(DevGraph g, DecCfg cfg, Work w, i
     const int wid = threadIdx.x >> 5;
     const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
     const int W2 = 2 * cfg.w;
+    Eng eng;
+    eng.load_graph(g);
     int* rc = round_ctr(w, r);
     const int nitems = *((volatile int*)(rc + 2));
     const int2* items = w.items + (size_t)(r & 1) * (size_t)w.C * (size_t)W2;
@@ -407,20 +607,20 @@ __global__ void __launch_bounds__(256) k_round(DevGraph g, DecCfg cfg, Work w, i
         const float4* pE = reinterpret_cast<const float4*>(w.slotE + pslot * (size_t)g.Epad);
         float4* sE = reinterpret_cast<float4*>(st.E);
         for (int q = lane; q < g.Epad / 4; q += 32) sE[q] = pE[q];
-        for (int j = lane; j < g.N; j += 32) st.sumllr[j] = 0.f;
+        eng.clear_sums(g, st);
         __syncwarp();
         for (int q = __ldg(g.col_ptr + pos) + lane; q < __ldg(g.col_ptr + pos + 1); q += 32)
             st.E[__ldg(g.col_edge + q)] = cfg.L;
         __syncwarp();
         int succ = 0;
-        const int iters = bp_iterate<DV>(g, cfg, st, cfg.iters_per_round, true, &succ, nullptr);
+        const int iters = eng.run(g, cfg, st, cfg.iters_per_round, true, &succ, nullptr);
         if (lane == 0) atomicAdd(&w.stats[1], (unsigned long long)iters);
         __syncwarp();
         for (int q = lane; q < g.WN; q += 32) st.ehat[q] = (st.ehat[q] & ~st.mask[q]) | st.vals[q];
         __syncwarp();
         int np;
         long long S;
-        argmin_and_score(g, st, &np, &S);
+        eng.argmin_score(g, st, &np, &S);
         float4* cE = reinterpret_cast<float4*>(w.slotE + cslot * (size_t)g.Epad);
         for (int q = lane; q < g.Epad / 4; q += 32) cE[q] = sE[q];
         uint32_t* cbits = w.slotBits + cslot * (size_t)w.SB;
@@ -646,7 +846,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
 // ----------------------------------------------------------------------------
 // plain BP for a fixed number of iterations (LLR measurement)
 // ----------------------------------------------------------------------------
-template <int DV>
+template <class Eng>
 __global__ void __launch_bounds__(256) k_bp_llr(DevGraph g, DecCfg cfg, const uint32_t* __restrict__ synd, long long B,
                                                 int T, float* llr, float* sum_llr)
 {
@@ -654,6 +854,8 @@ __global__ void __launch_bounds__(256) k_bp_llr(DevGraph g, DecCfg cfg, const ui
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
+    Eng eng;
+    eng.load_graph(g);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long b = (long long)blockIdx.x * (blockDim.x >> 5) + wid; b < B; b += nw) {
         for (int q = lane; q < g.WM; q += 32) st.sp[q] = synd[b * g.WM + q];
@@ -661,13 +863,12 @@ __global__ void __launch_bounds__(256) k_bp_llr(DevGraph g, DecCfg cfg, const ui
         const float4* src = reinterpret_cast<const float4*>(g.lamE);
         float4* dst = reinterpret_cast<float4*>(st.E);
         for (int q = lane; q < g.Epad / 4; q += 32) dst[q] = __ldg(src + q);
-        for (int j = lane; j < g.N; j += 32) st.sumllr[j] = 0.f;
+        eng.clear_sums(g, st);
         __syncwarp();
         int succ;
-        bp_iterate<DV>(g, cfg, st, T, false, &succ, llr + b * g.N);
+        eng.run(g, cfg, st, T, false, &succ, llr + b * g.N);
         __syncwarp();
-        if (sum_llr != nullptr)
-            for (int j = lane; j < g.N; j += 32) sum_llr[b * g.N + j] = st.sumllr[j];
+        if (sum_llr != nullptr) eng.write_sums(g, st, sum_llr + b * g.N);
         __syncwarp();
     }
 }
@@ -675,32 +876,52 @@ __global__ void __launch_bounds__(256) k_bp_llr(DevGraph g, DecCfg cfg, const ui
 // ----------------------------------------------------------------------------
 // host-side launch helpers
 // ----------------------------------------------------------------------------
-template <int DV>
-static int set_attrs(size_t smem_bp, size_t smem_sel)
+// engine ids: 0..2 generic with column degree bound 3 / 6 / 16;
+// 3: small (CPL 3, RPL 2, row degree 6), 4: small (CPL 5, RPL 3, row degree 6)
+using Generic3 = GenericEngine<3>;
+using Generic6 = GenericEngine<6>;
+using Generic16 = GenericEngine<16>;
+using Small326 = SmallEngine<3, 2, 6>;
+using Small536 = SmallEngine<5, 3, 6>;
+#define BSD_ENGINES(X) X(0, Generic3) X(1, Generic6) X(2, Generic16) X(3, Small326) X(4, Small536)
+
+template <class Eng>
+static int set_attrs(size_t smem_bp)
 {
-    if (cudaFuncSetAttribute(k_seed<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
-        cudaFuncSetAttribute(k_round<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
-        cudaFuncSetAttribute(k_bp_llr<DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
-        cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sel) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_seed<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
+        cudaFuncSetAttribute(k_round<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
+        cudaFuncSetAttribute(k_bp_llr<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess)
         return -2;
     return 0;
 }
 
-template <int DV>
-static int occupancy(int threads, size_t smem_bp, size_t smem_sel, int* bps_bp, int* bps_sel)
+template <class Eng>
+static int occupancy(int threads, size_t smem_bp, int* bps)
 {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_bp, k_round<DV>, threads, smem_bp) != cudaSuccess) return -2;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps_sel, k_select, threads, smem_sel) != cudaSuccess) return -2;
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_round<Eng>, threads, smem_bp) != cudaSuccess) return -2;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_seed<Eng>, threads, smem_bp) != cudaSuccess) return -2;
+    *bps = a < b ? a : b;
     return 0;
+}
+
+// can the small engine run this code? (column degree 3, row degree 6 laid out at 6 i)
+static bool small_fits(const DevGraph& g, int cpl, int rpl)
+{
+    if (g.max_col_deg != 3 || g.max_row_deg != 6 || g.E != 3 * g.N || g.E != 6 * g.M) return false;
+    if (g.E >= 65536 || g.M >= 65536) return false;
+    return g.WN == cpl && (g.M + 31) / 32 == rpl;
 }
 
 int configure_kernels(const DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls)
 {
     (void)cfg;
-    int dv;
-    if (g.max_col_deg <= 3) dv = 3;
-    else if (g.max_col_deg <= 6) dv = 6;
-    else if (g.max_col_deg <= 16) dv = 16;
+    int eng;
+    if (small_fits(g, 3, 2)) eng = 3;
+    else if (small_fits(g, 5, 3)) eng = 4;
+    else if (g.max_col_deg <= 3) eng = 0;
+    else if (g.max_col_deg <= 6) eng = 1;
+    else if (g.max_col_deg <= 16) eng = 2;
     else return -5;
     const size_t per_warp = warp_smem_bytes(g);
     int max_optin = 0, sms = 0;
@@ -714,15 +935,24 @@ int configure_kernels(const DevGraph& g, const DecCfg& cfg, int device, LaunchSh
     ls->warps_per_block = wpb;
     ls->smem_bp = per_warp * (size_t)wpb;
     ls->smem_select = sizeof(SelScratch) * (size_t)wpb;
-    ls->dv = dv;
-    int rc = 0, bps_bp = 0, bps_sel = 0;
+    ls->dv = eng;
     const int threads = 32 * wpb;
-    switch (dv) {
-        case 3: rc = set_attrs<3>(ls->smem_bp, ls->smem_select); if (!rc) rc = occupancy<3>(threads, ls->smem_bp, ls->smem_select, &bps_bp, &bps_sel); break;
-        case 6: rc = set_attrs<6>(ls->smem_bp, ls->smem_select); if (!rc) rc = occupancy<6>(threads, ls->smem_bp, ls->smem_select, &bps_bp, &bps_sel); break;
-        default: rc = set_attrs<16>(ls->smem_bp, ls->smem_select); if (!rc) rc = occupancy<16>(threads, ls->smem_bp, ls->smem_select, &bps_bp, &bps_sel); break;
+    int rc = 0, bps_bp = 0, bps_sel = 0;
+    switch (eng) {
+#define X(id, E)                                                                \
+    case id:                                                                    \
+        rc = set_attrs<E>(ls->smem_bp);                             \
+        if (!rc) rc = occupancy<E>(threads, ls->smem_bp, &bps_bp);  \
+        break;
+        BSD_ENGINES(X)
+#undef X
+        default: return -5;
     }
     if (rc) return rc;
+    if (cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls->smem_select) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_sel, k_select, threads, ls->smem_select) != cudaSuccess)
+        return -2;
     if (bps_bp < 1 || bps_sel < 1) return -5;
     ls->grid_seed = sms * bps_bp;
     ls->grid_round = sms * bps_bp;
@@ -730,19 +960,19 @@ int configure_kernels(const DevGraph& g, const DecCfg& cfg, int device, LaunchSh
     return 0;
 }
 
-template <int DV>
+template <class Eng>
 static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls,
                           const uint32_t* synd, long long base, long long n, const Outputs& out, cudaStream_t s,
                           const LaunchHooks* hk)
 {
     const int threads = 32 * ls.warps_per_block;
     if (hk) hk->before(hk->ctx, 0);
-    k_seed<DV><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, synd, base, n, out);
+    k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, synd, base, n, out);
     if (hk) hk->after(hk->ctx, 0);
     if (cudaGetLastError() != cudaSuccess) return -2;
     for (int r = 1; r <= cfg.max_rounds; ++r) {
         if (hk) hk->before(hk->ctx, 1);
-        k_round<DV><<<ls.grid_round, threads, ls.smem_bp, s>>>(g, cfg, w, r);
+        k_round<Eng><<<ls.grid_round, threads, ls.smem_bp, s>>>(g, cfg, w, r);
         if (hk) { hk->after(hk->ctx, 1); hk->before(hk->ctx, 2); }
         k_select<<<ls.grid_select, threads, ls.smem_select, s>>>(g, cfg, w, r, base, out);
         if (hk) hk->after(hk->ctx, 2);
@@ -756,24 +986,34 @@ int launch_chunk(const DevGraph& g, const DecCfg& cfg, const Work& w, const Laun
 {
     cudaStream_t s = (cudaStream_t)stream;
     switch (ls.dv) {
-        case 3: return launch_chunk_t<3>(g, cfg, w, ls, synd, base, n, out, s, hooks);
-        case 6: return launch_chunk_t<6>(g, cfg, w, ls, synd, base, n, out, s, hooks);
-        default: return launch_chunk_t<16>(g, cfg, w, ls, synd, base, n, out, s, hooks);
+#define X(id, E) \
+    case id: return launch_chunk_t<E>(g, cfg, w, ls, synd, base, n, out, s, hooks);
+        BSD_ENGINES(X)
+#undef X
+        default: return -5;
     }
+}
+
+template <class Eng>
+static void launch_llr_t(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, const uint32_t* synd,
+                         long long B, int T, float* llr, float* sum_llr, cudaStream_t s, int blocks)
+{
+    k_bp_llr<Eng><<<blocks, 32 * ls.warps_per_block, ls.smem_bp, s>>>(g, cfg, synd, B, T, llr, sum_llr);
 }
 
 int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, const uint32_t* synd, long long B,
                   int T, float* llr, float* sum_llr, void* stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    const int threads = 32 * ls.warps_per_block;
     long long blocks = (B + ls.warps_per_block - 1) / ls.warps_per_block;
     if (blocks > ls.grid_round) blocks = ls.grid_round;
     if (blocks < 1) blocks = 1;
     switch (ls.dv) {
-        case 3: k_bp_llr<3><<<(int)blocks, threads, ls.smem_bp, s>>>(g, cfg, synd, B, T, llr, sum_llr); break;
-        case 6: k_bp_llr<6><<<(int)blocks, threads, ls.smem_bp, s>>>(g, cfg, synd, B, T, llr, sum_llr); break;
-        default: k_bp_llr<16><<<(int)blocks, threads, ls.smem_bp, s>>>(g, cfg, synd, B, T, llr, sum_llr); break;
+#define X(id, E) \
+    case id: launch_llr_t<E>(g, cfg, ls, synd, B, T, llr, sum_llr, s, (int)blocks); break;
+        BSD_ENGINES(X)
+#undef X
+        default: return -5;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
