@@ -31,6 +31,7 @@ struct DevGraph {
     int Epad, Npad;        // E, N rounded up to a multiple of 4
     int max_col_deg, max_row_deg;
     int all_lam_pos;       // every Lambda_j > 0 (all p_j < 1/2)
+    int det_bytes;         // per-warp detector-side shared memory (set with the engine)
     const int* row_ptr;
     const int* col_ptr;
     const int* col_edge;
@@ -108,7 +109,7 @@ struct LaunchHooks {
     void* ctx;
 };
 
-int configure_kernels(const DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls);
+int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls);
 int launch_chunk(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls,
                  const uint32_t* synd, long long chunk_base, long long chunk_n, const Outputs& out,
                  void* stream, const LaunchHooks* hooks);

@@ -41,15 +41,21 @@ enum : uint32_t { ST_SEED = 1u, ST_BEAM = 2u, ST_FAILED = 4u };
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // per-warp shared-memory footprint of one BP candidate
+// detector-side region: M records of 16 bytes (GenericEngine), or one D
+// message per edge and at least M records (SmallEngine); g.det_bytes is set
+// with the engine choice
+__host__ __device__ inline size_t det_region_bytes(const DevGraph& g) { return (size_t)g.det_bytes; }
+
 __host__ __device__ inline size_t warp_smem_bytes(const DevGraph& g)
 {
-    return align16(sizeof(float) * (size_t)g.Epad) + sizeof(float4) * (size_t)g.M +
+    return align16(sizeof(float) * (size_t)g.Epad) + det_region_bytes(g) +
            align16(sizeof(float) * (size_t)g.Npad) + align16(sizeof(uint32_t) * (size_t)(2 * g.WM + 3 * g.WN));
 }
 
 struct WarpState {
     float* E;          // [Epad] E_{j->i}, CSR edge order
     float4* rs;        // [M]    (min1, min2, argmin edge id, s'_i xor parity of negatives)
+    float* D;          // [Epad] D_{i->j} per CSR edge (same storage as rs)
     float* sumllr;     // [Npad]
     uint32_t* sp;      // [WM] s' = s with the columns of nodes fixed to 1 folded in
     uint32_t* par;     // [WM] s' xor H e^ (zero iff converged)
@@ -63,7 +69,8 @@ __device__ inline WarpState carve(char* base, const DevGraph& g)
     WarpState s;
     char* p = base;
     s.E = reinterpret_cast<float*>(p);       p += align16(sizeof(float) * (size_t)g.Epad);
-    s.rs = reinterpret_cast<float4*>(p);     p += sizeof(float4) * (size_t)g.M;
+    s.rs = reinterpret_cast<float4*>(p);
+    s.D = reinterpret_cast<float*>(p);       p += det_region_bytes(g);
     s.sumllr = reinterpret_cast<float*>(p);  p += align16(sizeof(float) * (size_t)g.Npad);
     uint32_t* b = reinterpret_cast<uint32_t*>(p);
     s.sp = b;
@@ -235,6 +242,7 @@ __device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, 
 // are read from global memory (L1-resident) and sum_LLR lives in shared memory.
 template <int DV>
 struct GenericEngine {
+    static constexpr int kMinBlocks = 1;
     __device__ void load_graph(const DevGraph&) {}
     __device__ void clear_sums(const DevGraph& g, const WarpState& st)
     {
@@ -259,12 +267,15 @@ struct GenericEngine {
 // degree exactly RD (row i's edges at RD*i .. RD*i+RD-1), N <= 32*CPL,
 // M <= 32*RPL and fewer than 65536 edges -- the bivariate bicycle codes.
 // Each lane keeps its columns' edge and row indices, priors, sum_LLR and
-// mask bits in registers for the warp's lifetime, detector records carry
-// alpha * min1 and alpha * min2 already scaled, and the ascending-order sums
-// of three messages are formed from min / max / median directly.  Every value
-// it produces is the one GenericEngine produces (same operations, same order).
+// mask bits in registers for the warp's lifetime.  The detector pass writes
+// D_{i->j} itself for every edge (row-contiguous vector stores), so the
+// error-node pass gathers one 4-byte message per edge; the ascending-order
+// sums of three messages are formed from min / max / median directly.  Every
+// value it produces is the one GenericEngine produces (same operations, same
+// order).
 template <int CPL, int RPL, int RD>
 struct SmallEngine {
+    static constexpr int kMinBlocks = 2;   // at most 128 registers: two 8-warp blocks per SM
     uint32_t ci[CPL][3];   // (CSR edge id << 16) | row, for column lane + 32 c
     float lam[CPL];
     float sum[CPL];
@@ -317,6 +328,7 @@ struct SmallEngine {
                     float m1 = L, m2 = L;
                     int pos = -1;
                     uint32_t neg = (st.sp[i >> 5] >> (i & 31)) & 1u;
+                    uint32_t negs[RD];
 #pragma unroll
                     for (int h = 0; h < RD / 2; ++h) {
                         const float2 x2 = er[h];
@@ -326,12 +338,25 @@ struct SmallEngine {
                             const float a = fabsf(xs[u]);
                             if (a < m1) { m2 = m1; m1 = a; pos = 2 * h + u; }
                             else if (a < m2) { m2 = a; }
-                            neg ^= (xs[u] < 0.f) ? 1u : 0u;
+                            negs[2 * h + u] = (xs[u] < 0.f) ? 1u : 0u;
+                            neg ^= negs[2 * h + u];
                         }
                     }
-                    const int id = pos < 0 ? -1 : RD * i + pos;
-                    st.rs[i] = make_float4(__fmul_rn(alpha, m1), __fmul_rn(alpha, m2), __int_as_float(id),
-                                           __uint_as_float(neg));
+                    // D_{i->j} for every edge of the row: alpha * (minimum over the
+                    // others), sign = s'_i xor parity of the others' signs
+                    const float d1 = __fmul_rn(alpha, m1), d2 = __fmul_rn(alpha, m2);
+                    float2* dr = reinterpret_cast<float2*>(st.D + RD * i);
+#pragma unroll
+                    for (int h = 0; h < RD / 2; ++h) {
+                        float dd[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int k = 2 * h + u;
+                            const float d = (k == pos) ? d2 : d1;
+                            dd[u] = (neg ^ negs[k]) ? -d : d;
+                        }
+                        dr[h] = make_float2(dd[0], dd[1]);
+                    }
                 }
             }
             __syncwarp();
@@ -344,14 +369,8 @@ struct SmallEngine {
                     int ed[3];
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        const int e = (int)(ci[c][k] >> 16);
-                        const int r = (int)(ci[c][k] & 0xffffu);
-                        const float4 s4 = st.rs[r];
-                        const float xo = st.E[e];
-                        const float d = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
-                        const uint32_t sg = __float_as_uint(s4.w) ^ ((xo < 0.f) ? 1u : 0u);
-                        v[k] = sg ? -d : d;
-                        ed[k] = e;
+                        ed[k] = (int)(ci[c][k] >> 16);
+                        v[k] = st.D[ed[k]];
                     }
                     const float l = lam[c];
                     // Eq. 2: each message leaves its own detector out; the other
@@ -463,7 +482,7 @@ __device__ inline size_t slot_index(const Work& w, int bank, int a, int c, int W
 // seed BP
 // ----------------------------------------------------------------------------
 template <class Eng>
-__global__ void __launch_bounds__(256) k_seed(DevGraph g, DecCfg cfg, Work w, const uint32_t* __restrict__ synd,
+__global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCfg cfg, Work w, const uint32_t* __restrict__ synd,
                                               long long base, long long n, Outputs out)
 {
     extern __shared__ __align__(16) char smem[];
@@ -561,7 +580,7 @@ __global__ void __launch_bounds__(256) k_seed(DevGraph g, DecCfg cfg, Work w, co
 // one beam round: expand every child and run masked BP (Alg. 2)
 // ----------------------------------------------------------------------------
 template <class Eng>
-__global__ void __launch_bounds__(256) k_round(DevGraph g, DecCfg cfg, Work w, int r)
+__global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecCfg cfg, Work w, int r)
 {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31;
@@ -847,7 +866,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
 // plain BP for a fixed number of iterations (LLR measurement)
 // ----------------------------------------------------------------------------
 template <class Eng>
-__global__ void __launch_bounds__(256) k_bp_llr(DevGraph g, DecCfg cfg, const uint32_t* __restrict__ synd, long long B,
+__global__ void __launch_bounds__(256, Eng::kMinBlocks) k_bp_llr(DevGraph g, DecCfg cfg, const uint32_t* __restrict__ synd, long long B,
                                                 int T, float* llr, float* sum_llr)
 {
     extern __shared__ __align__(16) char smem[];
@@ -913,7 +932,7 @@ static bool small_fits(const DevGraph& g, int cpl, int rpl)
     return g.WN == cpl && (g.M + 31) / 32 == rpl;
 }
 
-int configure_kernels(const DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls)
+int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls)
 {
     (void)cfg;
     int eng;
@@ -923,6 +942,8 @@ int configure_kernels(const DevGraph& g, const DecCfg& cfg, int device, LaunchSh
     else if (g.max_col_deg <= 6) eng = 1;
     else if (g.max_col_deg <= 16) eng = 2;
     else return -5;
+    const size_t recs = sizeof(float4) * (size_t)g.M, msgs = sizeof(float) * (size_t)g.Epad;
+    g.det_bytes = (int)align16(eng >= 3 && msgs > recs ? msgs : recs);
     const size_t per_warp = warp_smem_bytes(g);
     int max_optin = 0, sms = 0;
     if (cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
