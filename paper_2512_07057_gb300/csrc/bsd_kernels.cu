@@ -325,25 +325,31 @@ struct SmallEngine {
                 const int i = lane + 32 * r;
                 if (i < g.M) {
                     const float2* er = reinterpret_cast<const float2*>(st.E + RD * i);
-                    float m1 = L, m2 = L;
-                    int pos = -1;
-                    uint32_t neg = (st.sp[i >> 5] >> (i & 31)) & 1u;
-                    uint32_t negs[RD];
+                    float x[RD];
 #pragma unroll
                     for (int h = 0; h < RD / 2; ++h) {
                         const float2 x2 = er[h];
-                        const float xs[2] = {x2.x, x2.y};
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const float a = fabsf(xs[u]);
-                            if (a < m1) { m2 = m1; m1 = a; pos = 2 * h + u; }
-                            else if (a < m2) { m2 = a; }
-                            negs[2 * h + u] = (xs[u] < 0.f) ? 1u : 0u;
-                            neg ^= negs[2 * h + u];
-                        }
+                        x[2 * h] = x2.x;
+                        x[2 * h + 1] = x2.y;
                     }
+                    // the two smallest magnitudes m1 <= m2 (m2 = m1 when the
+                    // minimum is attained twice), starting from L_MAX (R3)
+                    float m1 = L, m2 = L;
+                    // sign parity in bit 31: a stored message is never -0 (it is
+                    // a clamped sum of terms that starts at Lambda_j or the
+                    // sentinel), so its sign bit is exactly x < 0
+                    uint32_t nb = ((st.sp[i >> 5] >> (i & 31)) & 1u) << 31;
+#pragma unroll
+                    for (int k = 0; k < RD; ++k) {
+                        const float a = fabsf(x[k]);
+                        m2 = fminf(m2, fmaxf(m1, a));
+                        m1 = fminf(m1, a);
+                        nb ^= __float_as_uint(x[k]);
+                    }
+                    nb &= 0x80000000u;
                     // D_{i->j} for every edge of the row: alpha * (minimum over the
-                    // others), sign = s'_i xor parity of the others' signs
+                    // others), which is m2 for an edge holding the minimum and m1
+                    // otherwise; sign = s'_i xor parity of the others' signs
                     const float d1 = __fmul_rn(alpha, m1), d2 = __fmul_rn(alpha, m2);
                     float2* dr = reinterpret_cast<float2*>(st.D + RD * i);
 #pragma unroll
@@ -352,8 +358,8 @@ struct SmallEngine {
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             const int k = 2 * h + u;
-                            const float d = (k == pos) ? d2 : d1;
-                            dd[u] = (neg ^ negs[k]) ? -d : d;
+                            const float d = (fabsf(x[k]) == m1) ? d2 : d1;
+                            dd[u] = __uint_as_float(__float_as_uint(d) ^ ((nb ^ __float_as_uint(x[k])) & 0x80000000u));
                         }
                         dr[h] = make_float2(dd[0], dd[1]);
                     }
