@@ -197,8 +197,13 @@ int bsd_profile_enable(bsd_decoder *dec, int enable);
  * of each kernel kind (index 0: seed BP, 1: expand + masked BP of a round,
  * 2: per-shot selection of a round), and the BP iterations executed on the
  * device (index 0: seed candidates, 1: round candidates, counting children
- * evaluated after a shot's first success).  Any pointer may be NULL. */
-int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2]);
+ * evaluated after a shot's first success), and the number of kernels of this
+ * library that ran for this decoder (counted on the device, with or without
+ * timing enabled).  While timing is enabled the kernels are launched one by
+ * one so that events can bracket them; otherwise each chunk runs as one CUDA
+ * graph.  Any pointer may be NULL. */
+int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2],
+                     uint64_t *kernel_launches);
 
 /* Static text for a return code. */
 const char *bsd_error_string(int code);

@@ -71,7 +71,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_get_info.argtypes = [P] + [C.POINTER(C.c_int32)] * 4 + [C.POINTER(C.c_int64)] * 2
     lib.bsd_decode_noalloc.argtypes = [P, P, C.c_int64, P, P, P, P, P]
     lib.bsd_profile_enable.argtypes = [P, C.c_int]
-    lib.bsd_profile_read.argtypes = [P, P, P, P]
+    lib.bsd_profile_read.argtypes = [P, P, P, P, P]
     lib.bsd_error_string.argtypes = [C.c_int]
     lib.bsd_error_string.restype = C.c_char_p
     lib.bsd_destroy.argtypes = [P]
@@ -156,9 +156,10 @@ def bsd_profile_read(dec) -> dict:
     ms = np.zeros(3, np.float64)
     ln = np.zeros(3, np.int64)
     it = np.zeros(2, np.uint64)
+    kl = np.zeros(1, np.uint64)
     p = lambda a: a.ctypes.data_as(C.c_void_p)
-    check(load().bsd_profile_read(dec, p(ms), p(ln), p(it)), "bsd_profile_read")
-    return dict(ms=ms, launches=ln, exec_iters=it)
+    check(load().bsd_profile_read(dec, p(ms), p(ln), p(it), p(kl)), "bsd_profile_read")
+    return dict(ms=ms, launches=ln, exec_iters=it, kernel_launches=int(kl[0]))
 
 
 def bsd_destroy(dec) -> None:

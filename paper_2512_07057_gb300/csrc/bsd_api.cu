@@ -33,7 +33,8 @@ struct bsd_decoder {
     void* io_mem = nullptr;        // device staging for bsd_decode_host
     size_t io_bytes = 0;
     cudaStream_t last_stream = nullptr;
-    unsigned long long* d_stats = nullptr;   // executed BP iterations (seed, rounds)
+    void* graph = nullptr;                   // instantiated per-chunk graph (or null)
+    int* h_nactive = nullptr;                // pinned: active entries of a chunk (launch path without graph)
     // opt-in kernel timing
     bool prof = false;
     cudaStream_t prof_stream = nullptr;
@@ -155,7 +156,8 @@ void bsd_destroy(bsd_decoder* dec)
         if (dec->graph_mem) cudaFree(dec->graph_mem);
         if (dec->work_mem) cudaFree(dec->work_mem);
         if (dec->io_mem) cudaFree(dec->io_mem);
-        if (dec->d_stats) cudaFree(dec->d_stats);
+        if (dec->graph) destroy_graph(dec->graph);
+        if (dec->h_nactive) cudaFreeHost(dec->h_nactive);
         for (cudaEvent_t e : dec->ev) cudaEventDestroy(e);
     }
     delete dec;
@@ -292,61 +294,41 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     rc = configure_kernels(g, cfg, device, &dec->ls);
     if (rc) { bsd_destroy(dec); return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA; }
 
-    // ---- workspace: two banks of 2w child slots per shot of a chunk
+    // ---- workspace: a seed store of S shots and a beam window of A active
+    // entries (two banks of 2w child slots each), about 1 : 4 in bytes
     const int W2 = 2 * cfg.w;
     const int SB = WM + 3 * WN;
     const int NR = cfg.num_results;
-    const size_t per_shot = 2ull * W2 * (sizeof(float) * Epad + sizeof(uint32_t) * SB + sizeof(SlotMeta)) +
-                            sizeof(int) * 3 + cfg.w + sizeof(unsigned long long) +
-                            (size_t)NR * (sizeof(uint32_t) * WN + sizeof(long long) + sizeof(int)) + sizeof(int) +
-                            2ull * W2 * sizeof(int2);
+    const double seed_b = sizeof(float) * (double)Epad + sizeof(uint32_t) * (double)SB + sizeof(SlotMeta) + 4.0;
+    const double win_b = 2.0 * W2 * (sizeof(float) * (double)Epad + sizeof(uint32_t) * (double)SB + sizeof(SlotMeta)) +
+                         12.0 + cfg.w + 8.0 + NR * (4.0 * WN + 12.0) + 4.0 + 2.0 * W2 * sizeof(int2);
     const long long budget = params->workspace_bytes > 0 ? params->workspace_bytes : (4ll << 30);
-    long long C = (long long)(budget / (long long)(per_shot + 64));
-    if (C > (1ll << 22)) C = 1ll << 22;
-    if (C < 1) C = 1;
-    dec->ctr_bytes = align256(sizeof(Counters) + sizeof(int) * 3 * (size_t)(cfg.max_rounds + 2));
+    long long A = (long long)(0.8 * (double)budget / win_b);
+    if (A < 1) A = 1;
+    long long S = (long long)(((double)budget - (double)A * win_b) / seed_b);
+    if (S > (1ll << 22)) S = 1ll << 22;
+    if (S < A) S = A;
+    if (A > (1ll << 22)) A = 1ll << 22;
     for (;;) {
-        size_t wb = dec->ctr_bytes;
-        wb += align256(sizeof(float) * 2ull * C * W2 * Epad);
-        wb += align256(sizeof(uint32_t) * 2ull * C * W2 * SB);
-        wb += align256(sizeof(SlotMeta) * 2ull * C * W2);
-        wb += 3 * align256(sizeof(int) * C) + align256((size_t)C * cfg.w) + align256(sizeof(unsigned long long) * C);
-        wb += align256(sizeof(uint32_t) * (size_t)C * NR * WN) + align256(sizeof(long long) * (size_t)C * NR) +
-              align256(sizeof(int) * (size_t)C * NR) + align256(sizeof(int) * C);
-        wb += align256(sizeof(int2) * 2ull * C * W2);
+        const size_t wb = work_layout(g, cfg, S, A, nullptr, nullptr);
         if (cudaMalloc(&dec->work_mem, wb) == cudaSuccess) { dec->work_bytes = wb; break; }
         cudaGetLastError();
         dec->work_mem = nullptr;
-        if (C == 1) { bsd_destroy(dec); return BSD_ERR_OOM; }
-        C = C / 2;
+        if (S == 1 && A == 1) { bsd_destroy(dec); return BSD_ERR_OOM; }
+        S = S > 1 ? S / 2 : 1;
+        A = A > 1 ? A / 2 : 1;
     }
     Work& w = dec->w;
-    char* q = (char*)dec->work_mem;
-    w.ctr = reinterpret_cast<Counters*>(q);
-    w.round_ctr = reinterpret_cast<int*>(q + sizeof(Counters));
-    q += dec->ctr_bytes;
-    w.C = C;
-    w.SB = SB;
-    w.slotE = carve<float>(q, 2ull * C * W2 * Epad);
-    w.slotBits = carve<uint32_t>(q, 2ull * C * W2 * SB);
-    w.slotMeta = carve<SlotMeta>(q, 2ull * C * W2);
-    w.shot_of = carve<int>(q, C);
-    w.set_size = carve<int>(q, C);
-    w.done = carve<int>(q, C);
-    w.set_idx = carve<uint8_t>(q, (size_t)C * cfg.w);
-    w.iters_acc = carve<unsigned long long>(q, C);
-    w.res_bits = carve<uint32_t>(q, (size_t)C * NR * WN);
-    w.res_w = carve<long long>(q, (size_t)C * NR);
-    w.res_origin = carve<int>(q, (size_t)C * NR);
-    w.res_n = carve<int>(q, C);
-    w.items = carve<int2>(q, 2ull * C * W2);
-    if (cudaMemset(dec->work_mem, 0, dec->ctr_bytes) != cudaSuccess) { bsd_destroy(dec); return BSD_ERR_CUDA; }
-    if (cudaMalloc(&dec->d_stats, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(dec->d_stats, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    work_layout(g, cfg, S, A, (char*)dec->work_mem, &w);
+    dec->ctr_bytes = work_head_bytes(cfg);
+    if (cudaMemset(dec->work_mem, 0, dec->ctr_bytes) != cudaSuccess ||
+        cudaMallocHost(&dec->h_nactive, sizeof(int)) != cudaSuccess) {
         bsd_destroy(dec);
-        return BSD_ERR_OOM;
+        return BSD_ERR_CUDA;
     }
-    w.stats = dec->d_stats;
+    // the per-chunk graph: seed kernel + WHILE over beam passes; without it
+    // decoding falls back to plain launches
+    if (build_graph(g, cfg, w, dec->ls, &dec->graph) != 0) dec->graph = nullptr;
     *out = dec;
     return BSD_OK;
 }
@@ -399,10 +381,10 @@ static void prof_collect(bsd_decoder* d)
 static int decode_impl(bsd_decoder* dec, const uint32_t* d_synd, long long base, long long n, const Outputs& o,
                        cudaStream_t s)
 {
-    if (cudaMemsetAsync(dec->work_mem, 0, dec->ctr_bytes, s) != cudaSuccess) return BSD_ERR_CUDA;
     LaunchHooks hk{prof_before, prof_after, dec};
     dec->prof_stream = s;
-    return launch_chunk(dec->g, dec->cfg, dec->w, dec->ls, d_synd, base, n, o, s, dec->prof ? &hk : nullptr)
+    return launch_chunk(dec->g, dec->cfg, dec->w, dec->ls, d_synd, base, n, o, s, dec->prof ? &hk : nullptr,
+                        dec->prof ? nullptr : dec->graph, dec->h_nactive)
                ? BSD_ERR_CUDA
                : BSD_OK;
 }
@@ -418,8 +400,8 @@ int bsd_decode(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, uint32_
     cudaStream_t s = (cudaStream_t)cuda_stream;
     dec->last_stream = s;
     Outputs o{d_corrections, dec->g.K > 0 ? d_obs_flips : nullptr, d_status, d_iters};
-    for (long long base = 0; base < B; base += dec->w.C) {
-        const long long n = (B - base) < dec->w.C ? (B - base) : dec->w.C;
+    for (long long base = 0; base < B; base += dec->w.S) {
+        const long long n = (B - base) < dec->w.S ? (B - base) : dec->w.S;
         const int rc = decode_impl(dec, d_syndromes, base, n, o, s);
         if (rc) return rc;
     }
@@ -437,7 +419,7 @@ int bsd_decode_host(bsd_decoder* dec, const uint32_t* h_syndromes, int64_t B, ui
     cudaStream_t s = (cudaStream_t)cuda_stream;
     dec->last_stream = s;
     const DevGraph& g = dec->g;
-    const long long C = dec->w.C;
+    const long long C = dec->w.S;
     const size_t need = align256(sizeof(uint32_t) * C * g.WM) + align256(sizeof(uint32_t) * C * g.WN) +
                         align256(sizeof(uint32_t) * C * (g.WK > 0 ? g.WK : 1)) + 2 * align256(sizeof(uint32_t) * C);
     if (dec->io_bytes < need) {
@@ -510,16 +492,17 @@ int bsd_profile_enable(bsd_decoder* dec, int enable)
     return BSD_OK;
 }
 
-int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2])
+int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2],
+                     uint64_t* kernel_launches)
 {
     if (!dec) return BSD_ERR_INVALID_ARG;
     DeviceGuard dg(dec->device);
     if (!dg.ok) return BSD_ERR_CUDA;
     if (cudaStreamSynchronize(dec->last_stream) != cudaSuccess) return BSD_ERR_CUDA;
     prof_collect(dec);
-    unsigned long long st[2] = {0, 0};
-    if (cudaMemcpy(st, dec->d_stats, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemset(dec->d_stats, 0, sizeof(st)) != cudaSuccess)
+    unsigned long long st[4] = {0, 0, 0, 0};
+    if (cudaMemcpy(st, dec->w.stats, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(dec->w.stats, 0, sizeof(st)) != cudaSuccess)
         return BSD_ERR_CUDA;
     for (int k = 0; k < 3; ++k) {
         if (ms) ms[k] = dec->ms[k];
@@ -528,6 +511,7 @@ int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64
         dec->launches[k] = 0;
     }
     if (exec_iters) { exec_iters[0] = st[0]; exec_iters[1] = st[1]; }
+    if (kernel_launches) *kernel_launches = st[2];
     return BSD_OK;
 }
 
@@ -557,7 +541,7 @@ int bsd_get_info(const bsd_decoder* dec, int32_t* M, int32_t* N, int32_t* K, int
     if (N) *N = dec->g.N;
     if (K) *K = dec->g.K;
     if (n_edges) *n_edges = dec->g.E;
-    if (chunk_shots) *chunk_shots = dec->w.C;
+    if (chunk_shots) *chunk_shots = dec->w.S;
     if (workspace_bytes) *workspace_bytes = (int64_t)dec->work_bytes;
     return BSD_OK;
 }

@@ -11,11 +11,14 @@
 //   acol[N][WK]           column j of A as a K-bit set (observable flips)
 //   lamq[N]               Lambda_j on the 2^-16 fixed-point grid (weights)
 //
-// Beam state per chunk of C shots (workspace):
-//   two banks of 2w child slots per active shot; round r writes bank r % 2
-//   and reads its parents from bank (r - 1) % 2 through set_idx, so surviving
-//   paths are never copied.  A slot holds the edge-message snapshot (Epad
-//   floats), the bit vectors s', mask, vals, e^ and a SlotMeta record.
+// Workspace (one decoder):
+//   seed store, S entries: the snapshot (E, s', mask, vals, e^, record) of
+//   every shot of a chunk of S shots whose seed BP did not end the search;
+//   beam window, A entries: the active shots of the current beam pass
+//   (entries pass*A .. pass*A + A - 1 of the seed store), with two banks of
+//   2w child slots each; round r writes bank r % 2 and reads its parents from
+//   bank (r - 1) % 2 (or the seed store for r = 1) through a rank -> slot
+//   table, so surviving paths are never copied.
 #pragma once
 #include <cstdint>
 
@@ -56,42 +59,68 @@ struct SlotMeta {
     int pad;
 };
 
-// per-chunk counters (zeroed before each chunk)
-struct Counters {
-    int claim_seed;
-    int n_active;
-    int err;
-    int pad;
-    // followed by 3 * (max_rounds + 2) ints: claim_round[r], claim_select[r], work_count[r]
-};
-
-struct Work {
-    long long C;           // chunk capacity in shots
-    int SB;                // words per slot bit record: sp[WM] mask[WN] vals[WN] ehat[WN]
-    float* slotE;          // [2][C][2w][Epad]
-    uint32_t* slotBits;    // [2][C][2w][SB]
-    SlotMeta* slotMeta;    // [2][C][2w]
-    int* shot_of;          // [C] chunk-local shot of an active entry
-    int* set_size;         // [C]
-    uint8_t* set_idx;      // [C][w] child index (in the parent bank) of the path of rank k
-    unsigned long long* iters_acc;   // [C]
-    int* done;             // [C]
-    uint32_t* res_bits;    // [C][num_results][WN]
-    long long* res_w;      // [C][num_results]
-    int* res_origin;       // [C][num_results]: 0 = seed, 1 = masked BP round
-    int* res_n;            // [C]
-    int2* items;           // [2][C * 2w] (active entry, child index)
-    Counters* ctr;
-    int* round_ctr;        // 3 * (max_rounds + 2) ints after ctr
-    unsigned long long* stats;   // [2] executed BP iterations: seed, beam rounds (not reset per chunk)
-};
-
 struct Outputs {
     uint32_t* corr;        // [B][WN]
     uint32_t* obs;         // [B][WK] (may be null when K = 0)
     uint32_t* status;      // [B]
     uint32_t* iters;       // [B] or null
 };
+
+// device-resident description of the chunk being decoded: kernels read their
+// buffers from here, so one instantiated CUDA graph serves every call
+struct RunDesc {
+    const uint32_t* synd;
+    Outputs out;
+    long long chunk_base;  // index of the chunk's first shot in the caller's batch
+    long long chunk_n;     // shots in the chunk
+    int pass;              // current beam pass
+    int pad;
+};
+
+// per-chunk counters (reset by k_begin_chunk)
+struct Counters {
+    int claim_seed;
+    int n_active;          // seed-store entries written by k_seed
+    int err;
+    int pad;
+    // followed by 3 * (max_rounds + 2) ints for the current pass:
+    // claim_round[r], claim_select[r], work_count[r] (reset by k_pass_end)
+};
+
+struct Work {
+    long long S;           // shots per chunk = seed-store entries
+    long long A;           // active entries per beam pass
+    int SB;                // words per slot bit record: sp[WM] mask[WN] vals[WN] ehat[WN]
+    // seed store [S]
+    float* seedE;          // [S][Epad]
+    uint32_t* seedBits;    // [S][SB]
+    SlotMeta* seedMeta;    // [S]
+    int* seed_shot;        // [S] chunk-local shot of a seed-store entry
+    // beam window [A]
+    float* slotE;          // [2][A][2w][Epad]
+    uint32_t* slotBits;    // [2][A][2w][SB]
+    SlotMeta* slotMeta;    // [2][A][2w]
+    int* shot_of;          // [A] chunk-local shot of a window entry
+    int* set_size;         // [A]
+    uint8_t* set_idx;      // [A][w] child index (in the parent bank) of the path of rank k
+    unsigned long long* iters_acc;   // [A]
+    int* done;             // [A]
+    uint32_t* res_bits;    // [A][num_results][WN]
+    long long* res_w;      // [A][num_results]
+    int* res_origin;       // [A][num_results]: 0 = seed, 1 = masked BP round
+    int* res_n;            // [A]
+    int2* items;           // [2][A * 2w] (window entry, child index) for rounds >= 2
+    Counters* ctr;
+    int* round_ctr;        // 3 * (max_rounds + 2) ints after ctr
+    RunDesc* desc;
+    unsigned long long* stats;   // [4]: executed BP iterations (seed, rounds), kernel launches; never reset by a chunk
+};
+
+// workspace layout for S seed entries and A window entries starting at base
+// (base may be null to size it); returns the bytes used.  The counters and the
+// run descriptor come first, in the first head_bytes(cfg) bytes.
+size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w);
+size_t work_head_bytes(const DecCfg& cfg);
 
 // host-side launch helpers (bsd_kernels.cu)
 struct LaunchShape {
@@ -110,9 +139,17 @@ struct LaunchHooks {
 };
 
 int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls);
+
+// decode one chunk: reset counters and set the run descriptor, then the seed
+// kernel and as many beam passes as the chunk has active windows.  With a
+// graph (built by build_graph) the passes run under a conditional WHILE node;
+// without one, n_active is read back after the seed kernel.
 int launch_chunk(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls,
                  const uint32_t* synd, long long chunk_base, long long chunk_n, const Outputs& out,
-                 void* stream, const LaunchHooks* hooks);
+                 void* stream, const LaunchHooks* hooks, void* graph_exec, int* host_n_active);
+// build and instantiate the per-chunk graph (seed kernel + WHILE over beam passes)
+int build_graph(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls, void** graph_exec);
+void destroy_graph(void* graph_exec);
 int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, const uint32_t* synd,
                   long long B, int T, float* llr, float* sum_llr, void* stream);
 

@@ -277,7 +277,6 @@ template <int CPL, int RPL, int RD>
 struct SmallEngine {
     static constexpr int kMinBlocks = 2;   // at most 128 registers: two 8-warp blocks per SM
     uint32_t ci[CPL][3];   // (CSR edge id << 16) | row, for column lane + 32 c
-    float lam[CPL];
     float sum[CPL];
     uint32_t mb;           // bit c: column lane + 32 c is masked or beyond N
 
@@ -287,14 +286,13 @@ struct SmallEngine {
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             const int j = lane + 32 * c;
-            lam[c] = 0.f;
             ci[c][0] = ci[c][1] = ci[c][2] = 0u;
             if (j < g.N) {
                 const int kb = __ldg(g.col_ptr + j);
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
                     ci[c][k] = ((uint32_t)__ldg(g.col_edge + kb + k) << 16) | (uint32_t)__ldg(g.col_row + kb + k);
-                lam[c] = __ldg(g.lam + j);
+
             }
         }
     }
@@ -378,7 +376,7 @@ struct SmallEngine {
                         ed[k] = (int)(ci[c][k] >> 16);
                         v[k] = st.D[ed[k]];
                     }
-                    const float l = lam[c];
+                    const float l = __ldg(g.lam + lane + 32 * c);
                     // Eq. 2: each message leaves its own detector out; the other
                     // two are added in ascending order
                     const float e0 = __fadd_rn(__fadd_rn(l, fminf(v[1], v[2])), fmaxf(v[1], v[2]));
@@ -479,32 +477,111 @@ __device__ inline long long vector_weight(const DevGraph& g, const uint32_t* bit
 
 __device__ inline int* round_ctr(const Work& w, int r) { return w.round_ctr + 3 * r; }
 
+// slot of child c of window entry a in bank `bank`
 __device__ inline size_t slot_index(const Work& w, int bank, int a, int c, int W2)
 {
-    return ((size_t)bank * (size_t)w.C + (size_t)a) * (size_t)W2 + (size_t)c;
+    return ((size_t)bank * (size_t)w.A + (size_t)a) * (size_t)W2 + (size_t)c;
+}
+
+// the parent of the rank-k path of window entry a in round r: the seed-store
+// entry for r = 1, else the slot of the previous round that won rank k
+struct SlotRef {
+    const float* E;
+    const uint32_t* bits;
+    const SlotMeta* meta;
+};
+
+__device__ inline SlotRef parent_ref(const DevGraph& g, const DecCfg& cfg, const Work& w, int r, long long pbase,
+                                     int a, int k)
+{
+    SlotRef s;
+    if (r == 1) {
+        const size_t e = (size_t)(pbase + a);
+        s.E = w.seedE + e * (size_t)g.Epad;
+        s.bits = w.seedBits + e * (size_t)w.SB;
+        s.meta = w.seedMeta + e;
+    } else {
+        const size_t e = slot_index(w, (r - 1) & 1, a, w.set_idx[(size_t)a * cfg.w + k], 2 * cfg.w);
+        s.E = w.slotE + e * (size_t)g.Epad;
+        s.bits = w.slotBits + e * (size_t)w.SB;
+        s.meta = w.slotMeta + e;
+    }
+    return s;
+}
+
+// entries of the current pass's window: [pbase, pbase + count)
+__device__ inline int window(const Work& w, long long* pbase)
+{
+    const int pass = *((volatile int*)&w.desc->pass);
+    const long long n_active = *((volatile int*)&w.ctr->n_active);
+    *pbase = (long long)pass * w.A;
+    long long cnt = n_active - *pbase;
+    if (cnt > w.A) cnt = w.A;
+    return cnt > 0 ? (int)cnt : 0;
+}
+
+// ----------------------------------------------------------------------------
+// chunk set-up and pass advance (one warp each)
+// ----------------------------------------------------------------------------
+__device__ inline void count_launch(const Work& w)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.stats[2], 1ull);
+}
+
+__global__ void k_begin_chunk(Work w, int n_round_ints, const uint32_t* synd, Outputs out, long long base,
+                              long long n)
+{
+    count_launch(w);
+    for (int q = threadIdx.x; q < n_round_ints; q += blockDim.x) w.round_ctr[q] = 0;
+    if (threadIdx.x == 0) {
+        w.ctr->claim_seed = 0;
+        w.ctr->n_active = 0;
+        w.ctr->err = 0;
+        RunDesc d;
+        d.synd = synd;
+        d.out = out;
+        d.chunk_base = base;
+        d.chunk_n = n;
+        d.pass = 0;
+        d.pad = 0;
+        *w.desc = d;
+    }
+}
+
+// after the last round of a pass: move to the next window, reset the per-pass
+// counters and, under a graph, set the WHILE condition (another window left)
+__global__ void k_pass_end(Work w, int n_round_ints, cudaGraphConditionalHandle cond, int use_cond)
+{
+    count_launch(w);
+    for (int q = threadIdx.x; q < n_round_ints; q += blockDim.x) w.round_ctr[q] = 0;
+    if (threadIdx.x == 0) {
+        const int pass = w.desc->pass + 1;
+        w.desc->pass = pass;
+        if (use_cond) cudaGraphSetConditional(cond, ((long long)pass * w.A < (long long)w.ctr->n_active) ? 1u : 0u);
+    }
 }
 
 // ----------------------------------------------------------------------------
 // seed BP
 // ----------------------------------------------------------------------------
 template <class Eng>
-__global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCfg cfg, Work w, const uint32_t* __restrict__ synd,
-                                              long long base, long long n, Outputs out)
+__global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCfg cfg, Work w)
 {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
-    const int W2 = 2 * cfg.w;
+    const RunDesc* dp = w.desc;                  // read fields when needed (keeps registers free)
+    count_launch(w);
     Eng eng;
     eng.load_graph(g);
     for (;;) {
         int b = 0;
         if (lane == 0) b = atomicAdd(&w.ctr->claim_seed, 1);
         b = __shfl_sync(FULLMASK, b, 0);
-        if (b >= n) break;
-        const long long gb = base + b;
-        const uint32_t* s = synd + gb * g.WM;
+        if (b >= dp->chunk_n) break;
+        const long long gb = dp->chunk_base + b;
+        const uint32_t* s = dp->synd + gb * g.WM;
         uint32_t nz = 0;
         for (int q = lane; q < g.WM; q += 32) {
             const uint32_t x = s[q];
@@ -516,7 +593,7 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCf
         // s = 0 with every Lambda_j > 0: D > 0 at t = 1, so e^(1) = 0 and the
         // seed converges after one iteration (exact, no BP needed)
         if (!__any_sync(FULLMASK, nz != 0u) && cfg.num_results == 1 && g.all_lam_pos) {
-            finalize_shot(g, out, gb, st.ehat, ST_SEED, 1ull);
+            finalize_shot(g, dp->out, gb, st.ehat, ST_SEED, 1ull);
             __syncwarp();
             continue;
         }
@@ -530,7 +607,7 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCf
         if (lane == 0) atomicAdd(&w.stats[0], (unsigned long long)it);
         __syncwarp();
         if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
-            finalize_shot(g, out, gb, st.ehat, succ ? ST_SEED : ST_FAILED, (unsigned long long)it);
+            finalize_shot(g, dp->out, gb, st.ehat, succ ? ST_SEED : ST_FAILED, (unsigned long long)it);
             __syncwarp();
             continue;
         }
@@ -540,43 +617,21 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCf
         int a = 0;
         if (lane == 0) a = atomicAdd(&w.ctr->n_active, 1);
         a = __shfl_sync(FULLMASK, a, 0);
-        // the seed path: bank 0, child index 0
-        const size_t slot = slot_index(w, 0, a, 0, W2);
-        float4* dE = reinterpret_cast<float4*>(w.slotE + slot * (size_t)g.Epad);
+        // the seed path (Alg. 3): snapshot, s' = s, no fixed node, e^, next_pos
+        float4* dE = reinterpret_cast<float4*>(w.seedE + (size_t)a * (size_t)g.Epad);
         for (int q = lane; q < g.Epad / 4; q += 32) dE[q] = dst[q];
-        uint32_t* bits = w.slotBits + slot * (size_t)w.SB;
+        uint32_t* bits = w.seedBits + (size_t)a * (size_t)w.SB;
         for (int q = lane; q < g.WM; q += 32) bits[q] = st.sp[q];
         for (int q = lane; q < g.WN; q += 32) {
             bits[g.WM + q] = 0u;
             bits[g.WM + g.WN + q] = 0u;
             bits[g.WM + 2 * g.WN + q] = st.ehat[q];
         }
-        long long W = 0;
-        if (succ) {                       // num_results > 1: the seed result opens `results`
-            uint32_t* rb = w.res_bits + (size_t)a * cfg.num_results * g.WN;
-            for (int q = lane; q < g.WN; q += 32) rb[q] = st.ehat[q];
-            W = vector_weight(g, st.ehat);
-        }
         if (lane == 0) {
             SlotMeta m;
             m.S = 0; m.iters = it; m.next_pos = np; m.success = succ; m.pad = 0;
-            w.slotMeta[slot] = m;
-            w.shot_of[a] = b;
-            w.set_size[a] = 1;
-            w.set_idx[(size_t)a * cfg.w] = 0;
-            w.iters_acc[a] = (unsigned long long)it;
-            w.done[a] = 0;
-            w.res_n[a] = succ ? 1 : 0;
-            if (succ) {
-                w.res_w[(size_t)a * cfg.num_results] = W;
-                w.res_origin[(size_t)a * cfg.num_results] = 0;
-            }
-            if (np >= 0) {
-                const int wb = atomicAdd(&round_ctr(w, 1)[2], 2);
-                int2* items = w.items + (size_t)1 * (size_t)w.C * (size_t)W2;
-                items[wb] = make_int2(a, 0);
-                items[wb + 1] = make_int2(a, 1);
-            }
+            w.seedMeta[a] = m;
+            w.seed_shot[a] = b;
         }
         __syncwarp();
     }
@@ -589,38 +644,42 @@ template <class Eng>
 __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecCfg cfg, Work w, int r)
 {
     extern __shared__ __align__(16) char smem[];
+    count_launch(w);
+    long long pbase;
+    const int cnt = window(w, &pbase);
+    if (cnt == 0) return;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
     const int W2 = 2 * cfg.w;
+    int* rc = round_ctr(w, r);
+    // round 1: two children of every window entry; later rounds: the work list
+    const int nitems = (r == 1) ? 2 * cnt : *((volatile int*)(rc + 2));
+    const int2* items = w.items + (size_t)(r & 1) * (size_t)w.A * (size_t)W2;
+    const int cb = r & 1;
     Eng eng;
     eng.load_graph(g);
-    int* rc = round_ctr(w, r);
-    const int nitems = *((volatile int*)(rc + 2));
-    const int2* items = w.items + (size_t)(r & 1) * (size_t)w.C * (size_t)W2;
-    const int pb = (r - 1) & 1, cb = r & 1;
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(&rc[0], 1);
         it = __shfl_sync(FULLMASK, it, 0);
         if (it >= nitems) break;
-        const int2 item = items[it];
+        const int2 item = (r == 1) ? make_int2(it >> 1, it & 1) : items[it];
         const int a = item.x, c = item.y;
         const int k = c >> 1, v = c & 1;
-        const int pc = w.set_idx[(size_t)a * cfg.w + k];
-        const size_t pslot = slot_index(w, pb, a, pc, W2);
+        const SlotRef par = parent_ref(g, cfg, w, r, pbase, a, k);
+        const int pos = par.meta->next_pos;
+        if (pos < 0) continue;                     // a path with no unmasked node has no children
         const size_t cslot = slot_index(w, cb, a, c, W2);
-        const int pos = w.slotMeta[pslot].next_pos;
-        const uint32_t* pbits = w.slotBits + pslot * (size_t)w.SB;
         // s' of the child: flip the detectors of pos when it is fixed to 1
         for (int q = lane; q < g.WM; q += 32) {
-            uint32_t x = pbits[q];
+            uint32_t x = par.bits[q];
             if (v) x ^= __ldg(g.hcol + (size_t)pos * g.WM + q);
             st.sp[q] = x;
         }
         for (int q = lane; q < g.WN; q += 32) {
-            uint32_t m = pbits[g.WM + q];
-            uint32_t vv = pbits[g.WM + g.WN + q];
+            uint32_t m = par.bits[g.WM + q];
+            uint32_t vv = par.bits[g.WM + g.WN + q];
             if (q == (pos >> 5)) {
                 m |= 1u << (pos & 31);
                 if (v) vv |= 1u << (pos & 31);
@@ -629,7 +688,7 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecC
             st.vals[q] = vv;
         }
         // warm start from the parent's snapshot
-        const float4* pE = reinterpret_cast<const float4*>(w.slotE + pslot * (size_t)g.Epad);
+        const float4* pE = reinterpret_cast<const float4*>(par.E);
         float4* sE = reinterpret_cast<float4*>(st.E);
         for (int q = lane; q < g.Epad / 4; q += 32) sE[q] = pE[q];
         eng.clear_sums(g, st);
@@ -685,29 +744,56 @@ __device__ void finalize_results(const DevGraph& g, const DecCfg& cfg, const Wor
     finalize_shot(g, out, gb, w.res_bits + ((size_t)a * cfg.num_results + bi) * g.WN, st, total);
 }
 
-__global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, int r, long long base, Outputs out)
+__global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, int r)
 {
     extern __shared__ __align__(16) char smem[];
+    count_launch(w);
+    long long pbase;
+    const int cnt = window(w, &pbase);
+    if (cnt == 0) return;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     SelScratch* sc = reinterpret_cast<SelScratch*>(smem) + wid;
     const int W2 = 2 * cfg.w;
-    const int n_active = *((volatile int*)&w.ctr->n_active);
+    const RunDesc d = *w.desc;
     int* rc = round_ctr(w, r);
-    const int pb = (r - 1) & 1, cb = r & 1;
+    const int cb = r & 1;
     for (;;) {
         int a = 0;
         if (lane == 0) a = atomicAdd(&rc[1], 1);
         a = __shfl_sync(FULLMASK, a, 0);
-        if (a >= n_active) break;
-        if (w.done[a]) continue;
-        const long long gb = base + w.shot_of[a];
+        if (a >= cnt) break;
+        if (r == 1) {
+            // a new window entry: the seed path is its only path (Alg. 3)
+            const size_t e = (size_t)(pbase + a);
+            const SlotMeta sm = w.seedMeta[e];
+            if (sm.success) {                  // num_results > 1: the seed result opens `results`
+                const uint32_t* eb = w.seedBits + e * (size_t)w.SB + g.WM + 2 * g.WN;
+                uint32_t* rb = w.res_bits + (size_t)a * cfg.num_results * g.WN;
+                for (int q = lane; q < g.WN; q += 32) rb[q] = eb[q];
+                const long long W = vector_weight(g, eb);
+                if (lane == 0) {
+                    w.res_w[(size_t)a * cfg.num_results] = W;
+                    w.res_origin[(size_t)a * cfg.num_results] = 0;
+                }
+            }
+            if (lane == 0) {
+                w.shot_of[a] = w.seed_shot[e];
+                w.set_size[a] = 1;
+                w.iters_acc[a] = (unsigned long long)sm.iters;
+                w.done[a] = 0;
+                w.res_n[a] = sm.success ? 1 : 0;
+            }
+            __syncwarp();
+        } else if (w.done[a]) {
+            continue;
+        }
+        const long long gb = d.chunk_base + w.shot_of[a];
         const int npar = w.set_size[a];
         const int nch = 2 * npar;
         // gather the children of this round in canonical order c = 2 * rank + val
         for (int c = lane; c < nch; c += 32) {
-            const int pc = w.set_idx[(size_t)a * cfg.w + (c >> 1)];
-            const int pnp = w.slotMeta[slot_index(w, pb, a, pc, W2)].next_pos;
+            const int pnp = parent_ref(g, cfg, w, r, pbase, a, c >> 1).meta->next_pos;
             int fl = 0, it = 0;
             double scv = 0.0;
             if (pnp >= 0) {
@@ -737,7 +823,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULLMASK, sum, o);
                 const uint32_t* eb = w.slotBits + slot_index(w, cb, a, first, W2) * (size_t)w.SB + g.WM + 2 * g.WN;
-                finalize_shot(g, out, gb, eb, ST_BEAM, acc + sum);
+                finalize_shot(g, d.out, gb, eb, ST_BEAM, acc + sum);
                 done = true;
             }
         } else {
@@ -769,7 +855,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                     }
                     __syncwarp();
                     if (nres + 1 >= cfg.num_results) {
-                        finalize_results(g, cfg, w, out, a, gb, acc + sum);
+                        finalize_results(g, cfg, w, d.out, a, gb, acc + sum);
                         done = true;
                     }
                 }
@@ -806,7 +892,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
             }
             if (r >= cfg.max_rounds || nex == 0) {
                 if (cfg.num_results > 1 && w.res_n[a] > 0) {
-                    finalize_results(g, cfg, w, out, a, gb, acc);
+                    finalize_results(g, cfg, w, d.out, a, gb, acc);
                 } else {
                     // no valid solution: the best path of the final set
                     int best = 0x7fffffff;
@@ -819,9 +905,8 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                     if (best != 0x7fffffff)
                         eb = w.slotBits + slot_index(w, cb, a, best, W2) * (size_t)w.SB + g.WM + 2 * g.WN;
                     else
-                        eb = w.slotBits + slot_index(w, pb, a, w.set_idx[(size_t)a * cfg.w], W2) * (size_t)w.SB +
-                             g.WM + 2 * g.WN;
-                    finalize_shot(g, out, gb, eb, ST_FAILED, acc);
+                        eb = parent_ref(g, cfg, w, r, pbase, a, 0).bits + g.WM + 2 * g.WN;
+                    finalize_shot(g, d.out, gb, eb, ST_FAILED, acc);
                 }
                 done = true;
             } else {
@@ -834,12 +919,12 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                         w.set_idx[(size_t)a * cfg.w + myrank[q]] = (uint8_t)(lane + 32 * q);
                 __syncwarp();
                 // children of round r + 1: two per kept path that has a next_pos
-                int cnt = 0;
+                int cntp = 0;
                 for (int k = lane; k < keep; k += 32) {
                     const int c = w.set_idx[(size_t)a * cfg.w + k];
-                    cnt += (w.slotMeta[slot_index(w, cb, a, c, W2)].next_pos >= 0) ? 1 : 0;
+                    cntp += (w.slotMeta[slot_index(w, cb, a, c, W2)].next_pos >= 0) ? 1 : 0;
                 }
-                int tot = cnt;
+                int tot = cntp;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULLMASK, tot, o);
                 int wbase = 0;
@@ -850,7 +935,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                 }
                 wbase = __shfl_sync(FULLMASK, wbase, 0);
                 if (tot > 0 && lane == 0) {
-                    int2* items = w.items + (size_t)((r + 1) & 1) * (size_t)w.C * (size_t)W2;
+                    int2* items = w.items + (size_t)((r + 1) & 1) * (size_t)w.A * (size_t)W2;
                     int o = 0;
                     for (int k = 0; k < keep; ++k) {
                         const int c = w.set_idx[(size_t)a * cfg.w + k];
@@ -990,35 +1075,195 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* l
 template <class Eng>
 static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls,
                           const uint32_t* synd, long long base, long long n, const Outputs& out, cudaStream_t s,
-                          const LaunchHooks* hk)
+                          const LaunchHooks* hk, cudaGraphExec_t gx, int* host_n_active)
 {
     const int threads = 32 * ls.warps_per_block;
+    const int nri = 3 * (cfg.max_rounds + 2);
+    k_begin_chunk<<<1, 128, 0, s>>>(w, nri, synd, out, base, n);
+    if (cudaGetLastError() != cudaSuccess) return -2;
+    if (gx != nullptr) return cudaGraphLaunch(gx, s) == cudaSuccess ? 0 : -2;
     if (hk) hk->before(hk->ctx, 0);
-    k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, synd, base, n, out);
+    k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w);
     if (hk) hk->after(hk->ctx, 0);
     if (cudaGetLastError() != cudaSuccess) return -2;
-    for (int r = 1; r <= cfg.max_rounds; ++r) {
-        if (hk) hk->before(hk->ctx, 1);
-        k_round<Eng><<<ls.grid_round, threads, ls.smem_bp, s>>>(g, cfg, w, r);
-        if (hk) { hk->after(hk->ctx, 1); hk->before(hk->ctx, 2); }
-        k_select<<<ls.grid_select, threads, ls.smem_select, s>>>(g, cfg, w, r, base, out);
-        if (hk) hk->after(hk->ctx, 2);
+    if (cfg.max_rounds == 0) return 0;
+    // without a graph: read the number of active entries back, then run
+    // exactly the passes it needs
+    if (cudaMemcpyAsync(host_n_active, &w.ctr->n_active, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return -2;
+    const long long passes = (*host_n_active + w.A - 1) / w.A;
+    for (long long p = 0; p < passes; ++p) {
+        for (int r = 1; r <= cfg.max_rounds; ++r) {
+            if (hk) hk->before(hk->ctx, 1);
+            k_round<Eng><<<ls.grid_round, threads, ls.smem_bp, s>>>(g, cfg, w, r);
+            if (hk) { hk->after(hk->ctx, 1); hk->before(hk->ctx, 2); }
+            k_select<<<ls.grid_select, threads, ls.smem_select, s>>>(g, cfg, w, r);
+            if (hk) hk->after(hk->ctx, 2);
+        }
+        k_pass_end<<<1, 128, 0, s>>>(w, nri, cudaGraphConditionalHandle{}, 0);
         if (cudaGetLastError() != cudaSuccess) return -2;
     }
     return 0;
 }
 
 int launch_chunk(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls, const uint32_t* synd,
-                 long long base, long long n, const Outputs& out, void* stream, const LaunchHooks* hooks)
+                 long long base, long long n, const Outputs& out, void* stream, const LaunchHooks* hooks,
+                 void* graph_exec, int* host_n_active)
 {
     cudaStream_t s = (cudaStream_t)stream;
+    cudaGraphExec_t gx = (cudaGraphExec_t)graph_exec;
     switch (ls.dv) {
 #define X(id, E) \
-    case id: return launch_chunk_t<E>(g, cfg, w, ls, synd, base, n, out, s, hooks);
+    case id: return launch_chunk_t<E>(g, cfg, w, ls, synd, base, n, out, s, hooks, gx, host_n_active);
         BSD_ENGINES(X)
 #undef X
         default: return -5;
     }
+}
+
+// ---- the per-chunk graph: k_seed, then WHILE(another window) { rounds, k_pass_end }
+static int add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cudaGraphNode_t* dep, void* func, int grid,
+                      int block, size_t smem, void** args)
+{
+    cudaKernelNodeParams p{};
+    p.func = func;
+    p.gridDim = dim3((unsigned)grid);
+    p.blockDim = dim3((unsigned)block);
+    p.sharedMemBytes = (unsigned)smem;
+    p.kernelParams = args;
+    return cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &p) == cudaSuccess ? 0 : -2;
+}
+
+template <class Eng>
+static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0, const LaunchShape& ls,
+                         cudaGraphExec_t* out)
+{
+    DevGraph g = g0;
+    DecCfg cfg = cfg0;
+    Work w = w0;
+    const int threads = 32 * ls.warps_per_block;
+    int nri = 3 * (cfg.max_rounds + 2);
+    cudaGraph_t graph = nullptr;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) return -2;
+    int rc = 0;
+    cudaGraphNode_t seed;
+    void* sargs[] = {&g, &cfg, &w};
+    rc = add_kernel(graph, &seed, nullptr, (void*)k_seed<Eng>, ls.grid_seed, threads, ls.smem_bp, sargs);
+    if (!rc && cfg.max_rounds > 0) {
+        cudaGraphConditionalHandle cond;
+        cudaGraphNode_t cnode;
+        cudaGraphNodeParams cp{};
+        if (cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+            rc = -2;
+        } else {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = cond;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            if (cudaGraphAddNode(&cnode, graph, &seed, nullptr, 1, &cp) != cudaSuccess) rc = -2;
+        }
+        if (!rc) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            cudaGraphNode_t prev = nullptr;
+            // kernel parameters are copied when a node is added
+            for (int r = 1; r <= cfg.max_rounds && !rc; ++r) {
+                cudaGraphNode_t nr, ns;
+                void* rargs[] = {&g, &cfg, &w, &r};
+                rc = add_kernel(body, &nr, prev ? &prev : nullptr, (void*)k_round<Eng>, ls.grid_round, threads,
+                                ls.smem_bp, rargs);
+                if (!rc) rc = add_kernel(body, &ns, &nr, (void*)k_select, ls.grid_select, threads, ls.smem_select, rargs);
+                prev = ns;
+            }
+            if (!rc) {
+                cudaGraphNode_t ne;
+                int use = 1;
+                void* eargs[] = {&w, &nri, &cond, &use};
+                rc = add_kernel(body, &ne, &prev, (void*)k_pass_end, 1, 128, 0, eargs);
+            }
+        }
+    }
+    cudaGraphExec_t gx = nullptr;
+    if (!rc && cudaGraphInstantiate(&gx, graph, 0) != cudaSuccess) rc = -2;
+    cudaGraphDestroy(graph);
+    if (rc) {
+        cudaGetLastError();
+        return rc;
+    }
+    *out = gx;
+    return 0;
+}
+
+int build_graph(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls, void** graph_exec)
+{
+    cudaGraphExec_t gx = nullptr;
+    int rc;
+    switch (ls.dv) {
+#define X(id, E) \
+    case id: rc = build_graph_t<E>(g, cfg, w, ls, &gx); break;
+        BSD_ENGINES(X)
+#undef X
+        default: rc = -5;
+    }
+    *graph_exec = rc ? nullptr : (void*)gx;
+    return rc;
+}
+
+void destroy_graph(void* graph_exec)
+{
+    if (graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)graph_exec);
+}
+
+// ---- workspace layout
+static inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t work_head_bytes(const DecCfg& cfg)
+{
+    return a256(sizeof(Counters) + sizeof(int) * 3 * (size_t)(cfg.max_rounds + 2)) + a256(sizeof(RunDesc)) +
+           a256(4 * sizeof(unsigned long long));
+}
+
+size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w)
+{
+    const size_t W2 = 2 * (size_t)cfg.w;
+    const size_t SB = (size_t)g.WM + 3 * (size_t)g.WN;
+    const size_t NR = (size_t)cfg.num_results;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base ? base + off : nullptr;
+        off += a256(bytes > 0 ? bytes : 1);
+        return p;
+    };
+    char* ctr = take(sizeof(Counters) + sizeof(int) * 3 * (size_t)(cfg.max_rounds + 2));
+    char* desc = take(sizeof(RunDesc));
+    char* stats = take(4 * sizeof(unsigned long long));
+    Work v{};
+    v.S = S;
+    v.A = A;
+    v.SB = (int)SB;
+    v.ctr = reinterpret_cast<Counters*>(ctr);
+    v.round_ctr = ctr ? reinterpret_cast<int*>(ctr + sizeof(Counters)) : nullptr;
+    v.desc = reinterpret_cast<RunDesc*>(desc);
+    v.stats = reinterpret_cast<unsigned long long*>(stats);
+    v.seedE = (float*)take(sizeof(float) * (size_t)S * (size_t)g.Epad);
+    v.seedBits = (uint32_t*)take(sizeof(uint32_t) * (size_t)S * SB);
+    v.seedMeta = (SlotMeta*)take(sizeof(SlotMeta) * (size_t)S);
+    v.seed_shot = (int*)take(sizeof(int) * (size_t)S);
+    v.slotE = (float*)take(sizeof(float) * 2 * (size_t)A * W2 * (size_t)g.Epad);
+    v.slotBits = (uint32_t*)take(sizeof(uint32_t) * 2 * (size_t)A * W2 * SB);
+    v.slotMeta = (SlotMeta*)take(sizeof(SlotMeta) * 2 * (size_t)A * W2);
+    v.shot_of = (int*)take(sizeof(int) * (size_t)A);
+    v.set_size = (int*)take(sizeof(int) * (size_t)A);
+    v.done = (int*)take(sizeof(int) * (size_t)A);
+    v.set_idx = (uint8_t*)take((size_t)A * (size_t)cfg.w);
+    v.iters_acc = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)A);
+    v.res_bits = (uint32_t*)take(sizeof(uint32_t) * (size_t)A * NR * (size_t)g.WN);
+    v.res_w = (long long*)take(sizeof(long long) * (size_t)A * NR);
+    v.res_origin = (int*)take(sizeof(int) * (size_t)A * NR);
+    v.res_n = (int*)take(sizeof(int) * (size_t)A);
+    v.items = (int2*)take(sizeof(int2) * 2 * (size_t)A * W2);
+    if (w) *w = v;
+    return off;
 }
 
 template <class Eng>
