@@ -367,39 +367,45 @@ struct SmallEngine {
             // ---- error-node pass (Eqs. 2-4)
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
-                uint32_t ebit = 0;
-                if (!((mb >> c) & 1u)) {
-                    float v[3];
-                    int ed[3];
+                // every column is computed; a masked column stores its sentinel
+                // +L_MAX back and a column beyond N stores nothing
+                const bool inr = (lane + 32 * c) < g.N;
+                const bool act = !((mb >> c) & 1u);
+                float v[3];
+                int ed[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    ed[k] = (int)(ci[c][k] >> 16);
+                    v[k] = st.D[ed[k]];
+                }
+                const float l = inr ? __ldg(g.lam + lane + 32 * c) : 0.f;
+                // Eq. 2: each message leaves its own detector out; the other two
+                // are added in ascending order.  Messages are stored unclamped:
+                // the detector pass reads min(|E|, L_MAX) and the sign, which is
+                // what a clamp at store time (R4) would leave, and |E| stays below
+                // Lambda_j + 3 alpha L_MAX
+                const float e0 = __fadd_rn(__fadd_rn(l, fminf(v[1], v[2])), fmaxf(v[1], v[2]));
+                const float e1 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[2])), fmaxf(v[0], v[2]));
+                const float e2 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[1])), fmaxf(v[0], v[1]));
+                if (inr) {
+                    st.E[ed[0]] = act ? e0 : L;
+                    st.E[ed[1]] = act ? e1 : L;
+                    st.E[ed[2]] = act ? e2 : L;
+                }
+                // Eq. 3 in ascending order: smallest, median, largest
+                const float lo01 = fminf(v[0], v[1]), hi01 = fmaxf(v[0], v[1]);
+                const float a0 = fminf(lo01, v[2]);
+                const float a2 = fmaxf(hi01, v[2]);
+                const float a1 = fmaxf(lo01, fminf(hi01, v[2]));
+                const float post = __fadd_rn(__fadd_rn(__fadd_rn(l, a0), a1), a2);
+                sum[c] = __fadd_rn(sum[c], post);           // unused for masked columns
+                if (post_out != nullptr && t == max_iters && inr) post_out[lane + 32 * c] = post;
+                const uint32_t ebit = (act && post <= 0.f) ? 1u : 0u;                // Eq. 4
+                if (ebit) {
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        ed[k] = (int)(ci[c][k] >> 16);
-                        v[k] = st.D[ed[k]];
-                    }
-                    const float l = __ldg(g.lam + lane + 32 * c);
-                    // Eq. 2: each message leaves its own detector out; the other
-                    // two are added in ascending order
-                    const float e0 = __fadd_rn(__fadd_rn(l, fminf(v[1], v[2])), fmaxf(v[1], v[2]));
-                    const float e1 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[2])), fmaxf(v[0], v[2]));
-                    const float e2 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[1])), fmaxf(v[0], v[1]));
-                    st.E[ed[0]] = fminf(fmaxf(e0, -L), L);
-                    st.E[ed[1]] = fminf(fmaxf(e1, -L), L);
-                    st.E[ed[2]] = fminf(fmaxf(e2, -L), L);
-                    // Eq. 3 in ascending order: smallest, median, largest
-                    const float lo01 = fminf(v[0], v[1]), hi01 = fmaxf(v[0], v[1]);
-                    const float a0 = fminf(lo01, v[2]);
-                    const float a2 = fmaxf(hi01, v[2]);
-                    const float a1 = fmaxf(lo01, fminf(hi01, v[2]));
-                    const float post = __fadd_rn(__fadd_rn(__fadd_rn(l, a0), a1), a2);
-                    sum[c] = __fadd_rn(sum[c], post);
-                    if (post_out != nullptr && t == max_iters) post_out[lane + 32 * c] = post;
-                    ebit = (post <= 0.f) ? 1u : 0u;                                   // Eq. 4
-                    if (ebit) {
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const int r = (int)(ci[c][k] & 0xffffu);
-                            atomicXor(&st.par[r >> 5], 1u << (r & 31));
-                        }
+                        const int r = (int)(ci[c][k] & 0xffffu);
+                        atomicXor(&st.par[r >> 5], 1u << (r & 31));
                     }
                 }
                 const uint32_t bal = __ballot_sync(FULLMASK, ebit);
