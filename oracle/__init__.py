@@ -35,7 +35,8 @@ class _Params(C.Structure):
     _fields_ = [("max_rounds", C.c_int32), ("beam_width", C.c_int32),
                 ("initial_iters", C.c_int32), ("iters_per_round", C.c_int32),
                 ("num_results", C.c_int32), ("prune_mode", C.c_int32),
-                ("ms_scale", C.c_double), ("llr_clamp", C.c_double)]
+                ("ms_scale", C.c_double), ("llr_clamp", C.c_double),
+                ("msg_storage", C.c_int32), ("pad0", C.c_int32), ("tie_guard", C.c_double)]
 
 
 class _Trace(C.Structure):
@@ -58,10 +59,13 @@ class Params:
     ms_scale: float = 1.0
     llr_clamp: float = 1e4
     prune_mode: int = 0      # 0: bounded insert (App. B), 1: collect then prune (Alg. 3)
+    msg_storage: int = 0     # float build: 0 float messages, 1 binary16, 2 bfloat16
+    tie_guard: float = 0.0   # near-tie flag (status bit 8) on argmin / pruning margins in (0, tie_guard)
 
     def _c(self) -> _Params:
         return _Params(self.max_rounds, self.beam_width, self.initial_iters, self.iters_per_round,
-                       self.num_results, self.prune_mode, float(self.ms_scale), float(self.llr_clamp))
+                       self.num_results, self.prune_mode, float(self.ms_scale), float(self.llr_clamp),
+                       int(self.msg_storage), 0, float(self.tie_guard))
 
 
 _LIBS: dict[str, C.CDLL] = {}
@@ -90,6 +94,7 @@ def _lib(precision: str) -> C.CDLL:
     lib.oracle_masked_bp.restype = C.c_int
     lib.oracle_prior_llr.argtypes = [P, P]
     lib.oracle_real_bytes.restype = C.c_int
+    lib.oracle_round_storage.argtypes = [P, C.c_int, C.c_int]
     lib._real = rt
     lib._np_real = np.float64 if precision == "f64" else np.float32
     _LIBS[precision] = lib
@@ -205,6 +210,16 @@ class Graph:
         E0 = np.clip(lam[col], -params.llr_clamp, params.llr_clamp).astype(self.real)
         z = np.zeros(self.N, np.uint8)
         return self.masked_bp(E0, z, z, s_bits, iters, params, stop_on_success=stop_on_success, record=True)
+
+
+def round_storage(x: np.ndarray, mode: int) -> np.ndarray:
+    """The float build's rounding of a float32 array to binary16 (mode 1) or bfloat16 (mode 2)."""
+    a = np.ascontiguousarray(x, np.float32).copy()
+    _lib("f32").oracle_round_storage(_ptr(a), int(a.size), int(mode))
+    return a
+
+
+STATUS_NEAR_TIE = 8
 
 
 # Table I of the paper: (max_rounds, beam_width, initial_iters, iters_per_round, num_results)

@@ -77,6 +77,9 @@ typedef struct {
     int32_t prune_mode;      /* 0: on-the-fly insert (App. B); 1: collect then prune (Alg. 3) */
     double ms_scale;         /* alpha of R1 */
     double llr_clamp;        /* L_MAX of R3/R4 */
+    int32_t msg_storage;     /* float build: 0 messages kept in float, 1 binary16, 2 bfloat16 */
+    int32_t pad0;
+    double tie_guard;        /* near-tie flag threshold on argmin and pruning margins (0: off) */
 } oracle_params;
 
 typedef struct {
@@ -156,6 +159,77 @@ oracle_graph *oracle_graph_create(int M, int N, int K,
 }
 
 /* ------------------------------------------------------------------------- */
+/* 16-bit message storage (float build only)                                  */
+/* ------------------------------------------------------------------------- */
+/* Nearest binary16 value of a float, ties to even, as a float: 10 fraction
+   bits for magnitudes from 2^-14 (normal), multiples of 2^-24 below it
+   (subnormal), infinity from 65520 up. */
+static float round_binary16(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    const uint32_t sign = u & 0x80000000u;
+    uint32_t a = u & 0x7fffffffu;
+    float ax;
+    memcpy(&ax, &a, 4);
+    if (a >= 0x7f800000u) return x;
+    if (ax >= 65520.0f) {
+        a = 0x7f800000u;
+    } else if (ax >= 6.103515625e-05f) {            /* 2^-14: keep 10 of 23 fraction bits */
+        const uint32_t rem = a & 0x1fffu, base = a & ~0x1fffu;
+        a = base;
+        if (rem > 0x1000u || (rem == 0x1000u && (base & 0x2000u))) a += 0x2000u;
+    } else {                                         /* subnormal: multiples of 2^-24 */
+        const float q = nearbyintf(ax * 16777216.0f);
+        const float r = q * 5.9604644775390625e-08f;
+        memcpy(&a, &r, 4);
+    }
+    a |= sign;
+    float y;
+    memcpy(&y, &a, 4);
+    return y;
+}
+
+/* Nearest bfloat16 value of a float (8 significant bits), ties to even. */
+static float round_bfloat16(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7fffffffu) >= 0x7f800000u) return x;
+    const uint32_t rem = u & 0xffffu, base = u & 0xffff0000u;
+    u = base;
+    if (rem > 0x8000u || (rem == 0x8000u && (base & 0x10000u))) u += 0x10000u;
+    float y;
+    memcpy(&y, &u, 4);
+    return y;
+}
+
+/* A stored message: rounded to the storage format, and a zero is stored as
+   +0 (R2 gives -0 and +0 the same sign, so this changes no decision). */
+static real store_msg(const oracle_params *prm, real x)
+{
+#ifdef ORACLE_FP32
+    if (prm->msg_storage == 1) x = round_binary16(x);
+    else if (prm->msg_storage == 2) x = round_bfloat16(x);
+    if (prm->msg_storage != 0 && x == 0) x = 0;
+#else
+    (void)prm;
+#endif
+    return x;
+}
+
+/* L_MAX as the storage format holds it */
+static real clamp_value(const oracle_params *prm)
+{
+    return store_msg(prm, (real)prm->llr_clamp);
+}
+
+void oracle_round_storage(float *x, int n, int mode)
+{
+    for (int k = 0; k < n; ++k) x[k] = mode == 1 ? round_binary16(x[k]) : mode == 2 ? round_bfloat16(x[k]) : x[k];
+}
+
+/* ------------------------------------------------------------------------- */
 /* masked BP (Alg. 2); plain BP is the case with no masked node              */
 /* ------------------------------------------------------------------------- */
 typedef struct {
@@ -205,7 +279,7 @@ static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *
 {
     const int M = g->M, N = g->N, E = g->E;
     const real alpha = (real)prm->ms_scale;
-    const real LMAX = (real)prm->llr_clamp;
+    const real LMAX = clamp_value(prm);
     uint8_t *sp = w->sp;
 
     /* syndrome pre-processing: flip s_i for every detector of a node fixed to 1 */
@@ -281,7 +355,7 @@ static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *
                 gap_update(&c->min_gap, (double)acc, sc);
                 if (acc > LMAX) acc = LMAX;          /* R4 */
                 if (acc < -LMAX) acc = -LMAX;
-                Em[w->ebuf[k]] = acc;
+                Em[w->ebuf[k]] = store_msg(prm, acc);
             }
             c->sum_llr[j] += post;                   /* R6 */
         }
@@ -418,6 +492,10 @@ typedef struct {
     double *res_w;
     int nres;
     int res_from_round, res_from_canon;
+    double *rscore;          /* scores of the current round's children, for the pruning margin */
+    int *rcanon;
+    int nr;
+    int near_tie;            /* an argmin or pruning margin fell in (0, tie_guard) */
 } dec_ctx;
 
 static void path_alloc(path_t *p, int E, int N)
@@ -467,7 +545,34 @@ static dec_ctx *ctx_new(const oracle_graph *g, const oracle_params *prm)
     int nr = prm->num_results > 0 ? prm->num_results : 1;
     x->results = (uint8_t *)malloc((size_t)nr * (size_t)(N > 0 ? N : 1));
     x->res_w = (double *)malloc(sizeof(double) * (size_t)nr);
+    x->rscore = (double *)malloc(sizeof(double) * (size_t)(2 * x->cap + 2));
+    x->rcanon = (int *)malloc(sizeof(int) * (size_t)(2 * x->cap + 2));
     return x;
+}
+
+/* near-tie flag: a decision margin strictly between 0 and tie_guard */
+static void tie_check(dec_ctx *x, double gap_rel)
+{
+    if (x->prm->tie_guard > 0 && gap_rel > 0 && gap_rel < x->prm->tie_guard) x->near_tie = 1;
+}
+
+/* margin at the pruning boundary of a round: the relative score gap between
+   the last kept child (rank w-1) and the first dropped one (rank w) */
+static void pruning_margin(dec_ctx *x, int w)
+{
+    if (x->nr <= w) return;
+    /* rank the round's children by (score desc, canonical index asc) */
+    for (int a = 1; a < x->nr; ++a)
+        for (int k = a; k > 0; --k) {
+            const int before = x->rscore[k] > x->rscore[k - 1] ||
+                               (x->rscore[k] == x->rscore[k - 1] && x->rcanon[k] < x->rcanon[k - 1]);
+            if (!before) break;
+            double ts = x->rscore[k]; x->rscore[k] = x->rscore[k - 1]; x->rscore[k - 1] = ts;
+            int tc = x->rcanon[k]; x->rcanon[k] = x->rcanon[k - 1]; x->rcanon[k - 1] = tc;
+        }
+    const double s0 = x->rscore[w - 1], s1 = x->rscore[w];
+    const double den = fabs(s0) > 1.0 ? fabs(s0) : 1.0;
+    tie_check(x, (s0 - s1) / den);
 }
 
 static void ctx_free(dec_ctx *x)
@@ -479,6 +584,7 @@ static void ctx_free(dec_ctx *x)
     free(x->cur); free(x->nxt);
     free(x->E_seed); free(x->sum_llr); free(x->ehat); free(x->cmask); free(x->cval);
     free(x->results); free(x->res_w);
+    free(x->rscore); free(x->rcanon);
     free(x);
 }
 
@@ -560,9 +666,10 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
     /* seed: plain BP from E(0) = Lambda for initial_iters iterations */
     for (int e = 0; e < E; ++e) {
         real l = g->lam[g->col_idx[e]];
-        if (l > (real)prm->llr_clamp) l = (real)prm->llr_clamp;
-        if (l < -(real)prm->llr_clamp) l = -(real)prm->llr_clamp;
-        x->E_seed[e] = l;
+        const real lmax = clamp_value(prm);
+        if (l > lmax) l = lmax;
+        if (l < -lmax) l = -lmax;
+        x->E_seed[e] = store_msg(prm, l);
     }
     memset(x->cmask, 0, (size_t)N);
     memset(x->cval, 0, (size_t)N);
@@ -584,16 +691,19 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
     memset(seed->val, 0, (size_t)N);
     if (tr) { tr->seed_iters = c->iters; tr->seed_success = c->success; tr->seed_next_pos = seed->next_pos; }
     int done = 0;
+    x->near_tie = 0;
     if (c->success) {
         if (results_insert(x, seed->ehat, 0, 0, &gap)) {
             done = 1;
             if (tr) { tr->ret_round = 0; tr->ret_canon = 0; }
         }
     }
+    if (!done && prm->max_rounds > 0) tie_check(x, agap);   /* the seed path will branch on next_pos */
     x->ncur = 1;
 
     for (int r = 1; r <= prm->max_rounds && !done; ++r) {
         x->nnxt = 0;
+        x->nr = 0;
         for (int pr = 0; pr < x->ncur && !done; ++pr) {
             path_t *par = &x->cur[pr];
             if (par->next_pos < 0) continue;                       /* R9 */
@@ -620,6 +730,10 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
                 else if (ch->next_pos >= 0 && agap < gap) gap = agap;
                 ch->score = path_score(g, x->sum_llr, x->cmask, c->iters, x->tmp);
                 ch->canon = canon;
+                if (ch->next_pos >= 0) tie_check(x, agap);
+                x->rscore[x->nr] = ch->score;
+                x->rcanon[x->nr] = canon;
+                x->nr++;
                 trace_child(tr, r, canon, pr, v, par->next_pos, succ, c->iters, ch->next_pos,
                             ch->score, &ch->trace_idx);
                 if (succ && results_insert(x, ch->ehat, r, canon, &gap)) {
@@ -645,6 +759,7 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
             }
         }
         if (done) break;
+        if (r < prm->max_rounds) pruning_margin(x, w);
         /* the new set, explored next round in descending score (App. B) */
         sort_paths(x->nxt, x->nnxt);
         if (prm->prune_mode == 1 && x->nnxt > w) x->nnxt = w;     /* Alg. 3: keep the top beam_width */
@@ -669,6 +784,7 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
         memcpy(out_e, x->cur[0].ehat, (size_t)N);
         st = 4;
     }
+    if (x->near_tie) st |= 8;
     *status = st;
     *iters_total = total;
     if (min_gap) *min_gap = gap;

@@ -396,3 +396,71 @@ def test_fp32_build_tracks_fp64(oracle_mod):
     # any disagreement must sit on a logged near-tie or exact tie of the double build
     assert np.all((r64["min_gap"][diff] < 1e-4) | (r64["ties"][diff] > 0))
     assert diff.sum() <= 2
+
+
+# ----------------------------------------------------------------------------
+# 16-bit message storage: rounding pinned to library conversions
+# ----------------------------------------------------------------------------
+def _rounding_cases():
+    rng = np.random.default_rng(7)
+    x = np.concatenate([
+        rng.normal(0, 1, 20000), rng.normal(0, 3000, 20000), rng.uniform(-1e-4, 1e-4, 20000),
+        rng.uniform(-1e-7, 1e-7, 5000), np.array([0.0, -0.0, 1e4, -1e4, 65504.0, 65519.0, 2049.0, 2051.0,
+                                                  6.103515625e-05, 5.9604644775390625e-08, 1.5 * 2 ** -24])])
+    # exact binary16 / bfloat16 halfway points
+    h = np.float16(rng.normal(0, 100, 5000)).astype(np.float32)
+    halves = (h + np.nextafter(h, np.float32(np.inf)).astype(np.float32)) / 2
+    return np.concatenate([x.astype(np.float32), halves]).astype(np.float32)
+
+
+def test_binary16_rounding_matches_numpy(oracle_mod):
+    x = _rounding_cases()
+    got = oracle_mod.round_storage(x, 1)
+    exp = x.astype(np.float16).astype(np.float32)
+    assert np.array_equal(got.view(np.uint32), exp.view(np.uint32))
+
+
+def test_bfloat16_rounding_matches_torch(oracle_mod):
+    torch = pytest.importorskip("torch")
+    x = _rounding_cases()
+    got = oracle_mod.round_storage(x, 2)
+    exp = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(got.view(np.uint32), exp.view(np.uint32))
+
+
+@pytest.mark.parametrize("mode,tol", [(1, 5e-3), (2, 5e-2)])
+def test_16bit_storage_tracks_double(oracle_mod, mode, tol):
+    """Messages stored in 16 bits, arithmetic in single precision: the seed
+    BP's LLRs stay close to double precision (binary16 keeps 11 significant
+    bits, bfloat16 8)."""
+    prob, sh = _bb_shots(0.03, 200, "storage16")
+    g64, g32 = oracle_mod.Graph(prob, "f64"), oracle_mod.Graph(prob, "f32")
+    prm64 = oracle_mod.Params(ms_scale=0.625)
+    prm16 = oracle_mod.Params(ms_scale=0.625, msg_storage=mode)
+    s_all = W.unpack_bits(sh.syndromes, prob.M)
+    med = []
+    for b in range(40):
+        a = g64.bp(s_all[b], 5, prm64)["llr"]
+        c = g32.bp(s_all[b], 5, prm16)["llr"].astype(np.float64)
+        med.append(np.median(np.abs(a - c) / np.maximum(1.0, np.abs(a))))
+    assert np.median(med) < tol
+
+
+def test_near_tie_flags(oracle_mod):
+    """Status bit 8 marks shots whose beam search met an argmin or pruning
+    margin inside (0, tie_guard): none without a guard, only beam shots, and
+    more with a wider guard."""
+    prob, sh = _bb_shots(0.05, 1500, "near_tie")
+    g = oracle_mod.Graph(prob, "f32")
+    base = dict(max_rounds=10, beam_width=8, initial_iters=30, iters_per_round=20, ms_scale=0.625, msg_storage=1)
+    r0 = g.decode_batch(sh.syndromes, oracle_mod.Params(**base), nthreads=4)
+    assert not (r0["status"] & 8).any()
+    r1 = g.decode_batch(sh.syndromes, oracle_mod.Params(tie_guard=1e-3, **base), nthreads=4)
+    r2 = g.decode_batch(sh.syndromes, oracle_mod.Params(tie_guard=1e-1, **base), nthreads=4)
+    f1, f2 = (r1["status"] & 8) > 0, (r2["status"] & 8) > 0
+    assert np.all(f2[f1]) and f2.sum() > f1.sum() > 0
+    assert np.all((r2["status"][f2] & 3) != 1)           # a shot ending in the seed has no beam decision
+    # the flag changes nothing else
+    for k in ("corrections", "iters"):
+        assert np.array_equal(r0[k], r2[k])
+    assert np.array_equal(r0["status"], r2["status"] & ~np.uint32(8))
