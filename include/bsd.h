@@ -59,14 +59,24 @@ extern "C" {
 #define BSD_ERR_DEVICE      (-6)   /* a device-side check recorded an error */
 #define BSD_ERR_SCRATCH     (-7)   /* bsd_decode_noalloc: one shot needs more than the static scratch */
 
-/* message storage precision (bsd_params.msg_precision) */
+/* message storage precision (bsd_params.msg_precision): the E messages are
+   stored in this format (rounded to nearest even, zero stored as +0, L_MAX
+   taken at its stored value); all arithmetic is single precision */
 #define BSD_FP32 0
+#define BSD_FP16 1
+#define BSD_BF16 2
 
 /* per-shot status words written by bsd_decode */
 #define BSD_STATUS_CONVERGED_SEED 1u  /* returned e^ comes from the seed BP (Alg. 3, first BP run) */
 #define BSD_STATUS_CONVERGED_BEAM 2u  /* returned e^ comes from a masked BP round (Alg. 2/3)    */
 #define BSD_STATUS_FAILED         4u  /* no e^ with H e^ = s was found: e^ is the hard decision
                                          of the best path of the final set, fixed values filled */
+#define BSD_STATUS_NEAR_TIE       8u  /* with 16-bit messages: an argmin (next_pos) margin of a
+                                         visited candidate or a pruning margin of a round lay
+                                         strictly inside (0, tie_guard_rel) */
+#define BSD_STATUS_FP32_RERUN    16u  /* the shot was decoded again with single-precision messages
+                                         because of a near tie; outputs and iteration count are
+                                         those of the re-run (bits 1/2/4 from it, 8 kept) */
 
 typedef struct bsd_decoder bsd_decoder;
 
@@ -81,13 +91,15 @@ typedef struct {
     int32_t  num_results;      /* valid solutions to collect before returning, 1..64 */
     float    ms_scale;         /* alpha in D = alpha * (-1)^s * prod sign * min; (0, 1] */
     float    llr_clamp;        /* L_MAX > 0 */
-    int32_t  msg_precision;    /* BSD_FP32 */
-    int32_t  reserved0;
+    int32_t  msg_precision;    /* BSD_FP32, BSD_FP16 or BSD_BF16 */
+    float    tie_guard_rel;    /* near-tie margin for 16-bit messages: > 0 this value, 0 the
+                                  default (1e-3 for FP16, 1e-2 for BF16), < 0 no near-tie
+                                  re-runs; with BSD_FP32 only a positive value flags shots */
     int64_t  workspace_bytes;  /* device workspace budget; 0 = library default (4 GiB) */
 } bsd_params;
 
 /* Fill *out with the library defaults: beam8_230iters, ms_scale 1,
-   llr_clamp 1e4, FP32.  Returns BSD_ERR_INVALID_ARG if out is NULL. */
+   llr_clamp 1e4, FP32, tie_guard_rel 0.  Returns BSD_ERR_INVALID_ARG if out is NULL. */
 int bsd_params_default(bsd_params *out);
 
 /* Fill *out with a Table I preset ("beam8_230iters", "beam32_340iters",
@@ -160,6 +172,8 @@ int bsd_decode_host(bsd_decoder *dec, const uint32_t *h_syndromes, int64_t B,
  *   whose work overlaps on the GPU (two streams, two host threads, two
  *   decoders at once) race on the array and corrupt each other's results.
  *   Serialise them.
+ *   Decoders with 16-bit messages and near-tie re-runs are not served here
+ *   (BSD_ERR_UNSUPPORTED): the re-run needs buffers of its own.
  *   Returns BSD_ERR_SCRATCH when the beam state of a single shot (two banks
  *   of 2 * beam_width edge-message snapshots plus bookkeeping) exceeds the
  *   array, BSD_ERR_INVALID_ARG as bsd_decode does, and BSD_ERR_CUDA when the

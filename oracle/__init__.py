@@ -207,7 +207,14 @@ class Graph:
         """Plain BP (Eqs. 1-4) from E(0) = Lambda, recording Lambda_j(t) for every t."""
         lam = self.prior_llr()
         col = np.asarray(self._keep[1])
-        E0 = np.clip(lam[col], -params.llr_clamp, params.llr_clamp).astype(self.real)
+        L = params.llr_clamp
+        if self.precision == "f32" and params.msg_storage:
+            # E(0) as the decoder stores it: L_MAX and Lambda in the storage format
+            L = float(round_storage(np.array([L], np.float32), params.msg_storage)[0])
+            E0 = round_storage(np.clip(lam[col], -L, L).astype(np.float32), params.msg_storage)
+            E0[E0 == 0] = 0.0
+        else:
+            E0 = np.clip(lam[col], -L, L).astype(self.real)
         z = np.zeros(self.N, np.uint8)
         return self.masked_bp(E0, z, z, s_bits, iters, params, stop_on_success=stop_on_success, record=True)
 

@@ -21,6 +21,10 @@ BSD_ERR_TIMEOUT = -4
 BSD_ERR_UNSUPPORTED = -5
 BSD_ERR_DEVICE = -6
 BSD_FP32 = 0
+BSD_FP16 = 1
+BSD_BF16 = 2
+BSD_STATUS_NEAR_TIE = 8
+BSD_STATUS_FP32_RERUN = 16
 BSD_STATUS_CONVERGED_SEED = 1
 BSD_STATUS_CONVERGED_BEAM = 2
 BSD_STATUS_FAILED = 4
@@ -36,7 +40,7 @@ class bsd_params(C.Structure):
     _fields_ = [("struct_version", C.c_uint32), ("max_rounds", C.c_int32), ("beam_width", C.c_int32),
                 ("initial_iters", C.c_int32), ("iters_per_round", C.c_int32), ("num_results", C.c_int32),
                 ("ms_scale", C.c_float), ("llr_clamp", C.c_float), ("msg_precision", C.c_int32),
-                ("reserved0", C.c_int32), ("workspace_bytes", C.c_int64)]
+                ("tie_guard_rel", C.c_float), ("workspace_bytes", C.c_int64)]
 
 
 class BsdError(RuntimeError):

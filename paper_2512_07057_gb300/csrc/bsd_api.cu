@@ -5,6 +5,8 @@
 // prior LLRs) and sizes the beam workspace; bsd_decode splits a batch into
 // chunks that fit the workspace and launches, per chunk, the seed kernel and
 // two kernels per beam round, all on the caller's stream.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -46,6 +48,10 @@ struct bsd_decoder {
     size_t open_ev = 0;
     double ms[3] = {0, 0, 0};
     long long launches[3] = {0, 0, 0};
+    // 16-bit messages: a single-precision decoder for near-tie re-runs
+    bsd_decoder* twin = nullptr;
+    void* rr_mem = nullptr;                  // flagged list, count, gathered syndromes, re-run outputs
+    long long rr_cap = 0;                    // capacity of the flagged list
 };
 
 namespace {
@@ -82,7 +88,9 @@ int validate_params(const bsd_params* p)
     if (p->num_results < 1 || p->num_results > kMaxResults) return BSD_ERR_INVALID_ARG;
     if (!(p->ms_scale > 0.f) || !(p->ms_scale <= 4.f)) return BSD_ERR_INVALID_ARG;
     if (!(p->llr_clamp > 0.f) || !std::isfinite(p->llr_clamp)) return BSD_ERR_INVALID_ARG;
-    if (p->msg_precision != BSD_FP32) return BSD_ERR_UNSUPPORTED;
+    if (p->msg_precision != BSD_FP32 && p->msg_precision != BSD_FP16 && p->msg_precision != BSD_BF16)
+        return BSD_ERR_UNSUPPORTED;
+    if (!std::isfinite(p->tie_guard_rel)) return BSD_ERR_INVALID_ARG;
     if (p->workspace_bytes < 0) return BSD_ERR_INVALID_ARG;
     return BSD_OK;
 }
@@ -158,8 +166,10 @@ void bsd_destroy(bsd_decoder* dec)
         if (dec->io_mem) cudaFree(dec->io_mem);
         if (dec->graph) destroy_graph(dec->graph);
         if (dec->h_nactive) cudaFreeHost(dec->h_nactive);
+        if (dec->rr_mem) cudaFree(dec->rr_mem);
         for (cudaEvent_t e : dec->ev) cudaEventDestroy(e);
     }
+    if (dec->twin) bsd_destroy(dec->twin);
     delete dec;
 }
 
@@ -204,7 +214,9 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
 
     // ---- host tables
     const int WM = words_of(M), WN = words_of(N), WK = words_of(K);
-    const int Epad = (int)((E + 3) / 4 * 4), Npad = (N + 3) / 4 * 4;
+    const int Epad = (int)((E + 7) / 8 * 8), Npad = (N + 3) / 4 * 4;
+    const int prec = params->msg_precision;
+    const int msg_bytes = prec == BSD_FP32 ? 4 : 2;
     std::vector<int> col_ptr(N + 1, 0), col_edge(E), col_row(E);
     for (long long e = 0; e < E; ++e) col_ptr[H_col_idx[e] + 1]++;
     for (int j = 0; j < N; ++j) col_ptr[j + 1] += col_ptr[j];
@@ -221,7 +233,14 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     int max_col = 0, max_row = 0;
     for (int j = 0; j < N; ++j) max_col = std::max(max_col, col_ptr[j + 1] - col_ptr[j]);
     for (int i = 0; i < M; ++i) max_row = std::max(max_row, H_row_ptr[i + 1] - H_row_ptr[i]);
-    const float L = params->llr_clamp;
+    // a stored message is the nearest value of the storage format (ties to
+    // even); L_MAX is taken at its stored value
+    auto store_round = [prec](float x) -> float {
+        if (prec == BSD_FP16) return __half2float(__float2half_rn(x));
+        if (prec == BSD_BF16) return __bfloat162float(__float2bfloat16_rn(x));
+        return x;
+    };
+    const float L = store_round(params->llr_clamp);
     std::vector<float> lam(Npad, 0.f), lamE(Epad, 0.f);
     std::vector<long long> lamq(N);
     int all_pos = 1;
@@ -231,7 +250,19 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
         lamq[j] = (long long)std::llrint((double)lam[j] * kFixScale);
         if (!(lam[j] > 0.f)) all_pos = 0;
     }
-    for (long long e = 0; e < E; ++e) lamE[e] = std::fmin(std::fmax(lam[H_col_idx[e]], -L), L);
+    for (long long e = 0; e < E; ++e) lamE[e] = store_round(std::fmin(std::fmax(lam[H_col_idx[e]], -L), L));
+    // E(0) in the storage format (a zero stored as +0)
+    std::vector<unsigned char> lamE_st((size_t)Epad * msg_bytes, 0);
+    for (int e = 0; e < Epad; ++e) {
+        const float v = lamE[e] == 0.f ? 0.f : lamE[e];
+        if (prec == BSD_FP32) {
+            std::memcpy(&lamE_st[(size_t)e * 4], &v, 4);
+        } else {
+            const unsigned short b = prec == BSD_FP16 ? __half_as_ushort(__float2half_rn(v))
+                                                     : __bfloat16_as_ushort(__float2bfloat16_rn(v));
+            std::memcpy(&lamE_st[(size_t)e * 2], &b, 2);
+        }
+    }
     std::vector<uint32_t> hcol((size_t)N * WM, 0u), acol((size_t)N * (WK > 0 ? WK : 1), 0u);
     for (int i = 0; i < M; ++i)
         for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e)
@@ -246,7 +277,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     gb += align256(sizeof(int) * (N + 1));
     gb += 2 * align256(sizeof(int) * E);
     gb += align256(sizeof(float) * Npad);
-    gb += align256(sizeof(float) * Epad);
+    gb += align256((size_t)msg_bytes * Epad);
     gb += align256(sizeof(uint32_t) * hcol.size());
     gb += align256(sizeof(uint32_t) * acol.size());
     gb += align256(sizeof(long long) * N);
@@ -258,7 +289,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     int* d_col_edge = carve<int>(p, E);
     int* d_col_row = carve<int>(p, E);
     float* d_lam = carve<float>(p, Npad);
-    float* d_lamE = carve<float>(p, Epad);
+    unsigned char* d_lamE = carve<unsigned char>(p, (size_t)msg_bytes * Epad);
     uint32_t* d_hcol = carve<uint32_t>(p, hcol.size());
     uint32_t* d_acol = carve<uint32_t>(p, acol.size());
     long long* d_lamq = carve<long long>(p, N);
@@ -267,7 +298,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
               cudaMemcpy(d_col_edge, col_edge.data(), sizeof(int) * E, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(d_col_row, col_row.data(), sizeof(int) * E, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(d_lam, lam.data(), sizeof(float) * Npad, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(d_lamE, lamE.data(), sizeof(float) * Epad, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(d_lamE, lamE_st.data(), lamE_st.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(d_hcol, hcol.data(), sizeof(uint32_t) * hcol.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(d_acol, acol.data(), sizeof(uint32_t) * acol.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(d_lamq, lamq.data(), sizeof(long long) * N, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -277,6 +308,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.M = M; g.N = N; g.K = K; g.E = (int)E;
     g.WM = WM; g.WN = WN; g.WK = WK;
     g.Epad = Epad; g.Npad = Npad;
+    g.msg_bytes = msg_bytes; g.prec = prec;
     g.max_col_deg = max_col; g.max_row_deg = max_row;
     g.all_lam_pos = all_pos;
     g.row_ptr = d_row_ptr; g.col_ptr = d_col_ptr; g.col_edge = d_col_edge; g.col_row = d_col_row;
@@ -289,7 +321,11 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     cfg.iters_per_round = params->iters_per_round;
     cfg.num_results = params->num_results;
     cfg.alpha = params->ms_scale;
-    cfg.L = params->llr_clamp;
+    cfg.L = L;
+    // near-tie margin: the given value, the precision's default for 16-bit
+    // messages when 0, no flags when negative (or 0 with single precision)
+    const float tg = params->tie_guard_rel;
+    cfg.tie_guard = tg > 0.f ? (double)tg : (tg == 0.f && prec == BSD_FP16) ? 1e-3 : (tg == 0.f && prec == BSD_BF16) ? 1e-2 : 0.0;
 
     rc = configure_kernels(g, cfg, device, &dec->ls);
     if (rc) { bsd_destroy(dec); return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA; }
@@ -299,8 +335,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     const int W2 = 2 * cfg.w;
     const int SB = WM + 3 * WN;
     const int NR = cfg.num_results;
-    const double seed_b = sizeof(float) * (double)Epad + sizeof(uint32_t) * (double)SB + sizeof(SlotMeta) + 4.0;
-    const double win_b = 2.0 * W2 * (sizeof(float) * (double)Epad + sizeof(uint32_t) * (double)SB + sizeof(SlotMeta)) +
+    const double seed_b = (double)msg_bytes * Epad + sizeof(uint32_t) * (double)SB + sizeof(SlotMeta) + 4.0;
+    const double win_b = 2.0 * W2 * ((double)msg_bytes * Epad + sizeof(uint32_t) * (double)SB + sizeof(SlotMeta)) +
                          12.0 + cfg.w + 8.0 + NR * (4.0 * WN + 12.0) + 4.0 + 2.0 * W2 * sizeof(int2);
     const long long budget = params->workspace_bytes > 0 ? params->workspace_bytes : (4ll << 30);
     long long A = (long long)(0.8 * (double)budget / win_b);
@@ -329,7 +365,60 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     // the per-chunk graph: seed kernel + WHILE over beam passes; without it
     // decoding falls back to plain launches
     if (build_graph(g, cfg, w, dec->ls, &dec->graph) != 0) dec->graph = nullptr;
+    // 16-bit messages with near-tie flags: shots flagged by the 16-bit run are
+    // decoded again by a single-precision twin
+    if (prec != BSD_FP32 && cfg.tie_guard > 0.0) {
+        bsd_params p2 = *params;
+        p2.msg_precision = BSD_FP32;
+        p2.tie_guard_rel = -1.f;
+        p2.workspace_bytes = budget / 4 > (256ll << 20) ? budget / 4 : (256ll << 20);
+        const int rc2 = bsd_create(M, N, K, H_row_ptr, H_col_idx, A_row_ptr, A_col_idx, priors, &p2, device,
+                                   &dec->twin);
+        if (rc2 != BSD_OK) { bsd_destroy(dec); return rc2; }
+    }
     *out = dec;
+    return BSD_OK;
+}
+
+// decode again, in single precision, every shot of [d_synd, B) whose status
+// carries the near-tie flag; outputs land where the 16-bit run put them
+static int rerun_flagged(bsd_decoder* dec, const uint32_t* d_synd, long long B, const Outputs& o, cudaStream_t s)
+{
+    if (!dec->twin || B <= 0) return BSD_OK;
+    const DevGraph& g = dec->g;
+    const int WKo = g.WK > 0 ? g.WK : 1;
+    const long long R = 65536;
+    if (dec->rr_cap < B) {
+        if (dec->rr_mem) cudaFree(dec->rr_mem);
+        dec->rr_mem = nullptr;
+        dec->rr_cap = 0;
+        const size_t need = align256(sizeof(long long) * (size_t)B) + 256 +
+                            align256(sizeof(uint32_t) * (size_t)R * (g.WM + g.WN + WKo + 2));
+        if (cudaMalloc(&dec->rr_mem, need) != cudaSuccess) { cudaGetLastError(); return BSD_ERR_OOM; }
+        dec->rr_cap = B;
+    }
+    char* p = (char*)dec->rr_mem;
+    long long* list = carve<long long>(p, (size_t)dec->rr_cap);
+    int* count = reinterpret_cast<int*>(p);
+    p += 256;
+    uint32_t* gs = carve<uint32_t>(p, (size_t)R * g.WM);
+    uint32_t* gc = carve<uint32_t>(p, (size_t)R * g.WN);
+    uint32_t* go = carve<uint32_t>(p, (size_t)R * WKo);
+    uint32_t* gst = carve<uint32_t>(p, (size_t)R);
+    uint32_t* git = carve<uint32_t>(p, (size_t)R);
+    if (launch_collect_flagged(o.status, B, list, count, s) != 0 ||
+        cudaMemcpyAsync(dec->h_nactive, count, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return BSD_ERR_CUDA;
+    const long long n = *dec->h_nactive;
+    for (long long off = 0; off < n; off += R) {
+        const int m = (int)((n - off) < R ? (n - off) : R);
+        if (launch_gather_rows(d_synd, list + off, m, g.WM, gs, s) != 0) return BSD_ERR_CUDA;
+        const int rc = bsd_decode(dec->twin, gs, m, gc, g.K > 0 ? go : nullptr, gst, git, s);
+        if (rc != BSD_OK) return rc;
+        Outputs from{gc, g.K > 0 ? go : nullptr, gst, git};
+        if (launch_scatter_results(list + off, m, g.WN, g.WK, from, o, s) != 0) return BSD_ERR_CUDA;
+    }
     return BSD_OK;
 }
 
@@ -405,7 +494,7 @@ int bsd_decode(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, uint32_
         const int rc = decode_impl(dec, d_syndromes, base, n, o, s);
         if (rc) return rc;
     }
-    return BSD_OK;
+    return rerun_flagged(dec, d_syndromes, B, o, s);
 }
 
 int bsd_decode_host(bsd_decoder* dec, const uint32_t* h_syndromes, int64_t B, uint32_t* h_corrections,
@@ -443,6 +532,9 @@ int bsd_decode_host(bsd_decoder* dec, const uint32_t* h_syndromes, int64_t B, ui
             return BSD_ERR_CUDA;
         int rc = decode_impl(dec, d_s, 0, n, o, s);
         if (rc) return rc;
+        // a re-run needs iteration counts to scatter: use the staging buffer
+        Outputs o_rr{d_c, g.K > 0 ? d_o : nullptr, d_st, d_it};
+        if (dec->twin && (rc = rerun_flagged(dec, d_s, n, o_rr, s)) != BSD_OK) return rc;
         bool ok = cudaMemcpyAsync(h_corrections + base * g.WN, d_c, sizeof(uint32_t) * n * g.WN,
                                   cudaMemcpyDeviceToHost, s) == cudaSuccess &&
                   cudaMemcpyAsync(h_status + base, d_st, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s) == cudaSuccess;
@@ -523,6 +615,7 @@ int decoder_view(const bsd_decoder* dec, const DevGraph** g, const DecCfg** cfg,
                  int* device)
 {
     if (!dec) return BSD_ERR_INVALID_ARG;
+    if (dec->twin) return BSD_ERR_UNSUPPORTED;   // near-tie re-runs need buffers of their own
     *g = &dec->g;
     *cfg = &dec->cfg;
     *ls = &dec->ls;

@@ -6,7 +6,7 @@
 //   col_edge[E]           CSR edge id of each (column, k) pair, rows ascending
 //   col_row[E]            detector (row) of that edge
 //   lam[N]                Lambda_j = log((1-p_j)/p_j) rounded to float
-//   lamE[E]               clamp(Lambda_{col(e)}), the seed's E(0) in CSR order
+//   lamE[Epad]            clamp(Lambda_{col(e)}), the seed's E(0) in CSR order, storage format
 //   hcol[N][WM]           column j of H as an M-bit set (syndrome flip for v = 1)
 //   acol[N][WK]           column j of A as a K-bit set (observable flips)
 //   lamq[N]               Lambda_j on the 2^-16 fixed-point grid (weights)
@@ -31,7 +31,9 @@ constexpr double kFixScale = 65536.0;   // fixed-point grid 2^-16 for scores and
 struct DevGraph {
     int M, N, K, E;
     int WM, WN, WK;        // words of M, N, K bits
-    int Epad, Npad;        // E, N rounded up to a multiple of 4
+    int Epad, Npad;        // E rounded up to a multiple of 8, N to a multiple of 4
+    int msg_bytes;         // bytes of a stored message: 4 (float), 2 (binary16 / bfloat16)
+    int prec;              // 0 float, 1 binary16, 2 bfloat16
     int max_col_deg, max_row_deg;
     int all_lam_pos;       // every Lambda_j > 0 (all p_j < 1/2)
     int det_bytes;         // per-warp detector-side shared memory (set with the engine)
@@ -40,7 +42,7 @@ struct DevGraph {
     const int* col_edge;
     const int* col_row;
     const float* lam;
-    const float* lamE;
+    const void* lamE;      // E(0) in the storage format
     const uint32_t* hcol;
     const uint32_t* acol;
     const long long* lamq;
@@ -48,7 +50,8 @@ struct DevGraph {
 
 struct DecCfg {
     int max_rounds, w, initial_iters, iters_per_round, num_results;
-    float alpha, L;
+    float alpha, L;        // L: L_MAX as the storage format holds it
+    double tie_guard;      // near-tie margin (0: no flags)
 };
 
 struct SlotMeta {
@@ -56,7 +59,7 @@ struct SlotMeta {
     int iters;             // iterations run by this BP call (>= 1)
     int next_pos;          // least reliable unmasked node, -1 if none
     int success;           // H e^ = s' at the last iteration
-    int pad;
+    int flags;             // bit 0: argmin margin inside (0, tie_guard)
 };
 
 struct Outputs {
@@ -92,12 +95,12 @@ struct Work {
     long long A;           // active entries per beam pass
     int SB;                // words per slot bit record: sp[WM] mask[WN] vals[WN] ehat[WN]
     // seed store [S]
-    float* seedE;          // [S][Epad]
+    unsigned char* seedE;  // [S][Epad] messages in the storage format
     uint32_t* seedBits;    // [S][SB]
     SlotMeta* seedMeta;    // [S]
     int* seed_shot;        // [S] chunk-local shot of a seed-store entry
     // beam window [A]
-    float* slotE;          // [2][A][2w][Epad]
+    unsigned char* slotE;  // [2][A][2w][Epad] messages in the storage format
     uint32_t* slotBits;    // [2][A][2w][SB]
     SlotMeta* slotMeta;    // [2][A][2w]
     int* shot_of;          // [A] chunk-local shot of a window entry
@@ -109,6 +112,7 @@ struct Work {
     long long* res_w;      // [A][num_results]
     int* res_origin;       // [A][num_results]: 0 = seed, 1 = masked BP round
     int* res_n;            // [A]
+    int* near;             // [A] a near-tie met by this shot's search so far
     int2* items;           // [2][A * 2w] (window entry, child index) for rounds >= 2
     Counters* ctr;
     int* round_ctr;        // 3 * (max_rounds + 2) ints after ctr
@@ -152,5 +156,10 @@ int build_graph(const DevGraph& g, const DecCfg& cfg, const Work& w, const Launc
 void destroy_graph(void* graph_exec);
 int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, const uint32_t* synd,
                   long long B, int T, float* llr, float* sum_llr, void* stream);
+// single-precision re-runs of near-tie shots
+int launch_collect_flagged(const uint32_t* status, long long B, long long* list, int* count, void* stream);
+int launch_gather_rows(const uint32_t* src, const long long* list, int n, int W, uint32_t* dst, void* stream);
+int launch_scatter_results(const long long* list, int n, int WN, int WK, const Outputs& from, const Outputs& to,
+                           void* stream);
 
 }  // namespace bsd

@@ -25,6 +25,8 @@
 // is masked.  A +L_MAX input never lowers a minimum below that of the other
 // inputs and never flips a sign, so the check pass needs no mask test; the
 // error-node pass skips masked nodes, whose messages therefore stay +L_MAX.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -36,7 +38,60 @@ namespace bsd {
 
 #define FULLMASK 0xffffffffu
 
-enum : uint32_t { ST_SEED = 1u, ST_BEAM = 2u, ST_FAILED = 4u };
+// ----------------------------------------------------------------------------
+// message storage: float, binary16 or bfloat16; arithmetic is always float.
+// A stored value is the round-to-nearest-even conversion of the float result,
+// and a zero is stored as +0 (the sign rule treats -0 as positive anyway).
+// ----------------------------------------------------------------------------
+template <int P> struct Store;
+template <> struct Store<0> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const T* p, int i) { return p[i]; }
+    static __device__ __forceinline__ void st(T* p, int i, float v) { p[i] = v; }
+    static __device__ __forceinline__ float2 ld2(const T* p, int i) { return *reinterpret_cast<const float2*>(p + i); }
+};
+template <> struct Store<1> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const T* p, int i) { return __half2float(p[i]); }
+    static __device__ __forceinline__ void st(T* p, int i, float v)
+    {
+        __half h = __float2half_rn(v);
+        if ((__half_as_ushort(h) & 0x7fffu) == 0) h = __ushort_as_half(0);
+        p[i] = h;
+    }
+    static __device__ __forceinline__ float2 ld2(const T* p, int i)
+    {
+        return __half22float2(*reinterpret_cast<const __half2*>(p + i));
+    }
+};
+template <> struct Store<2> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float ld(const T* p, int i) { return __bfloat162float(p[i]); }
+    static __device__ __forceinline__ void st(T* p, int i, float v)
+    {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        if ((__bfloat16_as_ushort(h) & 0x7fffu) == 0) h = __ushort_as_bfloat16(0);
+        p[i] = h;
+    }
+    static __device__ __forceinline__ float2 ld2(const T* p, int i)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + i));
+    }
+};
+
+// bytes and 16-byte vectors of one E snapshot (Epad is a multiple of 8)
+__host__ __device__ __forceinline__ size_t snap_bytes(const DevGraph& g) { return (size_t)g.Epad * (size_t)g.msg_bytes; }
+__host__ __device__ __forceinline__ int snap_vec16(const DevGraph& g) { return (int)(snap_bytes(g) / 16); }
+
+// copy n16 16-byte vectors (the E snapshot) with a warp
+__device__ __forceinline__ void warp_copy16(void* dst, const void* src, int n16)
+{
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (int q = (threadIdx.x & 31); q < n16; q += 32) d[q] = s[q];
+}
+
+enum : uint32_t { ST_SEED = 1u, ST_BEAM = 2u, ST_FAILED = 4u, ST_NEAR = 8u, ST_RERUN = 16u };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -48,12 +103,12 @@ __host__ __device__ inline size_t det_region_bytes(const DevGraph& g) { return (
 
 __host__ __device__ inline size_t warp_smem_bytes(const DevGraph& g)
 {
-    return align16(sizeof(float) * (size_t)g.Epad) + det_region_bytes(g) +
+    return align16((size_t)g.msg_bytes * (size_t)g.Epad) + det_region_bytes(g) +
            align16(sizeof(float) * (size_t)g.Npad) + align16(sizeof(uint32_t) * (size_t)(2 * g.WM + 3 * g.WN));
 }
 
 struct WarpState {
-    float* E;          // [Epad] E_{j->i}, CSR edge order
+    void* E;           // [Epad] E_{j->i} in the storage format, CSR edge order
     float4* rs;        // [M]    (min1, min2, argmin edge id, s'_i xor parity of negatives)
     float* D;          // [Epad] D_{i->j} per CSR edge (same storage as rs)
     float* sumllr;     // [Npad]
@@ -68,7 +123,7 @@ __device__ inline WarpState carve(char* base, const DevGraph& g)
 {
     WarpState s;
     char* p = base;
-    s.E = reinterpret_cast<float*>(p);       p += align16(sizeof(float) * (size_t)g.Epad);
+    s.E = p;                                 p += align16((size_t)g.msg_bytes * (size_t)g.Epad);
     s.rs = reinterpret_cast<float4*>(p);
     s.D = reinterpret_cast<float*>(p);       p += det_region_bytes(g);
     s.sumllr = reinterpret_cast<float*>(p);  p += align16(sizeof(float) * (size_t)g.Npad);
@@ -94,10 +149,12 @@ __device__ inline unsigned long long fixq(float x)
 // st.ehat holds e^(t) of the last iteration (masked positions 0), st.sumllr
 // holds the sum over the iterations run of Lambda_j(t).  If post_out is not
 // null, Lambda_j(max_iters) is written there.
-template <int DV>
+template <int DV, int P>
 __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
                           bool stop, int* success, float* post_out)
 {
+    using S = Store<P>;
+    typename S::T* const E = reinterpret_cast<typename S::T*>(st.E);
     const int lane = threadIdx.x & 31;
     const float alpha = cfg.alpha;
     const float L = cfg.L;
@@ -113,7 +170,7 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
             int id = -1;
             uint32_t neg = (st.sp[i >> 5] >> (i & 31)) & 1u;
             for (int e = rb; e < re; ++e) {
-                const float x = st.E[e];
+                const float x = S::ld(E, e);
                 const float a = fabsf(x);
                 if (a < m1) { m2 = m1; m1 = a; id = e; }
                 else if (a < m2) { m2 = a; }
@@ -139,7 +196,7 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
                         const int e = __ldg(g.col_edge + kb + k);
                         const int r = __ldg(g.col_row + kb + k);
                         const float4 s4 = st.rs[r];
-                        const float xo = st.E[e];
+                        const float xo = S::ld(E, e);
                         const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
                         const uint32_t sg = __float_as_uint(s4.w) ^ ((xo < 0.f) ? 1u : 0u);
                         const float d = __fmul_rn(alpha, m);
@@ -173,7 +230,7 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
 #pragma unroll
                         for (int k2 = 0; k2 < DV; ++k2)
                             if (k2 != k && k2 < deg) acc = __fadd_rn(acc, v[k2]);
-                        st.E[ed[k]] = fminf(fmaxf(acc, -L), L);
+                        S::st(E, ed[k], fminf(fmaxf(acc, -L), L));
                     }
                 }
                 st.sumllr[j] = __fadd_rn(st.sumllr[j], post);
@@ -203,36 +260,61 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
     return iters;
 }
 
-// warp reduction of per-lane (min |sum_LLR|, its node, sum of q(|sum_LLR|)):
-// the smaller value wins, equal values go to the lower node index
-__device__ inline void reduce_argmin_score(float best, int bj, unsigned long long s, int* next_pos, long long* S)
+// warp reduction of per-lane (two smallest |sum_LLR|, node of the smallest,
+// sum of q(|sum_LLR|)): the smaller value wins, equal values go to the lower
+// node index.  *tie is set when the relative margin between the smallest and
+// the second smallest lies strictly inside (0, guard).
+__device__ inline void reduce_argmin_score(float best, float second, int bj, unsigned long long s, double guard,
+                                           int* next_pos, long long* S, int* tie)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float ob = __shfl_xor_sync(FULLMASK, best, o);
+        const float os = __shfl_xor_sync(FULLMASK, second, o);
         const int oj = __shfl_xor_sync(FULLMASK, bj, o);
+        second = fminf(fmaxf(best, ob), fminf(second, os));
         if (oj >= 0 && (bj < 0 || ob < best || (ob == best && oj < bj))) { best = ob; bj = oj; }
         s += __shfl_xor_sync(FULLMASK, s, o);
     }
     *next_pos = bj;
     *S = (long long)s;
+    int t = 0;
+    if (guard > 0.0 && bj >= 0 && second != INFINITY) {
+        const double den = fabs((double)second) > 1.0 ? fabs((double)second) : 1.0;
+        const double gap = ((double)second - (double)best) / den;
+        t = (gap > 0.0 && gap < guard) ? 1 : 0;
+    }
+    *tie = t;
+}
+
+// per-lane update of (smallest, second smallest, node of the smallest); nodes
+// arrive in ascending order, so the lowest index keeps ties
+__device__ __forceinline__ void two_smallest(float a, int j, float* best, float* second, int* bj)
+{
+    if (*bj < 0 || a < *best) {
+        *second = *best;
+        *best = a;
+        *bj = j;
+    } else if (a < *second) {
+        *second = a;
+    }
 }
 
 // least reliable unmasked node (lowest index on ties) and the score numerator
-__device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, int* next_pos,
-                                        long long* S)
+__device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, double guard, int* next_pos,
+                                        long long* S, int* tie)
 {
     const int lane = threadIdx.x & 31;
-    float best = INFINITY;
+    float best = INFINITY, second = INFINITY;
     int bj = -1;
     unsigned long long s = 0;
     for (int j = lane; j < g.N; j += 32) {
         if ((st.mask[j >> 5] >> (j & 31)) & 1u) continue;
         const float a = fabsf(st.sumllr[j]);
-        if (bj < 0 || a < best) { best = a; bj = j; }
+        two_smallest(a, j, &best, &second, &bj);
         s += fixq(a);
     }
-    reduce_argmin_score(best, bj, s, next_pos, S);
+    reduce_argmin_score(best, second, bj, s, guard, next_pos, S, tie);
 }
 
 // ----------------------------------------------------------------------------
@@ -240,9 +322,10 @@ __device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, 
 // ----------------------------------------------------------------------------
 // GenericEngine: any code whose column degree is at most DV; graph tables
 // are read from global memory (L1-resident) and sum_LLR lives in shared memory.
-template <int DV>
+template <int DV, int P>
 struct GenericEngine {
     static constexpr int kMinBlocks = 1;
+    static constexpr int kPrec = P;
     __device__ void load_graph(const DevGraph&) {}
     __device__ void clear_sums(const DevGraph& g, const WarpState& st)
     {
@@ -251,11 +334,12 @@ struct GenericEngine {
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
                        int* success, float* post_out)
     {
-        return bp_iterate<DV>(g, cfg, st, max_iters, stop, success, post_out);
+        return bp_iterate<DV, P>(g, cfg, st, max_iters, stop, success, post_out);
     }
-    __device__ void argmin_score(const DevGraph& g, const WarpState& st, int* np, long long* S)
+    __device__ void argmin_score(const DevGraph& g, const WarpState& st, double guard, int* np, long long* S,
+                                 int* tie)
     {
-        argmin_and_score(g, st, np, S);
+        argmin_and_score(g, st, guard, np, S, tie);
     }
     __device__ void write_sums(const DevGraph& g, const WarpState& st, float* dst)
     {
@@ -273,9 +357,11 @@ struct GenericEngine {
 // sums of three messages are formed from min / max / median directly.  Every
 // value it produces is the one GenericEngine produces (same operations, same
 // order).
-template <int CPL, int RPL, int RD>
+template <int CPL, int RPL, int RD, int P>
 struct SmallEngine {
     static constexpr int kMinBlocks = 2;   // at most 128 registers: two 8-warp blocks per SM
+    static constexpr int kPrec = P;
+    using S = Store<P>;
     uint32_t ci[CPL][3];   // (CSR edge id << 16) | row, for column lane + 32 c
     float sum[CPL];
     uint32_t mb;           // bit c: column lane + 32 c is masked or beyond N
@@ -307,6 +393,7 @@ struct SmallEngine {
         const int lane = threadIdx.x & 31;
         const float alpha = cfg.alpha;
         const float L = cfg.L;
+        typename S::T* const E = reinterpret_cast<typename S::T*>(st.E);
         mb = 0u;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -322,11 +409,11 @@ struct SmallEngine {
             for (int r = 0; r < RPL; ++r) {
                 const int i = lane + 32 * r;
                 if (i < g.M) {
-                    const float2* er = reinterpret_cast<const float2*>(st.E + RD * i);
+                    const int eb = RD * i;
                     float x[RD];
 #pragma unroll
                     for (int h = 0; h < RD / 2; ++h) {
-                        const float2 x2 = er[h];
+                        const float2 x2 = S::ld2(E, eb + 2 * h);
                         x[2 * h] = x2.x;
                         x[2 * h + 1] = x2.y;
                     }
@@ -388,9 +475,9 @@ struct SmallEngine {
                 const float e1 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[2])), fmaxf(v[0], v[2]));
                 const float e2 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[1])), fmaxf(v[0], v[1]));
                 if (inr) {
-                    st.E[ed[0]] = act ? e0 : L;
-                    st.E[ed[1]] = act ? e1 : L;
-                    st.E[ed[2]] = act ? e2 : L;
+                    S::st(E, ed[0], act ? e0 : L);
+                    S::st(E, ed[1], act ? e1 : L);
+                    S::st(E, ed[2], act ? e2 : L);
                 }
                 // Eq. 3 in ascending order: smallest, median, largest
                 const float lo01 = fminf(v[0], v[1]), hi01 = fmaxf(v[0], v[1]);
@@ -422,20 +509,21 @@ struct SmallEngine {
         *success = ok;
         return iters;
     }
-    __device__ void argmin_score(const DevGraph&, const WarpState&, int* np, long long* S)
+    __device__ void argmin_score(const DevGraph&, const WarpState&, double guard, int* np, long long* S,
+                                 int* tie)
     {
         const int lane = threadIdx.x & 31;
-        float best = INFINITY;
+        float best = INFINITY, second = INFINITY;
         int bj = -1;
         unsigned long long s = 0;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             if ((mb >> c) & 1u) continue;
             const float a = fabsf(sum[c]);
-            if (bj < 0 || a < best) { best = a; bj = lane + 32 * c; }
+            two_smallest(a, lane + 32 * c, &best, &second, &bj);
             s += fixq(a);
         }
-        reduce_argmin_score(best, bj, s, np, S);
+        reduce_argmin_score(best, second, bj, s, guard, np, S, tie);
     }
     __device__ void write_sums(const DevGraph& g, const WarpState&, float* dst)
     {
@@ -492,7 +580,7 @@ __device__ inline size_t slot_index(const Work& w, int bank, int a, int c, int W
 // the parent of the rank-k path of window entry a in round r: the seed-store
 // entry for r = 1, else the slot of the previous round that won rank k
 struct SlotRef {
-    const float* E;
+    const unsigned char* E;   // snapshot, Epad messages in the storage format
     const uint32_t* bits;
     const SlotMeta* meta;
 };
@@ -503,12 +591,12 @@ __device__ inline SlotRef parent_ref(const DevGraph& g, const DecCfg& cfg, const
     SlotRef s;
     if (r == 1) {
         const size_t e = (size_t)(pbase + a);
-        s.E = w.seedE + e * (size_t)g.Epad;
+        s.E = w.seedE + e * snap_bytes(g);
         s.bits = w.seedBits + e * (size_t)w.SB;
         s.meta = w.seedMeta + e;
     } else {
         const size_t e = slot_index(w, (r - 1) & 1, a, w.set_idx[(size_t)a * cfg.w + k], 2 * cfg.w);
-        s.E = w.slotE + e * (size_t)g.Epad;
+        s.E = w.slotE + e * snap_bytes(g);
         s.bits = w.slotBits + e * (size_t)w.SB;
         s.meta = w.slotMeta + e;
     }
@@ -603,9 +691,7 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCf
             __syncwarp();
             continue;
         }
-        const float4* src = reinterpret_cast<const float4*>(g.lamE);
-        float4* dst = reinterpret_cast<float4*>(st.E);
-        for (int q = lane; q < g.Epad / 4; q += 32) dst[q] = __ldg(src + q);
+        warp_copy16(st.E, g.lamE, snap_vec16(g));
         eng.clear_sums(g, st);
         __syncwarp();
         int succ = 0;
@@ -617,15 +703,14 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCf
             __syncwarp();
             continue;
         }
-        int np;
+        int np, tie;
         long long S;
-        eng.argmin_score(g, st, &np, &S);
+        eng.argmin_score(g, st, cfg.tie_guard, &np, &S, &tie);
         int a = 0;
         if (lane == 0) a = atomicAdd(&w.ctr->n_active, 1);
         a = __shfl_sync(FULLMASK, a, 0);
         // the seed path (Alg. 3): snapshot, s' = s, no fixed node, e^, next_pos
-        float4* dE = reinterpret_cast<float4*>(w.seedE + (size_t)a * (size_t)g.Epad);
-        for (int q = lane; q < g.Epad / 4; q += 32) dE[q] = dst[q];
+        warp_copy16(w.seedE + (size_t)a * snap_bytes(g), st.E, snap_vec16(g));
         uint32_t* bits = w.seedBits + (size_t)a * (size_t)w.SB;
         for (int q = lane; q < g.WM; q += 32) bits[q] = st.sp[q];
         for (int q = lane; q < g.WN; q += 32) {
@@ -635,7 +720,7 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCf
         }
         if (lane == 0) {
             SlotMeta m;
-            m.S = 0; m.iters = it; m.next_pos = np; m.success = succ; m.pad = 0;
+            m.S = 0; m.iters = it; m.next_pos = np; m.success = succ; m.flags = tie;
             w.seedMeta[a] = m;
             w.seed_shot[a] = b;
         }
@@ -694,13 +779,11 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecC
             st.vals[q] = vv;
         }
         // warm start from the parent's snapshot
-        const float4* pE = reinterpret_cast<const float4*>(par.E);
-        float4* sE = reinterpret_cast<float4*>(st.E);
-        for (int q = lane; q < g.Epad / 4; q += 32) sE[q] = pE[q];
+        warp_copy16(st.E, par.E, snap_vec16(g));
         eng.clear_sums(g, st);
         __syncwarp();
         for (int q = __ldg(g.col_ptr + pos) + lane; q < __ldg(g.col_ptr + pos + 1); q += 32)
-            st.E[__ldg(g.col_edge + q)] = cfg.L;
+            Store<Eng::kPrec>::st(reinterpret_cast<typename Store<Eng::kPrec>::T*>(st.E), __ldg(g.col_edge + q), cfg.L);
         __syncwarp();
         int succ = 0;
         const int iters = eng.run(g, cfg, st, cfg.iters_per_round, true, &succ, nullptr);
@@ -708,11 +791,10 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecC
         __syncwarp();
         for (int q = lane; q < g.WN; q += 32) st.ehat[q] = (st.ehat[q] & ~st.mask[q]) | st.vals[q];
         __syncwarp();
-        int np;
+        int np, tie;
         long long S;
-        eng.argmin_score(g, st, &np, &S);
-        float4* cE = reinterpret_cast<float4*>(w.slotE + cslot * (size_t)g.Epad);
-        for (int q = lane; q < g.Epad / 4; q += 32) cE[q] = sE[q];
+        eng.argmin_score(g, st, cfg.tie_guard, &np, &S, &tie);
+        warp_copy16(w.slotE + cslot * snap_bytes(g), st.E, snap_vec16(g));
         uint32_t* cbits = w.slotBits + cslot * (size_t)w.SB;
         for (int q = lane; q < g.WM; q += 32) cbits[q] = st.sp[q];
         for (int q = lane; q < g.WN; q += 32) {
@@ -722,7 +804,7 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecC
         }
         if (lane == 0) {
             SlotMeta m;
-            m.S = S; m.iters = iters; m.next_pos = np; m.success = succ; m.pad = 0;
+            m.S = S; m.iters = iters; m.next_pos = np; m.success = succ; m.flags = tie;
             w.slotMeta[cslot] = m;
         }
         __syncwarp();
@@ -735,11 +817,11 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecC
 struct SelScratch {
     double score[2 * kMaxBeam];
     int iters[2 * kMaxBeam];
-    int flags[2 * kMaxBeam];     // bit0 exists, bit1 success
+    int flags[2 * kMaxBeam];     // bit0 exists, bit1 success, bit2 argmin near-tie
 };
 
 __device__ void finalize_results(const DevGraph& g, const DecCfg& cfg, const Work& w, const Outputs& out,
-                                 int a, long long gb, unsigned long long total)
+                                 int a, long long gb, unsigned long long total, uint32_t extra)
 {
     const int n = w.res_n[a];
     const long long* rw = w.res_w + (size_t)a * cfg.num_results;
@@ -747,7 +829,7 @@ __device__ void finalize_results(const DevGraph& g, const DecCfg& cfg, const Wor
     for (int q = 1; q < n; ++q)
         if (rw[q] < rw[bi]) bi = q;
     const uint32_t st = (w.res_origin[(size_t)a * cfg.num_results + bi] == 0) ? ST_SEED : ST_BEAM;
-    finalize_shot(g, out, gb, w.res_bits + ((size_t)a * cfg.num_results + bi) * g.WN, st, total);
+    finalize_shot(g, out, gb, w.res_bits + ((size_t)a * cfg.num_results + bi) * g.WN, st | extra, total);
 }
 
 __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, int r)
@@ -789,6 +871,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                 w.iters_acc[a] = (unsigned long long)sm.iters;
                 w.done[a] = 0;
                 w.res_n[a] = sm.success ? 1 : 0;
+                w.near[a] = sm.flags & 1;      // the seed path branches on its argmin
             }
             __syncwarp();
         } else if (w.done[a]) {
@@ -804,7 +887,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
             double scv = 0.0;
             if (pnp >= 0) {
                 const SlotMeta m = w.slotMeta[slot_index(w, cb, a, c, W2)];
-                fl = 1 | (m.success ? 2 : 0);
+                fl = 1 | (m.success ? 2 : 0) | ((m.flags & 1) << 2);
                 it = m.iters;
                 scv = ((double)m.S / kFixScale) / (double)m.iters;
             }
@@ -815,6 +898,14 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
         __syncwarp();
         unsigned long long acc = w.iters_acc[a];
         bool done = false;
+        // near-tie record: argmin margins of the children the sequential
+        // algorithm visits, and the pruning margin of the round
+        int near = w.near[a];
+        auto near_upto = [&](int last) {
+            int f = 0;
+            for (int c = lane; c <= last && c < nch; c += 32) f |= (sc->flags[c] >> 2) & 1;
+            return __any_sync(FULLMASK, f != 0) ? 1 : 0;
+        };
         if (cfg.num_results == 1) {
             // Alg. 3: the first successful child in visit order ends the search
             int first = 0x7fffffff;
@@ -829,7 +920,8 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULLMASK, sum, o);
                 const uint32_t* eb = w.slotBits + slot_index(w, cb, a, first, W2) * (size_t)w.SB + g.WM + 2 * g.WN;
-                finalize_shot(g, d.out, gb, eb, ST_BEAM, acc + sum);
+                near |= near_upto(first);
+                finalize_shot(g, d.out, gb, eb, ST_BEAM | (near ? ST_NEAR : 0u), acc + sum);
                 done = true;
             }
         } else {
@@ -861,7 +953,8 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                     }
                     __syncwarp();
                     if (nres + 1 >= cfg.num_results) {
-                        finalize_results(g, cfg, w, d.out, a, gb, acc + sum);
+                        near |= near_upto(c);
+                        finalize_results(g, cfg, w, d.out, a, gb, acc + sum, near ? ST_NEAR : 0u);
                         done = true;
                     }
                 }
@@ -879,6 +972,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                 nex += __shfl_xor_sync(FULLMASK, nex, o);
             }
             acc += sum;
+            near |= near_upto(nch - 1);
             // rank of each existing child under (score desc, canonical index asc)
             int myrank[4];
 #pragma unroll
@@ -898,7 +992,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
             }
             if (r >= cfg.max_rounds || nex == 0) {
                 if (cfg.num_results > 1 && w.res_n[a] > 0) {
-                    finalize_results(g, cfg, w, d.out, a, gb, acc);
+                    finalize_results(g, cfg, w, d.out, a, gb, acc, near ? ST_NEAR : 0u);
                 } else {
                     // no valid solution: the best path of the final set
                     int best = 0x7fffffff;
@@ -912,13 +1006,30 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                         eb = w.slotBits + slot_index(w, cb, a, best, W2) * (size_t)w.SB + g.WM + 2 * g.WN;
                     else
                         eb = parent_ref(g, cfg, w, r, pbase, a, 0).bits + g.WM + 2 * g.WN;
-                    finalize_shot(g, d.out, gb, eb, ST_FAILED, acc);
+                    finalize_shot(g, d.out, gb, eb, ST_FAILED | (near ? ST_NEAR : 0u), acc);
                 }
                 done = true;
             } else {
                 // keep the top beam_width; their slots become the next round's parents
                 __syncwarp();
                 const int keep = nex < cfg.w ? nex : cfg.w;
+                if (cfg.tie_guard > 0.0 && nex > keep) {
+                    // pruning margin: last kept (rank keep-1) against first dropped (rank keep)
+                    double s_in = -INFINITY, s_out = -INFINITY;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (myrank[q] == keep - 1) s_in = sc->score[lane + 32 * q];
+                        if (myrank[q] == keep) s_out = sc->score[lane + 32 * q];
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s_in = fmax(s_in, __shfl_xor_sync(FULLMASK, s_in, o));
+                        s_out = fmax(s_out, __shfl_xor_sync(FULLMASK, s_out, o));
+                    }
+                    const double den = fabs(s_in) > 1.0 ? fabs(s_in) : 1.0;
+                    const double gap = (s_in - s_out) / den;
+                    if (gap > 0.0 && gap < cfg.tie_guard) near = 1;
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (myrank[q] >= 0 && myrank[q] < keep)
@@ -937,6 +1048,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                 if (lane == 0) {
                     w.set_size[a] = keep;
                     w.iters_acc[a] = acc;
+                    w.near[a] = near;
                     if (tot > 0) wbase = atomicAdd(&round_ctr(w, r + 1)[2], 2 * tot);
                 }
                 wbase = __shfl_sync(FULLMASK, wbase, 0);
@@ -976,9 +1088,7 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_bp_llr(DevGraph g, Dec
     for (long long b = (long long)blockIdx.x * (blockDim.x >> 5) + wid; b < B; b += nw) {
         for (int q = lane; q < g.WM; q += 32) st.sp[q] = synd[b * g.WM + q];
         for (int q = lane; q < g.WN; q += 32) { st.mask[q] = 0u; st.vals[q] = 0u; }
-        const float4* src = reinterpret_cast<const float4*>(g.lamE);
-        float4* dst = reinterpret_cast<float4*>(st.E);
-        for (int q = lane; q < g.Epad / 4; q += 32) dst[q] = __ldg(src + q);
+        warp_copy16(st.E, g.lamE, snap_vec16(g));
         eng.clear_sums(g, st);
         __syncwarp();
         int succ;
@@ -992,14 +1102,24 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_bp_llr(DevGraph g, Dec
 // ----------------------------------------------------------------------------
 // host-side launch helpers
 // ----------------------------------------------------------------------------
-// engine ids: 0..2 generic with column degree bound 3 / 6 / 16;
-// 3: small (CPL 3, RPL 2, row degree 6), 4: small (CPL 5, RPL 3, row degree 6)
-using Generic3 = GenericEngine<3>;
-using Generic6 = GenericEngine<6>;
-using Generic16 = GenericEngine<16>;
-using Small326 = SmallEngine<3, 2, 6>;
-using Small536 = SmallEngine<5, 3, 6>;
-#define BSD_ENGINES(X) X(0, Generic3) X(1, Generic6) X(2, Generic16) X(3, Small326) X(4, Small536)
+// engine id = 3 * kind + storage precision; kinds: 0..2 generic with column
+// degree bound 3 / 6 / 16, 3: small (CPL 3, RPL 2, row degree 6), 4: small
+// (CPL 5, RPL 3, row degree 6); precision 0 float, 1 binary16, 2 bfloat16
+#define BSD_KIND_ALIASES(P, SFX)                          \
+    using Generic3##SFX = GenericEngine<3, P>;            \
+    using Generic6##SFX = GenericEngine<6, P>;            \
+    using Generic16##SFX = GenericEngine<16, P>;          \
+    using Small326##SFX = SmallEngine<3, 2, 6, P>;        \
+    using Small536##SFX = SmallEngine<5, 3, 6, P>;
+BSD_KIND_ALIASES(0, _f32)
+BSD_KIND_ALIASES(1, _f16)
+BSD_KIND_ALIASES(2, _bf16)
+#define BSD_ENGINES(X)                                                                          \
+    X(0, Generic3_f32) X(1, Generic3_f16) X(2, Generic3_bf16)                                   \
+    X(3, Generic6_f32) X(4, Generic6_f16) X(5, Generic6_bf16)                                   \
+    X(6, Generic16_f32) X(7, Generic16_f16) X(8, Generic16_bf16)                                \
+    X(9, Small326_f32) X(10, Small326_f16) X(11, Small326_bf16)                                 \
+    X(12, Small536_f32) X(13, Small536_f16) X(14, Small536_bf16)
 
 template <class Eng>
 static int set_attrs(size_t smem_bp)
@@ -1032,15 +1152,17 @@ static bool small_fits(const DevGraph& g, int cpl, int rpl)
 int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls)
 {
     (void)cfg;
-    int eng;
-    if (small_fits(g, 3, 2)) eng = 3;
-    else if (small_fits(g, 5, 3)) eng = 4;
-    else if (g.max_col_deg <= 3) eng = 0;
-    else if (g.max_col_deg <= 6) eng = 1;
-    else if (g.max_col_deg <= 16) eng = 2;
+    int kind;
+    if (small_fits(g, 3, 2)) kind = 3;
+    else if (small_fits(g, 5, 3)) kind = 4;
+    else if (g.max_col_deg <= 3) kind = 0;
+    else if (g.max_col_deg <= 6) kind = 1;
+    else if (g.max_col_deg <= 16) kind = 2;
     else return -5;
+    const int eng = 3 * kind + g.prec;
+    // the small engine keeps D per edge in float; the generic one a record per detector
     const size_t recs = sizeof(float4) * (size_t)g.M, msgs = sizeof(float) * (size_t)g.Epad;
-    g.det_bytes = (int)align16(eng >= 3 && msgs > recs ? msgs : recs);
+    g.det_bytes = (int)align16(kind >= 3 && msgs > recs ? msgs : recs);
     const size_t per_warp = warp_smem_bytes(g);
     int max_optin = 0, sms = 0;
     if (cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
@@ -1251,11 +1373,11 @@ size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long 
     v.round_ctr = ctr ? reinterpret_cast<int*>(ctr + sizeof(Counters)) : nullptr;
     v.desc = reinterpret_cast<RunDesc*>(desc);
     v.stats = reinterpret_cast<unsigned long long*>(stats);
-    v.seedE = (float*)take(sizeof(float) * (size_t)S * (size_t)g.Epad);
+    v.seedE = (unsigned char*)take((size_t)S * snap_bytes(g));
     v.seedBits = (uint32_t*)take(sizeof(uint32_t) * (size_t)S * SB);
     v.seedMeta = (SlotMeta*)take(sizeof(SlotMeta) * (size_t)S);
     v.seed_shot = (int*)take(sizeof(int) * (size_t)S);
-    v.slotE = (float*)take(sizeof(float) * 2 * (size_t)A * W2 * (size_t)g.Epad);
+    v.slotE = (unsigned char*)take(2 * (size_t)A * W2 * snap_bytes(g));
     v.slotBits = (uint32_t*)take(sizeof(uint32_t) * 2 * (size_t)A * W2 * SB);
     v.slotMeta = (SlotMeta*)take(sizeof(SlotMeta) * 2 * (size_t)A * W2);
     v.shot_of = (int*)take(sizeof(int) * (size_t)A);
@@ -1267,6 +1389,7 @@ size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long 
     v.res_w = (long long*)take(sizeof(long long) * (size_t)A * NR);
     v.res_origin = (int*)take(sizeof(int) * (size_t)A * NR);
     v.res_n = (int*)take(sizeof(int) * (size_t)A);
+    v.near = (int*)take(sizeof(int) * (size_t)A);
     v.items = (int2*)take(sizeof(int2) * 2 * (size_t)A * W2);
     if (w) *w = v;
     return off;
@@ -1293,6 +1416,68 @@ int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, c
 #undef X
         default: return -5;
     }
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+}  // namespace bsd
+
+// ----------------------------------------------------------------------------
+// single-precision re-runs of near-tie shots (16-bit messages)
+// ----------------------------------------------------------------------------
+namespace bsd {
+
+__global__ void k_collect_flagged(const uint32_t* __restrict__ status, long long B, long long* list, int* count)
+{
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x)
+        if (status[b] & ST_NEAR) list[atomicAdd(count, 1)] = b;
+}
+
+__global__ void k_gather_rows(const uint32_t* __restrict__ src, const long long* __restrict__ list, int n, int W,
+                              uint32_t* __restrict__ dst)
+{
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < (long long)n * W;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = k / W, q = k % W;
+        dst[k] = src[list[i] * W + q];
+    }
+}
+
+__global__ void k_scatter_results(const long long* __restrict__ list, int n, int WN, int WK, Outputs from, Outputs to)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = list[i];
+        for (int q = 0; q < WN; ++q) to.corr[b * WN + q] = from.corr[i * WN + q];
+        if (to.obs != nullptr)
+            for (int q = 0; q < WK; ++q) to.obs[b * WK + q] = from.obs[i * WK + q];
+        to.status[b] = from.status[i] | ST_NEAR | ST_RERUN;
+        if (to.iters != nullptr) to.iters[b] = from.iters[i];
+    }
+}
+
+int launch_collect_flagged(const uint32_t* status, long long B, long long* list, int* count, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(count, 0, sizeof(int), s) != cudaSuccess) return -2;
+    long long blocks = (B + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_collect_flagged<<<(int)(blocks > 0 ? blocks : 1), 256, 0, s>>>(status, B, list, count);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_gather_rows(const uint32_t* src, const long long* list, int n, int W, uint32_t* dst, void* stream)
+{
+    long long blocks = ((long long)n * W + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_gather_rows<<<(int)(blocks > 0 ? blocks : 1), 256, 0, (cudaStream_t)stream>>>(src, list, n, W, dst);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_scatter_results(const long long* list, int n, int WN, int WK, const Outputs& from, const Outputs& to,
+                           void* stream)
+{
+    long long blocks = ((long long)n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_scatter_results<<<(int)(blocks > 0 ? blocks : 1), 256, 0, (cudaStream_t)stream>>>(list, n, WN, WK, from, to);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -79,7 +79,9 @@ extern "C" int bsd_decode_noalloc(const bsd_decoder* dec, const uint32_t* d_synd
     const DecCfg* cfg;
     const LaunchShape* ls;
     int device;
-    if (!dec || B < 0 || decoder_view(dec, &g, &cfg, &ls, &device) != BSD_OK) return BSD_ERR_INVALID_ARG;
+    if (!dec || B < 0) return BSD_ERR_INVALID_ARG;
+    const int vrc = decoder_view(dec, &g, &cfg, &ls, &device);
+    if (vrc != BSD_OK) return vrc;
     if (B == 0) return BSD_OK;
     if (!d_syndromes || !d_corrections || !d_status || (g->K > 0 && !d_obs_flips)) return BSD_ERR_INVALID_ARG;
     long long S, A;
