@@ -36,7 +36,8 @@ class _Params(C.Structure):
                 ("initial_iters", C.c_int32), ("iters_per_round", C.c_int32),
                 ("num_results", C.c_int32), ("prune_mode", C.c_int32),
                 ("ms_scale", C.c_double), ("llr_clamp", C.c_double),
-                ("msg_storage", C.c_int32), ("pad0", C.c_int32), ("tie_guard", C.c_double)]
+                ("msg_storage", C.c_int32), ("pad0", C.c_int32), ("tie_guard", C.c_double),
+                ("weights", C.c_void_p), ("weights_iters", C.c_int32), ("pad1", C.c_int32)]
 
 
 class _Trace(C.Structure):
@@ -61,11 +62,18 @@ class Params:
     prune_mode: int = 0      # 0: bounded insert (App. B), 1: collect then prune (Alg. 3)
     msg_storage: int = 0     # float build: 0 float messages, 1 binary16, 2 bfloat16
     tie_guard: float = 0.0   # near-tie flag (status bit 8) on argmin / pruning margins in (0, tie_guard)
+    weights: object = None   # optional float32 [T, E]: w_{e,t} in place of ms_scale (CSR edge order)
 
     def _c(self) -> _Params:
+        w, T = None, 0
+        if self.weights is not None:
+            self._w32 = np.ascontiguousarray(self.weights, np.float32)
+            if self._w32.ndim != 2:
+                raise ValueError("weights must be [T, E]")
+            w, T = self._w32.ctypes.data, int(self._w32.shape[0])
         return _Params(self.max_rounds, self.beam_width, self.initial_iters, self.iters_per_round,
                        self.num_results, self.prune_mode, float(self.ms_scale), float(self.llr_clamp),
-                       int(self.msg_storage), 0, float(self.tie_guard))
+                       int(self.msg_storage), 0, float(self.tie_guard), w, T, 0)
 
 
 _LIBS: dict[str, C.CDLL] = {}

@@ -80,6 +80,9 @@ typedef struct {
     int32_t msg_storage;     /* float build: 0 messages kept in float, 1 binary16, 2 bfloat16 */
     int32_t pad0;
     double tie_guard;        /* near-tie flag threshold on argmin and pruning margins (0: off) */
+    const float *weights;    /* optional [weights_iters][E] per-edge weights in place of alpha, CSR edge order */
+    int32_t weights_iters;   /* iteration t of a BP call uses row min(t, weights_iters) - 1 */
+    int32_t pad1;
 } oracle_params;
 
 typedef struct {
@@ -299,6 +302,11 @@ static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *
     c->min_gap = INFINITY;
 
     for (int t = 1; t <= c->max_iters; ++t) {
+        /* weighted min-sum: w_{e,t} in place of alpha, t counted from 1 in
+           every BP call, the last row reused beyond weights_iters */
+        const float *wt = NULL;
+        if (prm->weights && prm->weights_iters > 0)
+            wt = prm->weights + (size_t)((t < prm->weights_iters ? t : prm->weights_iters) - 1) * (size_t)E;
         /* Eq. 1, ignoring masked nodes: D_{i->j} is not formed for a masked j,
            and masked neighbours j' do not enter the product or the minimum */
         for (int i = 0; i < M; ++i) {
@@ -316,7 +324,7 @@ static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *
                     if (ax < mn) mn = ax;
                     if (x < 0) neg ^= 1;             /* R2 */
                 }
-                real d = alpha * mn;                 /* R1 */
+                real d = (wt ? (real)wt[e] : alpha) * mn;   /* R1 */
                 w->D[e] = neg ? -d : d;
             }
         }
