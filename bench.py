@@ -43,6 +43,11 @@ WORKLOAD = "bb144_code_capacity beam32_340iters alpha=0.625 p={0.01,0.03,0.05}"
 OPS_PER_UPDATE = 12
 LANES_PER_SM = 128          # FP32/INT32 lanes per Blackwell SM
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+# phenomenological DEM of the [[144,12,12]] code (12 noisy rounds + 1 perfect, 936 x 2592, 6912 edges)
+PHEN_PS = (1e-3, 2e-3, 3e-3)
+PHEN_SHOTS = 100_000
+PHEN_PRESET = "beam64_640iters"
+PHEN_WORKLOAD = "bb144_phenomenological_dem beam64_640iters alpha=0.625 p=q={1e-3,2e-3,3e-3}"
 
 
 def parse():
@@ -57,7 +62,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ps", default="0.01,0.03,0.05", help="physical error rates (a smaller case for profiling)")
     ap.add_argument("--workspace-gb", type=float, default=32.0, help="device workspace per decoder")
+    ap.add_argument("--workload", choices=("bb144_code_capacity", "phenom_precision"), default="bb144_code_capacity",
+                    help="phenom_precision: the phenomenological DEM with FP32, FP16 and BF16 message storage")
     a = ap.parse_args()
+    if a.workload == "phenom_precision":
+        if a.ps == "0.01,0.03,0.05":
+            a.ps = ",".join(str(x) for x in PHEN_PS)
+        if a.shots == 1_000_000:
+            a.shots = PHEN_SHOTS
     a.ps = tuple(float(x) for x in a.ps.split(","))
     return a
 
@@ -130,6 +142,16 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+def make_phen_workload(rank: int, shots: int, ps=PHEN_PS):
+    from paper_2512_07057_gb300 import workloads as W
+    out = []
+    for p in ps:
+        prob = W.bb_phenomenological(12, 6, 12, p, p)
+        sh = W.sample_shots(prob, shots, W.shot_seed(f"bb144_phen_p{p}", rank))
+        out.append((p, prob, sh))
+    return out
+
+
 def make_workload(rank: int, shots: int, ps=PS):
     from paper_2512_07057_gb300 import workloads as W
     out = []
@@ -151,14 +173,14 @@ def ler_of(prob, shots, obs, status):
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline line and reference arm)
 # ----------------------------------------------------------------------------
-def oracle_rate(work, target_s: float, nthreads: int):
+def oracle_rate(work, target_s: float, nthreads: int, preset: str = PRESET):
     """Oracle (double precision) on a bounded prefix of each p batch, sized
     from a short calibration run so the whole sample takes about target_s."""
     import oracle
     per = []
     for p, prob, sh in work:
         g = oracle.Graph(prob, "f64")
-        prm = oracle.preset(PRESET, ms_scale=ALPHA)
+        prm = oracle.preset(preset, ms_scale=ALPHA)
         n0 = min(2000, sh.B)
         t0 = time.perf_counter()
         g.decode_batch(sh.syndromes[:n0], prm, nthreads=nthreads)
@@ -183,13 +205,15 @@ def cores() -> int:
 def run_reference(args, rank: int):
     if rank != 0:
         return
-    work = make_workload(0, min(args.shots, 200_000), args.ps)
+    phen = args.workload == "phenom_precision"
+    work = (make_phen_workload if phen else make_workload)(0, min(args.shots, 200_000), args.ps)
+    preset = PHEN_PRESET if phen else PRESET
     nth = cores()
     import oracle
     gs = [(oracle.Graph(prob, "f64"), sh) for _, prob, sh in work]
-    prm = oracle.preset(PRESET, ms_scale=ALPHA)
+    prm = oracle.preset(preset, ms_scale=ALPHA)
     # one step: a bounded equal-size prefix of each p batch
-    rate, n, _ = oracle_rate(work, 8.0, nth)
+    rate, n, _ = oracle_rate(work, 8.0, nth, preset)
     for _ in range(args.warmup):
         for g, sh in gs:
             g.decode_batch(sh.syndromes[:max(1000, n // 10)], prm, nthreads=nth)
@@ -203,10 +227,86 @@ def run_reference(args, rank: int):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "shots_per_p_per_step": n, "l2": "n/a (host)"},
+            "config": {"workload": PHEN_WORKLOAD if phen else WORKLOAD, "shots_per_p_per_step": n,
+                       "l2": "n/a (host)"},
             "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": nth, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def alu_roofline(prof, E: int, dev: int, traffic_case: str):
+    """Roofline of the dominant BP kernel from per-kernel event times.
+
+    Algorithmic lane operations of a launch = OPS_PER_UPDATE x the BP
+    iterations it executed (counted on the device) x E; the peak is the
+    lane-operation rate of the chip at its maximum SM clock."""
+    import torch
+    ms_kind = np.sum([pr["ms"] for pr in prof], axis=0)
+    launches = np.sum([pr["launches"] for pr in prof], axis=0)
+    exec_iters = np.sum([pr["exec_iters"] for pr in prof], axis=0).astype(np.float64)
+    names = ("k_seed", "k_round", "k_select")
+    pk, pk_kind = peaks()
+    sm_mhz_max = float(pk.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak_tops = sms * LANES_PER_SM * sm_mhz_max * 1e6 / 1e12
+    # the selection kernel runs no BP, so its share is reported but it is never the roofline kernel
+    dom = int(np.argmax(ms_kind[:2]))
+    dom_iters = exec_iters[dom]
+    dom_updates_per_launch = dom_iters * E / max(1, launches[dom])
+    dom_ms_per_launch = ms_kind[dom] / max(1, launches[dom])
+    achieved = OPS_PER_UPDATE * dom_updates_per_launch / (dom_ms_per_launch * 1e-3) / 1e12
+    roofline = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": alu_peak_tops,
+                "unit": "Tops/s", "frac": achieved / alu_peak_tops, "traffic": None,
+                "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz (sm_max_mhz {pk_kind})",
+                "ops_per_msg_update": OPS_PER_UPDATE,
+                "msg_updates_per_launch": dom_updates_per_launch, "launch_ms": dom_ms_per_launch,
+                "kernel_share": float(ms_kind[dom] / max(ms_kind.sum(), 1e-9)),
+                "measured_in": "second timed region: same steps, each kernel launched alone between CUDA events "
+                               "on the decode stream"}
+    # DRAM bytes per candidate-iteration from an ncu capture of a smaller case
+    # (profiles/), scaled to this run's average launch; null once the kernel
+    # sources differ from the ones that were captured
+    tr = _traffic_record(names[dom], E)
+    if tr is not None:
+        roofline["traffic"] = tr * (dom_iters / max(1, launches[dom]))
+        roofline["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum on a {traffic_case}, " \
+                                     "scaled by candidate-iterations"
+    return roofline, exec_iters
+
+
+def timed_region(decs, step, flush, stream, dev, steps, world, rank, profiled: bool, sample_clocks: bool):
+    """`steps` calls of step() between barrier + synchronize; L2 flushed before
+    each step outside the step events.  Returns (ms per step list, wall s,
+    clocks, per-decoder profile reads)."""
+    import torch
+    import torch.distributed as dist
+    for d in decs:
+        d.profile(profiled)
+        d.profile_read()                  # reset the device counters
+    sampler = ClockSampler(dev) if (rank == 0 and sample_clocks) else None
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clk = sampler.stop() if sampler else None
+    prof = [d.profile_read() for d in decs]
+    for d in decs:
+        d.profile(False)
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)], wall, clk, prof
 
 
 # ----------------------------------------------------------------------------
@@ -246,43 +346,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         step()
     torch.cuda.synchronize(dev)
 
-    def timed_region(profiled: bool, sample_clocks: bool):
-        """K steps between barrier + synchronize; L2 flushed before each step
-        outside the step events.  Returns (ms per step list, wall s, clocks,
-        per-decoder profile reads)."""
-        for d in decs:
-            d.profile(profiled)
-            d.profile_read()                  # reset the device counters
-        sampler = ClockSampler(dev) if (rank == 0 and sample_clocks) else None
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        if sampler:
-            sampler.start()
-            time.sleep(0.3)
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            starts[k].record(stream)
-            step()
-            ends[k].record(stream)
-        torch.cuda.synchronize(dev)
-        wall = time.perf_counter() - t0
-        if world > 1:
-            dist.barrier()
-        clk = sampler.stop() if sampler else None
-        prof = [d.profile_read() for d in decs]
-        for d in decs:
-            d.profile(False)
-        return [s.elapsed_time(e) for s, e in zip(starts, ends)], wall, clk, prof
-
+    tr_args = (decs, step, flush, stream, dev, args.steps, world, rank)
     # region 1 (headline): each chunk runs as one CUDA graph
-    ms_steps, t_wall, clocks, prof_graph = timed_region(False, True)
+    ms_steps, t_wall, clocks, prof_graph = timed_region(*tr_args, profiled=False, sample_clocks=True)
     ms_total = float(sum(ms_steps))
     # region 2 (roofline): the same steps with every kernel bracketed by events
-    ms_steps_p, _, _, prof = timed_region(True, False)
+    ms_steps_p, _, _, prof = timed_region(*tr_args, profiled=True, sample_clocks=False)
     shots_per_step = sum(sh.B for _, _, sh in work)
     if world > 1:
         t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
@@ -303,41 +372,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         per_p[str(p)] = {"ler": ler_of(prob, sh, obs, st), "seed_converged": float((st == 1).mean()),
                          "beam_converged": float((st == 2).mean()), "failed": float((st == 4).mean()),
                          "mean_alg_iters": float(it.mean())}
-    ms_kind = np.sum([pr["ms"] for pr in prof], axis=0)
-    launches = np.sum([pr["launches"] for pr in prof], axis=0)
-    exec_iters = np.sum([pr["exec_iters"] for pr in prof], axis=0).astype(np.float64)
     names = ("k_seed", "k_round", "k_select")
     for (p, _, _), pr in zip(work, prof):
         per_p[str(p)]["kernel_ms_per_step"] = {n: float(x) / args.steps for n, x in zip(names, pr["ms"])}
-    dom = int(np.argmax(ms_kind))
-    pk, pk_kind = peaks()
-    sm_mhz_max = float(pk.get("sm_max_mhz", 2070.0))
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_peak_tops = sms * LANES_PER_SM * sm_mhz_max * 1e6 / 1e12
-    # executed message updates of the dominant kernel (all edges of every candidate-iteration it ran);
-    # the selection kernel runs no BP, so its share is reported but it is never the roofline kernel
-    if dom == 2:
-        dom = int(np.argmax(ms_kind[:2]))
-    dom_iters = exec_iters[dom]
-    dom_updates_per_launch = dom_iters * E / max(1, launches[dom])
-    dom_ms_per_launch = ms_kind[dom] / max(1, launches[dom])
-    achieved = OPS_PER_UPDATE * dom_updates_per_launch / (dom_ms_per_launch * 1e-3) / 1e12
-    roofline = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": alu_peak_tops,
-                "unit": "Tops/s", "frac": achieved / alu_peak_tops, "traffic": None,
-                "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz (sm_max_mhz {pk_kind})",
-                "ops_per_msg_update": OPS_PER_UPDATE,
-                "msg_updates_per_launch": dom_updates_per_launch, "launch_ms": dom_ms_per_launch,
-                "kernel_share": float(ms_kind[dom] / max(ms_kind.sum(), 1e-9)),
-                "measured_in": "second timed region: same steps, each kernel launched alone between CUDA events "
-                               "on the decode stream"}
-    # DRAM bytes per candidate-iteration from an ncu capture of a smaller case
-    # (profiles/), scaled to this run's average launch; null once the kernel
-    # sources differ from the ones that were captured
-    tr = _traffic_record(names[dom])
-    if tr is not None:
-        roofline["traffic"] = tr * (dom_iters / max(1, launches[dom]))
-        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum on a 16000-shot case, " \
-                                     "scaled by candidate-iterations"
+    roofline, exec_iters = alu_roofline(prof, E, dev, "16000-shot case")
+    pk, _ = peaks()
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     steps_total_s = ms_total_max * 1e-3
     value = world * shots_per_step * args.steps / steps_total_s
@@ -378,6 +417,123 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         d.close()
 
 
+def run_precision(args, rank: int, world: int, local_rank: int):
+    """The phenomenological DEM decoded with FP32 (the plain path), FP16 and
+    BF16 message storage, side by side; the line's value is the FP16 form.
+    The cpu_baseline leg decodes a bounded prefix with the double-precision
+    oracle and states, per form, how many decisions differ from it."""
+    import torch
+    import torch.distributed as dist
+
+    from __graft_entry__ import build
+    from paper_2512_07057_gb300 import binding as B
+    from paper_2512_07057_gb300 import decoder as D
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+        build()
+    work = make_phen_workload(rank, args.shots, args.ps)
+    synd = [D.to_torch_words(sh.syndromes, dev) for _, _, sh in work]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream(dev)
+    E = work[0][1].n_edges
+    shots_per_step = sum(sh.B for _, _, sh in work)
+    forms, host_out, e2e = {}, {}, None
+    for name, prec in (("fp32", B.BSD_FP32), ("fp16", B.BSD_FP16), ("bf16", B.BSD_BF16)):
+        decs, outs = [], []
+        for p, prob, sh in work:
+            params = D.make_params(PHEN_PRESET, ms_scale=ALPHA, msg_precision=prec,
+                                   workspace_bytes=int(args.workspace_gb * (1 << 30)))
+            decs.append(D.BeamSearchDecoder(prob, params, device=dev))
+            outs.append(decs[-1].alloc_outputs(sh.B))
+
+        def step():
+            for d, s, o in zip(decs, synd, outs):
+                d.decode(s, o, stream=stream)
+
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step()
+        torch.cuda.synchronize(dev)
+        tr_args = (decs, step, flush, stream, dev, args.steps, world, rank)
+        ms_steps, _, clocks, prof_graph = timed_region(*tr_args, profiled=False, sample_clocks=True)
+        _, _, _, prof = timed_region(*tr_args, profiled=True, sample_clocks=False)
+        ms_total = float(sum(ms_steps))
+        if world > 1:
+            t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_total = float(t.item())
+        roofline, exec_iters = alu_roofline(prof, E, dev, "small case of the same DEM")
+        per_p = {}
+        for (p, prob, sh), o in zip(work, outs):
+            st = D.from_torch_words(o.status)
+            it = D.from_torch_words(o.iters).astype(np.int64)
+            per_p[str(p)] = {"ler": ler_of(prob, sh, D.from_torch_words(o.obs_flips), st & 7),
+                             "seed_converged": float(((st & 7) == 1).mean()),
+                             "beam_converged": float(((st & 7) == 2).mean()),
+                             "failed": float(((st & 7) == 4).mean()),
+                             "near_tie_flagged": float(((st & B.BSD_STATUS_NEAR_TIE) > 0).mean()),
+                             "fp32_rerun": float(((st & B.BSD_STATUS_FP32_RERUN) > 0).mean()),
+                             "mean_alg_iters": float(it.mean())}
+            host_out[(name, p)] = (D.from_torch_words(o.corrections).copy(), st.copy())
+        steps_s = ms_total * 1e-3
+        forms[name] = {"value": world * shots_per_step * args.steps / steps_s, "unit": "syndromes/s",
+                       "ms_per_step": ms_total / args.steps, "msg_bytes": 4 if prec == B.BSD_FP32 else 2,
+                       "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / args.steps,
+                                                  "round": float(exec_iters[1]) / args.steps},
+                       "roofline": roofline, "gpu_launches": int(sum(pr["kernel_launches"] for pr in prof_graph)),
+                       "clocks": clocks, "per_p": per_p}
+        if name == "fp16" and rank == 0 and not args.no_e2e:
+            e2e = e2e_host(decs, work, args, dev)
+        for d in decs:
+            d.close()
+    main_form = forms["fp16"]
+    line = {
+        "metric": METRIC, "value": main_form["value"], "unit": "syndromes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_form["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "msg_storage": "f16",
+        "data": "synthetic",
+        "config": {"workload": PHEN_WORKLOAD, "code": "[[144,12,12]] phenomenological DEM, 936 x 2592, 6912 edges",
+                   "shots_per_p_per_gpu": args.shots, "syndromes_per_step_per_gpu": shots_per_step,
+                   "l2": "flushed before every timed step (256 MiB write outside the step events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": main_form["roofline"], "gpu_launches": main_form["gpu_launches"], "clocks": main_form["clocks"],
+        "forms": forms,
+        "fp16_vs_plain_fp32": main_form["value"] / forms["fp32"]["value"],
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        nth = cores()
+        rate, n, dt = oracle_rate(work, args.cpu_seconds, nth, PHEN_PRESET)
+        line["cpu_baseline"] = {"value": rate, "unit": "syndromes/s", "cores": nth, "kind": "oracle",
+                                "sample": f"first {n} shots of each p batch, double-precision oracle, "
+                                          f"{dt:.1f} s on {nth} host threads"}
+        # the same prefix decoded by the double-precision oracle: decisions of each form that differ
+        agree = {}
+        for p, prob, sh in work:
+            r = oracle.Graph(prob, "f64").decode_batch(sh.syndromes[:n], oracle.preset(PHEN_PRESET, ms_scale=ALPHA),
+                                                       nthreads=nth)
+            near = (r["min_gap"] > 0) & (r["min_gap"] < 1e-4)      # a margin in (0, 1e-4) relative
+            exact = r["ties"] > 0                                      # an exact tie decided by R5 / R7 / R8
+            for name in forms:
+                corr, st = host_out[(name, p)]
+                diff = (corr[:n] != r["corrections"]).any(1) | ((st[:n] & 7) != r["status"])
+                agree.setdefault(name, {})[str(p)] = {
+                    "shots": int(n), "differ": int(diff.sum()),
+                    "differ_on_fp64_near_tie": int((diff & near).sum()),
+                    "differ_on_fp64_exact_tie": int((diff & exact & ~near).sum()),
+                    "fp64_near_tie_shots": int(near.sum()), "fp64_exact_tie_shots": int(exact.sum())}
+        line["fp64_agreement"] = agree
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def e2e_host(decs, work, args, dev):
     """Same metric through bsd_decode_host: pinned host syndromes in, host results out."""
     import torch
@@ -413,8 +569,9 @@ def e2e_host(decs, work, args, dev):
             "d2h_bytes_per_step": int(d2h), "api": "bsd_decode_host (pinned host buffers)"}
 
 
-def _traffic_record(kernel: str):
-    """bytes per candidate-iteration recorded for `kernel`, if captured on the current sources."""
+def _traffic_record(kernel: str, edges: int):
+    """bytes per candidate-iteration recorded for `kernel` on a problem with
+    `edges` edges, if captured on the current sources."""
     import glob
     import re
     for path in glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_traffic_*.md")):
@@ -422,6 +579,9 @@ def _traffic_record(kernel: str):
         h = re.search(r"^source_hash: (\w+)$", txt, re.M)
         k = re.search(r"^kernel: (\w+)$", txt, re.M)
         b = re.search(r"^bytes_per_candidate_iteration: ([0-9.]+)$", txt, re.M)
+        e = re.search(r"^edges: (\d+)$", txt, re.M)
+        if e is not None and int(e.group(1)) != edges:
+            continue
         if h and k and b and k.group(1) == kernel and h.group(1) == _source_hash():
             return float(b.group(1))
     return None
@@ -450,7 +610,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "phenom_precision":
+            run_precision(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -219,8 +219,29 @@ int bsd_profile_enable(bsd_decoder *dec, int enable);
 int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2],
                      uint64_t *kernel_launches);
 
+/* Weighted min-sum: replace the scale alpha of Eq. 1 by a weight per edge and
+ * iteration, D_{i->j}(t) = w[t', e] * (-1)^{s'_i} * prod sign * min, with
+ * t' = min(t, T) - 1 and t counted from 1 in every BP call (the seed run and
+ * every child's masked run alike).  Weights come from training the unrolled
+ * decoder (bsd_unrolled_forward / bsd_unrolled_backward).
+ *   h_weights  host, float [T][E], E in the CSR edge order of H given to
+ *              bsd_create; copied, so the caller keeps ownership.  Each
+ *              weight must be finite with |w| <= 1e6.
+ *   T          rows; 0 (h_weights ignored) returns to the scale ms_scale.
+ * Waits for the work queued on the stream of the decoder's last call, then
+ * re-selects the kernels.  Errors: BSD_ERR_INVALID_ARG (bad weights),
+ * BSD_ERR_UNSUPPORTED (16-bit message storage), BSD_ERR_OOM, BSD_ERR_CUDA;
+ * on error the decoder keeps its previous weights. */
+int bsd_set_weights(bsd_decoder *dec, const float *h_weights, int32_t T);
+
 /* Static text for a return code. */
 const char *bsd_error_string(int code);
+
+/* The CUDA runtime's name and description of the most recent CUDA call made
+ * by this library on the calling thread that failed, with the library source
+ * line that checked it ("" if none): the reason behind a BSD_ERR_CUDA.  The text stays valid until the next call of
+ * this function on the same thread. */
+const char *bsd_last_cuda_error(void);
 
 /* Release the decoder's device memory.  NULL is ignored. */
 void bsd_destroy(bsd_decoder *dec);

@@ -32,7 +32,7 @@ BSD_STATUS_FAILED = 4
 # every symbol include/bsd.h declares
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
            "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_profile_enable", "bsd_profile_read",
-           "bsd_decode_noalloc", "bsd_error_string", "bsd_destroy")
+           "bsd_decode_noalloc", "bsd_set_weights", "bsd_error_string", "bsd_last_cuda_error", "bsd_destroy")
 BSD_ERR_SCRATCH = -7
 
 
@@ -46,7 +46,8 @@ class bsd_params(C.Structure):
 class BsdError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
-        super().__init__(f"{what}: {bsd_error_string(code)} ({code})")
+        detail = bsd_last_cuda_error() if code == BSD_ERR_CUDA else ""
+        super().__init__(f"{what}: {bsd_error_string(code)} ({code})" + (f" [{detail}]" if detail else ""))
 
 
 _lib = None
@@ -75,13 +76,16 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_get_info.argtypes = [P] + [C.POINTER(C.c_int32)] * 4 + [C.POINTER(C.c_int64)] * 2
     lib.bsd_decode_noalloc.argtypes = [P, P, C.c_int64, P, P, P, P, P]
     lib.bsd_profile_enable.argtypes = [P, C.c_int]
+    lib.bsd_set_weights.argtypes = [P, P, C.c_int32]
     lib.bsd_profile_read.argtypes = [P, P, P, P, P]
     lib.bsd_error_string.argtypes = [C.c_int]
     lib.bsd_error_string.restype = C.c_char_p
+    lib.bsd_last_cuda_error.argtypes = []
+    lib.bsd_last_cuda_error.restype = C.c_char_p
     lib.bsd_destroy.argtypes = [P]
     lib.bsd_destroy.restype = None
     for nm in EXPORTS:
-        if nm not in ("bsd_error_string", "bsd_destroy"):
+        if nm not in ("bsd_error_string", "bsd_last_cuda_error", "bsd_destroy"):
             getattr(lib, nm).restype = C.c_int
     _lib = lib
     return lib
@@ -95,6 +99,10 @@ def check(code: int, what: str) -> None:
 # ---- the C ABI, same names ---------------------------------------------------
 def bsd_error_string(code: int) -> str:
     return load().bsd_error_string(int(code)).decode()
+
+
+def bsd_last_cuda_error() -> str:
+    return load().bsd_last_cuda_error().decode()
 
 
 def bsd_params_default() -> bsd_params:
@@ -148,6 +156,11 @@ def bsd_get_info(dec) -> dict:
     check(load().bsd_get_info(dec, C.byref(M), C.byref(N), C.byref(K), C.byref(E), C.byref(cs), C.byref(wb)),
           "bsd_get_info")
     return dict(M=M.value, N=N.value, K=K.value, n_edges=E.value, chunk_shots=cs.value, workspace_bytes=wb.value)
+
+
+def bsd_set_weights(dec, h_weights, T: int) -> None:
+    """h_weights: host address of float32 [T][E] (CSR edge order), or None with T = 0."""
+    check(load().bsd_set_weights(dec, h_weights, int(T)), "bsd_set_weights")
 
 
 def bsd_profile_enable(dec, enable: bool) -> None:

@@ -11,6 +11,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -52,6 +53,7 @@ struct bsd_decoder {
     bsd_decoder* twin = nullptr;
     void* rr_mem = nullptr;                  // flagged list, count, gathered syndromes, re-run outputs
     long long rr_cap = 0;                    // capacity of the flagged list
+    float* weights_mem = nullptr;            // [wT][Epad] weights of weighted min-sum (bsd_set_weights)
 };
 
 namespace {
@@ -61,8 +63,8 @@ struct DeviceGuard {
     bool ok = false;
     explicit DeviceGuard(int dev)
     {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
+        if (CUDA_FAILED(cudaGetDevice(&prev))) prev = -1;
+        ok = !CUDA_FAILED(cudaSetDevice(dev));
     }
     ~DeviceGuard()
     {
@@ -105,7 +107,35 @@ T* carve(char*& p, size_t count)
 
 }  // namespace
 
+namespace bsd {
+namespace {
+thread_local cudaError_t t_last_cuda_error = cudaSuccess;
+thread_local const char* t_last_cuda_file = "";
+thread_local int t_last_cuda_line = 0;
+thread_local char t_last_cuda_text[320];
+}  // namespace
+
+bool cuda_failed_at(cudaError_t e, const char* file, int line)
+{
+    if (e == cudaSuccess) return false;
+    t_last_cuda_error = e;
+    t_last_cuda_file = file;
+    t_last_cuda_line = line;
+    return true;
+}
+}  // namespace bsd
+
 extern "C" {
+
+const char* bsd_last_cuda_error(void)
+{
+    const cudaError_t e = bsd::t_last_cuda_error;
+    if (e == cudaSuccess) return "";
+    const char* f = strrchr(bsd::t_last_cuda_file, '/');
+    snprintf(bsd::t_last_cuda_text, sizeof(bsd::t_last_cuda_text), "%s: %s (%s:%d)", cudaGetErrorName(e),
+             cudaGetErrorString(e), f ? f + 1 : bsd::t_last_cuda_file, bsd::t_last_cuda_line);
+    return bsd::t_last_cuda_text;
+}
 
 const char* bsd_error_string(int code)
 {
@@ -167,6 +197,7 @@ void bsd_destroy(bsd_decoder* dec)
         if (dec->graph) destroy_graph(dec->graph);
         if (dec->h_nactive) cudaFreeHost(dec->h_nactive);
         if (dec->rr_mem) cudaFree(dec->rr_mem);
+        if (dec->weights_mem) cudaFree(dec->weights_mem);
         for (cudaEvent_t e : dec->ev) cudaEventDestroy(e);
     }
     if (dec->twin) bsd_destroy(dec->twin);
@@ -281,7 +312,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     gb += align256(sizeof(uint32_t) * hcol.size());
     gb += align256(sizeof(uint32_t) * acol.size());
     gb += align256(sizeof(long long) * N);
-    if (cudaMalloc(&dec->graph_mem, gb) != cudaSuccess) { bsd_destroy(dec); return BSD_ERR_OOM; }
+    if (CUDA_FAILED(cudaMalloc(&dec->graph_mem, gb))) { bsd_destroy(dec); return BSD_ERR_OOM; }
     dec->graph_bytes = gb;
     char* p = (char*)dec->graph_mem;
     int* d_row_ptr = carve<int>(p, M + 1);
@@ -293,15 +324,15 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     uint32_t* d_hcol = carve<uint32_t>(p, hcol.size());
     uint32_t* d_acol = carve<uint32_t>(p, acol.size());
     long long* d_lamq = carve<long long>(p, N);
-    bool ok = cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(d_col_edge, col_edge.data(), sizeof(int) * E, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(d_col_row, col_row.data(), sizeof(int) * E, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(d_lam, lam.data(), sizeof(float) * Npad, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(d_lamE, lamE_st.data(), lamE_st.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(d_hcol, hcol.data(), sizeof(uint32_t) * hcol.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(d_acol, acol.data(), sizeof(uint32_t) * acol.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(d_lamq, lamq.data(), sizeof(long long) * N, cudaMemcpyHostToDevice) == cudaSuccess;
+    bool ok = !CUDA_FAILED(cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_col_edge, col_edge.data(), sizeof(int) * E, cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_col_row, col_row.data(), sizeof(int) * E, cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_lam, lam.data(), sizeof(float) * Npad, cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_lamE, lamE_st.data(), lamE_st.size(), cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_hcol, hcol.data(), sizeof(uint32_t) * hcol.size(), cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_acol, acol.data(), sizeof(uint32_t) * acol.size(), cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_lamq, lamq.data(), sizeof(long long) * N, cudaMemcpyHostToDevice));
     if (!ok) { bsd_destroy(dec); return BSD_ERR_CUDA; }
 
     DevGraph& g = dec->g;
@@ -326,6 +357,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     // messages when 0, no flags when negative (or 0 with single precision)
     const float tg = params->tie_guard_rel;
     cfg.tie_guard = tg > 0.f ? (double)tg : (tg == 0.f && prec == BSD_FP16) ? 1e-3 : (tg == 0.f && prec == BSD_BF16) ? 1e-2 : 0.0;
+    cfg.weights = nullptr;         // the scale alpha until bsd_set_weights
+    cfg.wT = 0;
 
     rc = configure_kernels(g, cfg, device, &dec->ls);
     if (rc) { bsd_destroy(dec); return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA; }
@@ -357,8 +390,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     Work& w = dec->w;
     work_layout(g, cfg, S, A, (char*)dec->work_mem, &w);
     dec->ctr_bytes = work_head_bytes(cfg);
-    if (cudaMemset(dec->work_mem, 0, dec->ctr_bytes) != cudaSuccess ||
-        cudaMallocHost(&dec->h_nactive, sizeof(int)) != cudaSuccess) {
+    if (CUDA_FAILED(cudaMemset(dec->work_mem, 0, dec->ctr_bytes)) ||
+        CUDA_FAILED(cudaMallocHost(&dec->h_nactive, sizeof(int)))) {
         bsd_destroy(dec);
         return BSD_ERR_CUDA;
     }
@@ -394,7 +427,7 @@ static int rerun_flagged(bsd_decoder* dec, const uint32_t* d_synd, long long B, 
         dec->rr_cap = 0;
         const size_t need = align256(sizeof(long long) * (size_t)B) + 256 +
                             align256(sizeof(uint32_t) * (size_t)R * (g.WM + g.WN + WKo + 2));
-        if (cudaMalloc(&dec->rr_mem, need) != cudaSuccess) { cudaGetLastError(); return BSD_ERR_OOM; }
+        if (CUDA_FAILED(cudaMalloc(&dec->rr_mem, need))) { cudaGetLastError(); return BSD_ERR_OOM; }
         dec->rr_cap = B;
     }
     char* p = (char*)dec->rr_mem;
@@ -407,8 +440,8 @@ static int rerun_flagged(bsd_decoder* dec, const uint32_t* d_synd, long long B, 
     uint32_t* gst = carve<uint32_t>(p, (size_t)R);
     uint32_t* git = carve<uint32_t>(p, (size_t)R);
     if (launch_collect_flagged(o.status, B, list, count, s) != 0 ||
-        cudaMemcpyAsync(dec->h_nactive, count, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+        CUDA_FAILED(cudaMemcpyAsync(dec->h_nactive, count, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+        CUDA_FAILED(cudaStreamSynchronize(s)))
         return BSD_ERR_CUDA;
     const long long n = *dec->h_nactive;
     for (long long off = 0; off < n; off += R) {
@@ -427,7 +460,7 @@ static size_t prof_event(bsd_decoder* d)
 {
     if (d->ev_used == d->ev.size()) {
         cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+        if (CUDA_FAILED(cudaEventCreate(&e))) return (size_t)-1;
         d->ev.push_back(e);
     }
     return d->ev_used++;
@@ -515,7 +548,7 @@ int bsd_decode_host(bsd_decoder* dec, const uint32_t* h_syndromes, int64_t B, ui
         if (dec->io_mem) cudaFree(dec->io_mem);
         dec->io_mem = nullptr;
         dec->io_bytes = 0;
-        if (cudaMalloc(&dec->io_mem, need) != cudaSuccess) { cudaGetLastError(); return BSD_ERR_OOM; }
+        if (CUDA_FAILED(cudaMalloc(&dec->io_mem, need))) { cudaGetLastError(); return BSD_ERR_OOM; }
         dec->io_bytes = need;
     }
     char* p = (char*)dec->io_mem;
@@ -527,25 +560,24 @@ int bsd_decode_host(bsd_decoder* dec, const uint32_t* h_syndromes, int64_t B, ui
     Outputs o{d_c, g.K > 0 ? d_o : nullptr, d_st, h_iters ? d_it : nullptr};
     for (long long base = 0; base < B; base += C) {
         const long long n = (B - base) < C ? (B - base) : C;
-        if (cudaMemcpyAsync(d_s, h_syndromes + base * g.WM, sizeof(uint32_t) * n * g.WM, cudaMemcpyHostToDevice, s) !=
-            cudaSuccess)
+        if (CUDA_FAILED(cudaMemcpyAsync(d_s, h_syndromes + base * g.WM, sizeof(uint32_t) * n * g.WM, cudaMemcpyHostToDevice, s)))
             return BSD_ERR_CUDA;
         int rc = decode_impl(dec, d_s, 0, n, o, s);
         if (rc) return rc;
         // a re-run needs iteration counts to scatter: use the staging buffer
         Outputs o_rr{d_c, g.K > 0 ? d_o : nullptr, d_st, d_it};
         if (dec->twin && (rc = rerun_flagged(dec, d_s, n, o_rr, s)) != BSD_OK) return rc;
-        bool ok = cudaMemcpyAsync(h_corrections + base * g.WN, d_c, sizeof(uint32_t) * n * g.WN,
-                                  cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-                  cudaMemcpyAsync(h_status + base, d_st, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        bool ok = !CUDA_FAILED(cudaMemcpyAsync(h_corrections + base * g.WN, d_c, sizeof(uint32_t) * n * g.WN,
+                                  cudaMemcpyDeviceToHost, s)) &&
+                  !CUDA_FAILED(cudaMemcpyAsync(h_status + base, d_st, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
         if (ok && g.K > 0)
-            ok = cudaMemcpyAsync(h_obs_flips + base * g.WK, d_o, sizeof(uint32_t) * n * g.WK, cudaMemcpyDeviceToHost,
-                                 s) == cudaSuccess;
+            ok = !CUDA_FAILED(cudaMemcpyAsync(h_obs_flips + base * g.WK, d_o, sizeof(uint32_t) * n * g.WK, cudaMemcpyDeviceToHost,
+                                 s));
         if (ok && h_iters)
-            ok = cudaMemcpyAsync(h_iters + base, d_it, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+            ok = !CUDA_FAILED(cudaMemcpyAsync(h_iters + base, d_it, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
         if (!ok) return BSD_ERR_CUDA;
     }
-    return cudaStreamSynchronize(s) == cudaSuccess ? BSD_OK : BSD_ERR_CUDA;
+    return !CUDA_FAILED(cudaStreamSynchronize(s)) ? BSD_OK : BSD_ERR_CUDA;
 }
 
 int bsd_bp_llr(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, int32_t T, float* d_llr, float* d_sum_llr,
@@ -566,14 +598,58 @@ int bsd_sync_error(bsd_decoder* dec)
     if (!dec) return BSD_ERR_INVALID_ARG;
     DeviceGuard dg(dec->device);
     if (!dg.ok) return BSD_ERR_CUDA;
-    if (cudaStreamSynchronize(dec->last_stream) != cudaSuccess) return BSD_ERR_CUDA;
+    if (CUDA_FAILED(cudaStreamSynchronize(dec->last_stream))) return BSD_ERR_CUDA;
     Counters c;
-    if (cudaMemcpy(&c, dec->w.ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return BSD_ERR_CUDA;
+    if (CUDA_FAILED(cudaMemcpy(&c, dec->w.ctr, sizeof(c), cudaMemcpyDeviceToHost))) return BSD_ERR_CUDA;
     if (c.err != 0) {
         const int zero = 0;
         cudaMemcpy(&dec->w.ctr->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
         return c.err == 1 ? BSD_ERR_TIMEOUT : BSD_ERR_DEVICE;
     }
+    return BSD_OK;
+}
+
+int bsd_set_weights(bsd_decoder* dec, const float* h_weights, int32_t T)
+{
+    if (!dec || T < 0 || (T > 0 && !h_weights)) return BSD_ERR_INVALID_ARG;
+    if (T > 0 && dec->g.prec != BSD_FP32) return BSD_ERR_UNSUPPORTED;
+    const size_t E = (size_t)dec->g.E, Epad = (size_t)dec->g.Epad;
+    for (size_t k = 0; k < (size_t)T * E; ++k)
+        if (!std::isfinite(h_weights[k]) || std::fabs(h_weights[k]) > 1e6f) return BSD_ERR_INVALID_ARG;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    // work already queued on the decoder's stream uses the current kernels and weights
+    if (CUDA_FAILED(cudaStreamSynchronize(dec->last_stream))) return BSD_ERR_CUDA;
+    float* d_w = nullptr;
+    if (T > 0) {
+        std::vector<float> hw((size_t)T * Epad, 0.f);
+        for (size_t t = 0; t < (size_t)T; ++t)
+            std::memcpy(hw.data() + t * Epad, h_weights + t * E, sizeof(float) * E);
+        if (CUDA_FAILED(cudaMalloc(&d_w, sizeof(float) * hw.size()))) return BSD_ERR_OOM;
+        if (CUDA_FAILED(cudaMemcpy(d_w, hw.data(), sizeof(float) * hw.size(), cudaMemcpyHostToDevice))) {
+            cudaFree(d_w);
+            return BSD_ERR_CUDA;
+        }
+    }
+    DecCfg cfg = dec->cfg;
+    cfg.weights = d_w;
+    cfg.wT = T;
+    DevGraph g = dec->g;
+    LaunchShape ls{};
+    const int rc = configure_kernels(g, cfg, dec->device, &ls);
+    if (rc) {
+        if (d_w) cudaFree(d_w);
+        return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA;
+    }
+    void* graph = nullptr;
+    if (build_graph(g, cfg, dec->w, ls, &graph) != 0) graph = nullptr;
+    if (dec->graph) destroy_graph(dec->graph);
+    if (dec->weights_mem) cudaFree(dec->weights_mem);
+    dec->graph = graph;
+    dec->g = g;
+    dec->cfg = cfg;
+    dec->ls = ls;
+    dec->weights_mem = d_w;
     return BSD_OK;
 }
 
@@ -590,11 +666,11 @@ int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64
     if (!dec) return BSD_ERR_INVALID_ARG;
     DeviceGuard dg(dec->device);
     if (!dg.ok) return BSD_ERR_CUDA;
-    if (cudaStreamSynchronize(dec->last_stream) != cudaSuccess) return BSD_ERR_CUDA;
+    if (CUDA_FAILED(cudaStreamSynchronize(dec->last_stream))) return BSD_ERR_CUDA;
     prof_collect(dec);
     unsigned long long st[4] = {0, 0, 0, 0};
-    if (cudaMemcpy(st, dec->w.stats, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemset(dec->w.stats, 0, sizeof(st)) != cudaSuccess)
+    if (CUDA_FAILED(cudaMemcpy(st, dec->w.stats, sizeof(st), cudaMemcpyDeviceToHost)) ||
+        CUDA_FAILED(cudaMemset(dec->w.stats, 0, sizeof(st))))
         return BSD_ERR_CUDA;
     for (int k = 0; k < 3; ++k) {
         if (ms) ms[k] = dec->ms[k];

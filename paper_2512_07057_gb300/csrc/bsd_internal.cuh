@@ -52,6 +52,8 @@ struct DecCfg {
     int max_rounds, w, initial_iters, iters_per_round, num_results;
     float alpha, L;        // L: L_MAX as the storage format holds it
     double tie_guard;      // near-tie margin (0: no flags)
+    const float* weights;  // optional [wT][Epad]: w_{e,t} in place of alpha (weighted engines only)
+    int wT;                // iteration t of a BP call uses row min(t, wT) - 1
 };
 
 struct SlotMeta {
@@ -123,6 +125,11 @@ struct Work {
 // workspace layout for S seed entries and A window entries starting at base
 // (base may be null to size it); returns the bytes used.  The counters and the
 // run descriptor come first, in the first head_bytes(cfg) bytes.
+// true if e is an error; the error and the source line of the call are then
+// kept as the calling thread's most recent CUDA failure (bsd_last_cuda_error)
+bool cuda_failed_at(cudaError_t e, const char* file, int line);
+#define CUDA_FAILED(x) ::bsd::cuda_failed_at((x), __FILE__, __LINE__)
+
 size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w);
 size_t work_head_bytes(const DecCfg& cfg);
 

@@ -149,7 +149,7 @@ __device__ inline unsigned long long fixq(float x)
 // st.ehat holds e^(t) of the last iteration (masked positions 0), st.sumllr
 // holds the sum over the iterations run of Lambda_j(t).  If post_out is not
 // null, Lambda_j(max_iters) is written there.
-template <int DV, int P>
+template <int DV, int P, bool W>
 __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
                           bool stop, int* success, float* post_out)
 {
@@ -162,6 +162,8 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
     int ok = 0;
     for (int t = 1; t <= max_iters; ++t) {
         for (int q = lane; q < g.WM; q += 32) st.par[q] = st.sp[q];
+        // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
+        const float* wt = W ? cfg.weights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
 
         // ---- detector pass (Eq. 1): min1, min2, argmin and sign parity per row
         for (int i = lane; i < g.M; i += 32) {
@@ -199,7 +201,7 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
                         const float xo = S::ld(E, e);
                         const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
                         const uint32_t sg = __float_as_uint(s4.w) ^ ((xo < 0.f) ? 1u : 0u);
-                        const float d = __fmul_rn(alpha, m);
+                        const float d = __fmul_rn(W ? __ldg(wt + e) : alpha, m);
                         v[k] = sg ? -d : d;
                         ed[k] = e;
                     } else {
@@ -322,7 +324,7 @@ __device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, 
 // ----------------------------------------------------------------------------
 // GenericEngine: any code whose column degree is at most DV; graph tables
 // are read from global memory (L1-resident) and sum_LLR lives in shared memory.
-template <int DV, int P>
+template <int DV, int P, bool W = false>
 struct GenericEngine {
     static constexpr int kMinBlocks = 1;
     static constexpr int kPrec = P;
@@ -334,7 +336,7 @@ struct GenericEngine {
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
                        int* success, float* post_out)
     {
-        return bp_iterate<DV, P>(g, cfg, st, max_iters, stop, success, post_out);
+        return bp_iterate<DV, P, W>(g, cfg, st, max_iters, stop, success, post_out);
     }
     __device__ void argmin_score(const DevGraph& g, const WarpState& st, double guard, int* np, long long* S,
                                  int* tie)
@@ -357,7 +359,7 @@ struct GenericEngine {
 // sums of three messages are formed from min / max / median directly.  Every
 // value it produces is the one GenericEngine produces (same operations, same
 // order).
-template <int CPL, int RPL, int RD, int P>
+template <int CPL, int RPL, int RD, int P, bool W = false>
 struct SmallEngine {
     static constexpr int kMinBlocks = 2;   // at most 128 registers: two 8-warp blocks per SM
     static constexpr int kPrec = P;
@@ -404,6 +406,8 @@ struct SmallEngine {
         int ok = 0;
         for (int t = 1; t <= max_iters; ++t) {
             for (int q = lane; q < g.WM; q += 32) st.par[q] = st.sp[q];
+            // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
+            const float* wt = W ? cfg.weights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
             // ---- detector pass (Eq. 1)
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
@@ -440,10 +444,13 @@ struct SmallEngine {
 #pragma unroll
                     for (int h = 0; h < RD / 2; ++h) {
                         float dd[2];
+                        float2 w2 = make_float2(alpha, alpha);
+                        if (W) w2 = __ldg(reinterpret_cast<const float2*>(wt + eb + 2 * h));
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             const int k = 2 * h + u;
-                            const float d = (fabsf(x[k]) == m1) ? d2 : d1;
+                            const float d = W ? __fmul_rn(u ? w2.y : w2.x, (fabsf(x[k]) == m1) ? m2 : m1)
+                                              : ((fabsf(x[k]) == m1) ? d2 : d1);
                             dd[u] = __uint_as_float(__float_as_uint(d) ^ ((nb ^ __float_as_uint(x[k])) & 0x80000000u));
                         }
                         dr[h] = make_float2(dd[0], dd[1]);
@@ -1102,9 +1109,10 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_bp_llr(DevGraph g, Dec
 // ----------------------------------------------------------------------------
 // host-side launch helpers
 // ----------------------------------------------------------------------------
-// engine id = 3 * kind + storage precision; kinds: 0..2 generic with column
-// degree bound 3 / 6 / 16, 3: small (CPL 3, RPL 2, row degree 6), 4: small
-// (CPL 5, RPL 3, row degree 6); precision 0 float, 1 binary16, 2 bfloat16
+// engine id = 3 * kind + storage precision, or 15 + kind for weighted min-sum;
+// kinds: 0..2 generic with column degree bound 3 / 6 / 16, 3: small (CPL 3,
+// RPL 2, row degree 6), 4: small (CPL 5, RPL 3, row degree 6); precision 0
+// float, 1 binary16, 2 bfloat16
 #define BSD_KIND_ALIASES(P, SFX)                          \
     using Generic3##SFX = GenericEngine<3, P>;            \
     using Generic6##SFX = GenericEngine<6, P>;            \
@@ -1114,19 +1122,27 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_bp_llr(DevGraph g, Dec
 BSD_KIND_ALIASES(0, _f32)
 BSD_KIND_ALIASES(1, _f16)
 BSD_KIND_ALIASES(2, _bf16)
+// weighted min-sum (per-edge, per-iteration weights), single-precision messages: id 15 + kind
+using Generic3_w = GenericEngine<3, 0, true>;
+using Generic6_w = GenericEngine<6, 0, true>;
+using Generic16_w = GenericEngine<16, 0, true>;
+using Small326_w = SmallEngine<3, 2, 6, 0, true>;
+using Small536_w = SmallEngine<5, 3, 6, 0, true>;
+constexpr int kWeightedEngine = 15;
 #define BSD_ENGINES(X)                                                                          \
     X(0, Generic3_f32) X(1, Generic3_f16) X(2, Generic3_bf16)                                   \
     X(3, Generic6_f32) X(4, Generic6_f16) X(5, Generic6_bf16)                                   \
     X(6, Generic16_f32) X(7, Generic16_f16) X(8, Generic16_bf16)                                \
     X(9, Small326_f32) X(10, Small326_f16) X(11, Small326_bf16)                                 \
-    X(12, Small536_f32) X(13, Small536_f16) X(14, Small536_bf16)
+    X(12, Small536_f32) X(13, Small536_f16) X(14, Small536_bf16)                                \
+    X(15, Generic3_w) X(16, Generic6_w) X(17, Generic16_w) X(18, Small326_w) X(19, Small536_w)
 
 template <class Eng>
 static int set_attrs(size_t smem_bp)
 {
-    if (cudaFuncSetAttribute(k_seed<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
-        cudaFuncSetAttribute(k_round<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess ||
-        cudaFuncSetAttribute(k_bp_llr<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp) != cudaSuccess)
+    if (CUDA_FAILED(cudaFuncSetAttribute(k_seed<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp)) ||
+        CUDA_FAILED(cudaFuncSetAttribute(k_round<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp)) ||
+        CUDA_FAILED(cudaFuncSetAttribute(k_bp_llr<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bp)))
         return -2;
     return 0;
 }
@@ -1135,8 +1151,8 @@ template <class Eng>
 static int occupancy(int threads, size_t smem_bp, int* bps)
 {
     int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_round<Eng>, threads, smem_bp) != cudaSuccess) return -2;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_seed<Eng>, threads, smem_bp) != cudaSuccess) return -2;
+    if (CUDA_FAILED(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_round<Eng>, threads, smem_bp))) return -2;
+    if (CUDA_FAILED(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_seed<Eng>, threads, smem_bp))) return -2;
     *bps = a < b ? a : b;
     return 0;
 }
@@ -1151,7 +1167,6 @@ static bool small_fits(const DevGraph& g, int cpl, int rpl)
 
 int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls)
 {
-    (void)cfg;
     int kind;
     if (small_fits(g, 3, 2)) kind = 3;
     else if (small_fits(g, 5, 3)) kind = 4;
@@ -1159,14 +1174,15 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* l
     else if (g.max_col_deg <= 6) kind = 1;
     else if (g.max_col_deg <= 16) kind = 2;
     else return -5;
-    const int eng = 3 * kind + g.prec;
+    if (cfg.weights != nullptr && g.prec != 0) return -5;   // weights: single-precision messages only
+    const int eng = cfg.weights != nullptr ? kWeightedEngine + kind : 3 * kind + g.prec;
     // the small engine keeps D per edge in float; the generic one a record per detector
     const size_t recs = sizeof(float4) * (size_t)g.M, msgs = sizeof(float) * (size_t)g.Epad;
     g.det_bytes = (int)align16(kind >= 3 && msgs > recs ? msgs : recs);
     const size_t per_warp = warp_smem_bytes(g);
     int max_optin = 0, sms = 0;
-    if (cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    if (CUDA_FAILED(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) ||
+        CUDA_FAILED(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)))
         return -2;
     if (per_warp > (size_t)max_optin) return -5;
     int wpb = (int)((96 * 1024) / per_warp);
@@ -1178,10 +1194,15 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* l
     ls->dv = eng;
     const int threads = 32 * wpb;
     int rc = 0, bps_bp = 0, bps_sel = 0;
+    // The dynamic shared-memory limit is a property of the kernel, shared by
+    // every decoder that launches it; it is raised to the device maximum so
+    // that no decoder created later can lower it below what an earlier one
+    // launches with (a CUDA graph keeps the value it was instantiated with,
+    // a direct launch checks the current one).
     switch (eng) {
 #define X(id, E)                                                                \
     case id:                                                                    \
-        rc = set_attrs<E>(ls->smem_bp);                             \
+        rc = set_attrs<E>((size_t)max_optin);                       \
         if (!rc) rc = occupancy<E>(threads, ls->smem_bp, &bps_bp);  \
         break;
         BSD_ENGINES(X)
@@ -1189,9 +1210,8 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* l
         default: return -5;
     }
     if (rc) return rc;
-    if (cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls->smem_select) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_sel, k_select, threads, ls->smem_select) != cudaSuccess)
+    if (CUDA_FAILED(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) ||
+        CUDA_FAILED(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_sel, k_select, threads, ls->smem_select)))
         return -2;
     if (bps_bp < 1 || bps_sel < 1) return -5;
     ls->grid_seed = sms * bps_bp;
@@ -1208,17 +1228,17 @@ static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, c
     const int threads = 32 * ls.warps_per_block;
     const int nri = 3 * (cfg.max_rounds + 2);
     k_begin_chunk<<<1, 128, 0, s>>>(w, nri, synd, out, base, n);
-    if (cudaGetLastError() != cudaSuccess) return -2;
-    if (gx != nullptr) return cudaGraphLaunch(gx, s) == cudaSuccess ? 0 : -2;
+    if (CUDA_FAILED(cudaGetLastError())) return -2;
+    if (gx != nullptr) return !CUDA_FAILED(cudaGraphLaunch(gx, s)) ? 0 : -2;
     if (hk) hk->before(hk->ctx, 0);
     k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w);
     if (hk) hk->after(hk->ctx, 0);
-    if (cudaGetLastError() != cudaSuccess) return -2;
+    if (CUDA_FAILED(cudaGetLastError())) return -2;
     if (cfg.max_rounds == 0) return 0;
     // without a graph: read the number of active entries back, then run
     // exactly the passes it needs
-    if (cudaMemcpyAsync(host_n_active, &w.ctr->n_active, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    if (CUDA_FAILED(cudaMemcpyAsync(host_n_active, &w.ctr->n_active, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+        CUDA_FAILED(cudaStreamSynchronize(s)))
         return -2;
     const long long passes = (*host_n_active + w.A - 1) / w.A;
     for (long long p = 0; p < passes; ++p) {
@@ -1230,7 +1250,7 @@ static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, c
             if (hk) hk->after(hk->ctx, 2);
         }
         k_pass_end<<<1, 128, 0, s>>>(w, nri, cudaGraphConditionalHandle{}, 0);
-        if (cudaGetLastError() != cudaSuccess) return -2;
+        if (CUDA_FAILED(cudaGetLastError())) return -2;
     }
     return 0;
 }
@@ -1260,7 +1280,7 @@ static int add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cudaGraphN
     p.blockDim = dim3((unsigned)block);
     p.sharedMemBytes = (unsigned)smem;
     p.kernelParams = args;
-    return cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &p) == cudaSuccess ? 0 : -2;
+    return !CUDA_FAILED(cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &p)) ? 0 : -2;
 }
 
 template <class Eng>
@@ -1273,7 +1293,7 @@ static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0,
     const int threads = 32 * ls.warps_per_block;
     int nri = 3 * (cfg.max_rounds + 2);
     cudaGraph_t graph = nullptr;
-    if (cudaGraphCreate(&graph, 0) != cudaSuccess) return -2;
+    if (CUDA_FAILED(cudaGraphCreate(&graph, 0))) return -2;
     int rc = 0;
     cudaGraphNode_t seed;
     void* sargs[] = {&g, &cfg, &w};
@@ -1282,14 +1302,14 @@ static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0,
         cudaGraphConditionalHandle cond;
         cudaGraphNode_t cnode;
         cudaGraphNodeParams cp{};
-        if (cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        if (CUDA_FAILED(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault))) {
             rc = -2;
         } else {
             cp.type = cudaGraphNodeTypeConditional;
             cp.conditional.handle = cond;
             cp.conditional.type = cudaGraphCondTypeWhile;
             cp.conditional.size = 1;
-            if (cudaGraphAddNode(&cnode, graph, &seed, nullptr, 1, &cp) != cudaSuccess) rc = -2;
+            if (CUDA_FAILED(cudaGraphAddNode(&cnode, graph, &seed, nullptr, 1, &cp))) rc = -2;
         }
         if (!rc) {
             cudaGraph_t body = cp.conditional.phGraph_out[0];
@@ -1312,7 +1332,7 @@ static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0,
         }
     }
     cudaGraphExec_t gx = nullptr;
-    if (!rc && cudaGraphInstantiate(&gx, graph, 0) != cudaSuccess) rc = -2;
+    if (!rc && CUDA_FAILED(cudaGraphInstantiate(&gx, graph, 0))) rc = -2;
     cudaGraphDestroy(graph);
     if (rc) {
         cudaGetLastError();
@@ -1416,7 +1436,7 @@ int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, c
 #undef X
         default: return -5;
     }
-    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+    return CUDA_FAILED(cudaGetLastError()) ? -2 : 0;
 }
 
 }  // namespace bsd
@@ -1457,11 +1477,11 @@ __global__ void k_scatter_results(const long long* __restrict__ list, int n, int
 int launch_collect_flagged(const uint32_t* status, long long B, long long* list, int* count, void* stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(count, 0, sizeof(int), s) != cudaSuccess) return -2;
+    if (CUDA_FAILED(cudaMemsetAsync(count, 0, sizeof(int), s))) return -2;
     long long blocks = (B + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     k_collect_flagged<<<(int)(blocks > 0 ? blocks : 1), 256, 0, s>>>(status, B, list, count);
-    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+    return CUDA_FAILED(cudaGetLastError()) ? -2 : 0;
 }
 
 int launch_gather_rows(const uint32_t* src, const long long* list, int n, int W, uint32_t* dst, void* stream)
@@ -1469,7 +1489,7 @@ int launch_gather_rows(const uint32_t* src, const long long* list, int n, int W,
     long long blocks = ((long long)n * W + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     k_gather_rows<<<(int)(blocks > 0 ? blocks : 1), 256, 0, (cudaStream_t)stream>>>(src, list, n, W, dst);
-    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+    return CUDA_FAILED(cudaGetLastError()) ? -2 : 0;
 }
 
 int launch_scatter_results(const long long* list, int n, int WN, int WK, const Outputs& from, const Outputs& to,
@@ -1478,7 +1498,7 @@ int launch_scatter_results(const long long* list, int n, int WN, int WK, const O
     long long blocks = ((long long)n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     k_scatter_results<<<(int)(blocks > 0 ? blocks : 1), 256, 0, (cudaStream_t)stream>>>(list, n, WN, WK, from, to);
-    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+    return CUDA_FAILED(cudaGetLastError()) ? -2 : 0;
 }
 
 }  // namespace bsd

@@ -43,7 +43,7 @@ int scratch_address(int device, void** out)
     if (device < 0 || device >= kMaxDevices) return BSD_ERR_UNSUPPORTED;
     if (!g_addr[device]) {
         void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_bsd_scratch) != cudaSuccess || ptr == nullptr) {
+        if (CUDA_FAILED(cudaGetSymbolAddress(&ptr, g_bsd_scratch)) || ptr == nullptr) {
             cudaGetLastError();
             return BSD_ERR_CUDA;
         }
@@ -89,8 +89,8 @@ extern "C" int bsd_decode_noalloc(const bsd_decoder* dec, const uint32_t* d_synd
 
     std::lock_guard<std::mutex> lk(g_mu);
     int prev = -1;
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (cudaSetDevice(device) != cudaSuccess) return BSD_ERR_CUDA;
+    if (CUDA_FAILED(cudaGetDevice(&prev))) prev = -1;
+    if (CUDA_FAILED(cudaSetDevice(device))) return BSD_ERR_CUDA;
     void* base = nullptr;
     int rc = scratch_address(device, &base);
     if (rc == BSD_OK) {
@@ -101,7 +101,7 @@ extern "C" int bsd_decode_noalloc(const bsd_decoder* dec, const uint32_t* d_synd
         // the launch statistics in the array's head start at zero; each chunk
         // resets its own counters and run descriptor (k_begin_chunk), and
         // everything else is written before it is read
-        if (cudaMemsetAsync(w.stats, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) rc = BSD_ERR_CUDA;
+        if (CUDA_FAILED(cudaMemsetAsync(w.stats, 0, 4 * sizeof(unsigned long long), s))) rc = BSD_ERR_CUDA;
         for (long long b0 = 0; b0 < B && rc == BSD_OK; b0 += S) {
             const long long n = (B - b0) < S ? (B - b0) : S;
             if (launch_chunk(*g, *cfg, w, *ls, d_syndromes, b0, n, o, s, nullptr, nullptr, &g_nactive) != 0)

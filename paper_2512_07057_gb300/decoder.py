@@ -57,6 +57,17 @@ class BeamSearchDecoder:
         self.h = B.bsd_create(self.M, self.N, self.K, ptr(hr), ptr(hc), ptr(ar), ptr(ac), ptr(pr), params, device)
         self.info = B.bsd_get_info(self.h)
 
+    def set_weights(self, weights) -> None:
+        """Weighted min-sum: float32 [T, E] per-edge, per-iteration weights in
+        place of ms_scale (CSR edge order); None returns to ms_scale."""
+        if weights is None:
+            B.bsd_set_weights(self.h, None, 0)
+            return
+        w = np.ascontiguousarray(np.asarray(weights, np.float32))
+        if w.ndim != 2:
+            raise ValueError("weights must be [T, E]")
+        B.bsd_set_weights(self.h, w.ctypes.data_as(C.c_void_p), w.shape[0])
+
     def close(self):
         if getattr(self, "h", None):
             B.bsd_destroy(self.h)

@@ -127,3 +127,29 @@ def test_16bit_llr_error_against_double(prec, tol):
         rel.append(np.median(np.abs(llr[b] - a) / np.maximum(1.0, np.abs(a))))
     assert np.median(rel) < tol
     dec.close()
+
+
+def test_direct_launches_after_later_decoders():
+    """Kernel attributes are shared by all decoders: a 16-bit decoder of the
+    phenomenological DEM (two warps per block), its single-precision twin
+    and a [[72,12,6]] decoder created afterwards (other block shapes) must
+    leave the first decoder's direct launches (kernel timing on) valid, with
+    the same outputs as its graph launches."""
+    prob = W.bb_phenomenological(12, 6, 12, 3e-3, 3e-3)
+    shots = W.sample_shots(prob, 3000, "phenom_direct")
+    dec = D.BeamSearchDecoder(prob, D.make_params("beam64_640iters", ms_scale=0.625, msg_precision=B.BSD_FP16,
+                                                  workspace_bytes=1 << 30))
+    other = D.BeamSearchDecoder(W.bb72_code_capacity(0.03), D.make_params(ms_scale=0.625))
+    s = D.to_torch_words(shots.syndromes)
+    ref = dec.decode(s)
+    torch.cuda.synchronize()
+    ref = {a: D.from_torch_words(getattr(ref, a)).copy() for a in ("corrections", "status", "iters")}
+    dec.profile(True)
+    out = dec.decode(s)
+    torch.cuda.synchronize()
+    prof = dec.profile_read()
+    for a in ("corrections", "status", "iters"):
+        assert np.array_equal(D.from_torch_words(getattr(out, a)), ref[a])
+    assert prof["launches"][0] >= 1
+    dec.close()
+    other.close()
