@@ -48,6 +48,9 @@ PHEN_PS = (1e-3, 2e-3, 3e-3)
 PHEN_SHOTS = 100_000
 PHEN_PRESET = "beam64_640iters"
 PHEN_WORKLOAD = "bb144_phenomenological_dem beam64_640iters alpha=0.625 p=q={1e-3,2e-3,3e-3}"
+# unrolled weighted min-sum training: 20 iterations, checkpoints every 5, batch 4096, p = q = 2e-3
+UNR_T, UNR_K, UNR_B, UNR_P, UNR_LR = 20, 5, 4096, 2e-3, 1e-2
+UNR_WORKLOAD = "bb144_phenomenological_dem unrolled weighted min-sum T=20 ckpt=5 batch=4096 p=q=2e-3"
 
 
 def parse():
@@ -62,8 +65,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ps", default="0.01,0.03,0.05", help="physical error rates (a smaller case for profiling)")
     ap.add_argument("--workspace-gb", type=float, default=32.0, help="device workspace per decoder")
-    ap.add_argument("--workload", choices=("bb144_code_capacity", "phenom_precision"), default="bb144_code_capacity",
-                    help="phenom_precision: the phenomenological DEM with FP32, FP16 and BF16 message storage")
+    ap.add_argument("--workload", choices=("bb144_code_capacity", "phenom_precision", "unrolled_training"),
+                    default="bb144_code_capacity",
+                    help="phenom_precision: the phenomenological DEM with FP32, FP16 and BF16 message storage; "
+                         "unrolled_training: training steps of the unrolled weighted min-sum on that DEM")
+    ap.add_argument("--train-steps", type=int, default=300, help="unrolled_training: steps before the LER judgement")
+    ap.add_argument("--judge-shots", type=int, default=1_000_000, help="unrolled_training: held-out shots")
     a = ap.parse_args()
     if a.workload == "phenom_precision":
         if a.ps == "0.01,0.03,0.05":
@@ -202,8 +209,45 @@ def cores() -> int:
         return os.cpu_count() or 1
 
 
+def run_reference_unrolled(args):
+    """Reference arm of the unrolled workload: the double-precision autograd
+    reference, forward + backward, on a bounded sample of each step's batch."""
+    import torch
+
+    from oracle import unrolled as U
+    from paper_2512_07057_gb300 import workloads as W
+    prob = W.bb_phenomenological(12, 6, 12, UNR_P, UNR_P)
+    tab = U.Tables(prob)
+    n = 16
+    w0 = np.full((UNR_T, prob.n_edges), ALPHA)
+    data = []
+    for i in range(args.warmup + args.steps):
+        sh = W.sample_shots(prob, n, W.shot_seed("unrolled_reference", i), keep_errors=True)
+        data.append((W.unpack_bits(sh.syndromes, prob.M), W.unpack_bits(sh.errors, prob.N)))
+    for i in range(args.warmup):
+        U.unrolled_grad(tab, *data[i], w0)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        U.unrolled_grad(tab, *data[args.warmup + i], w0)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    nth = torch.get_num_threads()
+    sample = f"{n} of the {UNR_B} shots of each step's batch, float64 autograd reference, {nth} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "training syndromes/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": UNR_WORKLOAD, "shots_per_step": n, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "training syndromes/s", "cores": nth, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "training syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank: int):
     if rank != 0:
+        return
+    if args.workload == "unrolled_training":
+        run_reference_unrolled(args)
         return
     phen = args.workload == "phenom_precision"
     work = (make_phen_workload if phen else make_workload)(0, min(args.shots, 200_000), args.ps)
@@ -534,6 +578,245 @@ def run_precision(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
 
 
+def unrolled_bytes_per_launch(kind: int, E: int, N: int, M: int, Bp: int, T: int) -> float:
+    """Algorithmic HBM bytes of one launch of an unrolled pass, averaged over
+    the launches of a training step (forward, recomputed segments, adjoint).
+    Per-edge arrays are float32 [E][Bp], per-node arrays [N][Bp]; bit planes
+    take one bit per shot and row."""
+    EB, NB = 4.0 * E * Bp, 4.0 * N * Bp
+    if kind == 3:      # check pass: E(t-1) in, D(t) out, syndrome bits
+        return 2 * EB + M * Bp / 8
+    if kind == 4:      # error pass: D(t) in, E(t) out; the recomputed half also writes Lambda(t)
+        return 2 * EB + NB / 2 + N * Bp / 8
+    if kind == 5:      # error adjoint: gE(t) (t < T) and E(t) in, Lambda(t) in, gD(t) out, error bits
+        return EB * (1 + (T - 1) / T) + NB + EB + N * Bp / 8
+    if kind == 6:      # check adjoint: E(t-1) and gD(t) in, gE(t-1) out (t > 1), syndrome bits
+        return 2 * EB + EB * (T - 1) / T + M * Bp / 8
+    raise ValueError(kind)
+
+
+def run_unrolled(args, rank: int, world: int, local_rank: int):
+    """Training steps of the unrolled decoder (forward + adjoint + Adam) on the
+    phenomenological DEM, then the learned weights judged by the plain and
+    the beam decoder's LER on held-out shots."""
+    import torch
+    import torch.distributed as dist
+
+    from __graft_entry__ import build
+    from paper_2512_07057_gb300 import decoder as D
+    from paper_2512_07057_gb300 import unrolled as G
+    from paper_2512_07057_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+        build()
+    prob = W.bb_phenomenological(12, 6, 12, UNR_P, UNR_P)
+    T, k, Bn = UNR_T, UNR_K, UNR_B
+    tr = G.UnrolledTrainer(prob, Bn, T, k, device=dev)
+    nb = args.warmup + 2 * args.steps
+    batches = [G.batch_tensors(prob, Bn, W.shot_seed(f"unrolled_bench_r{rank}", i), dev)[:2] for i in range(nb)]
+    w = torch.full((T, prob.n_edges), ALPHA, dtype=torch.float32, device=f"cuda:{dev}", requires_grad=True)
+    opt = torch.optim.Adam([w], lr=UNR_LR)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+
+    def step(i):
+        s_t, e_t = batches[i]
+        opt.zero_grad(set_to_none=True)
+        loss = G.unrolled_loss(w, tr, s_t, e_t)
+        loss.backward()
+        opt.step()
+        return loss
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+
+    def region(profiled: bool, first: int):
+        tr.dec.profile(profiled)
+        tr.dec.profile_read_kinds()
+        sampler = ClockSampler(dev) if (rank == 0 and not profiled) else None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        for q in range(args.steps):
+            flush.fill_(float(q))
+            ev[q][0].record(stream)
+            step(first + q)
+            ev[q][1].record(stream)
+        torch.cuda.synchronize(dev)
+        clk = sampler.stop() if sampler else None
+        prof = tr.dec.profile_read_kinds()
+        tr.dec.profile(False)
+        return [a.elapsed_time(b) for a, b in ev], clk, prof
+
+    ms_steps, clocks, _ = region(False, args.warmup)
+    _, _, prof = region(True, args.warmup + args.steps)
+    ms_total = float(sum(ms_steps))
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    E, N, M = prob.n_edges, prob.N, prob.M
+    Bp = (Bn + 511) // 512 * 512
+    names = {3: "k_u_check", 4: "k_u_var", 5: "k_u_bvar", 6: "k_u_bcheck"}
+    per_kind = {names[kd]: {"ms_per_step": float(prof["ms"][kd]) / args.steps,
+                            "launches_per_step": float(prof["launches"][kd]) / args.steps} for kd in names}
+    dom = max(names, key=lambda kd: prof["ms"][kd])
+    launch_ms = float(prof["ms"][dom]) / max(1, int(prof["launches"][dom]))
+    alg = unrolled_bytes_per_launch(dom, E, N, M, Bp, T)
+    pk, pk_kind = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    achieved = alg / (launch_ms * 1e-3) / 1e9
+    roofline = {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms,
+                "kernel_share": float(prof["ms"][dom] / max(prof["ms"][3:7].sum(), 1e-9)),
+                "peak_source": f"hbm_gbs ({pk_kind})",
+                "measured_in": "second timed region: same steps, each pass launched between CUDA events"}
+    tr_bytes = _traffic_record(names[dom], E)
+    if tr_bytes is not None:
+        roofline["traffic"] = tr_bytes
+        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of this workload"
+    steps_s = ms_total * 1e-3
+    value = world * Bn * args.steps / steps_s
+    # edge updates: forward T iterations, the recomputed T, the adjoint T (check + error pass each)
+    upd = 3.0 * T * E * Bn
+    line = {
+        "metric": METRIC, "value": value, "unit": "training syndromes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": UNR_WORKLOAD, "code": "[[144,12,12]] phenomenological DEM, 936 x 2592, 6912 edges",
+                   "batch": Bn, "T": T, "ckpt_every": k, "weights": T * E, "optimizer": f"Adam lr={UNR_LR}",
+                   "l2": "flushed before every timed step (256 MiB write outside the step events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "edge_updates_per_s": world * upd * args.steps / steps_s,
+        "kernels": per_kind, "roofline": roofline, "clocks": clocks,
+        # per step: forward 2 bit-plane + 1 initial-message + T check + T error + 1 loss kernels; backward
+        # T recomputed check + T recomputed error + T error-adjoint + T check-adjoint + 1 gradient kernels
+        "gpu_launches": (6 * T + 5) * args.steps,
+        "timed_launches_per_step": {"check": float(prof["launches"][3]) / args.steps,
+                                    "error": float(prof["launches"][4]) / args.steps,
+                                    "error_adjoint": float(prof["launches"][5]) / args.steps,
+                                    "check_adjoint": float(prof["launches"][6]) / args.steps},
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = _unrolled_e2e(tr, w, opt, prob, Bn, args, dev)
+    if rank == 0:
+        line["ler_judgement"] = _judge_weights(prob, args, dev)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _unrolled_cpu_baseline(prob, T, args.cpu_seconds)
+    tr.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _unrolled_e2e(tr, w, opt, prob, Bn, args, dev):
+    """Training steps with each batch copied from pinned host memory and the loss read back."""
+    import torch
+
+    from paper_2512_07057_gb300 import unrolled as G
+    from paper_2512_07057_gb300 import workloads as W
+    host = []
+    for i in range(args.steps + 1):
+        sh = W.sample_shots(prob, Bn, W.shot_seed("unrolled_bench_e2e", i), keep_errors=True)
+        host.append((torch.from_numpy(sh.syndromes.view(np.int32)).pin_memory(),
+                     torch.from_numpy(sh.errors.view(np.int32)).pin_memory()))
+    h2d = host[0][0].numel() * 4 + host[0][1].numel() * 4
+
+    def step(i):
+        s_t = host[i][0].to(f"cuda:{dev}", non_blocking=True)
+        e_t = host[i][1].to(f"cuda:{dev}", non_blocking=True)
+        opt.zero_grad(set_to_none=True)
+        loss = G.unrolled_loss(w, tr, s_t, e_t)
+        loss.backward()
+        opt.step()
+        return float(loss.detach())            # device -> host read of the step's loss
+
+    step(0)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(1, args.steps + 1):
+        step(i)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    return {"value": Bn * args.steps / dt, "unit": "training syndromes/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": 4, "api": "UnrolledLoss (torch.autograd) over bsd_unrolled_forward/backward"}
+
+
+def _judge_weights(prob, args, dev):
+    """Train the weights, then decode held-out shots with the plain decoder
+    (BP alone, T iterations) and the beam decoder, with the scale 0.625 and
+    with the learned weights."""
+    import torch
+
+    from paper_2512_07057_gb300 import decoder as D
+    from paper_2512_07057_gb300 import unrolled as G
+    from paper_2512_07057_gb300 import workloads as W
+    t0 = time.perf_counter()
+    wl, hist = G.train_weights(prob, T=UNR_T, ckpt_every=UNR_K, batch=UNR_B, steps=args.train_steps, lr=UNR_LR,
+                               init=ALPHA, tag="unrolled_judge_train", device=dev)
+    train_s = time.perf_counter() - t0
+    # the loss on one fixed held-out batch, with the initial and the learned weights
+    tr = G.UnrolledTrainer(prob, UNR_B, UNR_T, UNR_K, device=dev)
+    vs, ve, _ = G.batch_tensors(prob, UNR_B, W.shot_seed("unrolled_judge_validation", 0), dev)
+    val = {}
+    for wname, wts in (("scale_0.625", np.full_like(wl, ALPHA)), ("learned", wl)):
+        lv = tr.forward(torch.from_numpy(wts).to(f"cuda:{dev}"), vs, ve).cpu().numpy()
+        val[wname] = {"loss": float(lv[0]), "loss_last_iteration": float(lv[-1])}
+    tr.close()
+    sh = W.sample_shots(prob, args.judge_shots, W.shot_seed("unrolled_judge_heldout", 0))
+    synd = D.to_torch_words(sh.syndromes, dev)
+    out = {"train_steps": args.train_steps, "train_s": train_s, "train_loss_first10": float(np.mean(hist[:10])),
+           "train_loss_last10": float(np.mean(hist[-10:])), "validation": val, "held_out_shots": args.judge_shots,
+           "weights_mean": float(wl.mean()), "weights_std": float(wl.std())}
+    for name, params in (("plain_bp_T20", D.make_params(ms_scale=ALPHA, max_rounds=0, initial_iters=UNR_T)),
+                         ("beam64_640iters", D.make_params(PHEN_PRESET, ms_scale=ALPHA))):
+        dec = D.BeamSearchDecoder(prob, params, device=dev)
+        res = {}
+        for wname, wts in (("scale_0.625", None), ("learned", wl)):
+            dec.set_weights(wts)
+            o = dec.decode(synd)
+            torch.cuda.synchronize(dev)
+            st = D.from_torch_words(o.status)
+            fails = int(round(ler_of(prob, sh, D.from_torch_words(o.obs_flips), st & 7) * sh.B))
+            res[wname] = {"ler": fails / sh.B, "failures": fails, "not_converged": int(((st & 7) == 4).sum())}
+        dec.close()
+        out[name] = res
+    return out
+
+
+def _unrolled_cpu_baseline(prob, T, target_s):
+    """The double-precision autograd reference (forward + backward) on the host cores."""
+    import torch
+
+    from oracle import unrolled as U
+    from paper_2512_07057_gb300 import workloads as W
+    tab = U.Tables(prob)
+    n = 8
+    sh = W.sample_shots(prob, n, "unrolled_cpu", keep_errors=True)
+    s, e = W.unpack_bits(sh.syndromes, prob.M), W.unpack_bits(sh.errors, prob.N)
+    w0 = np.full((T, prob.n_edges), ALPHA)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        U.unrolled_grad(tab, s, e, w0)
+        reps += 1
+        if time.perf_counter() - t0 > target_s / 3:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * reps / dt, "unit": "training syndromes/s", "cores": torch.get_num_threads(),
+            "kind": "oracle", "sample": f"{reps} forward+backward passes of {n} shots, T={T}, float64 autograd "
+                                        f"reference, {dt:.1f} s"}
+
+
 def e2e_host(decs, work, args, dev):
     """Same metric through bsd_decode_host: pinned host syndromes in, host results out."""
     import torch
@@ -612,6 +895,8 @@ def main():
     try:
         if args.workload == "phenom_precision":
             run_precision(args, rank, world, local_rank)
+        elif args.workload == "unrolled_training":
+            run_unrolled(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

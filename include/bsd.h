@@ -219,6 +219,16 @@ int bsd_profile_enable(bsd_decoder *dec, int enable);
 int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2],
                      uint64_t *kernel_launches);
 
+/* Kernel kinds timed while timing is enabled: 0..2 as above, then the
+ * unrolled decoder's passes (bsd_unrolled_forward / _backward): 3 check pass,
+ * 4 error-node pass, 5 error-node adjoint, 6 check adjoint, 7 its other
+ * kernels (bit planes, initial messages, loss and gradient reductions). */
+#define BSD_PROFILE_KINDS 8
+
+/* Synchronise the stream of the last timed launch, then return and reset the
+ * summed event-timed milliseconds and launch counts of every kind. */
+int bsd_profile_read_kinds(bsd_decoder *dec, double ms[BSD_PROFILE_KINDS], int64_t launches[BSD_PROFILE_KINDS]);
+
 /* Weighted min-sum: replace the scale alpha of Eq. 1 by a weight per edge and
  * iteration, D_{i->j}(t) = w[t', e] * (-1)^{s'_i} * prod sign * min, with
  * t' = min(t, T) - 1 and t counted from 1 in every BP call (the seed run and
@@ -233,6 +243,52 @@ int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64
  * BSD_ERR_UNSUPPORTED (16-bit message storage), BSD_ERR_OOM, BSD_ERR_CUDA;
  * on error the decoder keeps its previous weights. */
 int bsd_set_weights(bsd_decoder *dec, const float *h_weights, int32_t T);
+
+/* ---- Differentiation: unrolled weighted min-sum ---------------------------
+ * T flooding iterations of Eqs. 1-3 with weights w[t][e] in place of the
+ * scale (t = 1..T, no stopping rule), on B shots of the decoder's problem, and
+ * the loss
+ *     loss = sum_{t=1..T} mean_{b,j} BCE(sigmoid(-Lambda_j(t)), e_j)
+ * (binary cross entropy between the error probability the posterior assigns
+ * and the true error).  The backward gives dloss/dw with the readings: sign()
+ * has zero derivative, d|x|/dx = sign(x) with 0 at 0, a minimum over the other
+ * edges passes its derivative to the lowest-index edge holding it, a message
+ * clamped to +-L_MAX passes none, the minimum over no edge is the constant
+ * L_MAX.  The decoder supplies H, the priors and L_MAX (single-precision
+ * message storage only; else BSD_ERR_UNSUPPORTED); its beam parameters and
+ * weights are not used.
+ *
+ * Workspace: device memory of bsd_unrolled_workspace() bytes, 256-byte
+ * aligned, owned by the caller.  The forward stores E at the checkpoints
+ * t = 0, k, 2k, ... (k = ckpt_every, 1 <= k <= T) and the bit planes of the
+ * batch there; the backward recomputes each segment of k iterations from its
+ * checkpoint.  A backward needs the forward of the same (B, T, k, weights,
+ * workspace) before it, with the workspace untouched in between.
+ *
+ * Memory: about (ceil(T/k) + k + 4) * E * Bp + k * N * Bp floats, Bp = B
+ * rounded up to a multiple of 512. */
+int bsd_unrolled_workspace(const bsd_decoder *dec, int64_t B, int32_t T, int32_t ckpt_every, int64_t *bytes);
+
+/*   d_syndromes  device, B x ceil(M/32) words (bitpacked like bsd_decode)
+ *   d_errors     device, B x ceil(N/32) words: the true errors e
+ *   d_weights    device, float [T][E] (CSR edge order)
+ *   d_loss       device, float [T + 1]: [0] the loss, [t] the term of iteration t
+ *   d_llr        device, float [T][B][N] Lambda_j(t), or NULL
+ * Asynchronous on cuda_stream.  Errors: BSD_ERR_INVALID_ARG (sizes, NULL
+ * buffers, a workspace too small or misaligned), BSD_ERR_UNSUPPORTED,
+ * BSD_ERR_CUDA. */
+int bsd_unrolled_forward(const bsd_decoder *dec, const uint32_t *d_syndromes, const uint32_t *d_errors, int64_t B,
+                         int32_t T, int32_t ckpt_every, const float *d_weights, float *d_loss, float *d_llr,
+                         void *d_work, int64_t work_bytes, void *cuda_stream);
+
+/*   d_grad_loss     device, float [1]: the derivative of the caller's objective
+ *                   with respect to the loss (1 for the loss itself)
+ *   d_grad_weights  device, float [T][E]: overwritten with d_grad_loss * dloss/dw
+ * Asynchronous on cuda_stream; same errors as the forward.  Weight gradients
+ * are sums over the batch taken in a fixed order: the result is deterministic. */
+int bsd_unrolled_backward(const bsd_decoder *dec, int64_t B, int32_t T, int32_t ckpt_every, const float *d_weights,
+                          const float *d_grad_loss, float *d_grad_weights, void *d_work, int64_t work_bytes,
+                          void *cuda_stream);
 
 /* Static text for a return code. */
 const char *bsd_error_string(int code);

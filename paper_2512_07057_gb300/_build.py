@@ -1,6 +1,6 @@
 """Build libbsd.so (the CUDA library behind include/bsd.h) in-tree for sm_103a.
 
-Two translation units compiled in parallel by nvcc, then linked into one
+The translation units are compiled in parallel by nvcc, then linked into one
 shared library next to this file.  No cmake, no torch extension machinery:
 the library exports only the C ABI and links only the CUDA runtime.
 """
@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbsd.so")
-SOURCES = ["bsd_kernels.cu", "bsd_api.cu", "bsd_noalloc.cu"]
+SOURCES = ["bsd_kernels.cu", "bsd_api.cu", "bsd_noalloc.cu", "bsd_unrolled.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

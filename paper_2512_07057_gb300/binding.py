@@ -32,7 +32,10 @@ BSD_STATUS_FAILED = 4
 # every symbol include/bsd.h declares
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
            "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_profile_enable", "bsd_profile_read",
-           "bsd_decode_noalloc", "bsd_set_weights", "bsd_error_string", "bsd_last_cuda_error", "bsd_destroy")
+           "bsd_decode_noalloc", "bsd_set_weights", "bsd_unrolled_workspace", "bsd_unrolled_forward",
+           "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_error_string", "bsd_last_cuda_error",
+           "bsd_destroy")
+BSD_PROFILE_KINDS = 8
 BSD_ERR_SCRATCH = -7
 
 
@@ -77,7 +80,11 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_decode_noalloc.argtypes = [P, P, C.c_int64, P, P, P, P, P]
     lib.bsd_profile_enable.argtypes = [P, C.c_int]
     lib.bsd_set_weights.argtypes = [P, P, C.c_int32]
+    lib.bsd_unrolled_workspace.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
+    lib.bsd_unrolled_forward.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, C.c_int64, P]
+    lib.bsd_unrolled_backward.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, C.c_int64, P]
     lib.bsd_profile_read.argtypes = [P, P, P, P, P]
+    lib.bsd_profile_read_kinds.argtypes = [P, P, P]
     lib.bsd_error_string.argtypes = [C.c_int]
     lib.bsd_error_string.restype = C.c_char_p
     lib.bsd_last_cuda_error.argtypes = []
@@ -163,6 +170,24 @@ def bsd_set_weights(dec, h_weights, T: int) -> None:
     check(load().bsd_set_weights(dec, h_weights, int(T)), "bsd_set_weights")
 
 
+def bsd_unrolled_workspace(dec, B: int, T: int, ckpt_every: int) -> int:
+    n = C.c_int64()
+    check(load().bsd_unrolled_workspace(dec, int(B), int(T), int(ckpt_every), C.byref(n)), "bsd_unrolled_workspace")
+    return n.value
+
+
+def bsd_unrolled_forward(dec, d_syndromes, d_errors, B, T, ckpt_every, d_weights, d_loss, d_llr, d_work,
+                         work_bytes, stream) -> None:
+    check(load().bsd_unrolled_forward(dec, d_syndromes, d_errors, int(B), int(T), int(ckpt_every), d_weights,
+                                      d_loss, d_llr, d_work, int(work_bytes), stream), "bsd_unrolled_forward")
+
+
+def bsd_unrolled_backward(dec, B, T, ckpt_every, d_weights, d_grad_loss, d_grad_weights, d_work, work_bytes,
+                          stream) -> None:
+    check(load().bsd_unrolled_backward(dec, int(B), int(T), int(ckpt_every), d_weights, d_grad_loss,
+                                       d_grad_weights, d_work, int(work_bytes), stream), "bsd_unrolled_backward")
+
+
 def bsd_profile_enable(dec, enable: bool) -> None:
     check(load().bsd_profile_enable(dec, int(bool(enable))), "bsd_profile_enable")
 
@@ -177,6 +202,17 @@ def bsd_profile_read(dec) -> dict:
     p = lambda a: a.ctypes.data_as(C.c_void_p)
     check(load().bsd_profile_read(dec, p(ms), p(ln), p(it), p(kl)), "bsd_profile_read")
     return dict(ms=ms, launches=ln, exec_iters=it, kernel_launches=int(kl[0]))
+
+
+def bsd_profile_read_kinds(dec) -> dict:
+    """Event-timed ms and launches of every kernel kind (0 seed, 1 round, 2 select,
+    3..6 unrolled check / error / error adjoint / check adjoint, 7 other unrolled)."""
+    import numpy as np
+    ms = np.zeros(BSD_PROFILE_KINDS, np.float64)
+    ln = np.zeros(BSD_PROFILE_KINDS, np.int64)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    check(load().bsd_profile_read_kinds(dec, p(ms), p(ln)), "bsd_profile_read_kinds")
+    return dict(ms=ms, launches=ln)
 
 
 def bsd_destroy(dec) -> None:

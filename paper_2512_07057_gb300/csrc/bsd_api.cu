@@ -47,8 +47,8 @@ struct bsd_decoder {
     std::vector<Rec> recs;
     int open_kind = -1;
     size_t open_ev = 0;
-    double ms[3] = {0, 0, 0};
-    long long launches[3] = {0, 0, 0};
+    double ms[kProfKinds] = {};
+    long long launches[kProfKinds] = {};
     // 16-bit messages: a single-precision decoder for near-tie re-runs
     bsd_decoder* twin = nullptr;
     void* rr_mem = nullptr;                  // flagged list, count, gathered syndromes, re-run outputs
@@ -683,6 +683,22 @@ int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64
     return BSD_OK;
 }
 
+int bsd_profile_read_kinds(bsd_decoder* dec, double ms[BSD_PROFILE_KINDS], int64_t launches[BSD_PROFILE_KINDS])
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    if (CUDA_FAILED(cudaStreamSynchronize(dec->prof_stream))) return BSD_ERR_CUDA;
+    prof_collect(dec);
+    for (int k = 0; k < kProfKinds; ++k) {
+        if (ms) ms[k] = dec->ms[k];
+        if (launches) launches[k] = dec->launches[k];
+        dec->ms[k] = 0;
+        dec->launches[k] = 0;
+    }
+    return BSD_OK;
+}
+
 }  // extern "C"
 
 namespace bsd {
@@ -695,6 +711,24 @@ int decoder_view(const bsd_decoder* dec, const DevGraph** g, const DecCfg** cfg,
     *g = &dec->g;
     *cfg = &dec->cfg;
     *ls = &dec->ls;
+    *device = dec->device;
+    return BSD_OK;
+}
+
+bool decoder_hooks(const bsd_decoder* dec, void* stream, LaunchHooks* hk)
+{
+    bsd_decoder* d = const_cast<bsd_decoder*>(dec);   // the timing records are not part of the decoder's state
+    if (!d || !d->prof) return false;
+    d->prof_stream = (cudaStream_t)stream;
+    *hk = LaunchHooks{prof_before, prof_after, d};
+    return true;
+}
+
+int decoder_graph(const bsd_decoder* dec, const DevGraph** g, const DecCfg** cfg, int* device)
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    *g = &dec->g;
+    *cfg = &dec->cfg;
     *device = dec->device;
     return BSD_OK;
 }

@@ -20,7 +20,11 @@
 //   bank (r - 1) % 2 (or the seed store for r = 1) through a rank -> slot
 //   table, so surviving paths are never copied.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
+
+#include "bsd.h"
 
 namespace bsd {
 
@@ -122,14 +126,14 @@ struct Work {
     unsigned long long* stats;   // [4]: executed BP iterations (seed, rounds), kernel launches; never reset by a chunk
 };
 
-// workspace layout for S seed entries and A window entries starting at base
-// (base may be null to size it); returns the bytes used.  The counters and the
-// run descriptor come first, in the first head_bytes(cfg) bytes.
 // true if e is an error; the error and the source line of the call are then
 // kept as the calling thread's most recent CUDA failure (bsd_last_cuda_error)
 bool cuda_failed_at(cudaError_t e, const char* file, int line);
 #define CUDA_FAILED(x) ::bsd::cuda_failed_at((x), __FILE__, __LINE__)
 
+// workspace layout for S seed entries and A window entries starting at base
+// (base may be null to size it); returns the bytes used.  The counters and the
+// run descriptor come first, in the first head_bytes(cfg) bytes.
 size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w);
 size_t work_head_bytes(const DecCfg& cfg);
 
@@ -142,7 +146,10 @@ struct LaunchShape {
     int dv;                // compiled column-degree bound used
 };
 
-// optional callbacks around every kernel launch (kind: 0 seed, 1 round, 2 select)
+// optional callbacks around every kernel launch; kinds 0 seed, 1 round,
+// 2 select, 3..6 the unrolled decoder's check / error / error adjoint / check
+// adjoint passes, 7 its other kernels
+constexpr int kProfKinds = BSD_PROFILE_KINDS;
 struct LaunchHooks {
     void (*before)(void* ctx, int kind);
     void (*after)(void* ctx, int kind);
@@ -168,5 +175,10 @@ int launch_collect_flagged(const uint32_t* status, long long B, long long* list,
 int launch_gather_rows(const uint32_t* src, const long long* list, int n, int W, uint32_t* dst, void* stream);
 int launch_scatter_results(const long long* list, int n, int WN, int WK, const Outputs& from, const Outputs& to,
                            void* stream);
+
+// the decoder's device graph, configuration and device (bsd_api.cu)
+int decoder_graph(const bsd_decoder* dec, const DevGraph** g, const DecCfg** cfg, int* device);
+// the decoder's timing hooks on `stream` when kernel timing is enabled
+bool decoder_hooks(const bsd_decoder* dec, void* stream, LaunchHooks* hk);
 
 }  // namespace bsd

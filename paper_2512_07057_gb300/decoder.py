@@ -151,6 +151,9 @@ class BeamSearchDecoder:
     def profile_read(self) -> dict:
         return B.bsd_profile_read(self.h)
 
+    def profile_read_kinds(self) -> dict:
+        return B.bsd_profile_read_kinds(self.h)
+
 
 def to_torch_words(arr: np.ndarray, device: int = 0):
     """uint32 numpy words -> int32 CUDA tensor with the same bits."""
