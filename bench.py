@@ -684,7 +684,8 @@ def run_unrolled(args, rank: int, world: int, local_rank: int):
     tr_bytes = _traffic_record(names[dom], E)
     if tr_bytes is not None:
         roofline["traffic"] = tr_bytes
-        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of this workload"
+        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, averaged over " \
+                                     "the launches of one training step of this workload"
     steps_s = ms_total * 1e-3
     value = world * Bn * args.steps / steps_s
     # edge updates: forward T iterations, the recomputed T, the adjoint T (check + error pass each)
@@ -853,28 +854,34 @@ def e2e_host(decs, work, args, dev):
 
 
 def _traffic_record(kernel: str, edges: int):
-    """bytes per candidate-iteration recorded for `kernel` on a problem with
-    `edges` edges, if captured on the current sources."""
+    """bytes per unit of work recorded for `kernel` on a problem with `edges`
+    edges, if the kernel sources the record names are unchanged since the
+    capture (per candidate-iteration for the decoder kernels, per launch for
+    the unrolled passes)."""
     import glob
     import re
     for path in glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_traffic_*.md")):
         txt = open(path).read()
         h = re.search(r"^source_hash: (\w+)$", txt, re.M)
         k = re.search(r"^kernel: (\w+)$", txt, re.M)
-        b = re.search(r"^bytes_per_candidate_iteration: ([0-9.]+)$", txt, re.M)
+        b = re.search(r"^bytes_per_(?:candidate_iteration|launch): ([0-9.]+)$", txt, re.M)
         e = re.search(r"^edges: (\d+)$", txt, re.M)
+        src = re.search(r"^sources: (.+)$", txt, re.M)
         if e is not None and int(e.group(1)) != edges:
             continue
-        if h and k and b and k.group(1) == kernel and h.group(1) == _source_hash():
+        files = src.group(1).split() if src else None
+        if h and k and b and k.group(1) == kernel and h.group(1) == _source_hash(files):
             return float(b.group(1))
     return None
 
 
-def _source_hash() -> str:
+def _source_hash(files=None) -> str:
+    """sha256[:16] over the named files of the CUDA sources (all of them by default)."""
     import hashlib
+    d = os.path.join(ROOT, "paper_2512_07057_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2512_07057_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_2512_07057_gb300", "csrc", f), "rb") as fh:
+    for f in (files if files else sorted(os.listdir(d))):
+        with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

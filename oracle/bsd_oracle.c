@@ -41,6 +41,19 @@
  *       the final set with masked values filled (FAILED)
  *   R11 results are deduplicated by exact equality; equal weights keep the
  *       element found first
+ *   R15 16-bit message storage (float build, msg_storage 1 / 2): every stored
+ *       E_{j->i}, E(0) included, is the float result rounded to binary16 /
+ *       bfloat16 to nearest even, a zero stored as +0, and L_MAX is taken at
+ *       its stored value; every sum is formed in float
+ *   R16 near-tie flag (tie_guard > 0): set when the seed path (if rounds
+ *       follow) or any visited child with a next_pos has a relative margin
+ *       between its smallest and second smallest |sum_LLR| strictly inside
+ *       (0, tie_guard), or when the score margin between the last kept and
+ *       the first dropped child of a round (before the last round) is; exact
+ *       ties are not flagged, since R5, R7 and R8 decide them the same way in
+ *       any precision
+ *   R17 weighted min-sum: a weight w[t'][e] per edge in place of alpha, with
+ *       t' = min(t, T) - 1 and t counted from 1 in every BP call
  *   Score and weight arithmetic:
  *     double build: score = (sum over U of |sum_LLR[j]| added in ascending
  *                   order) / iters; weight = sum of Lambda_j over the support

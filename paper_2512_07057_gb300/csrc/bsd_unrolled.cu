@@ -31,7 +31,7 @@
 // e = i1, or the constant L_MAX when no such edge exists (a row of weight 1,
 // or every |E| at L_MAX).  sign() has zero derivative, d|x|/dx = sign(x) with
 // 0 at 0, and a message at +-L_MAX passes none.  Loss and weight gradients
-// are reduced through per-tile partial sums added in a fixed order, so every
+// are reduced through per-warp partial sums added in a fixed order, so every
 // result is deterministic.
 #include <cuda_runtime.h>
 
@@ -46,7 +46,9 @@ namespace {
 
 constexpr int kThreads = 128;            // threads per block
 constexpr int kTile = 4 * kThreads;      // shots per block (4 per thread)
-constexpr int kCap = 8;                  // rows / columns up to this degree are held in registers
+// a row or column of degree <= CAP (4 or 8) keeps its vectors in registers
+// between passes; CAP = 0 loads them again
+constexpr int kWarps = kThreads / 32;    // partial sums are kept per warp (no block barrier)
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -74,8 +76,8 @@ struct ULayout {
     float* D;                // [E][Bp]
     float* gE[2];            // [E][Bp]
     float* gD;               // [E][Bp]
-    float* loss_part;        // [T][N][ntile]
-    float* gw_part;          // [T][ntile][E]
+    float* loss_part;        // [T][N][ntile * kWarps]: per-warp loss sums
+    float* gw_part;          // [T][ntile * kWarps][E]: per-warp weight-gradient sums
     size_t bytes;
 };
 
@@ -101,8 +103,8 @@ ULayout layout(const DevGraph& g, long long B, int T, int k, char* base)
     u.gE[0] = (float*)take(sizeof(float) * EB);
     u.gE[1] = (float*)take(sizeof(float) * EB);
     u.gD = (float*)take(sizeof(float) * EB);
-    u.loss_part = (float*)take(sizeof(float) * (size_t)T * (size_t)g.N * ntile);
-    u.gw_part = (float*)take(sizeof(float) * (size_t)T * ntile * (size_t)g.E);
+    u.loss_part = (float*)take(sizeof(float) * (size_t)T * (size_t)g.N * ntile * kWarps);
+    u.gw_part = (float*)take(sizeof(float) * (size_t)T * ntile * kWarps * (size_t)g.E);
     u.bytes = off;
     return u;
 }
@@ -128,16 +130,15 @@ __device__ __forceinline__ uint32_t bits4(const uint32_t* plane, int row, long l
 __device__ __forceinline__ float softplus(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); }
 __device__ __forceinline__ float sgn0(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
-// sum over the block (128 threads); every thread gets the total
-__device__ float block_sum(float v, float* red)
+// sum over the warp; every lane gets the total
+__device__ __forceinline__ float warp_sum(float v)
 {
 _Pragma("unroll")
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    return (red[0] + red[1]) + (red[2] + red[3]);
+    return v;
 }
+// slot of this warp among the per-warp partial sums of a tile
+__device__ __forceinline__ int warp_slot() { return (int)blockIdx.x * kWarps + (int)(threadIdx.x >> 5); }
 
 // ---------------------------------------------------------------------------
 // batch intake: bitpacked [B][W] words -> bit planes [nbits][Bp/32]
@@ -145,18 +146,22 @@ _Pragma("unroll")
 __global__ void k_u_planes(const uint32_t* __restrict__ src, long long B, int W, int nbits, long long Bp,
                            uint32_t* __restrict__ dst)
 {
+    // one warp per (32 shots, one source word): lane l loads shot 32 wd + l's
+    // word, and the ballot over bit k is row 32 w + k of those 32 shots
     const long long W32 = Bp / 32;
-    const long long total = (long long)nbits * W32;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(q / W32);
-        const long long wd = q % W32;
-        uint32_t v = 0;
+    const long long nwarp = W32 * (long long)W;
+    const int lane = threadIdx.x & 31;
+    for (long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nwarp;
+         q += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const long long wd = q / W;
+        const int w = (int)(q % W);
+        const long long b = 32 * wd + lane;
+        const uint32_t v = (b < B) ? src[(size_t)b * W + w] : 0u;
         for (int k = 0; k < 32; ++k) {
-            const long long b = 32 * wd + k;
-            if (b < B) v |= ((src[(size_t)b * W + (i >> 5)] >> (i & 31)) & 1u) << k;
+            const uint32_t bal = __ballot_sync(0xffffffffu, (v >> k) & 1u);
+            const int i = 32 * w + k;
+            if (lane == k && i < nbits) dst[(size_t)i * (size_t)W32 + (size_t)wd] = bal;
         }
-        dst[(size_t)i * (size_t)W32 + (size_t)wd] = v;
     }
 }
 
@@ -171,12 +176,12 @@ __global__ void k_u_init(UArgs a, float* __restrict__ E0)
     }
 }
 
-// Loops over the edges of a row or column: with CACHE the loop is unrolled up
-// to kCap with compile-time indices, so each edge's vector stays in a
-// register between passes; without it the vector is loaded again.
-#define U_FOR_EDGES(CACHE, k, deg, ...)                      \
-    if (CACHE) {                                            \
-        _Pragma("unroll") for (int k = 0; k < kCap; ++k)    \
+// Loops over the edges of a row or column: with CAP > 0 the loop is unrolled
+// up to CAP with compile-time indices, so each edge's vector stays in a
+// register between passes; with CAP = 0 the vector is loaded again.
+#define U_FOR_EDGES(CAP, k, deg, ...)                        \
+    if (CAP > 0) {                                          \
+        _Pragma("unroll") for (int k = 0; k < CAP; ++k)     \
             if (k < (deg)) { __VA_ARGS__ }                  \
     } else {                                                \
         for (int k = 0; k < (deg); ++k) { __VA_ARGS__ }     \
@@ -185,7 +190,7 @@ __global__ void k_u_init(UArgs a, float* __restrict__ E0)
 // ---------------------------------------------------------------------------
 // check pass (Eq. 1 with weights): D(t) from E(t-1)
 // ---------------------------------------------------------------------------
-template <bool CACHE>
+template <int CAP>
 __global__ void __launch_bounds__(kThreads) k_u_check(UArgs a, const float* __restrict__ Ein, float* __restrict__ D,
                                                       int t)
 {
@@ -198,10 +203,10 @@ __global__ void __launch_bounds__(kThreads) k_u_check(UArgs a, const float* __re
         uint32_t neg[4];
 _Pragma("unroll")
         for (int c = 0; c < 4; ++c) { m1[c] = a.L; m2[c] = a.L; neg[c] = (s4 >> c) & 1u; }
-        float4 x[CACHE ? kCap : 1];
-        U_FOR_EDGES(CACHE, k, deg, {
+        float4 x[CAP > 0 ? CAP : 1];
+        U_FOR_EDGES(CAP, k, deg, {
             const float4 v = ld4(Ein, rb + k, a.Bp, b);
-            if (CACHE) x[CACHE ? k : 0] = v;
+            if (CAP > 0) x[CAP > 0 ? k : 0] = v;
 _Pragma("unroll")
             for (int c = 0; c < 4; ++c) {
                 const float y = comp(v, c), m = fabsf(y);
@@ -210,8 +215,8 @@ _Pragma("unroll")
                 neg[c] ^= (y < 0.f) ? 1u : 0u;
             }
         })
-        U_FOR_EDGES(CACHE, k, deg, {
-            const float4 v = CACHE ? x[CACHE ? k : 0] : ld4(Ein, rb + k, a.Bp, b);
+        U_FOR_EDGES(CAP, k, deg, {
+            const float4 v = CAP > 0 ? x[CAP > 0 ? k : 0] : ld4(Ein, rb + k, a.Bp, b);
             const float wv = __ldg(wt + rb + k);
             float4 d;
 _Pragma("unroll")
@@ -229,29 +234,28 @@ _Pragma("unroll")
 // ---------------------------------------------------------------------------
 // error pass (Eqs. 2-3): Lambda(t), E(t), loss terms
 // ---------------------------------------------------------------------------
-template <bool CACHE>
+template <int CAP>
 __global__ void __launch_bounds__(kThreads) k_u_var(UArgs a, const float* __restrict__ D, float* __restrict__ Eout,
                                                     float* __restrict__ lamT, float* __restrict__ llr,
                                                     float* __restrict__ loss_part)
 {
-    __shared__ float red[4];
     const long long b = (long long)blockIdx.x * kTile + 4 * threadIdx.x;
     for (int j = blockIdx.y; j < a.N; j += gridDim.y) {
         const int kb = __ldg(a.col_ptr + j), deg = __ldg(a.col_ptr + j + 1) - kb;
         const float lj = __ldg(a.lam + j);
         float4 post = make_float4(lj, lj, lj, lj);
-        float4 x[CACHE ? kCap : 1];
-        U_FOR_EDGES(CACHE, k, deg, {
+        float4 x[CAP > 0 ? CAP : 1];
+        U_FOR_EDGES(CAP, k, deg, {
             const float4 v = ld4(D, __ldg(a.col_edge + kb + k), a.Bp, b);
-            if (CACHE) x[CACHE ? k : 0] = v;
+            if (CAP > 0) x[CAP > 0 ? k : 0] = v;
             post.x = __fadd_rn(post.x, v.x);
             post.y = __fadd_rn(post.y, v.y);
             post.z = __fadd_rn(post.z, v.z);
             post.w = __fadd_rn(post.w, v.w);
         })
-        U_FOR_EDGES(CACHE, k, deg, {
+        U_FOR_EDGES(CAP, k, deg, {
             const int e = __ldg(a.col_edge + kb + k);
-            const float4 v = CACHE ? x[CACHE ? k : 0] : ld4(D, e, a.Bp, b);
+            const float4 v = CAP > 0 ? x[CAP > 0 ? k : 0] : ld4(D, e, a.Bp, b);
             float4 o;
 _Pragma("unroll")
             for (int c = 0; c < 4; ++c) setc(o, c, fminf(fmaxf(__fsub_rn(comp(post, c), comp(v, c)), -a.L), a.L));
@@ -271,41 +275,43 @@ _Pragma("unroll")
                 const float p = comp(post, c);
                 if (b + c < a.B) l += ((y4 >> c) & 1u) ? softplus(p) : softplus(-p);
             }
-            l = block_sum(l, red);
-            if (threadIdx.x == 0) loss_part[(size_t)j * a.ntile + blockIdx.x] = l;
+            l = warp_sum(l);
+            if ((threadIdx.x & 31) == 0) loss_part[(size_t)j * a.ntile * kWarps + warp_slot()] = l;
         }
     }
 }
 
-// loss per iteration: partial sums in a fixed order, in double
-__global__ void k_u_loss(const float* __restrict__ loss_part, int T, int N, int ntile, double scale,
-                         float* __restrict__ out)
+// loss term of iteration t (block t): its partial sums added in a fixed order, in double
+__global__ void k_u_loss(const float* __restrict__ loss_part, int N, int nslot, double scale, float* __restrict__ out)
 {
     __shared__ double red[256];
-    double total = 0.0;
-    for (int t = 0; t < T; ++t) {
-        const float* p = loss_part + (size_t)t * N * ntile;
-        double s = 0.0;
-        for (long long q = threadIdx.x; q < (long long)N * ntile; q += blockDim.x) s += (double)p[q];
-        red[threadIdx.x] = s;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            out[1 + t] = (float)(red[0] * scale);
-            total += red[0] * scale;
-        }
+    const int t = blockIdx.x;
+    const float* p = loss_part + (size_t)t * N * nslot;
+    double s = 0.0;
+    for (long long q = threadIdx.x; q < (long long)N * nslot; q += blockDim.x) s += (double)p[q];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = (float)total;
+    if (threadIdx.x == 0) out[1 + t] = (float)(red[0] * scale);
+}
+
+// the loss: the T terms added in order
+__global__ void k_u_loss_total(int T, float* __restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int t = 0; t < T; ++t) s += (double)out[1 + t];
+        out[0] = (float)s;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // adjoint of the error pass at iteration t: gD(t) from gE(t) and the loss
 // ---------------------------------------------------------------------------
-template <bool CACHE>
+template <int CAP>
 __global__ void __launch_bounds__(kThreads) k_u_bvar(UArgs a, const float* __restrict__ gEin,
                                                      const float* __restrict__ Et, const float* __restrict__ lamT,
                                                      const float* __restrict__ gout, double scale,
@@ -334,18 +340,18 @@ _Pragma("unroll")
                 if (!(fabsf(comp(v, c)) < a.L)) setc(g, c, 0.f);
             return g;
         };
-        float4 ge[CACHE ? kCap : 1];
+        float4 ge[CAP > 0 ? CAP : 1];
         if (gEin) {
-            U_FOR_EDGES(CACHE, k, deg, {
+            U_FOR_EDGES(CAP, k, deg, {
                 const float4 g = gE_of(__ldg(a.col_edge + kb + k));
-                if (CACHE) ge[CACHE ? k : 0] = g;
+                if (CAP > 0) ge[CAP > 0 ? k : 0] = g;
                 gl.x += g.x; gl.y += g.y; gl.z += g.z; gl.w += g.w;
             })
         }
-        U_FOR_EDGES(CACHE, k, deg, {
+        U_FOR_EDGES(CAP, k, deg, {
             const int e = __ldg(a.col_edge + kb + k);
             float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gEin) g = CACHE ? ge[CACHE ? k : 0] : gE_of(e);
+            if (gEin) g = CAP > 0 ? ge[CAP > 0 ? k : 0] : gE_of(e);
             st4(gD, e, a.Bp, b, make_float4(gl.x - g.x, gl.y - g.y, gl.z - g.z, gl.w - g.w));
         })
     }
@@ -354,12 +360,11 @@ _Pragma("unroll")
 // ---------------------------------------------------------------------------
 // adjoint of the check pass at iteration t: weight gradients and gE(t-1)
 // ---------------------------------------------------------------------------
-template <bool CACHE>
+template <int CAP>
 __global__ void __launch_bounds__(kThreads) k_u_bcheck(UArgs a, const float* __restrict__ Eprev,
                                                        const float* __restrict__ gD, float* __restrict__ gEprev,
                                                        float* __restrict__ gw_part, int t)
 {
-    __shared__ float red[4];
     const long long b = (long long)blockIdx.x * kTile + 4 * threadIdx.x;
     const float* wt = a.w + (size_t)(t - 1) * (size_t)a.E;
     for (int i = blockIdx.y; i < a.M; i += gridDim.y) {
@@ -373,11 +378,11 @@ _Pragma("unroll")
             m1[c] = a.L; m2[c] = a.L; v1[c] = 0.f; v2[c] = 0.f; i1[c] = -1; i2[c] = -1;
             neg[c] = (s4 >> c) & 1u;
         }
-        float4 x[CACHE ? kCap : 1];
+        float4 x[CAP > 0 ? CAP : 1];
         // the two smallest magnitudes with their edges (lowest index among equals)
-        U_FOR_EDGES(CACHE, k, deg, {
+        U_FOR_EDGES(CAP, k, deg, {
             const float4 v = ld4(Eprev, rb + k, a.Bp, b);
-            if (CACHE) x[CACHE ? k : 0] = v;
+            if (CAP > 0) x[CAP > 0 ? k : 0] = v;
 _Pragma("unroll")
             for (int c = 0; c < 4; ++c) {
                 const float y = comp(v, c), m = fabsf(y);
@@ -391,8 +396,8 @@ _Pragma("unroll")
             }
         })
         float acc1[4] = {0.f, 0.f, 0.f, 0.f}, g1[4] = {0.f, 0.f, 0.f, 0.f};
-        U_FOR_EDGES(CACHE, k, deg, {
-            const float4 v = CACHE ? x[CACHE ? k : 0] : ld4(Eprev, rb + k, a.Bp, b);
+        U_FOR_EDGES(CAP, k, deg, {
+            const float4 v = CAP > 0 ? x[CAP > 0 ? k : 0] : ld4(Eprev, rb + k, a.Bp, b);
             const float4 g = ld4(gD, rb + k, a.Bp, b);
             const float wv = __ldg(wt + rb + k);
             float gw = 0.f;
@@ -406,11 +411,11 @@ _Pragma("unroll")
                 const float gm = gd * wv * sig;
                 if (k == i1[c]) g1[c] = gm; else acc1[c] += gm;
             }
-            gw = block_sum(gw, red);
-            if (threadIdx.x == 0) gw_part[(size_t)blockIdx.x * a.E + rb + k] = gw;
+            gw = warp_sum(gw);
+            if ((threadIdx.x & 31) == 0) gw_part[(size_t)warp_slot() * a.E + rb + k] = gw;
         })
         if (gEprev) {
-            U_FOR_EDGES(CACHE, k, deg, {
+            U_FOR_EDGES(CAP, k, deg, {
                 float4 o;
 _Pragma("unroll")
                 for (int c = 0; c < 4; ++c) {
@@ -425,7 +430,7 @@ _Pragma("unroll")
     }
 }
 
-// weight gradients: partial sums over shot tiles added in a fixed order
+// weight gradients: the per-warp partial sums added in a fixed order
 __global__ void k_u_gw(const float* __restrict__ gw_part, int T, int ntile, int E, float* __restrict__ grad)
 {
     const long long total = (long long)T * E;
@@ -438,6 +443,9 @@ __global__ void k_u_gw(const float* __restrict__ gw_part, int T, int ntile, int 
         grad[q] = s;
     }
 }
+
+// register cache for rows / columns of degree at most 4 or 8, none beyond
+int cap_of(int max_deg) { return max_deg <= 4 ? 4 : (max_deg <= 8 ? 8 : 0); }
 
 int grid_y(int items) { return items < 65535 ? (items > 0 ? items : 1) : 65535; }
 
@@ -497,8 +505,11 @@ void launch_check(const UArgs& a, const DevGraph& g, const float* Ein, float* D,
 {
     const dim3 grid(a.ntile, grid_y(a.M));
     Timed tm(hk, kKindCheck);
-    if (g.max_row_deg <= kCap) k_u_check<true><<<grid, kThreads, 0, s>>>(a, Ein, D, t);
-    else k_u_check<false><<<grid, kThreads, 0, s>>>(a, Ein, D, t);
+    switch (cap_of(g.max_row_deg)) {
+        case 4: k_u_check<4><<<grid, kThreads, 0, s>>>(a, Ein, D, t); break;
+        case 8: k_u_check<8><<<grid, kThreads, 0, s>>>(a, Ein, D, t); break;
+        default: k_u_check<0><<<grid, kThreads, 0, s>>>(a, Ein, D, t); break;
+    }
 }
 
 void launch_var(const UArgs& a, const DevGraph& g, const float* D, float* Eout, float* lamT, float* llr,
@@ -506,8 +517,11 @@ void launch_var(const UArgs& a, const DevGraph& g, const float* D, float* Eout, 
 {
     const dim3 grid(a.ntile, grid_y(a.N));
     Timed tm(hk, kKindVar);
-    if (g.max_col_deg <= kCap) k_u_var<true><<<grid, kThreads, 0, s>>>(a, D, Eout, lamT, llr, loss_part);
-    else k_u_var<false><<<grid, kThreads, 0, s>>>(a, D, Eout, lamT, llr, loss_part);
+    switch (cap_of(g.max_col_deg)) {
+        case 4: k_u_var<4><<<grid, kThreads, 0, s>>>(a, D, Eout, lamT, llr, loss_part); break;
+        case 8: k_u_var<8><<<grid, kThreads, 0, s>>>(a, D, Eout, lamT, llr, loss_part); break;
+        default: k_u_var<0><<<grid, kThreads, 0, s>>>(a, D, Eout, lamT, llr, loss_part); break;
+    }
 }
 
 }  // namespace
@@ -561,12 +575,13 @@ int bsd_unrolled_forward(const bsd_decoder* dec, const uint32_t* d_syndromes, co
         launch_check(a, *g, src, u.D, t, s, hk);
         float* dst = (t % k == 0 && t < T) ? u.ck + (size_t)(t / k) * EB : u.seg;
         launch_var(a, *g, u.D, dst, nullptr, d_llr ? d_llr + (size_t)(t - 1) * (size_t)B * g->N : nullptr,
-                   u.loss_part + (size_t)(t - 1) * g->N * a.ntile, s, hk);
+                   u.loss_part + (size_t)(t - 1) * g->N * a.ntile * kWarps, s, hk);
         src = dst;
     }
     {
         Timed tm(hk, kKindOther);
-        k_u_loss<<<1, 256, 0, s>>>(u.loss_part, T, g->N, a.ntile, 1.0 / ((double)B * (double)g->N), d_loss);
+        k_u_loss<<<T, 256, 0, s>>>(u.loss_part, g->N, a.ntile * kWarps, 1.0 / ((double)B * (double)g->N), d_loss);
+        k_u_loss_total<<<1, 32, 0, s>>>(T, d_loss);
     }
     return CUDA_FAILED(cudaGetLastError()) ? BSD_ERR_CUDA : BSD_OK;
 }
@@ -590,7 +605,7 @@ int bsd_unrolled_backward(const bsd_decoder* dec, int64_t B, int32_t T, int32_t 
     const int k = ckpt_every;
     const size_t EB = (size_t)g->E * (size_t)a.Bp, NB = (size_t)g->N * (size_t)a.Bp;
     const double scale = 1.0 / ((double)B * (double)g->N);
-    const bool cache_c = g->max_col_deg <= kCap, cache_r = g->max_row_deg <= kCap;
+    const int cap_c = cap_of(g->max_col_deg), cap_r = cap_of(g->max_row_deg);
     const dim3 gcol(a.ntile, grid_y(g->N)), grow(a.ntile, grid_y(g->M));
     LaunchHooks hks;
     const LaunchHooks* hk = decoder_hooks(dec, s, &hks) ? &hks : nullptr;
@@ -612,23 +627,25 @@ int bsd_unrolled_backward(const bsd_decoder* dec, int64_t B, int32_t T, int32_t 
             const float* gEin = (t == T) ? nullptr : u.gE[cur];
             {
                 Timed tm(hk, kKindBVar);
-                if (cache_c) k_u_bvar<true><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, u.gD);
-                else k_u_bvar<false><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, u.gD);
+                if (cap_c == 4) k_u_bvar<4><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, u.gD);
+                else if (cap_c == 8) k_u_bvar<8><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, u.gD);
+                else k_u_bvar<0><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, u.gD);
             }
             const float* Eprev = (t == t0 + 1) ? u.ck + (size_t)c * EB : u.seg + (size_t)(t - t0 - 2) * EB;
             float* gEout = (t > 1) ? u.gE[cur ^ 1] : nullptr;
-            float* gwp = u.gw_part + (size_t)(t - 1) * a.ntile * g->E;
+            float* gwp = u.gw_part + (size_t)(t - 1) * a.ntile * kWarps * g->E;
             {
                 Timed tm(hk, kKindBCheck);
-                if (cache_r) k_u_bcheck<true><<<grow, kThreads, 0, s>>>(a, Eprev, u.gD, gEout, gwp, t);
-                else k_u_bcheck<false><<<grow, kThreads, 0, s>>>(a, Eprev, u.gD, gEout, gwp, t);
+                if (cap_r == 4) k_u_bcheck<4><<<grow, kThreads, 0, s>>>(a, Eprev, u.gD, gEout, gwp, t);
+                else if (cap_r == 8) k_u_bcheck<8><<<grow, kThreads, 0, s>>>(a, Eprev, u.gD, gEout, gwp, t);
+                else k_u_bcheck<0><<<grow, kThreads, 0, s>>>(a, Eprev, u.gD, gEout, gwp, t);
             }
             cur ^= 1;
         }
     }
     {
         Timed tm(hk, kKindOther);
-        k_u_gw<<<1024, 256, 0, s>>>(u.gw_part, T, a.ntile, g->E, d_grad_weights);
+        k_u_gw<<<1024, 256, 0, s>>>(u.gw_part, T, a.ntile * kWarps, g->E, d_grad_weights);
     }
     return CUDA_FAILED(cudaGetLastError()) ? BSD_ERR_CUDA : BSD_OK;
 }
