@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define BSD_PARAMS_VERSION 1u
+#define BSD_PARAMS_VERSION 2u
 
 /* return codes */
 #define BSD_OK               0
@@ -96,6 +96,11 @@ typedef struct {
                                   default (1e-3 for FP16, 1e-2 for BF16), < 0 no near-tie
                                   re-runs; with BSD_FP32 only a positive value flags shots */
     int64_t  workspace_bytes;  /* device workspace budget; 0 = library default (4 GiB) */
+    int32_t  group_warps;      /* threads per BP candidate: 0 chosen by the library (and by
+                                  bsd_autotune), 1 one warp per candidate, 2..16 a block of
+                                  that many warps per candidate (codes without the small engine's
+                                  layout, or forced); results do not depend on it */
+    int32_t  reserved0;        /* must be 0 */
 } bsd_params;
 
 /* Fill *out with the library defaults: beam8_230iters, ms_scale 1,

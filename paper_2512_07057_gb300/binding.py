@@ -12,7 +12,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbsd.so")
 
-BSD_PARAMS_VERSION = 1
+BSD_PARAMS_VERSION = 2
 BSD_OK = 0
 BSD_ERR_INVALID_ARG = -1
 BSD_ERR_CUDA = -2
@@ -43,7 +43,8 @@ class bsd_params(C.Structure):
     _fields_ = [("struct_version", C.c_uint32), ("max_rounds", C.c_int32), ("beam_width", C.c_int32),
                 ("initial_iters", C.c_int32), ("iters_per_round", C.c_int32), ("num_results", C.c_int32),
                 ("ms_scale", C.c_float), ("llr_clamp", C.c_float), ("msg_precision", C.c_int32),
-                ("tie_guard_rel", C.c_float), ("workspace_bytes", C.c_int64)]
+                ("tie_guard_rel", C.c_float), ("workspace_bytes", C.c_int64), ("group_warps", C.c_int32),
+                ("reserved0", C.c_int32)]
 
 
 class BsdError(RuntimeError):

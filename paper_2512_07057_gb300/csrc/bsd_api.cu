@@ -94,6 +94,7 @@ int validate_params(const bsd_params* p)
         return BSD_ERR_UNSUPPORTED;
     if (!std::isfinite(p->tie_guard_rel)) return BSD_ERR_INVALID_ARG;
     if (p->workspace_bytes < 0) return BSD_ERR_INVALID_ARG;
+    if (p->group_warps < 0 || p->group_warps > 16 || p->reserved0 != 0) return BSD_ERR_INVALID_ARG;
     return BSD_OK;
 }
 
@@ -360,7 +361,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     cfg.weights = nullptr;         // the scale alpha until bsd_set_weights
     cfg.wT = 0;
 
-    rc = configure_kernels(g, cfg, device, &dec->ls);
+    rc = configure_kernels(g, cfg, device, params->group_warps, 0, &dec->ls);
     if (rc) { bsd_destroy(dec); return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA; }
 
     // ---- workspace: a seed store of S shots and a beam window of A active
@@ -636,7 +637,9 @@ int bsd_set_weights(bsd_decoder* dec, const float* h_weights, int32_t T)
     cfg.wT = T;
     DevGraph g = dec->g;
     LaunchShape ls{};
-    const int rc = configure_kernels(g, cfg, dec->device, &ls);
+    // keep the decoder's launch shape (engine family, block size)
+    const int rc = configure_kernels(g, cfg, dec->device, dec->ls.group_warps >= 2 ? dec->ls.group_warps : 1,
+                                     dec->ls.group_warps >= 2 ? 0 : dec->ls.warps_per_block, &ls);
     if (rc) {
         if (d_w) cudaFree(d_w);
         return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA;

@@ -140,10 +140,12 @@ size_t work_head_bytes(const DecCfg& cfg);
 // host-side launch helpers (bsd_kernels.cu)
 struct LaunchShape {
     int warps_per_block;
+    int group_warps;       // warps per BP candidate: 1 (a warp) or the whole block
+    int select_warps;      // block size of the selection kernel, in warps (<= 8)
     int grid_seed, grid_round, grid_select;
     size_t smem_bp;        // dynamic shared memory of the seed / round kernels
     size_t smem_select;
-    int dv;                // compiled column-degree bound used
+    int dv;                // engine id
 };
 
 // optional callbacks around every kernel launch; kinds 0 seed, 1 round,
@@ -156,7 +158,11 @@ struct LaunchHooks {
     void* ctx;
 };
 
-int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls);
+// choose the engine and launch shape; group_warps 0 = automatic, 1 = a warp
+// per candidate, >= 2 = a block of that many warps per candidate;
+// warps_per_block 0 = automatic (warp engines only)
+int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, int group_warps, int warps_per_block,
+                      LaunchShape* ls);
 
 // decode one chunk: reset counters and set the run descriptor, then the seed
 // kernel and as many beam passes as the chunk has active windows.  With a

@@ -83,15 +83,85 @@ template <> struct Store<2> {
 __host__ __device__ __forceinline__ size_t snap_bytes(const DevGraph& g) { return (size_t)g.Epad * (size_t)g.msg_bytes; }
 __host__ __device__ __forceinline__ int snap_vec16(const DevGraph& g) { return (int)(snap_bytes(g) / 16); }
 
-// copy n16 16-byte vectors (the E snapshot) with a warp
-__device__ __forceinline__ void warp_copy16(void* dst, const void* src, int n16)
+// copy n16 16-byte vectors (the E snapshot) with the threads of a candidate group
+template <class G>
+__device__ __forceinline__ void group_copy16(const G& grp, void* dst, const void* src, int n16)
 {
     const uint4* s = reinterpret_cast<const uint4*>(src);
     uint4* d = reinterpret_cast<uint4*>(dst);
-    for (int q = (threadIdx.x & 31); q < n16; q += 32) d[q] = s[q];
+    for (int q = grp.rank(); q < n16; q += grp.size()) d[q] = s[q];
 }
 
 enum : uint32_t { ST_SEED = 1u, ST_BEAM = 2u, ST_FAILED = 4u, ST_NEAR = 8u, ST_RERUN = 16u };
+
+// ----------------------------------------------------------------------------
+// candidate groups: the threads that process one BP candidate together.
+// WarpGroup is one warp (a block holds several candidates); BlockGroup is a
+// whole block (one candidate per block), for codes whose per-candidate state
+// leaves room for only a few warps per SM.  Every row and column is computed
+// by one thread and every reduction is exact (minima with index ties, integer
+// sums, XOR), so both give the same results bit for bit.
+// ----------------------------------------------------------------------------
+struct ArgRec {                // per-warp partial of the argmin / score reduction
+    float best, second;
+    int bj, pad;
+    unsigned long long s;
+};
+
+struct WarpGroup {
+    static constexpr bool kBlock = false;
+    __device__ static WarpGroup make(char*) { return WarpGroup{}; }
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ int size() const { return 32; }
+    __device__ __forceinline__ int warp() const { return 0; }
+    __device__ __forceinline__ int nwarps() const { return 1; }
+    __device__ __forceinline__ int index() const { return threadIdx.x >> 5; }       // candidate slot of the block
+    __device__ __forceinline__ int per_block() const { return blockDim.x >> 5; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ bool any(bool p) const { return __any_sync(FULLMASK, p); }
+    __device__ __forceinline__ int bcast(int v) const { return __shfl_sync(FULLMASK, v, 0); }
+    __device__ __forceinline__ uint32_t xor_all(uint32_t v) const
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(FULLMASK, v, o);
+        return v;
+    }
+};
+
+struct BlockGroup {
+    static constexpr bool kBlock = true;
+    ArgRec* rec;               // shared scratch: one record per warp (16 at most)
+    __device__ static BlockGroup make(char* scratch) { return BlockGroup{reinterpret_cast<ArgRec*>(scratch)}; }
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ int size() const { return blockDim.x; }
+    __device__ __forceinline__ int warp() const { return threadIdx.x >> 5; }
+    __device__ __forceinline__ int nwarps() const { return blockDim.x >> 5; }
+    __device__ __forceinline__ int index() const { return 0; }
+    __device__ __forceinline__ int per_block() const { return 1; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p ? 1 : 0) != 0; }
+    __device__ __forceinline__ int bcast(int v) const
+    {
+        if (threadIdx.x == 0) rec[0].bj = v;
+        __syncthreads();
+        const int r = rec[0].bj;
+        __syncthreads();
+        return r;
+    }
+    __device__ __forceinline__ uint32_t xor_all(uint32_t v) const
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(FULLMASK, v, o);
+        if ((threadIdx.x & 31) == 0) rec[threadIdx.x >> 5].pad = (int)v;
+        __syncthreads();
+        uint32_t r = 0;
+        for (int q = 0; q < nwarps(); ++q) r ^= (uint32_t)rec[q].pad;
+        __syncthreads();
+        return r;
+    }
+};
+
+// shared scratch a candidate group needs beyond the candidate's own state
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -149,8 +219,8 @@ __device__ inline unsigned long long fixq(float x)
 // st.ehat holds e^(t) of the last iteration (masked positions 0), st.sumllr
 // holds the sum over the iterations run of Lambda_j(t).  If post_out is not
 // null, Lambda_j(max_iters) is written there.
-template <int DV, int P, bool W>
-__device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
+template <int DV, int P, bool W, class G>
+__device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
                           bool stop, int* success, float* post_out)
 {
     using S = Store<P>;
@@ -161,12 +231,12 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
     int iters = 0;
     int ok = 0;
     for (int t = 1; t <= max_iters; ++t) {
-        for (int q = lane; q < g.WM; q += 32) st.par[q] = st.sp[q];
+        for (int q = grp.rank(); q < g.WM; q += grp.size()) st.par[q] = st.sp[q];
         // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
         const float* wt = W ? cfg.weights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
 
         // ---- detector pass (Eq. 1): min1, min2, argmin and sign parity per row
-        for (int i = lane; i < g.M; i += 32) {
+        for (int i = grp.rank(); i < g.M; i += grp.size()) {
             const int rb = __ldg(g.row_ptr + i), re = __ldg(g.row_ptr + i + 1);
             float m1 = L, m2 = L;
             int id = -1;
@@ -180,10 +250,11 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
             }
             st.rs[i] = make_float4(m1, m2, __int_as_float(id), __uint_as_float(neg));
         }
-        __syncwarp();
+        grp.sync();
 
-        // ---- error-node pass (Eqs. 2-4) and syndrome parity
-        for (int jb = 0; jb < g.N; jb += 32) {
+        // ---- error-node pass (Eqs. 2-4) and syndrome parity; each warp owns
+        // whole 32-column words of e^
+        for (int jb = 32 * grp.warp(); jb < g.N; jb += 32 * grp.nwarps()) {
             const int j = jb + lane;
             uint32_t ebit = 0;
             const bool act = (j < g.N) && !((st.mask[jb >> 5] >> lane) & 1u);
@@ -248,35 +319,54 @@ __device__ int bp_iterate(const DevGraph& g, const DecCfg& cfg, const WarpState&
             const uint32_t bal = __ballot_sync(FULLMASK, ebit);
             if (lane == 0) st.ehat[jb >> 5] = bal;
         }
-        __syncwarp();
+        grp.sync();
 
         // ---- stopping rule: H e^(t) = s'
         uint32_t nz = 0;
-        for (int q = lane; q < g.WM; q += 32) nz |= st.par[q];
-        ok = !__any_sync(FULLMASK, nz != 0u);
+        for (int q = grp.rank(); q < g.WM; q += grp.size()) nz |= st.par[q];
+        ok = !grp.any(nz != 0u);
         iters = t;
-        __syncwarp();
+        grp.sync();
         if (ok && stop) break;
     }
     *success = ok;
     return iters;
 }
 
-// warp reduction of per-lane (two smallest |sum_LLR|, node of the smallest,
-// sum of q(|sum_LLR|)): the smaller value wins, equal values go to the lower
-// node index.  *tie is set when the relative margin between the smallest and
-// the second smallest lies strictly inside (0, guard).
-__device__ inline void reduce_argmin_score(float best, float second, int bj, unsigned long long s, double guard,
-                                           int* next_pos, long long* S, int* tie)
+// reduction of per-thread (two smallest |sum_LLR|, node of the smallest, sum
+// of q(|sum_LLR|)) over a candidate group: the smaller value wins, equal
+// values go to the lower node index; every step is exact, so the result does
+// not depend on the group's shape.  *tie is set when the relative margin
+// between the smallest and the second smallest lies strictly inside
+// (0, guard).
+__device__ __forceinline__ void merge_argmin(float& best, float& second, int& bj, float ob, float os, int oj)
+{
+    second = fminf(fmaxf(best, ob), fminf(second, os));
+    if (oj >= 0 && (bj < 0 || ob < best || (ob == best && oj < bj))) { best = ob; bj = oj; }
+}
+
+template <class G>
+__device__ inline void reduce_argmin_score(const G& grp, float best, float second, int bj, unsigned long long s,
+                                           double guard, int* next_pos, long long* S, int* tie)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float ob = __shfl_xor_sync(FULLMASK, best, o);
         const float os = __shfl_xor_sync(FULLMASK, second, o);
         const int oj = __shfl_xor_sync(FULLMASK, bj, o);
-        second = fminf(fmaxf(best, ob), fminf(second, os));
-        if (oj >= 0 && (bj < 0 || ob < best || (ob == best && oj < bj))) { best = ob; bj = oj; }
+        merge_argmin(best, second, bj, ob, os, oj);
         s += __shfl_xor_sync(FULLMASK, s, o);
+    }
+    if constexpr (G::kBlock) {
+        if ((threadIdx.x & 31) == 0) grp.rec[threadIdx.x >> 5] = ArgRec{best, second, bj, 0, s};
+        __syncthreads();
+        best = INFINITY; second = INFINITY; bj = -1; s = 0;
+        for (int q = 0; q < grp.nwarps(); ++q) {
+            const ArgRec r = grp.rec[q];
+            merge_argmin(best, second, bj, r.best, r.second, r.bj);
+            s += r.s;
+        }
+        __syncthreads();
     }
     *next_pos = bj;
     *S = (long long)s;
@@ -303,20 +393,20 @@ __device__ __forceinline__ void two_smallest(float a, int j, float* best, float*
 }
 
 // least reliable unmasked node (lowest index on ties) and the score numerator
-__device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, double guard, int* next_pos,
-                                        long long* S, int* tie)
+template <class G>
+__device__ inline void argmin_and_score(const G& grp, const DevGraph& g, const WarpState& st, double guard,
+                                        int* next_pos, long long* S, int* tie)
 {
-    const int lane = threadIdx.x & 31;
     float best = INFINITY, second = INFINITY;
     int bj = -1;
     unsigned long long s = 0;
-    for (int j = lane; j < g.N; j += 32) {
+    for (int j = grp.rank(); j < g.N; j += grp.size()) {
         if ((st.mask[j >> 5] >> (j & 31)) & 1u) continue;
         const float a = fabsf(st.sumllr[j]);
         two_smallest(a, j, &best, &second, &bj);
         s += fixq(a);
     }
-    reduce_argmin_score(best, second, bj, s, guard, next_pos, S, tie);
+    reduce_argmin_score(grp, best, second, bj, s, guard, next_pos, S, tie);
 }
 
 // ----------------------------------------------------------------------------
@@ -324,28 +414,31 @@ __device__ inline void argmin_and_score(const DevGraph& g, const WarpState& st, 
 // ----------------------------------------------------------------------------
 // GenericEngine: any code whose column degree is at most DV; graph tables
 // are read from global memory (L1-resident) and sum_LLR lives in shared memory.
-template <int DV, int P, bool W = false>
+template <int DV, int P, bool W = false, class G = WarpGroup>
 struct GenericEngine {
+    using Grp = G;
     static constexpr int kMinBlocks = 1;
+    static constexpr int kMaxThreads = G::kBlock ? 512 : 256;
     static constexpr int kPrec = P;
+    G grp;
     __device__ void load_graph(const DevGraph&) {}
     __device__ void clear_sums(const DevGraph& g, const WarpState& st)
     {
-        for (int j = (threadIdx.x & 31); j < g.N; j += 32) st.sumllr[j] = 0.f;
+        for (int j = grp.rank(); j < g.N; j += grp.size()) st.sumllr[j] = 0.f;
     }
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
                        int* success, float* post_out)
     {
-        return bp_iterate<DV, P, W>(g, cfg, st, max_iters, stop, success, post_out);
+        return bp_iterate<DV, P, W>(grp, g, cfg, st, max_iters, stop, success, post_out);
     }
     __device__ void argmin_score(const DevGraph& g, const WarpState& st, double guard, int* np, long long* S,
                                  int* tie)
     {
-        argmin_and_score(g, st, guard, np, S, tie);
+        argmin_and_score(grp, g, st, guard, np, S, tie);
     }
     __device__ void write_sums(const DevGraph& g, const WarpState& st, float* dst)
     {
-        for (int j = (threadIdx.x & 31); j < g.N; j += 32) dst[j] = st.sumllr[j];
+        for (int j = grp.rank(); j < g.N; j += grp.size()) dst[j] = st.sumllr[j];
     }
 };
 
@@ -361,8 +454,11 @@ struct GenericEngine {
 // order).
 template <int CPL, int RPL, int RD, int P, bool W = false>
 struct SmallEngine {
+    using Grp = WarpGroup;
     static constexpr int kMinBlocks = 2;   // at most 128 registers: two 8-warp blocks per SM
+    static constexpr int kMaxThreads = 256;
     static constexpr int kPrec = P;
+    WarpGroup grp;
     using S = Store<P>;
     uint32_t ci[CPL][3];   // (CSR edge id << 16) | row, for column lane + 32 c
     float sum[CPL];
@@ -530,7 +626,7 @@ struct SmallEngine {
             two_smallest(a, lane + 32 * c, &best, &second, &bj);
             s += fixq(a);
         }
-        reduce_argmin_score(best, second, bj, s, guard, np, S, tie);
+        reduce_argmin_score(grp, best, second, bj, s, guard, np, S, tie);
     }
     __device__ void write_sums(const DevGraph& g, const WarpState&, float* dst)
     {
@@ -542,23 +638,22 @@ struct SmallEngine {
 };
 
 // write one shot's outputs: e^, A e^, status, iteration count
+template <class G = WarpGroup>
 __device__ void finalize_shot(const DevGraph& g, const Outputs& out, long long gb, const uint32_t* ehat,
-                              uint32_t status, unsigned long long iters)
+                              uint32_t status, unsigned long long iters, const G& grp = G{})
 {
-    const int lane = threadIdx.x & 31;
     uint32_t* corr = out.corr + gb * g.WN;
-    for (int q = lane; q < g.WN; q += 32) corr[q] = ehat[q];
+    for (int q = grp.rank(); q < g.WN; q += grp.size()) corr[q] = ehat[q];
     if (out.obs != nullptr) {
         for (int wq = 0; wq < g.WK; ++wq) {
             uint32_t acc = 0;
-            for (int j = lane; j < g.N; j += 32)
+            for (int j = grp.rank(); j < g.N; j += grp.size())
                 if ((ehat[j >> 5] >> (j & 31)) & 1u) acc ^= __ldg(g.acol + (size_t)j * g.WK + wq);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(FULLMASK, acc, o);
-            if (lane == 0) out.obs[gb * g.WK + wq] = acc;
+            acc = grp.xor_all(acc);
+            if (grp.rank() == 0) out.obs[gb * g.WK + wq] = acc;
         }
     }
-    if (lane == 0) {
+    if (grp.rank() == 0) {
         out.status[gb] = status;
         if (out.iters != nullptr) out.iters[gb] = iters > 0xffffffffull ? 0xffffffffu : (uint32_t)iters;
     }
@@ -666,72 +761,72 @@ __global__ void k_pass_end(Work w, int n_round_ints, cudaGraphConditionalHandle 
 // seed BP
 // ----------------------------------------------------------------------------
 template <class Eng>
-__global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCfg cfg, Work w)
+__global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevGraph g, DecCfg cfg, Work w)
 {
     extern __shared__ __align__(16) char smem[];
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
+    Eng eng;
+    eng.grp = Eng::Grp::make(smem + warp_smem_bytes(g));
+    const auto& grp = eng.grp;
+    const WarpState st = carve(smem + (size_t)grp.index() * warp_smem_bytes(g), g);
     const RunDesc* dp = w.desc;                  // read fields when needed (keeps registers free)
     count_launch(w);
-    Eng eng;
     eng.load_graph(g);
     for (;;) {
         int b = 0;
-        if (lane == 0) b = atomicAdd(&w.ctr->claim_seed, 1);
-        b = __shfl_sync(FULLMASK, b, 0);
+        if (grp.rank() == 0) b = atomicAdd(&w.ctr->claim_seed, 1);
+        b = grp.bcast(b);
         if (b >= dp->chunk_n) break;
         const long long gb = dp->chunk_base + b;
         const uint32_t* s = dp->synd + gb * g.WM;
         uint32_t nz = 0;
-        for (int q = lane; q < g.WM; q += 32) {
+        for (int q = grp.rank(); q < g.WM; q += grp.size()) {
             const uint32_t x = s[q];
             st.sp[q] = x;
             nz |= x;
         }
-        for (int q = lane; q < g.WN; q += 32) { st.mask[q] = 0u; st.vals[q] = 0u; st.ehat[q] = 0u; }
-        __syncwarp();
+        for (int q = grp.rank(); q < g.WN; q += grp.size()) { st.mask[q] = 0u; st.vals[q] = 0u; st.ehat[q] = 0u; }
+        grp.sync();
         // s = 0 with every Lambda_j > 0: D > 0 at t = 1, so e^(1) = 0 and the
         // seed converges after one iteration (exact, no BP needed)
-        if (!__any_sync(FULLMASK, nz != 0u) && cfg.num_results == 1 && g.all_lam_pos) {
-            finalize_shot(g, dp->out, gb, st.ehat, ST_SEED, 1ull);
-            __syncwarp();
+        if (!grp.any(nz != 0u) && cfg.num_results == 1 && g.all_lam_pos) {
+            finalize_shot(g, dp->out, gb, st.ehat, ST_SEED, 1ull, grp);
+            grp.sync();
             continue;
         }
-        warp_copy16(st.E, g.lamE, snap_vec16(g));
+        group_copy16(grp, st.E, g.lamE, snap_vec16(g));
         eng.clear_sums(g, st);
-        __syncwarp();
+        grp.sync();
         int succ = 0;
         const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr);
-        if (lane == 0) atomicAdd(&w.stats[0], (unsigned long long)it);
-        __syncwarp();
+        if (grp.rank() == 0) atomicAdd(&w.stats[0], (unsigned long long)it);
+        grp.sync();
         if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
-            finalize_shot(g, dp->out, gb, st.ehat, succ ? ST_SEED : ST_FAILED, (unsigned long long)it);
-            __syncwarp();
+            finalize_shot(g, dp->out, gb, st.ehat, succ ? ST_SEED : ST_FAILED, (unsigned long long)it, grp);
+            grp.sync();
             continue;
         }
         int np, tie;
         long long S;
         eng.argmin_score(g, st, cfg.tie_guard, &np, &S, &tie);
         int a = 0;
-        if (lane == 0) a = atomicAdd(&w.ctr->n_active, 1);
-        a = __shfl_sync(FULLMASK, a, 0);
+        if (grp.rank() == 0) a = atomicAdd(&w.ctr->n_active, 1);
+        a = grp.bcast(a);
         // the seed path (Alg. 3): snapshot, s' = s, no fixed node, e^, next_pos
-        warp_copy16(w.seedE + (size_t)a * snap_bytes(g), st.E, snap_vec16(g));
+        group_copy16(grp, w.seedE + (size_t)a * snap_bytes(g), st.E, snap_vec16(g));
         uint32_t* bits = w.seedBits + (size_t)a * (size_t)w.SB;
-        for (int q = lane; q < g.WM; q += 32) bits[q] = st.sp[q];
-        for (int q = lane; q < g.WN; q += 32) {
+        for (int q = grp.rank(); q < g.WM; q += grp.size()) bits[q] = st.sp[q];
+        for (int q = grp.rank(); q < g.WN; q += grp.size()) {
             bits[g.WM + q] = 0u;
             bits[g.WM + g.WN + q] = 0u;
             bits[g.WM + 2 * g.WN + q] = st.ehat[q];
         }
-        if (lane == 0) {
+        if (grp.rank() == 0) {
             SlotMeta m;
             m.S = 0; m.iters = it; m.next_pos = np; m.success = succ; m.flags = tie;
             w.seedMeta[a] = m;
             w.seed_shot[a] = b;
         }
-        __syncwarp();
+        grp.sync();
     }
 }
 
@@ -739,28 +834,28 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_seed(DevGraph g, DecCf
 // one beam round: expand every child and run masked BP (Alg. 2)
 // ----------------------------------------------------------------------------
 template <class Eng>
-__global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecCfg cfg, Work w, int r)
+__global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_round(DevGraph g, DecCfg cfg, Work w, int r)
 {
     extern __shared__ __align__(16) char smem[];
     count_launch(w);
     long long pbase;
     const int cnt = window(w, &pbase);
     if (cnt == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
+    Eng eng;
+    eng.grp = Eng::Grp::make(smem + warp_smem_bytes(g));
+    const auto& grp = eng.grp;
+    const WarpState st = carve(smem + (size_t)grp.index() * warp_smem_bytes(g), g);
     const int W2 = 2 * cfg.w;
     int* rc = round_ctr(w, r);
     // round 1: two children of every window entry; later rounds: the work list
     const int nitems = (r == 1) ? 2 * cnt : *((volatile int*)(rc + 2));
     const int2* items = w.items + (size_t)(r & 1) * (size_t)w.A * (size_t)W2;
     const int cb = r & 1;
-    Eng eng;
     eng.load_graph(g);
     for (;;) {
         int it = 0;
-        if (lane == 0) it = atomicAdd(&rc[0], 1);
-        it = __shfl_sync(FULLMASK, it, 0);
+        if (grp.rank() == 0) it = atomicAdd(&rc[0], 1);
+        it = grp.bcast(it);
         if (it >= nitems) break;
         const int2 item = (r == 1) ? make_int2(it >> 1, it & 1) : items[it];
         const int a = item.x, c = item.y;
@@ -770,12 +865,12 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecC
         if (pos < 0) continue;                     // a path with no unmasked node has no children
         const size_t cslot = slot_index(w, cb, a, c, W2);
         // s' of the child: flip the detectors of pos when it is fixed to 1
-        for (int q = lane; q < g.WM; q += 32) {
+        for (int q = grp.rank(); q < g.WM; q += grp.size()) {
             uint32_t x = par.bits[q];
             if (v) x ^= __ldg(g.hcol + (size_t)pos * g.WM + q);
             st.sp[q] = x;
         }
-        for (int q = lane; q < g.WN; q += 32) {
+        for (int q = grp.rank(); q < g.WN; q += grp.size()) {
             uint32_t m = par.bits[g.WM + q];
             uint32_t vv = par.bits[g.WM + g.WN + q];
             if (q == (pos >> 5)) {
@@ -786,35 +881,35 @@ __global__ void __launch_bounds__(256, Eng::kMinBlocks) k_round(DevGraph g, DecC
             st.vals[q] = vv;
         }
         // warm start from the parent's snapshot
-        warp_copy16(st.E, par.E, snap_vec16(g));
+        group_copy16(grp, st.E, par.E, snap_vec16(g));
         eng.clear_sums(g, st);
-        __syncwarp();
-        for (int q = __ldg(g.col_ptr + pos) + lane; q < __ldg(g.col_ptr + pos + 1); q += 32)
+        grp.sync();
+        for (int q = __ldg(g.col_ptr + pos) + grp.rank(); q < __ldg(g.col_ptr + pos + 1); q += grp.size())
             Store<Eng::kPrec>::st(reinterpret_cast<typename Store<Eng::kPrec>::T*>(st.E), __ldg(g.col_edge + q), cfg.L);
-        __syncwarp();
+        grp.sync();
         int succ = 0;
         const int iters = eng.run(g, cfg, st, cfg.iters_per_round, true, &succ, nullptr);
-        if (lane == 0) atomicAdd(&w.stats[1], (unsigned long long)iters);
-        __syncwarp();
-        for (int q = lane; q < g.WN; q += 32) st.ehat[q] = (st.ehat[q] & ~st.mask[q]) | st.vals[q];
-        __syncwarp();
+        if (grp.rank() == 0) atomicAdd(&w.stats[1], (unsigned long long)iters);
+        grp.sync();
+        for (int q = grp.rank(); q < g.WN; q += grp.size()) st.ehat[q] = (st.ehat[q] & ~st.mask[q]) | st.vals[q];
+        grp.sync();
         int np, tie;
         long long S;
         eng.argmin_score(g, st, cfg.tie_guard, &np, &S, &tie);
-        warp_copy16(w.slotE + cslot * snap_bytes(g), st.E, snap_vec16(g));
+        group_copy16(grp, w.slotE + cslot * snap_bytes(g), st.E, snap_vec16(g));
         uint32_t* cbits = w.slotBits + cslot * (size_t)w.SB;
-        for (int q = lane; q < g.WM; q += 32) cbits[q] = st.sp[q];
-        for (int q = lane; q < g.WN; q += 32) {
+        for (int q = grp.rank(); q < g.WM; q += grp.size()) cbits[q] = st.sp[q];
+        for (int q = grp.rank(); q < g.WN; q += grp.size()) {
             cbits[g.WM + q] = st.mask[q];
             cbits[g.WM + g.WN + q] = st.vals[q];
             cbits[g.WM + 2 * g.WN + q] = st.ehat[q];
         }
-        if (lane == 0) {
+        if (grp.rank() == 0) {
             SlotMeta m;
             m.S = S; m.iters = iters; m.next_pos = np; m.success = succ; m.flags = tie;
             w.slotMeta[cslot] = m;
         }
-        __syncwarp();
+        grp.sync();
     }
 }
 
@@ -1082,27 +1177,29 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
 // plain BP for a fixed number of iterations (LLR measurement)
 // ----------------------------------------------------------------------------
 template <class Eng>
-__global__ void __launch_bounds__(256, Eng::kMinBlocks) k_bp_llr(DevGraph g, DecCfg cfg, const uint32_t* __restrict__ synd, long long B,
-                                                int T, float* llr, float* sum_llr)
+__global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_bp_llr(DevGraph g, DecCfg cfg,
+                                                                           const uint32_t* __restrict__ synd,
+                                                                           long long B, int T, float* llr,
+                                                                           float* sum_llr)
 {
     extern __shared__ __align__(16) char smem[];
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const WarpState st = carve(smem + (size_t)wid * warp_smem_bytes(g), g);
     Eng eng;
+    eng.grp = Eng::Grp::make(smem + warp_smem_bytes(g));
+    const auto& grp = eng.grp;
+    const WarpState st = carve(smem + (size_t)grp.index() * warp_smem_bytes(g), g);
     eng.load_graph(g);
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long b = (long long)blockIdx.x * (blockDim.x >> 5) + wid; b < B; b += nw) {
-        for (int q = lane; q < g.WM; q += 32) st.sp[q] = synd[b * g.WM + q];
-        for (int q = lane; q < g.WN; q += 32) { st.mask[q] = 0u; st.vals[q] = 0u; }
-        warp_copy16(st.E, g.lamE, snap_vec16(g));
+    const long long nw = (long long)gridDim.x * grp.per_block();
+    for (long long b = (long long)blockIdx.x * grp.per_block() + grp.index(); b < B; b += nw) {
+        for (int q = grp.rank(); q < g.WM; q += grp.size()) st.sp[q] = synd[b * g.WM + q];
+        for (int q = grp.rank(); q < g.WN; q += grp.size()) { st.mask[q] = 0u; st.vals[q] = 0u; }
+        group_copy16(grp, st.E, g.lamE, snap_vec16(g));
         eng.clear_sums(g, st);
-        __syncwarp();
+        grp.sync();
         int succ;
         eng.run(g, cfg, st, T, false, &succ, llr + b * g.N);
-        __syncwarp();
+        grp.sync();
         if (sum_llr != nullptr) eng.write_sums(g, st, sum_llr + b * g.N);
-        __syncwarp();
+        grp.sync();
     }
 }
 
@@ -1129,13 +1226,27 @@ using Generic16_w = GenericEngine<16, 0, true>;
 using Small326_w = SmallEngine<3, 2, 6, 0, true>;
 using Small536_w = SmallEngine<5, 3, 6, 0, true>;
 constexpr int kWeightedEngine = 15;
+// a block of warps per candidate (generic engines only): id 20 + 4 * kind + (0 float, 1 binary16,
+// 2 bfloat16, 3 weighted float)
+#define BSD_BLOCK_ALIASES(DV)                                                   \
+    using Block##DV##_f32 = GenericEngine<DV, 0, false, BlockGroup>;            \
+    using Block##DV##_f16 = GenericEngine<DV, 1, false, BlockGroup>;            \
+    using Block##DV##_bf16 = GenericEngine<DV, 2, false, BlockGroup>;           \
+    using Block##DV##_w = GenericEngine<DV, 0, true, BlockGroup>;
+BSD_BLOCK_ALIASES(3)
+BSD_BLOCK_ALIASES(6)
+BSD_BLOCK_ALIASES(16)
+constexpr int kBlockEngine = 20;
 #define BSD_ENGINES(X)                                                                          \
     X(0, Generic3_f32) X(1, Generic3_f16) X(2, Generic3_bf16)                                   \
     X(3, Generic6_f32) X(4, Generic6_f16) X(5, Generic6_bf16)                                   \
     X(6, Generic16_f32) X(7, Generic16_f16) X(8, Generic16_bf16)                                \
     X(9, Small326_f32) X(10, Small326_f16) X(11, Small326_bf16)                                 \
     X(12, Small536_f32) X(13, Small536_f16) X(14, Small536_bf16)                                \
-    X(15, Generic3_w) X(16, Generic6_w) X(17, Generic16_w) X(18, Small326_w) X(19, Small536_w)
+    X(15, Generic3_w) X(16, Generic6_w) X(17, Generic16_w) X(18, Small326_w) X(19, Small536_w)  \
+    X(20, Block3_f32) X(21, Block3_f16) X(22, Block3_bf16) X(23, Block3_w)                      \
+    X(24, Block6_f32) X(25, Block6_f16) X(26, Block6_bf16) X(27, Block6_w)                      \
+    X(28, Block16_f32) X(29, Block16_f16) X(30, Block16_bf16) X(31, Block16_w)
 
 template <class Eng>
 static int set_attrs(size_t smem_bp)
@@ -1165,32 +1276,57 @@ static bool small_fits(const DevGraph& g, int cpl, int rpl)
     return g.WN == cpl && (g.M + 31) / 32 == rpl;
 }
 
-int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* ls)
+int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, int group_warps, int warps_per_block,
+                      LaunchShape* ls)
 {
-    int kind;
-    if (small_fits(g, 3, 2)) kind = 3;
-    else if (small_fits(g, 5, 3)) kind = 4;
-    else if (g.max_col_deg <= 3) kind = 0;
-    else if (g.max_col_deg <= 6) kind = 1;
-    else if (g.max_col_deg <= 16) kind = 2;
-    else return -5;
     if (cfg.weights != nullptr && g.prec != 0) return -5;   // weights: single-precision messages only
-    const int eng = cfg.weights != nullptr ? kWeightedEngine + kind : 3 * kind + g.prec;
-    // the small engine keeps D per edge in float; the generic one a record per detector
-    const size_t recs = sizeof(float4) * (size_t)g.M, msgs = sizeof(float) * (size_t)g.Epad;
-    g.det_bytes = (int)align16(kind >= 3 && msgs > recs ? msgs : recs);
-    const size_t per_warp = warp_smem_bytes(g);
+    if (group_warps < 0 || group_warps > 16 || warps_per_block < 0 || warps_per_block > 8) return -5;
+    int gkind;                                               // generic kind: column degree bound 3 / 6 / 16
+    if (g.max_col_deg <= 3) gkind = 0;
+    else if (g.max_col_deg <= 6) gkind = 1;
+    else if (g.max_col_deg <= 16) gkind = 2;
+    else return -5;
+    int skind = -1;                                          // small engine kind, if the code has its layout
+    if (small_fits(g, 3, 2)) skind = 3;
+    else if (small_fits(g, 5, 3)) skind = 4;
     int max_optin = 0, sms = 0;
     if (CUDA_FAILED(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) ||
         CUDA_FAILED(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)))
         return -2;
-    if (per_warp > (size_t)max_optin) return -5;
-    int wpb = (int)((96 * 1024) / per_warp);
-    if (wpb > 8) wpb = 8;
-    if (wpb < 1) wpb = 1;
+    // per-candidate state with the generic engine's detector records
+    g.det_bytes = (int)align16(sizeof(float4) * (size_t)g.M);
+    const size_t generic_bytes = warp_smem_bytes(g);
+    // automatic choice: the small engine where it fits; otherwise a warp per
+    // candidate while eight or more candidates fit on an SM, a block of 8
+    // warps per candidate beyond
+    int gw = group_warps;
+    if (gw == 0) gw = (skind >= 0 || generic_bytes * 8 <= (size_t)max_optin) ? 1 : 8;
+    const bool weighted = cfg.weights != nullptr;
+    int eng, wpb;
+    if (gw >= 2) {
+        eng = kBlockEngine + 4 * gkind + (weighted ? 3 : g.prec);
+        wpb = gw;
+    } else {
+        const int kind = skind >= 0 ? skind : gkind;
+        eng = weighted ? kWeightedEngine + kind : 3 * kind + g.prec;
+        // the small engine keeps D per edge in float; the generic one a record per detector
+        const size_t recs = sizeof(float4) * (size_t)g.M, msgs = sizeof(float) * (size_t)g.Epad;
+        g.det_bytes = (int)align16(kind >= 3 && msgs > recs ? msgs : recs);
+        const size_t per_warp = warp_smem_bytes(g);
+        if (per_warp > (size_t)max_optin) return -5;
+        wpb = warps_per_block > 0 ? warps_per_block : (int)((96 * 1024) / per_warp);
+        if (wpb > 8) wpb = 8;
+        if (wpb < 1) wpb = 1;
+        if (per_warp * (size_t)wpb > (size_t)max_optin) return -5;
+    }
+    const size_t per_cand = warp_smem_bytes(g);
+    ls->group_warps = gw >= 2 ? gw : 1;
     ls->warps_per_block = wpb;
-    ls->smem_bp = per_warp * (size_t)wpb;
-    ls->smem_select = sizeof(SelScratch) * (size_t)wpb;
+    ls->smem_bp = gw >= 2 ? per_cand + 16 * sizeof(ArgRec) : per_cand * (size_t)wpb;
+    if (ls->smem_bp > (size_t)max_optin) return -5;
+    // the selection kernel handles one shot per warp in blocks of at most 8 warps
+    ls->select_warps = wpb < 8 ? wpb : 8;
+    ls->smem_select = sizeof(SelScratch) * (size_t)ls->select_warps;
     ls->dv = eng;
     const int threads = 32 * wpb;
     int rc = 0, bps_bp = 0, bps_sel = 0;
@@ -1211,7 +1347,8 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, LaunchShape* l
     }
     if (rc) return rc;
     if (CUDA_FAILED(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) ||
-        CUDA_FAILED(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_sel, k_select, threads, ls->smem_select)))
+        CUDA_FAILED(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_sel, k_select, 32 * ls->select_warps,
+                                                                  ls->smem_select)))
         return -2;
     if (bps_bp < 1 || bps_sel < 1) return -5;
     ls->grid_seed = sms * bps_bp;
@@ -1246,7 +1383,7 @@ static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, c
             if (hk) hk->before(hk->ctx, 1);
             k_round<Eng><<<ls.grid_round, threads, ls.smem_bp, s>>>(g, cfg, w, r);
             if (hk) { hk->after(hk->ctx, 1); hk->before(hk->ctx, 2); }
-            k_select<<<ls.grid_select, threads, ls.smem_select, s>>>(g, cfg, w, r);
+            k_select<<<ls.grid_select, 32 * ls.select_warps, ls.smem_select, s>>>(g, cfg, w, r);
             if (hk) hk->after(hk->ctx, 2);
         }
         k_pass_end<<<1, 128, 0, s>>>(w, nri, cudaGraphConditionalHandle{}, 0);
@@ -1320,7 +1457,8 @@ static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0,
                 void* rargs[] = {&g, &cfg, &w, &r};
                 rc = add_kernel(body, &nr, prev ? &prev : nullptr, (void*)k_round<Eng>, ls.grid_round, threads,
                                 ls.smem_bp, rargs);
-                if (!rc) rc = add_kernel(body, &ns, &nr, (void*)k_select, ls.grid_select, threads, ls.smem_select, rargs);
+                if (!rc) rc = add_kernel(body, &ns, &nr, (void*)k_select, ls.grid_select, 32 * ls.select_warps,
+                                            ls.smem_select, rargs);
                 prev = ns;
             }
             if (!rc) {
