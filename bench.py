@@ -318,6 +318,14 @@ def alu_roofline(prof, E: int, dev: int, traffic_case: str):
     return roofline, exec_iters
 
 
+def autotune(dec, synd, sample: int = 65536) -> dict:
+    """Launch-shape autotuning on a prefix of the decoder's own batch (outside the timed regions)."""
+    rep = dec.autotune(synd[:min(sample, synd.shape[0])].contiguous())
+    gw, wpb = dec.shape
+    return {"group_warps": gw, "warps_per_block": wpb, "sample_shots": int(min(sample, synd.shape[0])),
+            "timed": [[a, b, round(ms, 4)] for a, b, ms in rep]}
+
+
 def timed_region(decs, step, flush, stream, dev, steps, world, rank, profiled: bool, sample_clocks: bool):
     """`steps` calls of step() between barrier + synchronize; L2 flushed before
     each step outside the step events.  Returns (ms per step list, wall s,
@@ -371,13 +379,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.barrier()
         build()
     work = make_workload(rank, args.shots, args.ps)
-    decs, synd, outs = [], [], []
+    decs, synd, outs, tuned = [], [], [], {}
     for p, prob, sh in work:
         params = D.make_params(PRESET, ms_scale=ALPHA, workspace_bytes=int(args.workspace_gb * (1 << 30)))
         d = D.BeamSearchDecoder(prob, params, device=dev)
         decs.append(d)
         synd.append(D.to_torch_words(sh.syndromes, dev))
         outs.append(d.alloc_outputs(sh.B))
+        tuned[str(p)] = autotune(d, synd[-1])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
     stream = torch.cuda.current_stream(dev)
 
@@ -435,7 +444,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "config": {"workload": WORKLOAD, "code": "[[144,12,12]] BB, H_X 72x144, 432 edges",
                    "shots_per_p_per_gpu": args.shots, "syndromes_per_step_per_gpu": shots_per_step,
                    "l2": "flushed before every timed step (256 MiB write outside the step events)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "launch_shapes": tuned},
         "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / args.steps, "round": float(exec_iters[1]) / args.steps},
         "msg_updates_per_s": {"algorithmic": msg_alg, "executed": msg_exec,
                               "executed_per_algorithmic": float(exec_iters.sum() / args.steps / max(alg_iters_step, 1)),
@@ -486,7 +495,7 @@ def run_precision(args, rank: int, world: int, local_rank: int):
     stream = torch.cuda.current_stream(dev)
     E = work[0][1].n_edges
     shots_per_step = sum(sh.B for _, _, sh in work)
-    forms, host_out, e2e = {}, {}, None
+    forms, host_out, e2e, tuned = {}, {}, None, {}
     for name, prec in (("fp32", B.BSD_FP32), ("fp16", B.BSD_FP16), ("bf16", B.BSD_BF16)):
         decs, outs = [], []
         for p, prob, sh in work:
@@ -494,6 +503,7 @@ def run_precision(args, rank: int, world: int, local_rank: int):
                                    workspace_bytes=int(args.workspace_gb * (1 << 30)))
             decs.append(D.BeamSearchDecoder(prob, params, device=dev))
             outs.append(decs[-1].alloc_outputs(sh.B))
+            tuned.setdefault(name, {})[str(p)] = autotune(decs[-1], synd[len(decs) - 1])
 
         def step():
             for d, s, o in zip(decs, synd, outs):
@@ -544,7 +554,7 @@ def run_precision(args, rank: int, world: int, local_rank: int):
         "config": {"workload": PHEN_WORKLOAD, "code": "[[144,12,12]] phenomenological DEM, 936 x 2592, 6912 edges",
                    "shots_per_p_per_gpu": args.shots, "syndromes_per_step_per_gpu": shots_per_step,
                    "l2": "flushed before every timed step (256 MiB write outside the step events)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "launch_shapes": tuned},
         "roofline": main_form["roofline"], "gpu_launches": main_form["gpu_launches"], "clocks": main_form["clocks"],
         "forms": forms,
         "fp16_vs_plain_fp32": main_form["value"] / forms["fp32"]["value"],

@@ -295,6 +295,30 @@ int bsd_unrolled_backward(const bsd_decoder *dec, int64_t B, int32_t T, int32_t 
                           const float *d_grad_loss, float *d_grad_weights, void *d_work, int64_t work_bytes,
                           void *cuda_stream);
 
+/* Launch-shape autotuner: decode the caller's sample batch with every launch
+ * shape the code can use -- one warp per candidate with 8, 4, 2 or 1
+ * candidates per block, then a block of 2, 4, 8 or 16 warps per candidate
+ * (fewer edges per thread) -- time each (the fastest of three decodes after
+ * two untimed ones, CUDA events on cuda_stream) and keep the fastest.
+ * Decoding results do not depend on the shape.  Synchronous.
+ *   d_syndromes  device, B x ceil(M/32) words: a sample of the workload
+ *   report       host, report_cap entries (may be NULL with report_cap 0):
+ *                the shapes timed and their milliseconds, in order
+ *   n_report     host (may be NULL): the number of shapes timed
+ * Errors: BSD_ERR_INVALID_ARG, BSD_ERR_OOM (scratch outputs for B shots),
+ * BSD_ERR_CUDA; on error the decoder keeps a valid shape. */
+typedef struct {
+    int32_t group_warps;       /* 1: a warp per candidate; >= 2: a block of that many warps */
+    int32_t warps_per_block;   /* block size in warps */
+    float   ms;                /* decode time of the sample */
+} bsd_shape_timing;
+
+int bsd_autotune(bsd_decoder *dec, const uint32_t *d_syndromes, int64_t B, void *cuda_stream,
+                 bsd_shape_timing *report, int32_t report_cap, int32_t *n_report);
+
+/* The decoder's current launch shape (either pointer may be NULL). */
+int bsd_get_shape(const bsd_decoder *dec, int32_t *group_warps, int32_t *warps_per_block);
+
 /* Static text for a return code. */
 const char *bsd_error_string(int code);
 

@@ -33,8 +33,8 @@ BSD_STATUS_FAILED = 4
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
            "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_profile_enable", "bsd_profile_read",
            "bsd_decode_noalloc", "bsd_set_weights", "bsd_unrolled_workspace", "bsd_unrolled_forward",
-           "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_error_string", "bsd_last_cuda_error",
-           "bsd_destroy")
+           "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_autotune", "bsd_get_shape",
+           "bsd_error_string", "bsd_last_cuda_error", "bsd_destroy")
 BSD_PROFILE_KINDS = 8
 BSD_ERR_SCRATCH = -7
 
@@ -45,6 +45,10 @@ class bsd_params(C.Structure):
                 ("ms_scale", C.c_float), ("llr_clamp", C.c_float), ("msg_precision", C.c_int32),
                 ("tie_guard_rel", C.c_float), ("workspace_bytes", C.c_int64), ("group_warps", C.c_int32),
                 ("reserved0", C.c_int32)]
+
+
+class bsd_shape_timing(C.Structure):
+    _fields_ = [("group_warps", C.c_int32), ("warps_per_block", C.c_int32), ("ms", C.c_float)]
 
 
 class BsdError(RuntimeError):
@@ -86,6 +90,8 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_unrolled_backward.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, C.c_int64, P]
     lib.bsd_profile_read.argtypes = [P, P, P, P, P]
     lib.bsd_profile_read_kinds.argtypes = [P, P, P]
+    lib.bsd_autotune.argtypes = [P, P, C.c_int64, P, P, C.c_int32, C.POINTER(C.c_int32)]
+    lib.bsd_get_shape.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.bsd_error_string.argtypes = [C.c_int]
     lib.bsd_error_string.restype = C.c_char_p
     lib.bsd_last_cuda_error.argtypes = []
@@ -214,6 +220,21 @@ def bsd_profile_read_kinds(dec) -> dict:
     p = lambda a: a.ctypes.data_as(C.c_void_p)
     check(load().bsd_profile_read_kinds(dec, p(ms), p(ln)), "bsd_profile_read_kinds")
     return dict(ms=ms, launches=ln)
+
+
+def bsd_autotune(dec, d_syndromes, B: int, stream) -> list:
+    """Time every launch shape on the sample and keep the fastest; returns [(group_warps, warps_per_block, ms)]."""
+    cap = 16
+    rep = (bsd_shape_timing * cap)()
+    n = C.c_int32()
+    check(load().bsd_autotune(dec, d_syndromes, int(B), stream, rep, cap, C.byref(n)), "bsd_autotune")
+    return [(rep[k].group_warps, rep[k].warps_per_block, float(rep[k].ms)) for k in range(min(n.value, cap))]
+
+
+def bsd_get_shape(dec) -> tuple:
+    gw, wpb = C.c_int32(), C.c_int32()
+    check(load().bsd_get_shape(dec, C.byref(gw), C.byref(wpb)), "bsd_get_shape")
+    return gw.value, wpb.value
 
 
 def bsd_destroy(dec) -> None:

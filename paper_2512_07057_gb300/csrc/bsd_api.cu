@@ -610,6 +610,94 @@ int bsd_sync_error(bsd_decoder* dec)
     return BSD_OK;
 }
 
+// switch the decoder to another launch shape (kernels, graph); results do not change
+static int apply_shape(bsd_decoder* dec, int group_warps, int warps_per_block)
+{
+    DevGraph g = dec->g;
+    LaunchShape ls{};
+    const int rc = configure_kernels(g, dec->cfg, dec->device, group_warps, warps_per_block, &ls);
+    if (rc) return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA;
+    void* graph = nullptr;
+    if (build_graph(g, dec->cfg, dec->w, ls, &graph) != 0) graph = nullptr;
+    if (dec->graph) destroy_graph(dec->graph);
+    dec->graph = graph;
+    dec->g = g;
+    dec->ls = ls;
+    return BSD_OK;
+}
+
+int bsd_get_shape(const bsd_decoder* dec, int32_t* group_warps, int32_t* warps_per_block)
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    if (group_warps) *group_warps = dec->ls.group_warps;
+    if (warps_per_block) *warps_per_block = dec->ls.warps_per_block;
+    return BSD_OK;
+}
+
+int bsd_autotune(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, void* cuda_stream,
+                 bsd_shape_timing* report, int32_t report_cap, int32_t* n_report)
+{
+    if (!dec || !d_syndromes || B < 1 || report_cap < 0 || (report_cap > 0 && !report)) return BSD_ERR_INVALID_ARG;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (CUDA_FAILED(cudaStreamSynchronize(dec->last_stream)) || CUDA_FAILED(cudaStreamSynchronize(s)))
+        return BSD_ERR_CUDA;
+    const DevGraph& g0 = dec->g;
+    const int WKo = g0.WK > 0 ? g0.WK : 1;
+    void* mem = nullptr;
+    const size_t need = sizeof(uint32_t) * (size_t)B * (size_t)(g0.WN + WKo + 2);
+    if (CUDA_FAILED(cudaMalloc(&mem, need))) return BSD_ERR_OOM;
+    uint32_t* d_c = (uint32_t*)mem;
+    uint32_t* d_o = d_c + (size_t)B * g0.WN;
+    uint32_t* d_st = d_o + (size_t)B * WKo;
+    uint32_t* d_it = d_st + B;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (CUDA_FAILED(cudaEventCreate(&e0)) || CUDA_FAILED(cudaEventCreate(&e1))) {
+        if (e0) cudaEventDestroy(e0);
+        cudaFree(mem);
+        return BSD_ERR_CUDA;
+    }
+    // candidate shapes: warps per block of the one-warp engines, then blocks
+    // of 2 .. 16 warps per candidate; shapes the code cannot use are skipped
+    const int cand[][2] = {{1, 8}, {1, 4}, {1, 2}, {1, 1}, {2, 0}, {4, 0}, {8, 0}, {16, 0}};
+    const int prev_gw = dec->ls.group_warps >= 2 ? dec->ls.group_warps : 1;
+    const int prev_wpb = dec->ls.group_warps >= 2 ? 0 : dec->ls.warps_per_block;
+    int best = -1, nrep = 0, rc = BSD_OK;
+    float best_ms = 0.f;
+    for (int c = 0; c < (int)(sizeof(cand) / sizeof(cand[0])) && rc == BSD_OK; ++c) {
+        const int r = apply_shape(dec, cand[c][0], cand[c][1]);
+        if (r == BSD_ERR_UNSUPPORTED) continue;
+        if (r != BSD_OK) { rc = r; break; }
+        // two untimed decodes (first-touch, caches), then the fastest of three
+        float ms = 0.f;
+        for (int rep = 0; rep < 5 && rc == BSD_OK; ++rep) {
+            if (rep >= 2 && CUDA_FAILED(cudaEventRecord(e0, s))) { rc = BSD_ERR_CUDA; break; }
+            rc = bsd_decode(dec, d_syndromes, B, d_c, g0.K > 0 ? d_o : nullptr, d_st, d_it, s);
+            if (rc != BSD_OK) break;
+            if (rep >= 2) {
+                float t = 0.f;
+                if (CUDA_FAILED(cudaEventRecord(e1, s)) || CUDA_FAILED(cudaEventSynchronize(e1)) ||
+                    CUDA_FAILED(cudaEventElapsedTime(&t, e0, e1))) { rc = BSD_ERR_CUDA; break; }
+                ms = (rep == 2 || t < ms) ? t : ms;
+            }
+        }
+        if (rc != BSD_OK) break;
+        if (nrep < report_cap) report[nrep] = bsd_shape_timing{dec->ls.group_warps, dec->ls.warps_per_block, ms};
+        ++nrep;
+        if (best < 0 || ms < best_ms) { best = c; best_ms = ms; }
+    }
+    if (CUDA_FAILED(cudaStreamSynchronize(s)) && rc == BSD_OK) rc = BSD_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(mem);
+    // keep the fastest shape (or the previous one if nothing could be timed)
+    const int r2 = best >= 0 && rc == BSD_OK ? apply_shape(dec, cand[best][0], cand[best][1])
+                                             : apply_shape(dec, prev_gw, prev_wpb);
+    if (n_report) *n_report = nrep;
+    return rc != BSD_OK ? rc : r2;
+}
+
 int bsd_set_weights(bsd_decoder* dec, const float* h_weights, int32_t T)
 {
     if (!dec || T < 0 || (T > 0 && !h_weights)) return BSD_ERR_INVALID_ARG;

@@ -68,6 +68,16 @@ class BeamSearchDecoder:
             raise ValueError("weights must be [T, E]")
         B.bsd_set_weights(self.h, w.ctypes.data_as(C.c_void_p), w.shape[0])
 
+    def autotune(self, syndromes, stream=None) -> list:
+        """Time the launch shapes on a sample batch (CUDA bit-word tensor) and keep the fastest."""
+        assert syndromes.is_cuda and syndromes.is_contiguous() and syndromes.element_size() == 4
+        return B.bsd_autotune(self.h, C.c_void_p(syndromes.data_ptr()), syndromes.shape[0], self._stream(stream))
+
+    @property
+    def shape(self) -> tuple:
+        """(group_warps, warps_per_block) of the current launch shape."""
+        return B.bsd_get_shape(self.h)
+
     def close(self):
         if getattr(self, "h", None):
             B.bsd_destroy(self.h)
