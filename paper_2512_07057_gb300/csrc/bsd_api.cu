@@ -295,6 +295,27 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
             std::memcpy(&lamE_st[(size_t)e * 2], &b, 2);
         }
     }
+    // detector records of E(0), the same for every seed run up to the syndrome
+    // sign: the two smallest stored |E(0)| from L_MAX, the edge of the
+    // smallest (first on ties) and the parity of the negative messages,
+    // formed by the same comparisons as the engines' detector pass
+    std::vector<float4> rs0(M);
+    for (int i = 0; i < M; ++i) {
+        float m1 = L, m2 = L;
+        int id = -1;
+        unsigned neg = 0;
+        for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e) {
+            const float x = lamE[e] == 0.f ? 0.f : lamE[e];
+            const float a = std::fabs(x);
+            if (a < m1) { m2 = m1; m1 = a; id = e; }
+            else if (a < m2) { m2 = a; }
+            neg ^= (x < 0.f) ? 1u : 0u;
+        }
+        float fid, fneg;
+        std::memcpy(&fid, &id, 4);
+        std::memcpy(&fneg, &neg, 4);
+        rs0[i] = make_float4(m1, m2, fid, fneg);
+    }
     std::vector<uint32_t> hcol((size_t)N * WM, 0u), acol((size_t)N * (WK > 0 ? WK : 1), 0u);
     for (int i = 0; i < M; ++i)
         for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e)
@@ -313,6 +334,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     gb += align256(sizeof(uint32_t) * hcol.size());
     gb += align256(sizeof(uint32_t) * acol.size());
     gb += align256(sizeof(long long) * N);
+    gb += align256(sizeof(float4) * M);
     if (CUDA_FAILED(cudaMalloc(&dec->graph_mem, gb))) { bsd_destroy(dec); return BSD_ERR_OOM; }
     dec->graph_bytes = gb;
     char* p = (char*)dec->graph_mem;
@@ -325,6 +347,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     uint32_t* d_hcol = carve<uint32_t>(p, hcol.size());
     uint32_t* d_acol = carve<uint32_t>(p, acol.size());
     long long* d_lamq = carve<long long>(p, N);
+    float4* d_rs0 = carve<float4>(p, M);
     bool ok = !CUDA_FAILED(cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_edge, col_edge.data(), sizeof(int) * E, cudaMemcpyHostToDevice)) &&
@@ -333,7 +356,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
               !CUDA_FAILED(cudaMemcpy(d_lamE, lamE_st.data(), lamE_st.size(), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_hcol, hcol.data(), sizeof(uint32_t) * hcol.size(), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_acol, acol.data(), sizeof(uint32_t) * acol.size(), cudaMemcpyHostToDevice)) &&
-              !CUDA_FAILED(cudaMemcpy(d_lamq, lamq.data(), sizeof(long long) * N, cudaMemcpyHostToDevice));
+              !CUDA_FAILED(cudaMemcpy(d_lamq, lamq.data(), sizeof(long long) * N, cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_rs0, rs0.data(), sizeof(float4) * M, cudaMemcpyHostToDevice));
     if (!ok) { bsd_destroy(dec); return BSD_ERR_CUDA; }
 
     DevGraph& g = dec->g;
@@ -344,7 +368,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.max_col_deg = max_col; g.max_row_deg = max_row;
     g.all_lam_pos = all_pos;
     g.row_ptr = d_row_ptr; g.col_ptr = d_col_ptr; g.col_edge = d_col_edge; g.col_row = d_col_row;
-    g.lam = d_lam; g.lamE = d_lamE; g.hcol = d_hcol; g.acol = d_acol; g.lamq = d_lamq;
+    g.lam = d_lam; g.lamE = d_lamE; g.hcol = d_hcol; g.acol = d_acol; g.lamq = d_lamq; g.rs0 = d_rs0;
 
     DecCfg& cfg = dec->cfg;
     cfg.max_rounds = params->max_rounds;

@@ -10,6 +10,7 @@
 //   hcol[N][WM]           column j of H as an M-bit set (syndrome flip for v = 1)
 //   acol[N][WK]           column j of A as a K-bit set (observable flips)
 //   lamq[N]               Lambda_j on the 2^-16 fixed-point grid (weights)
+//   rs0[M]                the detector records of E(0) (a seed run's first check pass, up to the syndrome)
 //
 // Workspace (one decoder):
 //   seed store, S entries: the snapshot (E, s', mask, vals, e^, record) of
@@ -50,6 +51,7 @@ struct DevGraph {
     const uint32_t* hcol;
     const uint32_t* acol;
     const long long* lamq;
+    const float4* rs0;     // [M] detector records of E(0): (min1, min2, argmin edge, parity of negatives)
 };
 
 struct DecCfg {

@@ -221,10 +221,11 @@ __device__ inline unsigned long long fixq(float x)
 // null, Lambda_j(max_iters) is written there.
 template <int DV, int P, bool W, class G>
 __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
-                          bool stop, int* success, float* post_out)
+                          bool stop, int* success, float* post_out, bool from_prior)
 {
     using S = Store<P>;
-    typename S::T* const E = reinterpret_cast<typename S::T*>(st.E);
+    using T = typename S::T;
+    T* const E = reinterpret_cast<T*>(st.E);
     const int lane = threadIdx.x & 31;
     const float alpha = cfg.alpha;
     const float L = cfg.L;
@@ -235,8 +236,21 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
         // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
         const float* wt = W ? cfg.weights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
 
+        // a run from E(0) (seed, LLRs): the first check pass is the
+        // precomputed E(0) record of each row with the syndrome bit folded into
+        // the sign parity, and E(0) itself (clamp(Lambda), the same on every
+        // edge of a column) is read from the graph, not from the candidate
+        const bool prior = from_prior && t == 1;
+        const T* const Ein = prior ? reinterpret_cast<const T*>(g.lamE) : E;
+        if (prior) {
+            for (int i = grp.rank(); i < g.M; i += grp.size()) {
+                const float4 r = __ldg(g.rs0 + i);
+                const uint32_t si = (st.sp[i >> 5] >> (i & 31)) & 1u;
+                st.rs[i] = make_float4(r.x, r.y, r.z, __uint_as_float(__float_as_uint(r.w) ^ si));
+            }
+        }
         // ---- detector pass (Eq. 1): min1, min2, argmin and sign parity per row
-        for (int i = grp.rank(); i < g.M; i += grp.size()) {
+        for (int i = prior ? g.M : grp.rank(); i < g.M; i += grp.size()) {
             const int rb = __ldg(g.row_ptr + i), re = __ldg(g.row_ptr + i + 1);
             float m1 = L, m2 = L;
             int id = -1;
@@ -269,7 +283,7 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
                         const int e = __ldg(g.col_edge + kb + k);
                         const int r = __ldg(g.col_row + kb + k);
                         const float4 s4 = st.rs[r];
-                        const float xo = S::ld(E, e);
+                        const float xo = S::ld(Ein, e);
                         const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
                         const uint32_t sg = __float_as_uint(s4.w) ^ ((xo < 0.f) ? 1u : 0u);
                         const float d = __fmul_rn(W ? __ldg(wt + e) : alpha, m);
@@ -420,6 +434,7 @@ struct GenericEngine {
     static constexpr int kMinBlocks = 1;
     static constexpr int kMaxThreads = G::kBlock ? 512 : 256;
     static constexpr int kPrec = P;
+    static constexpr bool kPriorStart = true;   // runs from E(0) need no copy of E(0)
     G grp;
     __device__ void load_graph(const DevGraph&) {}
     __device__ void clear_sums(const DevGraph& g, const WarpState& st)
@@ -427,9 +442,9 @@ struct GenericEngine {
         for (int j = grp.rank(); j < g.N; j += grp.size()) st.sumllr[j] = 0.f;
     }
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
-                       int* success, float* post_out)
+                       int* success, float* post_out, bool from_prior = false)
     {
-        return bp_iterate<DV, P, W>(grp, g, cfg, st, max_iters, stop, success, post_out);
+        return bp_iterate<DV, P, W>(grp, g, cfg, st, max_iters, stop, success, post_out, from_prior);
     }
     __device__ void argmin_score(const DevGraph& g, const WarpState& st, double guard, int* np, long long* S,
                                  int* tie)
@@ -458,6 +473,7 @@ struct SmallEngine {
     static constexpr int kMinBlocks = 2;   // at most 128 registers: two 8-warp blocks per SM
     static constexpr int kMaxThreads = 256;
     static constexpr int kPrec = P;
+    static constexpr bool kPriorStart = false;  // runs from E(0) read a copy of E(0)
     WarpGroup grp;
     using S = Store<P>;
     uint32_t ci[CPL][3];   // (CSR edge id << 16) | row, for column lane + 32 c
@@ -486,7 +502,7 @@ struct SmallEngine {
         for (int c = 0; c < CPL; ++c) sum[c] = 0.f;
     }
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
-                       int* success, float* post_out)
+                       int* success, float* post_out, bool = false)
     {
         const int lane = threadIdx.x & 31;
         const float alpha = cfg.alpha;
@@ -793,11 +809,11 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
             grp.sync();
             continue;
         }
-        group_copy16(grp, st.E, g.lamE, snap_vec16(g));
+        if (!Eng::kPriorStart) group_copy16(grp, st.E, g.lamE, snap_vec16(g));
         eng.clear_sums(g, st);
         grp.sync();
         int succ = 0;
-        const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr);
+        const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr, true);
         if (grp.rank() == 0) atomicAdd(&w.stats[0], (unsigned long long)it);
         grp.sync();
         if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
@@ -1192,11 +1208,11 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_bp_llr(De
     for (long long b = (long long)blockIdx.x * grp.per_block() + grp.index(); b < B; b += nw) {
         for (int q = grp.rank(); q < g.WM; q += grp.size()) st.sp[q] = synd[b * g.WM + q];
         for (int q = grp.rank(); q < g.WN; q += grp.size()) { st.mask[q] = 0u; st.vals[q] = 0u; }
-        group_copy16(grp, st.E, g.lamE, snap_vec16(g));
+        if (!Eng::kPriorStart) group_copy16(grp, st.E, g.lamE, snap_vec16(g));
         eng.clear_sums(g, st);
         grp.sync();
         int succ;
-        eng.run(g, cfg, st, T, false, &succ, llr + b * g.N);
+        eng.run(g, cfg, st, T, false, &succ, llr + b * g.N, true);
         grp.sync();
         if (sum_llr != nullptr) eng.write_sums(g, st, sum_llr + b * g.N);
         grp.sync();
