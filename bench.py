@@ -51,6 +51,15 @@ PHEN_WORKLOAD = "bb144_phenomenological_dem beam64_640iters alpha=0.625 p=q={1e-
 # unrolled weighted min-sum training: 20 iterations, checkpoints every 5, batch 4096, p = q = 2e-3
 UNR_T, UNR_K, UNR_B, UNR_P, UNR_LR = 20, 5, 4096, 2e-3, 1e-2
 UNR_WORKLOAD = "bb144_phenomenological_dem unrolled weighted min-sum T=20 ckpt=5 batch=4096 p=q=2e-3"
+# circuit-shaped synthetic DEM: 936 x 8800, column weight 2-6, priors log-uniform [1e-5, 1e-3]
+SYN_PRESETS = ("beam8_230iters", "beam32_340iters", "beam64_640iters")
+SYN_SHOTS = 1_000_000
+SYN_WORKLOAD = "synthetic_dem_936x8800 beam8_230iters/beam32_340iters/beam64_640iters alpha=0.625"
+# XYZ decoding: [[144,12,12]] code capacity depolarizing noise, both stabilizer types in H
+XYZ_PS = (0.03, 0.05, 0.07)
+XYZ_SHOTS = 100_000
+XYZ_PRESET = "beam64_640iters"
+XYZ_WORKLOAD = "bb144_xyz_depolarizing beam64_640iters alpha=0.625 p={0.03,0.05,0.07} vs XZ decoding"
 
 
 def parse():
@@ -65,10 +74,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ps", default="0.01,0.03,0.05", help="physical error rates (a smaller case for profiling)")
     ap.add_argument("--workspace-gb", type=float, default=32.0, help="device workspace per decoder")
-    ap.add_argument("--workload", choices=("bb144_code_capacity", "phenom_precision", "unrolled_training"),
+    ap.add_argument("--workload", choices=("bb144_code_capacity", "phenom_precision", "unrolled_training",
+                                           "synthetic_dem", "xyz"),
                     default="bb144_code_capacity",
                     help="phenom_precision: the phenomenological DEM with FP32, FP16 and BF16 message storage; "
-                         "unrolled_training: training steps of the unrolled weighted min-sum on that DEM")
+                         "unrolled_training: training steps of the unrolled weighted min-sum on that DEM; "
+                         "synthetic_dem: the 936 x 8800 circuit-shaped DEM with beam widths 8, 32, 64; "
+                         "xyz: XYZ against XZ decoding of [[144,12,12]] under depolarizing noise")
     ap.add_argument("--train-steps", type=int, default=300, help="unrolled_training: steps before the LER judgement")
     ap.add_argument("--judge-shots", type=int, default=1_000_000, help="unrolled_training: held-out shots")
     a = ap.parse_args()
@@ -243,15 +255,56 @@ def run_reference_unrolled(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_synthetic(args):
+    """Reference arm of the synthetic-DEM workload: the double-precision oracle
+    with the three presets on a bounded prefix of the same shots."""
+    import oracle
+    from paper_2512_07057_gb300 import workloads as W
+    prob = W.synthetic_dem()
+    sh = W.sample_shots(prob, min(args.shots, 100_000), W.shot_seed("synthetic_dem", 0))
+    nth = cores()
+    g = oracle.Graph(prob, "f64")
+    prms = [oracle.preset(p, ms_scale=ALPHA) for p in SYN_PRESETS]
+    _, n, _ = oracle_rate([(SYN_PRESETS[1], prob, sh)], 3.0, nth, SYN_PRESETS[1])
+    for _ in range(args.warmup):
+        for prm in prms:
+            g.decode_batch(sh.syndromes[:max(100, n // 10)], prm, nthreads=nth)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for prm in prms:
+            g.decode_batch(sh.syndromes[:n], prm, nthreads=nth)
+    dt = time.perf_counter() - t0
+    value = len(prms) * n * args.steps / dt
+    sample = f"first {n} of the seeded shots per width per step, double-precision oracle, {nth} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": SYN_WORKLOAD, "shots_per_width_per_step": n, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": nth, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
     if args.workload == "unrolled_training":
         run_reference_unrolled(args)
         return
+    if args.workload == "synthetic_dem":
+        run_reference_synthetic(args)
+        return
     phen = args.workload == "phenom_precision"
-    work = (make_phen_workload if phen else make_workload)(0, min(args.shots, 200_000), args.ps)
-    preset = PHEN_PRESET if phen else PRESET
+    if args.workload == "xyz":
+        from paper_2512_07057_gb300 import workloads as W
+        work = []
+        for p in XYZ_PS:
+            prob = W.bb_xyz_code_capacity(12, 6, p)
+            work.append((p, prob, W.sample_shots(prob, 20_000, W.shot_seed(f"bb144_xyz_p{p}", 0))))
+        preset, wl_name = XYZ_PRESET, XYZ_WORKLOAD
+    else:
+        work = (make_phen_workload if phen else make_workload)(0, min(args.shots, 200_000), args.ps)
+        preset, wl_name = (PHEN_PRESET, PHEN_WORKLOAD) if phen else (PRESET, WORKLOAD)
     nth = cores()
     import oracle
     gs = [(oracle.Graph(prob, "f64"), sh) for _, prob, sh in work]
@@ -271,8 +324,7 @@ def run_reference(args, rank: int):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": PHEN_WORKLOAD if phen else WORKLOAD, "shots_per_p_per_step": n,
-                       "l2": "n/a (host)"},
+            "config": {"workload": wl_name, "shots_per_p_per_step": n, "l2": "n/a (host)"},
             "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": nth, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -828,6 +880,207 @@ def _unrolled_cpu_baseline(prob, T, target_s):
                                         f"reference, {dt:.1f} s"}
 
 
+def run_synthetic(args, rank: int, world: int, local_rank: int):
+    """The 936 x 8800 synthetic DEM decoded with beam widths 8, 32 and 64 (the
+    matching Table I presets), 10^6 seeded shots each per step."""
+    import torch
+    import torch.distributed as dist
+
+    from __graft_entry__ import build
+    from paper_2512_07057_gb300 import decoder as D
+    from paper_2512_07057_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+        build()
+    prob = W.synthetic_dem()
+    sh = W.sample_shots(prob, args.shots, W.shot_seed("synthetic_dem", rank))
+    synd = D.to_torch_words(sh.syndromes, dev)
+    decs, outs, tuned = [], [], {}
+    for preset in SYN_PRESETS:
+        d = D.BeamSearchDecoder(prob, D.make_params(preset, ms_scale=ALPHA,
+                                                    workspace_bytes=int(args.workspace_gb * (1 << 30))), device=dev)
+        decs.append(d)
+        outs.append(d.alloc_outputs(sh.B))
+        tuned[preset] = autotune(d, synd, 16384)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for d, o in zip(decs, outs):
+            d.decode(synd, o, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize(dev)
+    tr_args = (decs, step, flush, stream, dev, args.steps, world, rank)
+    ms_steps, _, clocks, prof_graph = timed_region(*tr_args, profiled=False, sample_clocks=True)
+    _, _, _, prof = timed_region(*tr_args, profiled=True, sample_clocks=False)
+    ms_total = float(sum(ms_steps))
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    roofline, exec_iters = alu_roofline(prof, prob.n_edges, dev, "small case of the same DEM")
+    per_w = {}
+    for preset, o, pr in zip(SYN_PRESETS, outs, prof):
+        st = D.from_torch_words(o.status)
+        it = D.from_torch_words(o.iters).astype(np.int64)
+        per_w[preset] = {"ler": ler_of(prob, sh, D.from_torch_words(o.obs_flips), st & 7),
+                         "seed_converged": float(((st & 7) == 1).mean()),
+                         "beam_converged": float(((st & 7) == 2).mean()),
+                         "failed": float(((st & 7) == 4).mean()), "mean_alg_iters": float(it.mean()),
+                         "kernel_ms_per_step": {n: float(x) / args.steps
+                                                for n, x in zip(("k_seed", "k_round", "k_select"), pr["ms"])}}
+    steps_s = ms_total * 1e-3
+    line = {
+        "metric": METRIC, "value": world * len(decs) * sh.B * args.steps / steps_s, "unit": "syndromes/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": SYN_WORKLOAD, "code": f"synthetic DEM {prob.M} x {prob.N}, {prob.n_edges} edges",
+                   "shots_per_width_per_gpu": sh.B, "syndromes_per_step_per_gpu": len(decs) * sh.B,
+                   "l2": "flushed before every timed step (256 MiB write outside the step events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "launch_shapes": tuned},
+        "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / args.steps,
+                                   "round": float(exec_iters[1]) / args.steps},
+        "roofline": roofline, "gpu_launches": int(sum(pr["kernel_launches"] for pr in prof_graph)),
+        "per_width": per_w, "clocks": clocks,
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_host(decs, [(w, prob, sh) for w in SYN_PRESETS], args, dev)
+    if rank == 0 and not args.no_cpu_baseline:
+        rates = []
+        for preset in SYN_PRESETS:
+            r, n, dt = oracle_rate([(preset, prob, sh)], args.cpu_seconds / 3, cores(), preset)
+            rates.append((r, n, dt))
+        tot = sum(n for _, n, _ in rates) / sum(n / r for r, n, _ in rates)
+        line["cpu_baseline"] = {"value": tot, "unit": "syndromes/s", "cores": cores(), "kind": "oracle",
+                                "sample": "first " + "/".join(str(n) for _, n, _ in rates) +
+                                          " shots for the three widths, double-precision oracle"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for d in decs:
+        d.close()
+
+
+def run_xyz(args, rank: int, world: int, local_rank: int):
+    """XYZ decoding (H with both stabilizer types) against XZ decoding (the X
+    and Z components decoded separately) of the same depolarizing shots, with
+    the beam decoder and with plain BP; the line's value is the XYZ beam
+    decoder's throughput."""
+    import torch
+    import torch.distributed as dist
+
+    from __graft_entry__ import build
+    from paper_2512_07057_gb300 import decoder as D
+    from paper_2512_07057_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+        build()
+    nshots = args.shots if args.shots != 1_000_000 else XYZ_SHOTS
+    budget = int(args.workspace_gb * (1 << 30)) // 4
+    work, decs, synd, outs, tuned = [], [], [], [], {}
+    for p in XYZ_PS:
+        prob = W.bb_xyz_code_capacity(12, 6, p)
+        sh = W.sample_shots(prob, nshots, W.shot_seed(f"bb144_xyz_p{p}", rank))
+        work.append((p, prob, sh))
+        d = D.BeamSearchDecoder(prob, D.make_params(XYZ_PRESET, ms_scale=ALPHA, workspace_bytes=budget), device=dev)
+        synd.append(D.to_torch_words(sh.syndromes, dev))
+        decs.append(d)
+        outs.append(d.alloc_outputs(sh.B))
+        tuned[str(p)] = autotune(d, synd[-1], 16384)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for d, s_, o in zip(decs, synd, outs):
+            d.decode(s_, o, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize(dev)
+    tr_args = (decs, step, flush, stream, dev, args.steps, world, rank)
+    ms_steps, _, clocks, prof_graph = timed_region(*tr_args, profiled=False, sample_clocks=True)
+    _, _, _, prof = timed_region(*tr_args, profiled=True, sample_clocks=False)
+    ms_total = float(sum(ms_steps))
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    roofline, _ = alu_roofline(prof, work[0][1].n_edges, dev, "small case")
+    # LER: XYZ and XZ, beam decoder and plain BP (max_rounds 0, the preset's first run)
+    per_p = {}
+    for (p, prob, sh), o, s_ in zip(work, outs, synd):
+        fail_xyz = _failures(prob, sh, o)
+        zp, xp = W.bb_xz_parts(12, 6, p)
+        s1, s2 = W.split_bits(sh.syndromes, prob.M, zp.M)
+        o1, o2 = W.split_bits(sh.obs, prob.K, zp.K)
+        res = {"xyz_beam": float(fail_xyz.mean())}
+        plain = D.BeamSearchDecoder(prob, D.make_params(XYZ_PRESET, ms_scale=ALPHA, max_rounds=0,
+                                                        workspace_bytes=budget), device=dev)
+        res["xyz_plain_bp"] = float(_failures(prob, sh, plain.decode(s_)).mean())
+        plain.close()
+        for mode, mr in (("beam", None), ("plain_bp", 0)):
+            fails = np.zeros(sh.B, bool)
+            for part, sp, op in ((zp, s1, o1), (xp, s2, o2)):
+                kw = {} if mr is None else {"max_rounds": 0}
+                dd = D.BeamSearchDecoder(part, D.make_params(XYZ_PRESET, ms_scale=ALPHA, workspace_bytes=budget,
+                                                             **kw), device=dev)
+                fails |= _failures(part, W.Shots(syndromes=sp, obs=op, errors=None),
+                                   dd.decode(D.to_torch_words(sp, dev)))
+                dd.close()
+            res[f"xz_{mode}"] = float(fails.mean())
+        res["xz_over_xyz_beam"] = res["xz_beam"] / res["xyz_beam"] if res["xyz_beam"] > 0 else None
+        per_p[str(p)] = res
+    steps_s = ms_total * 1e-3
+    line = {
+        "metric": METRIC, "value": world * sum(sh.B for _, _, sh in work) * args.steps / steps_s,
+        "unit": "syndromes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": XYZ_WORKLOAD, "code": "[[144,12,12]] BB, H = [H_X on (Z,Y); H_Z on (X,Y)], "
+                                                     "144 x 432, 1728 edges",
+                   "shots_per_p_per_gpu": nshots, "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "launch_shapes": tuned},
+        "roofline": roofline, "gpu_launches": int(sum(pr["kernel_launches"] for pr in prof_graph)),
+        "ler": per_p, "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        r, n, dt = oracle_rate(work, args.cpu_seconds, cores(), XYZ_PRESET)
+        line["cpu_baseline"] = {"value": r, "unit": "syndromes/s", "cores": cores(), "kind": "oracle",
+                                "sample": f"first {n} shots of each p batch, double-precision oracle, {dt:.1f} s"}
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_host(decs, work, args, dev)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for d in decs:
+        d.close()
+
+
+def _failures(prob, sh, out):
+    """Logical failures per shot: a wrong observable vector or no converged correction."""
+    import torch
+
+    from paper_2512_07057_gb300 import decoder as D
+    from paper_2512_07057_gb300 import workloads as W
+    torch.cuda.synchronize()
+    st = D.from_torch_words(out.status) & 7
+    o = W.unpack_bits(D.from_torch_words(out.obs_flips)[:, :(prob.K + 31) // 32], prob.K)
+    t = W.unpack_bits(sh.obs, prob.K)
+    return (o != t).any(1) | (st == 4)
+
+
 def e2e_host(decs, work, args, dev):
     """Same metric through bsd_decode_host: pinned host syndromes in, host results out."""
     import torch
@@ -914,6 +1167,10 @@ def main():
             run_precision(args, rank, world, local_rank)
         elif args.workload == "unrolled_training":
             run_unrolled(args, rank, world, local_rank)
+        elif args.workload == "synthetic_dem":
+            run_synthetic(args, rank, world, local_rank)
+        elif args.workload == "xyz":
+            run_xyz(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

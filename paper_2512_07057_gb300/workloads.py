@@ -238,6 +238,55 @@ def bb_code_capacity(l: int, m: int, p: float, name: str | None = None) -> Probl
                    meta={"l": l, "m": m, "HZ": HZ, "kind": "bb_code_capacity", "p": p})
 
 
+def bb_xyz_code_capacity(l: int, m: int, p: float) -> Problem:
+    """XYZ decoding problem of a BB code under depolarizing noise.
+
+    Columns are the per-qubit mechanisms X_q (index q), Z_q (n + q) and Y_q
+    (2n + q), each with prior p/3.  H stacks both stabilizer types: the
+    X-check rows (H_X) see the Z component (Z_q and Y_q), the Z-check rows
+    (H_Z, after them) see the X component (X_q and Y_q); the Y columns make
+    length-4 cycles.  A holds the X-type logicals on the Z component, then
+    the Z-type logicals on the X component.
+    """
+    HX, HZ = bb_matrices(l, m, BB_A_TERMS, BB_B_TERMS)
+    LX = logical_basis(HX, HZ)       # detect Z-type residuals
+    LZ = logical_basis(HZ, HX)       # detect X-type residuals
+    n = HX.shape[1]
+    z = np.zeros_like(HX)
+    H = np.block([[z, HX, HX], [HZ, np.zeros_like(HZ), HZ]]).astype(np.uint8)
+    A = np.block([[np.zeros_like(LX), LX, LX], [LZ, np.zeros_like(LZ), LZ]]).astype(np.uint8)
+    hr, hc = dense_to_csr(H)
+    ar, ac = dense_to_csr(A)
+    return Problem(name=f"bb_{n}_xyz_p{p}", M=H.shape[0], N=3 * n, K=A.shape[0],
+                   H_row_ptr=hr, H_col_idx=hc, A_row_ptr=ar, A_col_idx=ac,
+                   priors=np.full(3 * n, p / 3.0),
+                   meta={"l": l, "m": m, "kind": "bb_xyz_code_capacity", "p": p, "mx": HX.shape[0],
+                         "kx": LX.shape[0]})
+
+
+def bb_xz_parts(l: int, m: int, p: float):
+    """The XZ-decoding counterpart of bb_xyz_code_capacity: the Z component
+    decoded with (H_X, X-type logicals) and the X component with (H_Z, Z-type
+    logicals), each node with the marginal prior of its component,
+    P(Z_q xor Y_q) = 2 (p/3)(1 - p/3)."""
+    HX, HZ = bb_matrices(l, m, BB_A_TERMS, BB_B_TERMS)
+    q = 2.0 * (p / 3.0) * (1.0 - p / 3.0)
+    parts = []
+    for Hm, Lm, tag in ((HX, logical_basis(HX, HZ), "z"), (HZ, logical_basis(HZ, HX), "x")):
+        hr, hc = dense_to_csr(Hm)
+        ar, ac = dense_to_csr(Lm)
+        parts.append(Problem(name=f"bb_{Hm.shape[1]}_xz_{tag}_p{p}", M=Hm.shape[0], N=Hm.shape[1], K=Lm.shape[0],
+                             H_row_ptr=hr, H_col_idx=hc, A_row_ptr=ar, A_col_idx=ac,
+                             priors=np.full(Hm.shape[1], q), meta={"kind": "bb_xz_part", "p": p}))
+    return parts
+
+
+def split_bits(packed: np.ndarray, n_total: int, n_first: int):
+    """Bit vectors [B, ceil(n_total/32)] -> (first n_first bits, the rest), repacked."""
+    b = unpack_bits(packed, n_total)
+    return pack_bits(b[:, :n_first]), pack_bits(b[:, n_first:])
+
+
 def bb72_code_capacity(p: float = 0.03) -> Problem:
     """[[72,12,6]] BB code (l = m = 6), i.i.d. Z flips with probability p."""
     return bb_code_capacity(6, 6, p, name=f"bb72_cc_p{p}")

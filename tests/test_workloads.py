@@ -79,3 +79,30 @@ def test_pack_roundtrip():
         assert np.array_equal(W.unpack_bits(packed, L), bits)
         if L % 32:
             assert (packed[:, -1] >> np.uint32(L % 32) == 0).all()
+
+
+def test_xyz_problem_halves_are_the_xz_problems():
+    """XYZ decoding's H stacks H_X over H_Z on (X, Z, Y) mechanism columns: the
+    two halves of every syndrome and observable vector equal those of the
+    XZ components z = Z xor Y (checked by H_X, X-type logicals) and x = X xor Y
+    (H_Z, Z-type logicals); Y columns create length-4 cycles."""
+    P = W.bb_xyz_code_capacity(6, 6, 0.06)
+    zp, xp = W.bb_xz_parts(6, 6, 0.06)
+    n = 72
+    sh = W.sample_shots(P, 500, "xyz_halves", keep_errors=True)
+    e = W.unpack_bits(sh.errors, P.N)
+    z, x = e[:, n:2 * n] ^ e[:, 2 * n:], e[:, :n] ^ e[:, 2 * n:]
+    s1, s2 = W.split_bits(sh.syndromes, P.M, zp.M)
+    o1, o2 = W.split_bits(sh.obs, P.K, zp.K)
+    assert np.array_equal(W.unpack_bits(s1, zp.M), (z @ zp.H_dense().T) % 2)
+    assert np.array_equal(W.unpack_bits(s2, xp.M), (x @ xp.H_dense().T) % 2)
+    assert np.array_equal(W.unpack_bits(o1, zp.K), (z @ zp.A_dense().T) % 2)
+    assert np.array_equal(W.unpack_bits(o2, xp.K), (x @ xp.A_dense().T) % 2)
+    Hd = P.H_dense().astype(np.int64)
+    # a length-4 cycle: two rows sharing two columns (an X check and a Z check through Y columns)
+    overlap = Hd @ Hd.T
+    np.fill_diagonal(overlap, 0)
+    assert overlap.max() >= 2
+    assert np.allclose(P.priors, 0.02)
+    # the Z-type residual of a Z-type logical operator is detected by the X-type logicals only
+    assert zp.K == xp.K == 12
