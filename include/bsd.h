@@ -319,6 +319,32 @@ int bsd_autotune(bsd_decoder *dec, const uint32_t *d_syndromes, int64_t B, void 
 /* The decoder's current launch shape (either pointer may be NULL). */
 int bsd_get_shape(const bsd_decoder *dec, int32_t *group_warps, int32_t *warps_per_block);
 
+/* ---- Detector error models as text ----------------------------------------
+ * Reads the common text format of detector error models into the decoding
+ * problem (H, A, p) of App. A: one column per error mechanism, in the order
+ * met.  Understood: error(p) with D<k> / L<k> targets and '^' separators (a
+ * mechanism's effect is the XOR of its parts; a target listed twice cancels),
+ * detector, logical_observable, shift_detectors, repeat N { ... } (nested),
+ * instruction tags in brackets (ignored), comments.  M (K) is one more than
+ * the largest detector (observable) index met or declared.
+ *   flags     0, or BSD_DEM_MERGE: merge mechanisms with identical detector and
+ *             observable sets, p = p1 (1 - p2) + p2 (1 - p1)
+ *   err_line  host (may be NULL): the 1-based line of the first error
+ * Errors: BSD_ERR_INVALID_ARG (syntax, a probability outside [0, 1]),
+ * BSD_ERR_UNSUPPORTED (an unknown instruction, an index beyond 2^31 - 2),
+ * BSD_ERR_OOM.  The handle owns host memory only. */
+#define BSD_DEM_MERGE 1
+typedef struct bsd_dem bsd_dem;
+int bsd_dem_parse(const char *text, int64_t len, int32_t flags, bsd_dem **out, int64_t *err_line);
+/* Sizes of the parsed problem: rows M, columns N, observables K, nonzeros of H and A. */
+int bsd_dem_sizes(const bsd_dem *dem, int32_t *M, int32_t *N, int32_t *K, int64_t *nnz_H, int64_t *nnz_A);
+/* Fill caller-owned host arrays: H_row_ptr[M+1], H_col_idx[nnz_H], A_row_ptr[K+1],
+ * A_col_idx[nnz_A], priors[N]; the CSR column indices of every row ascend,
+ * as bsd_create requires. */
+int bsd_dem_fill(const bsd_dem *dem, int32_t *H_row_ptr, int32_t *H_col_idx, int32_t *A_row_ptr,
+                 int32_t *A_col_idx, double *priors);
+void bsd_dem_free(bsd_dem *dem);
+
 /* Static text for a return code. */
 const char *bsd_error_string(int code);
 

@@ -33,9 +33,11 @@ BSD_STATUS_FAILED = 4
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
            "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_profile_enable", "bsd_profile_read",
            "bsd_decode_noalloc", "bsd_set_weights", "bsd_unrolled_workspace", "bsd_unrolled_forward",
-           "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_autotune", "bsd_get_shape",
+           "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_autotune", "bsd_get_shape", "bsd_dem_parse",
+           "bsd_dem_sizes", "bsd_dem_fill", "bsd_dem_free",
            "bsd_error_string", "bsd_last_cuda_error", "bsd_destroy")
 BSD_PROFILE_KINDS = 8
+BSD_DEM_MERGE = 1
 BSD_ERR_SCRATCH = -7
 
 
@@ -92,6 +94,11 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_profile_read_kinds.argtypes = [P, P, P]
     lib.bsd_autotune.argtypes = [P, P, C.c_int64, P, P, C.c_int32, C.POINTER(C.c_int32)]
     lib.bsd_get_shape.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.bsd_dem_parse.argtypes = [C.c_char_p, C.c_int64, C.c_int32, C.POINTER(P), C.POINTER(C.c_int64)]
+    lib.bsd_dem_sizes.argtypes = [P] + [C.POINTER(C.c_int32)] * 3 + [C.POINTER(C.c_int64)] * 2
+    lib.bsd_dem_fill.argtypes = [P, P, P, P, P, P]
+    lib.bsd_dem_free.argtypes = [P]
+    lib.bsd_dem_free.restype = None
     lib.bsd_error_string.argtypes = [C.c_int]
     lib.bsd_error_string.restype = C.c_char_p
     lib.bsd_last_cuda_error.argtypes = []
@@ -99,7 +106,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_destroy.argtypes = [P]
     lib.bsd_destroy.restype = None
     for nm in EXPORTS:
-        if nm not in ("bsd_error_string", "bsd_last_cuda_error", "bsd_destroy"):
+        if nm not in ("bsd_error_string", "bsd_last_cuda_error", "bsd_destroy", "bsd_dem_free"):
             getattr(lib, nm).restype = C.c_int
     _lib = lib
     return lib
@@ -235,6 +242,36 @@ def bsd_get_shape(dec) -> tuple:
     gw, wpb = C.c_int32(), C.c_int32()
     check(load().bsd_get_shape(dec, C.byref(gw), C.byref(wpb)), "bsd_get_shape")
     return gw.value, wpb.value
+
+
+def bsd_dem_read(text: str, merge: bool = False) -> dict:
+    """bsd_dem_parse + bsd_dem_sizes + bsd_dem_fill + bsd_dem_free: a text detector
+    error model -> dict(M, N, K, H_row_ptr, H_col_idx, A_row_ptr, A_col_idx, priors)."""
+    import numpy as np
+    lib = load()
+    raw = text.encode()
+    h = C.c_void_p()
+    line = C.c_int64()
+    rc = lib.bsd_dem_parse(raw, len(raw), BSD_DEM_MERGE if merge else 0, C.byref(h), C.byref(line))
+    if rc != BSD_OK:
+        raise BsdError(rc, f"bsd_dem_parse (line {line.value})")
+    try:
+        M, N, K = C.c_int32(), C.c_int32(), C.c_int32()
+        nh, na = C.c_int64(), C.c_int64()
+        check(lib.bsd_dem_sizes(h, C.byref(M), C.byref(N), C.byref(K), C.byref(nh), C.byref(na)), "bsd_dem_sizes")
+        out = dict(M=M.value, N=N.value, K=K.value,
+                   H_row_ptr=np.zeros(M.value + 1, np.int32), H_col_idx=np.zeros(max(nh.value, 1), np.int32),
+                   A_row_ptr=np.zeros(K.value + 1, np.int32), A_col_idx=np.zeros(max(na.value, 1), np.int32),
+                   priors=np.zeros(max(N.value, 1), np.float64))
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        check(lib.bsd_dem_fill(h, p(out["H_row_ptr"]), p(out["H_col_idx"]), p(out["A_row_ptr"]),
+                               p(out["A_col_idx"]), p(out["priors"])), "bsd_dem_fill")
+        out["H_col_idx"] = out["H_col_idx"][:nh.value]
+        out["A_col_idx"] = out["A_col_idx"][:na.value]
+        out["priors"] = out["priors"][:N.value]
+        return out
+    finally:
+        lib.bsd_dem_free(h)
 
 
 def bsd_destroy(dec) -> None:

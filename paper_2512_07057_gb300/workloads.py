@@ -287,6 +287,37 @@ def split_bits(packed: np.ndarray, n_total: int, n_first: int):
     return pack_bits(b[:, :n_first]), pack_bits(b[:, n_first:])
 
 
+def problem_to_dem(prob: Problem) -> str:
+    """The problem (H, A, p) as a text detector error model: one error line per
+    column, probabilities written with 17 significant digits (exact round trip),
+    then the detector and observable declarations that fix M and K."""
+    Hc = [[] for _ in range(prob.N)]
+    Ac = [[] for _ in range(prob.N)]
+    for i in range(prob.M):
+        for e in range(prob.H_row_ptr[i], prob.H_row_ptr[i + 1]):
+            Hc[prob.H_col_idx[e]].append(i)
+    for k in range(prob.K):
+        for e in range(prob.A_row_ptr[k], prob.A_row_ptr[k + 1]):
+            Ac[prob.A_col_idx[e]].append(k)
+    lines = []
+    for j in range(prob.N):
+        t = " ".join([f"D{i}" for i in Hc[j]] + [f"L{k}" for k in Ac[j]])
+        lines.append(f"error({float(prob.priors[j]):.17g}) {t}".rstrip())
+    if prob.M:
+        lines.append(f"detector D{prob.M - 1}")
+    if prob.K:
+        lines.append(f"logical_observable L{prob.K - 1}")
+    return "\n".join(lines) + "\n"
+
+
+def problem_from_dem_arrays(d: dict, name: str = "dem") -> Problem:
+    """A Problem from the arrays of a DEM reader (M, N, K, CSR of H and A, priors)."""
+    return Problem(name=name, M=int(d["M"]), N=int(d["N"]), K=int(d["K"]),
+                   H_row_ptr=np.asarray(d["H_row_ptr"], np.int32), H_col_idx=np.asarray(d["H_col_idx"], np.int32),
+                   A_row_ptr=np.asarray(d["A_row_ptr"], np.int32), A_col_idx=np.asarray(d["A_col_idx"], np.int32),
+                   priors=np.asarray(d["priors"], np.float64), meta={"kind": "dem"})
+
+
 def bb72_code_capacity(p: float = 0.03) -> Problem:
     """[[72,12,6]] BB code (l = m = 6), i.i.d. Z flips with probability p."""
     return bb_code_capacity(6, 6, p, name=f"bb72_cc_p{p}")

@@ -322,3 +322,15 @@ def test_xyz_decoding_bit_exact(gw):
     gpu = _gpu_decode(prob, params, shots.syndromes)
     ref = oracle.Graph(prob, "f32").decode_batch(shots.syndromes, _oracle_params(params), nthreads=8)
     _assert_bit_exact(gpu, ref, prob.K)
+
+
+def test_dem_text_problem_decodes_bit_exact():
+    """A problem read from DEM text (the phenomenological DEM written out and read
+    back through bsd_dem_parse) decodes like the oracle on the same arrays."""
+    src = W.bb_phenomenological(12, 6, 12, 4e-3, 4e-3)
+    prob = W.problem_from_dem_arrays(D.B.bsd_dem_read(W.problem_to_dem(src)), name="dem_text")
+    shots = W.sample_shots(prob, 2000, "dem_text")
+    params = D.make_params("beam64_640iters", ms_scale=0.625, workspace_bytes=1 << 30)
+    gpu = _gpu_decode(prob, params, shots.syndromes)
+    ref = oracle.Graph(src, "f32").decode_batch(shots.syndromes, _oracle_params(params), nthreads=8)
+    _assert_bit_exact(gpu, ref, prob.K)
