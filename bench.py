@@ -60,6 +60,9 @@ XYZ_PS = (0.03, 0.05, 0.07)
 XYZ_SHOTS = 100_000
 XYZ_PRESET = "beam64_640iters"
 XYZ_WORKLOAD = "bb144_xyz_depolarizing beam64_640iters alpha=0.625 p={0.03,0.05,0.07} vs XZ decoding"
+LAT_WORKLOAD = "single-syndrome latency: bb144 p=0.03 beam32_340iters; phenomenological DEM p=q=3e-3 beam32_340iters; " \
+               "synthetic DEM beam32_340iters"
+LAT_PER_STEP = 1000       # single-syndrome decodes per step
 
 
 def parse():
@@ -75,12 +78,13 @@ def parse():
     ap.add_argument("--ps", default="0.01,0.03,0.05", help="physical error rates (a smaller case for profiling)")
     ap.add_argument("--workspace-gb", type=float, default=32.0, help="device workspace per decoder")
     ap.add_argument("--workload", choices=("bb144_code_capacity", "phenom_precision", "unrolled_training",
-                                           "synthetic_dem", "xyz"),
+                                           "synthetic_dem", "xyz", "latency"),
                     default="bb144_code_capacity",
                     help="phenom_precision: the phenomenological DEM with FP32, FP16 and BF16 message storage; "
                          "unrolled_training: training steps of the unrolled weighted min-sum on that DEM; "
                          "synthetic_dem: the 936 x 8800 circuit-shaped DEM with beam widths 8, 32, 64; "
-                         "xyz: XYZ against XZ decoding of [[144,12,12]] under depolarizing noise")
+                         "xyz: XYZ against XZ decoding of [[144,12,12]] under depolarizing noise; "
+                         "latency: one syndrome at a time (mean and 99.9 percentile per syndrome)")
     ap.add_argument("--train-steps", type=int, default=300, help="unrolled_training: steps before the LER judgement")
     ap.add_argument("--judge-shots", type=int, default=1_000_000, help="unrolled_training: held-out shots")
     a = ap.parse_args()
@@ -285,6 +289,40 @@ def run_reference_synthetic(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_latency(args):
+    """Reference arm of the latency workload: the double-precision oracle
+    decoding one syndrome at a time on one host thread."""
+    import oracle
+    from paper_2512_07057_gb300 import workloads as W
+    cases = [("bb144_cc_p0.03", W.bb144_code_capacity(0.03)),
+             ("phenom_p0.003", W.bb_phenomenological(12, 6, 12, 3e-3, 3e-3)),
+             ("synthetic_dem", W.synthetic_dem())]
+    n = min(args.steps * 200, 2000)
+    res, means = {}, []
+    for name, prob in cases:
+        sh = W.sample_shots(prob, n, W.shot_seed(f"latency_{name}", 0))
+        g = oracle.Graph(prob, "f64")
+        prm = oracle.preset("beam32_340iters", ms_scale=ALPHA)
+        lat = np.zeros(n)
+        for i in range(n):
+            t0 = time.perf_counter()
+            g.decode_batch(sh.syndromes[i:i + 1], prm, nthreads=1)
+            lat[i] = time.perf_counter() - t0
+        res[name] = {"mean_us": float(lat.mean() * 1e6), "p99.9_us": float(np.quantile(lat, 0.999) * 1e6),
+                     "syndromes": n}
+        means.append(lat.mean())
+    mean_us = float(np.mean(means) * 1e6)
+    line = {"impl": "reference", "metric": METRIC, "value": 1e6 / mean_us, "unit": "syndromes/s (one at a time)",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_us * 1e-3 * 200,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": LAT_WORKLOAD, "l2": "n/a (host)"}, "latency": res,
+            "cpu_baseline": {"value": 1e6 / mean_us, "unit": "syndromes/s (one at a time)", "cores": 1,
+                             "kind": "oracle", "sample": f"{n} single-syndrome decodes per case, one thread"},
+            "e2e": {"value": 1e6 / mean_us, "unit": "syndromes/s (one at a time)", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -293,6 +331,9 @@ def run_reference(args, rank: int):
         return
     if args.workload == "synthetic_dem":
         run_reference_synthetic(args)
+        return
+    if args.workload == "latency":
+        run_reference_latency(args)
         return
     phen = args.workload == "phenom_precision"
     if args.workload == "xyz":
@@ -1081,6 +1122,86 @@ def _failures(prob, sh, out):
     return (o != t).any(1) | (st == 4)
 
 
+def run_latency(args, rank: int, world: int, local_rank: int):
+    """Low-latency mode: each syndrome decoded alone (B = 1) as soon as it is
+    submitted; latency = host wall time from the call to the correction and
+    status being readable on the host.  Two paths: the syndrome resident on
+    the device (decode + a 12-byte device-to-host read of status and the first
+    correction words), and host buffers end to end (bsd_decode_host).  Each
+    with the small-chunk graph (grids sized to one shot) and without it."""
+    import torch
+
+    from __graft_entry__ import build
+    from paper_2512_07057_gb300 import decoder as D
+    from paper_2512_07057_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    if rank == 0:
+        build()
+    cases = [("bb144_cc_p0.03", W.bb144_code_capacity(0.03), "beam32_340iters"),
+             ("phenom_p0.003", W.bb_phenomenological(12, 6, 12, 3e-3, 3e-3), "beam32_340iters"),
+             ("synthetic_dem", W.synthetic_dem(), "beam32_340iters")]
+    n = args.steps * LAT_PER_STEP
+    stream = torch.cuda.current_stream(dev)
+    results, all_mean = {}, []
+    for name, prob, preset in cases:
+        sh = W.sample_shots(prob, n + 64, W.shot_seed(f"latency_{name}", rank))
+        synd = D.to_torch_words(sh.syndromes, dev)
+        res = {}
+        for mode, sb in (("small_graph", 0), ("full_grid", -1)):
+            d = D.BeamSearchDecoder(prob, D.make_params(preset, ms_scale=ALPHA, workspace_bytes=1 << 30,
+                                                        small_batch=sb), device=dev)
+            out = d.alloc_outputs(1)
+            host = torch.empty(3, dtype=torch.int32).pin_memory()
+            lat = np.zeros(n)
+            for i in range(-32, n):                       # 32 warm-up decodes
+                k = (i + 64) % (n + 64)
+                t0 = time.perf_counter()
+                d.decode(synd[k:k + 1], out, stream=stream)
+                host[0:1].copy_(out.status, non_blocking=True)
+                host[1:3].copy_(out.corrections[0, :2], non_blocking=True)
+                stream.synchronize()
+                if i >= 0:
+                    lat[i] = time.perf_counter() - t0
+            hs = torch.from_numpy(sh.syndromes.view(np.int32)).pin_memory()
+            WN, WK = (prob.N + 31) // 32, max((prob.K + 31) // 32, 1)
+            hc = torch.empty(WN, dtype=torch.int32).pin_memory()
+            ho = torch.empty(WK, dtype=torch.int32).pin_memory()
+            hst = torch.empty(1, dtype=torch.int32).pin_memory()
+            lat_h = np.zeros(n)
+            row = hs.shape[1] * 4
+            for i in range(-32, n):
+                k = (i + 64) % (n + 64)
+                t0 = time.perf_counter()
+                d.decode_host_ptrs(hs.data_ptr() + k * row, 1, hc.data_ptr(), ho.data_ptr(), hst.data_ptr(), None,
+                                   stream=stream)
+                if i >= 0:
+                    lat_h[i] = time.perf_counter() - t0
+            d.close()
+            us = lambda a, q: float(np.quantile(a, q) * 1e6)
+            res[mode] = {
+                "device_resident_us": {"mean": float(lat.mean() * 1e6), "p50": us(lat, 0.5), "p99": us(lat, 0.99),
+                                       "p99.9": us(lat, 0.999), "max": float(lat.max() * 1e6)},
+                "host_buffers_us": {"mean": float(lat_h.mean() * 1e6), "p50": us(lat_h, 0.5),
+                                    "p99": us(lat_h, 0.99), "p99.9": us(lat_h, 0.999),
+                                    "max": float(lat_h.max() * 1e6)}}
+        results[name] = {"preset": preset, "syndromes": n, **res}
+        all_mean.append(res["small_graph"]["device_resident_us"]["mean"])
+    mean_us = float(np.mean(all_mean))
+    line = {"metric": METRIC, "value": 1e6 / mean_us, "unit": "syndromes/s (one at a time)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_us * LAT_PER_STEP / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": LAT_WORKLOAD, "step": f"{LAT_PER_STEP} single-syndrome decodes",
+                       "timer": "host wall clock per syndrome, submit to result on the host",
+                       "l2": "not flushed: consecutive single decodes, the latency setting"},
+            "latency": results,
+            "context": "the paper reports 99.9 percentile decoding times per syndrome on one CPU core for its "
+                       "circuit-level [[144,12,12]] workload (Tables II-III); that workload is not available here"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def e2e_host(decs, work, args, dev):
     """Same metric through bsd_decode_host: pinned host syndromes in, host results out."""
     import torch
@@ -1171,6 +1292,8 @@ def main():
             run_synthetic(args, rank, world, local_rank)
         elif args.workload == "xyz":
             run_xyz(args, rank, world, local_rank)
+        elif args.workload == "latency":
+            run_latency(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -100,7 +100,9 @@ typedef struct {
                                   bsd_autotune), 1 one warp per candidate, 2..16 a block of
                                   that many warps per candidate (codes without the small engine's
                                   layout, or forced); results do not depend on it */
-    int32_t  reserved0;        /* must be 0 */
+    int32_t  small_batch;      /* chunks of at most this many shots launch a second graph whose
+                                  grids are sized to them (low latency for single syndromes):
+                                  0 the default 32, -1 never, else 1..65536 */
 } bsd_params;
 
 /* Fill *out with the library defaults: beam8_230iters, ms_scale 1,

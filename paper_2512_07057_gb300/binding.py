@@ -46,7 +46,7 @@ class bsd_params(C.Structure):
                 ("initial_iters", C.c_int32), ("iters_per_round", C.c_int32), ("num_results", C.c_int32),
                 ("ms_scale", C.c_float), ("llr_clamp", C.c_float), ("msg_precision", C.c_int32),
                 ("tie_guard_rel", C.c_float), ("workspace_bytes", C.c_int64), ("group_warps", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("small_batch", C.c_int32)]
 
 
 class bsd_shape_timing(C.Structure):

@@ -54,6 +54,8 @@ struct bsd_decoder {
     void* rr_mem = nullptr;                  // flagged list, count, gathered syndromes, re-run outputs
     long long rr_cap = 0;                    // capacity of the flagged list
     float* weights_mem = nullptr;            // [wT][Epad] weights of weighted min-sum (bsd_set_weights)
+    void* graph_small = nullptr;             // the same graph with grids sized for chunks of <= small_n shots
+    int small_n = 0;
 };
 
 namespace {
@@ -94,7 +96,8 @@ int validate_params(const bsd_params* p)
         return BSD_ERR_UNSUPPORTED;
     if (!std::isfinite(p->tie_guard_rel)) return BSD_ERR_INVALID_ARG;
     if (p->workspace_bytes < 0) return BSD_ERR_INVALID_ARG;
-    if (p->group_warps < 0 || p->group_warps > 16 || p->reserved0 != 0) return BSD_ERR_INVALID_ARG;
+    if (p->group_warps < 0 || p->group_warps > 16 || p->small_batch < -1 || p->small_batch > 65536)
+        return BSD_ERR_INVALID_ARG;
     return BSD_OK;
 }
 
@@ -106,6 +109,33 @@ T* carve(char*& p, size_t count)
     return r;
 }
 
+
+// launch grids for a chunk of at most n shots: the persistent kernels claim
+// their work, so fewer blocks suffice and none of them starts only to find
+// nothing to claim
+LaunchShape small_shape(const LaunchShape& ls, const DecCfg& cfg, int n)
+{
+    LaunchShape s = ls;
+    const long long per_block = ls.group_warps >= 2 ? 1 : ls.warps_per_block;
+    auto cap = [](long long v, int full) { return (int)(v < 1 ? 1 : (v < full ? v : full)); };
+    s.grid_seed = cap((n + per_block - 1) / per_block, ls.grid_seed);
+    s.grid_round = cap(((long long)n * 2 * cfg.w + per_block - 1) / per_block, ls.grid_round);
+    s.grid_select = cap((n + ls.select_warps - 1) / ls.select_warps, ls.grid_select);
+    return s;
+}
+
+// (re)build the decoder's graphs from its current graph, configuration and
+// shape; a graph that cannot be built leaves the direct-launch path
+void rebuild_graphs(bsd_decoder* dec)
+{
+    if (dec->graph) destroy_graph(dec->graph);
+    if (dec->graph_small) destroy_graph(dec->graph_small);
+    dec->graph = dec->graph_small = nullptr;
+    if (build_graph(dec->g, dec->cfg, dec->w, dec->ls, &dec->graph) != 0) dec->graph = nullptr;
+    if (dec->small_n > 0 &&
+        build_graph(dec->g, dec->cfg, dec->w, small_shape(dec->ls, dec->cfg, dec->small_n), &dec->graph_small) != 0)
+        dec->graph_small = nullptr;
+}
 }  // namespace
 
 namespace bsd {
@@ -196,6 +226,7 @@ void bsd_destroy(bsd_decoder* dec)
         if (dec->work_mem) cudaFree(dec->work_mem);
         if (dec->io_mem) cudaFree(dec->io_mem);
         if (dec->graph) destroy_graph(dec->graph);
+        if (dec->graph_small) destroy_graph(dec->graph_small);
         if (dec->h_nactive) cudaFreeHost(dec->h_nactive);
         if (dec->rr_mem) cudaFree(dec->rr_mem);
         if (dec->weights_mem) cudaFree(dec->weights_mem);
@@ -422,7 +453,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     }
     // the per-chunk graph: seed kernel + WHILE over beam passes; without it
     // decoding falls back to plain launches
-    if (build_graph(g, cfg, w, dec->ls, &dec->graph) != 0) dec->graph = nullptr;
+    dec->small_n = params->small_batch > 0 ? params->small_batch : (params->small_batch == 0 ? 32 : 0);
+    rebuild_graphs(dec);
     // 16-bit messages with near-tie flags: shots flagged by the 16-bit run are
     // decoded again by a single-precision twin
     if (prec != BSD_FP32 && cfg.tie_guard > 0.0) {
@@ -530,8 +562,9 @@ static int decode_impl(bsd_decoder* dec, const uint32_t* d_synd, long long base,
 {
     LaunchHooks hk{prof_before, prof_after, dec};
     dec->prof_stream = s;
-    return launch_chunk(dec->g, dec->cfg, dec->w, dec->ls, d_synd, base, n, o, s, dec->prof ? &hk : nullptr,
-                        dec->prof ? nullptr : dec->graph, dec->h_nactive)
+    void* gx = dec->prof ? nullptr : (n <= dec->small_n && dec->graph_small ? dec->graph_small : dec->graph);
+    return launch_chunk(dec->g, dec->cfg, dec->w, dec->ls, d_synd, base, n, o, s, dec->prof ? &hk : nullptr, gx,
+                        dec->h_nactive)
                ? BSD_ERR_CUDA
                : BSD_OK;
 }
@@ -641,12 +674,9 @@ static int apply_shape(bsd_decoder* dec, int group_warps, int warps_per_block)
     LaunchShape ls{};
     const int rc = configure_kernels(g, dec->cfg, dec->device, group_warps, warps_per_block, &ls);
     if (rc) return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA;
-    void* graph = nullptr;
-    if (build_graph(g, dec->cfg, dec->w, ls, &graph) != 0) graph = nullptr;
-    if (dec->graph) destroy_graph(dec->graph);
-    dec->graph = graph;
     dec->g = g;
     dec->ls = ls;
+    rebuild_graphs(dec);
     return BSD_OK;
 }
 
@@ -756,15 +786,12 @@ int bsd_set_weights(bsd_decoder* dec, const float* h_weights, int32_t T)
         if (d_w) cudaFree(d_w);
         return rc == -5 ? BSD_ERR_UNSUPPORTED : BSD_ERR_CUDA;
     }
-    void* graph = nullptr;
-    if (build_graph(g, cfg, dec->w, ls, &graph) != 0) graph = nullptr;
-    if (dec->graph) destroy_graph(dec->graph);
     if (dec->weights_mem) cudaFree(dec->weights_mem);
-    dec->graph = graph;
     dec->g = g;
     dec->cfg = cfg;
     dec->ls = ls;
     dec->weights_mem = d_w;
+    rebuild_graphs(dec);
     return BSD_OK;
 }
 

@@ -85,7 +85,7 @@ struct RunDesc {
     long long chunk_base;  // index of the chunk's first shot in the caller's batch
     long long chunk_n;     // shots in the chunk
     int pass;              // current beam pass
-    int pad;
+    int round;             // current beam round of the pass (graph launches read it from here)
 };
 
 // per-chunk counters (reset by k_begin_chunk)

@@ -755,7 +755,7 @@ __global__ void k_begin_chunk(Work w, int n_round_ints, const uint32_t* synd, Ou
         d.chunk_base = base;
         d.chunk_n = n;
         d.pass = 0;
-        d.pad = 0;
+        d.round = 1;
         *w.desc = d;
     }
 }
@@ -769,7 +769,39 @@ __global__ void k_pass_end(Work w, int n_round_ints, cudaGraphConditionalHandle 
     if (threadIdx.x == 0) {
         const int pass = w.desc->pass + 1;
         w.desc->pass = pass;
+        w.desc->round = 1;
         if (use_cond) cudaGraphSetConditional(cond, ((long long)pass * w.A < (long long)w.ctr->n_active) ? 1u : 0u);
+    }
+}
+
+// graph only, after the seed kernel: enter the loop over beam passes only if
+// some shot of the chunk needs beam rounds
+__global__ void k_pass_gate(Work w, cudaGraphConditionalHandle cond)
+{
+    count_launch(w);
+    if (threadIdx.x == 0) cudaGraphSetConditional(cond, w.ctr->n_active > 0 ? 1u : 0u);
+}
+
+// graph only, at the start of a pass: the loop over rounds begins with round 1
+__global__ void k_rounds_begin(Work w, cudaGraphConditionalHandle cond)
+{
+    count_launch(w);
+    if (threadIdx.x == 0) {
+        w.desc->round = 1;
+        cudaGraphSetConditional(cond, 1u);
+    }
+}
+
+// graph only, after the selection of round r: run round r + 1 only if it has
+// children to expand (a shot with none left was finalised by the selection)
+__global__ void k_round_end(Work w, int max_rounds, cudaGraphConditionalHandle cond)
+{
+    count_launch(w);
+    if (threadIdx.x == 0) {
+        const int r = w.desc->round;
+        const int more = (r < max_rounds && *((volatile int*)(w.round_ctr + 3 * (r + 1) + 2)) > 0) ? 1 : 0;
+        w.desc->round = r + 1;
+        cudaGraphSetConditional(cond, (unsigned)more);
     }
 }
 
@@ -854,6 +886,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_round(Dev
 {
     extern __shared__ __align__(16) char smem[];
     count_launch(w);
+    if (r <= 0) r = *((volatile int*)&w.desc->round);   // graph launches: the round counter
     long long pbase;
     const int cnt = window(w, &pbase);
     if (cnt == 0) return;
@@ -954,6 +987,7 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
 {
     extern __shared__ __align__(16) char smem[];
     count_launch(w);
+    if (r <= 0) r = *((volatile int*)&w.desc->round);   // graph launches: the round counter
     long long pbase;
     const int cnt = window(w, &pbase);
     if (cnt == 0) return;
@@ -1108,29 +1142,13 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                     myrank[q] = rk;
                 }
             }
-            if (r >= cfg.max_rounds || nex == 0) {
-                if (cfg.num_results > 1 && w.res_n[a] > 0) {
-                    finalize_results(g, cfg, w, d.out, a, gb, acc, near ? ST_NEAR : 0u);
-                } else {
-                    // no valid solution: the best path of the final set
-                    int best = 0x7fffffff;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (myrank[q] == 0) best = lane + 32 * q;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(FULLMASK, best, o));
-                    const uint32_t* eb;
-                    if (best != 0x7fffffff)
-                        eb = w.slotBits + slot_index(w, cb, a, best, W2) * (size_t)w.SB + g.WM + 2 * g.WN;
-                    else
-                        eb = parent_ref(g, cfg, w, r, pbase, a, 0).bits + g.WM + 2 * g.WN;
-                    finalize_shot(g, d.out, gb, eb, ST_FAILED | (near ? ST_NEAR : 0u), acc);
-                }
-                done = true;
-            } else {
-                // keep the top beam_width; their slots become the next round's parents
+            // the kept paths of a round before the last, and how many of them
+            // have a node left to branch on (their children make round r + 1)
+            const bool last = (r >= cfg.max_rounds || nex == 0);
+            int keep = 0, tot = 0;
+            if (!last) {
                 __syncwarp();
-                const int keep = nex < cfg.w ? nex : cfg.w;
+                keep = nex < cfg.w ? nex : cfg.w;
                 if (cfg.tie_guard > 0.0 && nex > keep) {
                     // pruning margin: last kept (rank keep-1) against first dropped (rank keep)
                     double s_in = -INFINITY, s_out = -INFINITY;
@@ -1153,24 +1171,48 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
                     if (myrank[q] >= 0 && myrank[q] < keep)
                         w.set_idx[(size_t)a * cfg.w + myrank[q]] = (uint8_t)(lane + 32 * q);
                 __syncwarp();
-                // children of round r + 1: two per kept path that has a next_pos
                 int cntp = 0;
                 for (int k = lane; k < keep; k += 32) {
                     const int c = w.set_idx[(size_t)a * cfg.w + k];
                     cntp += (w.slotMeta[slot_index(w, cb, a, c, W2)].next_pos >= 0) ? 1 : 0;
                 }
-                int tot = cntp;
+                tot = cntp;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULLMASK, tot, o);
+            }
+            if (last || tot == 0) {
+                // the search ends here: the last round, no child, or no kept
+                // path with a node left (the next round would have no child)
+                if (cfg.num_results > 1 && w.res_n[a] > 0) {
+                    finalize_results(g, cfg, w, d.out, a, gb, acc, near ? ST_NEAR : 0u);
+                } else {
+                    // no valid solution: the best path of the final set
+                    int best = 0x7fffffff;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (myrank[q] == 0) best = lane + 32 * q;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(FULLMASK, best, o));
+                    const uint32_t* eb;
+                    if (best != 0x7fffffff)
+                        eb = w.slotBits + slot_index(w, cb, a, best, W2) * (size_t)w.SB + g.WM + 2 * g.WN;
+                    else
+                        eb = parent_ref(g, cfg, w, r, pbase, a, 0).bits + g.WM + 2 * g.WN;
+                    finalize_shot(g, d.out, gb, eb, ST_FAILED | (near ? ST_NEAR : 0u), acc);
+                }
+                done = true;
+            } else {
+                // the kept slots become the next round's parents: two children per
+                // kept path that has a next_pos
                 int wbase = 0;
                 if (lane == 0) {
                     w.set_size[a] = keep;
                     w.iters_acc[a] = acc;
                     w.near[a] = near;
-                    if (tot > 0) wbase = atomicAdd(&round_ctr(w, r + 1)[2], 2 * tot);
+                    wbase = atomicAdd(&round_ctr(w, r + 1)[2], 2 * tot);
                 }
                 wbase = __shfl_sync(FULLMASK, wbase, 0);
-                if (tot > 0 && lane == 0) {
+                if (lane == 0) {
                     int2* items = w.items + (size_t)((r + 1) & 1) * (size_t)w.A * (size_t)W2;
                     int o = 0;
                     for (int k = 0; k < keep; ++k) {
@@ -1451,38 +1493,56 @@ static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0,
     cudaGraphNode_t seed;
     void* sargs[] = {&g, &cfg, &w};
     rc = add_kernel(graph, &seed, nullptr, (void*)k_seed<Eng>, ls.grid_seed, threads, ls.smem_bp, sargs);
+    // seed, then WHILE (a window of active shots left) { round 1, WHILE (the
+    // next round has children) { round r, selection, round end }, pass end }:
+    // a chunk runs exactly the passes and rounds it needs
     if (!rc && cfg.max_rounds > 0) {
-        cudaGraphConditionalHandle cond;
-        cudaGraphNode_t cnode;
+        cudaGraphConditionalHandle cpass, cround;
+        cudaGraphNode_t gate, wpass, rbegin, wround, pend;
         cudaGraphNodeParams cp{};
-        if (CUDA_FAILED(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault))) {
-            rc = -2;
-        } else {
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = cond;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            if (CUDA_FAILED(cudaGraphAddNode(&cnode, graph, &seed, nullptr, 1, &cp))) rc = -2;
+        if (CUDA_FAILED(cudaGraphConditionalHandleCreate(&cpass, graph, 0, cudaGraphCondAssignDefault))) rc = -2;
+        if (!rc) {
+            void* gargs[] = {&w, &cpass};
+            rc = add_kernel(graph, &gate, &seed, (void*)k_pass_gate, 1, 32, 0, gargs);
         }
         if (!rc) {
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            cudaGraphNode_t prev = nullptr;
-            // kernel parameters are copied when a node is added
-            for (int r = 1; r <= cfg.max_rounds && !rc; ++r) {
-                cudaGraphNode_t nr, ns;
-                void* rargs[] = {&g, &cfg, &w, &r};
-                rc = add_kernel(body, &nr, prev ? &prev : nullptr, (void*)k_round<Eng>, ls.grid_round, threads,
-                                ls.smem_bp, rargs);
-                if (!rc) rc = add_kernel(body, &ns, &nr, (void*)k_select, ls.grid_select, 32 * ls.select_warps,
-                                            ls.smem_select, rargs);
-                prev = ns;
-            }
-            if (!rc) {
-                cudaGraphNode_t ne;
-                int use = 1;
-                void* eargs[] = {&w, &nri, &cond, &use};
-                rc = add_kernel(body, &ne, &prev, (void*)k_pass_end, 1, 128, 0, eargs);
-            }
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = cpass;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            if (CUDA_FAILED(cudaGraphAddNode(&wpass, graph, &gate, nullptr, 1, &cp))) rc = -2;
+        }
+        cudaGraph_t body = rc ? nullptr : cp.conditional.phGraph_out[0];
+        if (!rc && CUDA_FAILED(cudaGraphConditionalHandleCreate(&cround, body, 0, 0))) rc = -2;
+        if (!rc) {
+            void* bargs[] = {&w, &cround};
+            rc = add_kernel(body, &rbegin, nullptr, (void*)k_rounds_begin, 1, 32, 0, bargs);
+        }
+        cudaGraphNodeParams cr{};
+        if (!rc) {
+            cr.type = cudaGraphNodeTypeConditional;
+            cr.conditional.handle = cround;
+            cr.conditional.type = cudaGraphCondTypeWhile;
+            cr.conditional.size = 1;
+            if (CUDA_FAILED(cudaGraphAddNode(&wround, body, &rbegin, nullptr, 1, &cr))) rc = -2;
+        }
+        if (!rc) {
+            // kernel parameters are copied when a node is added; round 0 means
+            // "read the round counter"
+            cudaGraph_t rbody = cr.conditional.phGraph_out[0];
+            cudaGraphNode_t nr, ns, ne;
+            int r0 = 0, maxr = cfg.max_rounds;
+            void* rargs[] = {&g, &cfg, &w, &r0};
+            rc = add_kernel(rbody, &nr, nullptr, (void*)k_round<Eng>, ls.grid_round, threads, ls.smem_bp, rargs);
+            if (!rc) rc = add_kernel(rbody, &ns, &nr, (void*)k_select, ls.grid_select, 32 * ls.select_warps,
+                                        ls.smem_select, rargs);
+            void* eargs[] = {&w, &maxr, &cround};
+            if (!rc) rc = add_kernel(rbody, &ne, &ns, (void*)k_round_end, 1, 32, 0, eargs);
+        }
+        if (!rc) {
+            int use = 1;
+            void* pargs[] = {&w, &nri, &cpass, &use};
+            rc = add_kernel(body, &pend, &wround, (void*)k_pass_end, 1, 128, 0, pargs);
         }
     }
     cudaGraphExec_t gx = nullptr;

@@ -37,3 +37,47 @@ def test_autotune_keeps_results_and_the_fastest_shape(name):
     dec.set_weights(np.full((2, prob.n_edges), 0.625, np.float32))
     assert dec.shape == (best[0], best[1])
     dec.close()
+
+
+def test_small_chunk_graph_changes_nothing():
+    """Chunks of a few shots run a graph with grids sized to them; outputs equal
+    the full-grid graph's, for one shot at a time and for a small batch."""
+    prob = W.bb144_code_capacity(0.05)
+    shots = W.sample_shots(prob, 40, "small_graph")
+    s = D.to_torch_words(shots.syndromes)
+    res = {}
+    for sb in (0, -1):
+        dec = D.BeamSearchDecoder(prob, D.make_params("beam32_340iters", ms_scale=0.625, small_batch=sb))
+        batch = dec.decode(s[:20])
+        single = [dec.decode(s[i:i + 1]) for i in range(20, 40)]
+        torch.cuda.synchronize()
+        res[sb] = (D.from_torch_words(batch.corrections).copy(), D.from_torch_words(batch.status).copy(),
+                   np.concatenate([D.from_torch_words(o.corrections) for o in single]),
+                   np.concatenate([D.from_torch_words(o.status) for o in single]))
+        dec.close()
+    for a, b in zip(res[0], res[-1]):
+        assert np.array_equal(a, b)
+
+
+def test_graph_runs_only_the_rounds_a_chunk_needs():
+    """Kernels launched per chunk, counted on the device: a chunk whose shots all
+    converge in the seed runs 3 (chunk set-up, seed, pass gate); one that needs
+    beam rounds adds the round loop of one pass (start, 3 per round, pass end)
+    and no round beyond the last one with children."""
+    prob = W.bb144_code_capacity(0.05)
+    dec = D.BeamSearchDecoder(prob, D.make_params("beam32_340iters", ms_scale=0.625))
+    zero = torch.zeros((64, 3), dtype=torch.int32, device="cuda")
+    dec.profile_read()
+    dec.decode(zero)
+    torch.cuda.synchronize()
+    assert dec.profile_read()["kernel_launches"] == 3
+    # shots that need rounds: the maximum round any shot reaches bounds the loop
+    shots = W.sample_shots(prob, 2000, "graph_rounds")
+    out = dec.decode(D.to_torch_words(shots.syndromes))
+    torch.cuda.synchronize()
+    launches = dec.profile_read()["kernel_launches"]
+    st = D.from_torch_words(out.status)
+    assert (st & 7 == 2).any()                       # some shots converged in a beam round
+    rounds = (launches - 3 - 2) // 3
+    assert launches == 3 + 1 + 3 * rounds + 1 and 1 <= rounds <= 10
+    dec.close()
