@@ -121,6 +121,7 @@ struct Work {
     int* res_origin;       // [A][num_results]: 0 = seed, 1 = masked BP round
     int* res_n;            // [A]
     int* near;             // [A] a near-tie met by this shot's search so far
+    unsigned long long* first_ok;  // [A] (round stamp << 32) | ~c of the lowest-index successful child so far
     int2* items;           // [2][A * 2w] (window entry, child index) for rounds >= 2
     Counters* ctr;
     int* round_ctr;        // 3 * (max_rounds + 2) ints after ctr

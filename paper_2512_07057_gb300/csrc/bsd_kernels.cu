@@ -83,6 +83,22 @@ template <> struct Store<2> {
 __host__ __device__ __forceinline__ size_t snap_bytes(const DevGraph& g) { return (size_t)g.Epad * (size_t)g.msg_bytes; }
 __host__ __device__ __forceinline__ int snap_vec16(const DevGraph& g) { return (int)(snap_bytes(g) / 16); }
 
+// Early abort of a beam child (num_results = 1): once a child of the same shot
+// with a lower canonical index has succeeded in this round, this child's
+// result can no longer be the first success in visit order and is never read.
+// The shot's key holds (round stamp << 32) | ~c of the lowest successful index
+// c so far (atomicMax); a run loads it at the start of an iteration and
+// checks it at the end, so the load's latency hides behind the iteration.
+struct AbortCheck {
+    const unsigned long long* key;   // null: never abort
+    unsigned long long stamp;        // this round's stamp << 32
+    unsigned c;                      // this child's canonical index
+    __device__ __forceinline__ bool hit(unsigned long long v) const
+    {
+        return (v & 0xffffffff00000000ull) == stamp && (0xffffffffu - (unsigned)v) < c;
+    }
+};
+
 // copy n16 16-byte vectors (the E snapshot) with the threads of a candidate group
 template <class G>
 __device__ __forceinline__ void group_copy16(const G& grp, void* dst, const void* src, int n16)
@@ -221,7 +237,7 @@ __device__ inline unsigned long long fixq(float x)
 // null, Lambda_j(max_iters) is written there.
 template <int DV, int P, bool W, class G>
 __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
-                          bool stop, int* success, float* post_out, bool from_prior)
+                          bool stop, int* success, float* post_out, bool from_prior, const AbortCheck& ab)
 {
     using S = Store<P>;
     using T = typename S::T;
@@ -232,6 +248,8 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
     int iters = 0;
     int ok = 0;
     for (int t = 1; t <= max_iters; ++t) {
+        unsigned long long ab_key = 0ull;
+        if (ab.key != nullptr && grp.rank() == 0) ab_key = *((volatile const unsigned long long*)ab.key);
         for (int q = grp.rank(); q < g.WM; q += grp.size()) st.par[q] = st.sp[q];
         // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
         const float* wt = W ? cfg.weights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
@@ -342,6 +360,7 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
         iters = t;
         grp.sync();
         if (ok && stop) break;
+        if (ab.key != nullptr && grp.any(grp.rank() == 0 && ab.hit(ab_key))) { ok = 0; break; }
     }
     *success = ok;
     return iters;
@@ -442,9 +461,9 @@ struct GenericEngine {
         for (int j = grp.rank(); j < g.N; j += grp.size()) st.sumllr[j] = 0.f;
     }
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
-                       int* success, float* post_out, bool from_prior = false)
+                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
     {
-        return bp_iterate<DV, P, W>(grp, g, cfg, st, max_iters, stop, success, post_out, from_prior);
+        return bp_iterate<DV, P, W>(grp, g, cfg, st, max_iters, stop, success, post_out, from_prior, ab);
     }
     __device__ void argmin_score(const DevGraph& g, const WarpState& st, double guard, int* np, long long* S,
                                  int* tie)
@@ -502,7 +521,7 @@ struct SmallEngine {
         for (int c = 0; c < CPL; ++c) sum[c] = 0.f;
     }
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
-                       int* success, float* post_out, bool = false)
+                       int* success, float* post_out, bool = false, const AbortCheck& ab = AbortCheck{})
     {
         const int lane = threadIdx.x & 31;
         const float alpha = cfg.alpha;
@@ -517,6 +536,8 @@ struct SmallEngine {
         int iters = 0;
         int ok = 0;
         for (int t = 1; t <= max_iters; ++t) {
+            unsigned long long ab_key = 0ull;
+            if (ab.key != nullptr && lane == 0) ab_key = *((volatile const unsigned long long*)ab.key);
             for (int q = lane; q < g.WM; q += 32) st.par[q] = st.sp[q];
             // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
             const float* wt = W ? cfg.weights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
@@ -624,6 +645,7 @@ struct SmallEngine {
             iters = t;
             __syncwarp();
             if (ok && stop) break;
+            if (ab.key != nullptr && __any_sync(FULLMASK, lane == 0 && ab.hit(ab_key))) { ok = 0; break; }
         }
         *success = ok;
         return iters;
@@ -745,6 +767,10 @@ __global__ void k_begin_chunk(Work w, int n_round_ints, const uint32_t* synd, Ou
 {
     count_launch(w);
     for (int q = threadIdx.x; q < n_round_ints; q += blockDim.x) w.round_ctr[q] = 0;
+    // early-abort keys of the window entries this chunk can use (stamps grow
+    // within a chunk, so only a new chunk needs them cleared)
+    const long long na = n < w.A ? n : w.A;
+    for (long long q = threadIdx.x; q < na; q += blockDim.x) w.first_ok[q] = 0ull;
     if (threadIdx.x == 0) {
         w.ctr->claim_seed = 0;
         w.ctr->n_active = 0;
@@ -890,6 +916,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_round(Dev
     long long pbase;
     const int cnt = window(w, &pbase);
     if (cnt == 0) return;
+    const int pass = *((volatile int*)&w.desc->pass);
     Eng eng;
     eng.grp = Eng::Grp::make(smem + warp_smem_bytes(g));
     const auto& grp = eng.grp;
@@ -936,9 +963,34 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_round(Dev
         for (int q = __ldg(g.col_ptr + pos) + grp.rank(); q < __ldg(g.col_ptr + pos + 1); q += grp.size())
             Store<Eng::kPrec>::st(reinterpret_cast<typename Store<Eng::kPrec>::T*>(st.E), __ldg(g.col_edge + q), cfg.L);
         grp.sync();
+        // with num_results = 1, only the first success in visit order matters:
+        // a child stops once a lower-index sibling of this round has succeeded
+        AbortCheck ab{};
+        if (cfg.num_results == 1) {
+            ab.key = w.first_ok + a;
+            ab.stamp = (unsigned long long)(pass * (cfg.max_rounds + 1) + r) << 32;
+            ab.c = (unsigned)c;
+        }
         int succ = 0;
-        const int iters = eng.run(g, cfg, st, cfg.iters_per_round, true, &succ, nullptr);
-        if (grp.rank() == 0) atomicAdd(&w.stats[1], (unsigned long long)iters);
+        const int iters = eng.run(g, cfg, st, cfg.iters_per_round, true, &succ, nullptr, false, ab);
+        int superseded = 0;
+        if (grp.rank() == 0) {
+            atomicAdd(&w.stats[1], (unsigned long long)iters);
+            if (ab.key != nullptr) {
+                if (succ) atomicMax(w.first_ok + a, ab.stamp | (0xffffffffull - (unsigned)c));
+                else superseded = ab.hit(*((volatile const unsigned long long*)ab.key)) ? 1 : 0;
+            }
+        }
+        // a superseded child's slot is never read: record only that it exists
+        if (grp.bcast(superseded)) {
+            if (grp.rank() == 0) {
+                SlotMeta m;
+                m.S = 0; m.iters = iters; m.next_pos = -1; m.success = 0; m.flags = 0;
+                w.slotMeta[cslot] = m;
+            }
+            grp.sync();
+            continue;
+        }
         grp.sync();
         for (int q = grp.rank(); q < g.WN; q += grp.size()) st.ehat[q] = (st.ehat[q] & ~st.mask[q]) | st.vals[q];
         grp.sync();
@@ -1623,6 +1675,7 @@ size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long 
     v.res_w = (long long*)take(sizeof(long long) * (size_t)A * NR);
     v.res_origin = (int*)take(sizeof(int) * (size_t)A * NR);
     v.res_n = (int*)take(sizeof(int) * (size_t)A);
+    v.first_ok = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)A);
     v.near = (int*)take(sizeof(int) * (size_t)A);
     v.items = (int2*)take(sizeof(int2) * 2 * (size_t)A * W2);
     if (w) *w = v;
