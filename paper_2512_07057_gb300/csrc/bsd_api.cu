@@ -347,6 +347,23 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
         std::memcpy(&fneg, &neg, 4);
         rs0[i] = make_float4(m1, m2, fid, fneg);
     }
+    // the first check messages of a seed run, before the syndrome sign:
+    // alpha * (the minimum over the other edges) with the sign of the others'
+    // parity, formed as the small engine forms them (its t = 1 detector pass
+    // only flips the sign bit when s_i = 1)
+    std::vector<float> D0(Epad, 0.f);
+    for (int i = 0; i < M; ++i) {
+        const float m1 = rs0[i].x, m2 = rs0[i].y;
+        unsigned neg;
+        std::memcpy(&neg, &rs0[i].w, 4);
+        const float d1 = params->ms_scale * m1, d2 = params->ms_scale * m2;
+        for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e) {
+            const float x = lamE[e] == 0.f ? 0.f : lamE[e];
+            float d = (std::fabs(x) == m1) ? d2 : d1;
+            if ((neg ^ (x < 0.f ? 1u : 0u)) & 1u) d = -d;
+            D0[e] = d;
+        }
+    }
     std::vector<uint32_t> hcol((size_t)N * WM, 0u), acol((size_t)N * (WK > 0 ? WK : 1), 0u);
     for (int i = 0; i < M; ++i)
         for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e)
@@ -366,6 +383,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     gb += align256(sizeof(uint32_t) * acol.size());
     gb += align256(sizeof(long long) * N);
     gb += align256(sizeof(float4) * M);
+    gb += align256(sizeof(float) * Epad);
     if (CUDA_FAILED(cudaMalloc(&dec->graph_mem, gb))) { bsd_destroy(dec); return BSD_ERR_OOM; }
     dec->graph_bytes = gb;
     char* p = (char*)dec->graph_mem;
@@ -379,6 +397,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     uint32_t* d_acol = carve<uint32_t>(p, acol.size());
     long long* d_lamq = carve<long long>(p, N);
     float4* d_rs0 = carve<float4>(p, M);
+    float* d_D0 = carve<float>(p, Epad);
     bool ok = !CUDA_FAILED(cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_edge, col_edge.data(), sizeof(int) * E, cudaMemcpyHostToDevice)) &&
@@ -388,7 +407,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
               !CUDA_FAILED(cudaMemcpy(d_hcol, hcol.data(), sizeof(uint32_t) * hcol.size(), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_acol, acol.data(), sizeof(uint32_t) * acol.size(), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_lamq, lamq.data(), sizeof(long long) * N, cudaMemcpyHostToDevice)) &&
-              !CUDA_FAILED(cudaMemcpy(d_rs0, rs0.data(), sizeof(float4) * M, cudaMemcpyHostToDevice));
+              !CUDA_FAILED(cudaMemcpy(d_rs0, rs0.data(), sizeof(float4) * M, cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_D0, D0.data(), sizeof(float) * Epad, cudaMemcpyHostToDevice));
     if (!ok) { bsd_destroy(dec); return BSD_ERR_CUDA; }
 
     DevGraph& g = dec->g;
@@ -399,7 +419,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.max_col_deg = max_col; g.max_row_deg = max_row;
     g.all_lam_pos = all_pos;
     g.row_ptr = d_row_ptr; g.col_ptr = d_col_ptr; g.col_edge = d_col_edge; g.col_row = d_col_row;
-    g.lam = d_lam; g.lamE = d_lamE; g.hcol = d_hcol; g.acol = d_acol; g.lamq = d_lamq; g.rs0 = d_rs0;
+    g.lam = d_lam; g.lamE = d_lamE; g.hcol = d_hcol; g.acol = d_acol; g.lamq = d_lamq; g.rs0 = d_rs0; g.D0 = d_D0;
 
     DecCfg& cfg = dec->cfg;
     cfg.max_rounds = params->max_rounds;

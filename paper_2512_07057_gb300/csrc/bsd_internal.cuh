@@ -11,6 +11,7 @@
 //   acol[N][WK]           column j of A as a K-bit set (observable flips)
 //   lamq[N]               Lambda_j on the 2^-16 fixed-point grid (weights)
 //   rs0[M]                the detector records of E(0) (a seed run's first check pass, up to the syndrome)
+//   D0[Epad]              the check messages of E(0) with the scale alpha, before the syndrome sign
 //
 // Workspace (one decoder):
 //   seed store, S entries: the snapshot (E, s', mask, vals, e^, record) of
@@ -52,6 +53,7 @@ struct DevGraph {
     const uint32_t* acol;
     const long long* lamq;
     const float4* rs0;     // [M] detector records of E(0): (min1, min2, argmin edge, parity of negatives)
+    const float* D0;       // [Epad] check messages of E(0) with scale alpha, before the syndrome sign
 };
 
 struct DecCfg {

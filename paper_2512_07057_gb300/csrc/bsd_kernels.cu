@@ -492,7 +492,7 @@ struct SmallEngine {
     static constexpr int kMinBlocks = 2;   // at most 128 registers: two 8-warp blocks per SM
     static constexpr int kMaxThreads = 256;
     static constexpr int kPrec = P;
-    static constexpr bool kPriorStart = false;  // runs from E(0) read a copy of E(0)
+    static constexpr bool kPriorStart = !W;  // unweighted runs from E(0) start from the table D0
     WarpGroup grp;
     using S = Store<P>;
     uint32_t ci[CPL][3];   // (CSR edge id << 16) | row, for column lane + 32 c
@@ -521,7 +521,7 @@ struct SmallEngine {
         for (int c = 0; c < CPL; ++c) sum[c] = 0.f;
     }
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
-                       int* success, float* post_out, bool = false, const AbortCheck& ab = AbortCheck{})
+                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
     {
         const int lane = threadIdx.x & 31;
         const float alpha = cfg.alpha;
@@ -541,9 +541,27 @@ struct SmallEngine {
             for (int q = lane; q < g.WM; q += 32) st.par[q] = st.sp[q];
             // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
             const float* wt = W ? cfg.weights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
-            // ---- detector pass (Eq. 1)
+            // ---- detector pass (Eq. 1); a run from E(0) takes its first check
+            // messages from the table D0, flipping the sign where s_i = 1
+            if (!W && from_prior && t == 1) {
 #pragma unroll
-            for (int r = 0; r < RPL; ++r) {
+                for (int r = 0; r < RPL; ++r) {
+                    const int i = lane + 32 * r;
+                    if (i < g.M) {
+                        const uint32_t sb = ((st.sp[i >> 5] >> (i & 31)) & 1u) << 31;
+                        const float2* src = reinterpret_cast<const float2*>(g.D0 + RD * i);
+                        float2* dr = reinterpret_cast<float2*>(st.D + RD * i);
+#pragma unroll
+                        for (int h = 0; h < RD / 2; ++h) {
+                            const float2 v = __ldg(src + h);
+                            dr[h] = make_float2(__uint_as_float(__float_as_uint(v.x) ^ sb),
+                                                __uint_as_float(__float_as_uint(v.y) ^ sb));
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < ((!W && from_prior && t == 1) ? 0 : RPL); ++r) {
                 const int i = lane + 32 * r;
                 if (i < g.M) {
                     const int eb = RD * i;

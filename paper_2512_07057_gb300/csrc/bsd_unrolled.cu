@@ -605,7 +605,7 @@ int bsd_unrolled_backward(const bsd_decoder* dec, int64_t B, int32_t T, int32_t 
     const int k = ckpt_every;
     const size_t EB = (size_t)g->E * (size_t)a.Bp, NB = (size_t)g->N * (size_t)a.Bp;
     const double scale = 1.0 / ((double)B * (double)g->N);
-    const int cap_c = cap_of(g->max_col_deg), cap_r = cap_of(g->max_row_deg);
+    const int cap_c = cap_of(g->max_col_deg);
     const dim3 gcol(a.ntile, grid_y(g->N)), grow(a.ntile, grid_y(g->M));
     LaunchHooks hks;
     const LaunchHooks* hk = decoder_hooks(dec, s, &hks) ? &hks : nullptr;
@@ -636,9 +636,9 @@ int bsd_unrolled_backward(const bsd_decoder* dec, int64_t B, int32_t T, int32_t 
             float* gwp = u.gw_part + (size_t)(t - 1) * a.ntile * kWarps * g->E;
             {
                 Timed tm(hk, kKindBCheck);
-                if (cap_r == 4) k_u_bcheck<4><<<grow, kThreads, 0, s>>>(a, Eprev, u.gD, gEout, gwp, t);
-                else if (cap_r == 8) k_u_bcheck<8><<<grow, kThreads, 0, s>>>(a, Eprev, u.gD, gEout, gwp, t);
-                else k_u_bcheck<0><<<grow, kThreads, 0, s>>>(a, Eprev, u.gD, gEout, gwp, t);
+                // the check adjoint reloads its vectors (64 registers, 8 blocks per SM):
+                // faster than holding them (96 registers, 5 blocks)
+                k_u_bcheck<0><<<grow, kThreads, 0, s>>>(a, Eprev, u.gD, gEout, gwp, t);
             }
             cur ^= 1;
         }
