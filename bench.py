@@ -85,6 +85,9 @@ def parse():
                          "synthetic_dem: the 936 x 8800 circuit-shaped DEM with beam widths 8, 32, 64; "
                          "xyz: XYZ against XZ decoding of [[144,12,12]] under depolarizing noise; "
                          "latency: one syndrome at a time (mean and 99.9 percentile per syndrome)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch shapes (for profiler runs, where tuning timings "
+                         "are distorted)")
     ap.add_argument("--train-steps", type=int, default=300, help="unrolled_training: steps before the LER judgement")
     ap.add_argument("--judge-shots", type=int, default=1_000_000, help="unrolled_training: held-out shots")
     a = ap.parse_args()
@@ -411,8 +414,14 @@ def alu_roofline(prof, E: int, dev: int, traffic_case: str):
     return roofline, exec_iters
 
 
+NO_AUTOTUNE = False
+
+
 def autotune(dec, synd, sample: int = 65536) -> dict:
     """Launch-shape autotuning on a prefix of the decoder's own batch (outside the timed regions)."""
+    if NO_AUTOTUNE:
+        gw, wpb = dec.shape
+        return {"group_warps": gw, "warps_per_block": wpb, "autotuned": False}
     rep = dec.autotune(synd[:min(sample, synd.shape[0])].contiguous())
     gw, wpb = dec.shape
     return {"group_warps": gw, "warps_per_block": wpb, "sample_shots": int(min(sample, synd.shape[0])),
@@ -1271,7 +1280,9 @@ def _source_hash(files=None) -> str:
 
 
 def main():
+    global NO_AUTOTUNE
     args = parse()
+    NO_AUTOTUNE = args.no_autotune
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
