@@ -63,6 +63,10 @@ XYZ_WORKLOAD = "bb144_xyz_depolarizing beam64_640iters alpha=0.625 p={0.03,0.05,
 LAT_WORKLOAD = "single-syndrome latency: bb144 p=0.03 beam32_340iters; phenomenological DEM p=q=3e-3 beam32_340iters; " \
                "synthetic DEM beam32_340iters"
 LAT_PER_STEP = 1000       # single-syndrome decodes per step
+NR_PS = (0.03, 0.05)
+NR_SHOTS = 100_000
+NR_PRESETS = ("beam64_640iters", "beam64_32res_640iters")
+NR_WORKLOAD = "bb144_code_capacity alpha=0.625 p={0.03,0.05}: beam64_640iters vs beam64_32res_640iters"
 
 
 def parse():
@@ -78,13 +82,14 @@ def parse():
     ap.add_argument("--ps", default="0.01,0.03,0.05", help="physical error rates (a smaller case for profiling)")
     ap.add_argument("--workspace-gb", type=float, default=32.0, help="device workspace per decoder")
     ap.add_argument("--workload", choices=("bb144_code_capacity", "phenom_precision", "unrolled_training",
-                                           "synthetic_dem", "xyz", "latency"),
+                                           "synthetic_dem", "xyz", "latency", "num_results"),
                     default="bb144_code_capacity",
                     help="phenom_precision: the phenomenological DEM with FP32, FP16 and BF16 message storage; "
                          "unrolled_training: training steps of the unrolled weighted min-sum on that DEM; "
                          "synthetic_dem: the 936 x 8800 circuit-shaped DEM with beam widths 8, 32, 64; "
                          "xyz: XYZ against XZ decoding of [[144,12,12]] under depolarizing noise; "
-                         "latency: one syndrome at a time (mean and 99.9 percentile per syndrome)")
+                         "latency: one syndrome at a time (mean and 99.9 percentile per syndrome); "
+                         "num_results: beam64_640iters against beam64_32res_640iters")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shapes (for profiler runs, where tuning timings "
                          "are distorted)")
@@ -339,7 +344,10 @@ def run_reference(args, rank: int):
         run_reference_latency(args)
         return
     phen = args.workload == "phenom_precision"
-    if args.workload == "xyz":
+    if args.workload == "num_results":
+        work = make_workload(0, min(args.shots, 20_000), NR_PS)
+        preset, wl_name = NR_PRESETS[1], NR_WORKLOAD
+    elif args.workload == "xyz":
         from paper_2512_07057_gb300 import workloads as W
         work = []
         for p in XYZ_PS:
@@ -1211,6 +1219,97 @@ def run_latency(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
 
 
+def run_num_results(args, rank: int, world: int, local_rank: int):
+    """num_results > 1: the best-LER preset of Table I (32 results, the
+    minimum-weight one returned) against the same beam with the first
+    result; throughput, LER, iterations and where the time goes (the
+    selection kernel holds the deduplication of results)."""
+    import torch
+    import torch.distributed as dist
+
+    from __graft_entry__ import build
+    from paper_2512_07057_gb300 import decoder as D
+    from paper_2512_07057_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+        build()
+    nshots = args.shots if args.shots != 1_000_000 else NR_SHOTS
+    work = []
+    for p in NR_PS:
+        prob = W.bb144_code_capacity(p)
+        work.append((p, prob, W.sample_shots(prob, nshots, W.shot_seed(f"bb144_cc_p{p}", rank))))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream(dev)
+    forms = {}
+    for preset in NR_PRESETS:
+        decs, synd, outs, tuned = [], [], [], {}
+        for p, prob, sh in work:
+            d = D.BeamSearchDecoder(prob, D.make_params(preset, ms_scale=ALPHA,
+                                                        workspace_bytes=int(args.workspace_gb * (1 << 30)) // 2),
+                                    device=dev)
+            decs.append(d)
+            synd.append(D.to_torch_words(sh.syndromes, dev))
+            outs.append(d.alloc_outputs(sh.B))
+            tuned[str(p)] = autotune(d, synd[-1], 16384)
+
+        def step():
+            for d, s_, o in zip(decs, synd, outs):
+                d.decode(s_, o, stream=stream)
+
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step()
+        torch.cuda.synchronize(dev)
+        tr_args = (decs, step, flush, stream, dev, args.steps, world, rank)
+        ms_steps, _, clocks, prof_graph = timed_region(*tr_args, profiled=False, sample_clocks=True)
+        _, _, _, prof = timed_region(*tr_args, profiled=True, sample_clocks=False)
+        ms_total = float(sum(ms_steps))
+        if world > 1:
+            t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_total = float(t.item())
+        roofline, exec_iters = alu_roofline(prof, work[0][1].n_edges, dev, "16000-shot case")
+        per_p = {}
+        for (p, prob, sh), o, pr in zip(work, outs, prof):
+            st = D.from_torch_words(o.status)
+            it = D.from_torch_words(o.iters).astype(np.int64)
+            per_p[str(p)] = {"ler": ler_of(prob, sh, D.from_torch_words(o.obs_flips), st & 7),
+                             "seed_converged": float(((st & 7) == 1).mean()),
+                             "beam_converged": float(((st & 7) == 2).mean()),
+                             "failed": float(((st & 7) == 4).mean()), "mean_alg_iters": float(it.mean()),
+                             "kernel_ms_per_step": {n: float(x) / args.steps
+                                                    for n, x in zip(("k_seed", "k_round", "k_select"), pr["ms"])}}
+        forms[preset] = {"value": world * sum(sh.B for _, _, sh in work) * args.steps / (ms_total * 1e-3),
+                         "unit": "syndromes/s", "ms_per_step": ms_total / args.steps, "roofline": roofline,
+                         "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / args.steps,
+                                                    "round": float(exec_iters[1]) / args.steps},
+                         "gpu_launches": int(sum(pr["kernel_launches"] for pr in prof_graph)), "clocks": clocks,
+                         "per_p": per_p, "launch_shapes": tuned}
+        for d in decs:
+            d.close()
+    main = forms[NR_PRESETS[1]]
+    line = {"metric": METRIC, "value": main["value"], "unit": "syndromes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": NR_WORKLOAD, "shots_per_p_per_gpu": nshots,
+                       "l2": "flushed before every timed step (256 MiB write outside the step events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": main["roofline"], "gpu_launches": main["gpu_launches"], "clocks": main["clocks"],
+            "forms": forms, "one_result_over_32_results": forms[NR_PRESETS[0]]["value"] / main["value"]}
+    if rank == 0 and not args.no_cpu_baseline:
+        r, n, dt = oracle_rate(work, args.cpu_seconds, cores(), NR_PRESETS[1])
+        line["cpu_baseline"] = {"value": r, "unit": "syndromes/s", "cores": cores(), "kind": "oracle",
+                                "sample": f"first {n} shots of each p batch, beam64_32res_640iters, double-precision "
+                                          f"oracle, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def e2e_host(decs, work, args, dev):
     """Same metric through bsd_decode_host: pinned host syndromes in, host results out."""
     import torch
@@ -1305,6 +1404,8 @@ def main():
             run_xyz(args, rank, world, local_rank)
         elif args.workload == "latency":
             run_latency(args, rank, world, local_rank)
+        elif args.workload == "num_results":
+            run_num_results(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:
