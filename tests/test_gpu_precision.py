@@ -153,3 +153,32 @@ def test_direct_launches_after_later_decoders():
     assert prof["launches"][0] >= 1
     dec.close()
     other.close()
+
+
+@pytest.mark.parametrize("prec", [B.BSD_FP32, B.BSD_FP16])
+def test_full_size_phenomenological_sampled(prec):
+    """The phenomenological DEM at the benchmark's size and launch shape: 10^5
+    shots at p = q = 3e-3 with beam64_640iters, autotuned as bench.py runs it;
+    1000 sampled shots against the oracle (for 16-bit storage: the 16-bit run,
+    or the single-precision run on shots it flags)."""
+    prob = W.bb_phenomenological(12, 6, 12, 3e-3, 3e-3)
+    shots = W.sample_shots(prob, 100_000, W.shot_seed("bb144_phen_p0.003", 0))
+    params = D.make_params("beam64_640iters", ms_scale=0.625, msg_precision=prec, workspace_bytes=16 << 30)
+    dec = D.BeamSearchDecoder(prob, params)
+    s = D.to_torch_words(shots.syndromes)
+    dec.autotune(s[:16384].contiguous())
+    out = dec.decode(s)
+    torch.cuda.synchronize()
+    gpu = {k: D.from_torch_words(getattr(out, a)).copy()
+           for k, a in (("corrections", "corrections"), ("obs", "obs_flips"), ("status", "status"), ("iters", "iters"))}
+    dec.close()
+    idx = np.sort(np.random.default_rng(2).choice(shots.B, size=1000, replace=False))
+    sub = {k: v[idx] for k, v in gpu.items()}
+    if prec == B.BSD_FP32:
+        base = dict(max_rounds=20, beam_width=64, initial_iters=40, iters_per_round=30, num_results=1,
+                    ms_scale=0.625, llr_clamp=1e4)
+        exp = oracle.Graph(prob, "f32").decode_batch(shots.syndromes[idx], oracle.Params(**base), nthreads=16)
+        exp = {k: exp[k] for k in ("corrections", "obs", "status", "iters")}
+    else:
+        exp, _ = _expected(prob, params, shots.syndromes[idx], prec)
+    _check(sub, exp, prob.K)

@@ -153,3 +153,42 @@ def test_unrolled_errors():
                                C.c_void_p(tr.work.data_ptr()), tr.work.numel() - 1, None)
     assert ei.value.code == B.BSD_ERR_INVALID_ARG
     tr.close()
+
+
+def test_full_size_training_batch():
+    """The benchmark's training configuration (phenomenological DEM, B = 4096,
+    T = 20, k = 5): posteriors of 12 sampled shots against the float64
+    reference run on those shots alone, the gradient's additivity over two
+    half batches (each term is a sum over shots), and central differences of
+    the loss along the gradient."""
+    prob = W.bb_phenomenological(12, 6, 12, 2e-3, 2e-3)
+    Bn, T, k = 4096, 20, 5
+    s_t, e_t, sh = G.batch_tensors(prob, Bn, W.shot_seed("unrolled_full_size", 0))
+    w = torch.from_numpy(_weights(prob, T, 21)).cuda()
+    tr = G.UnrolledTrainer(prob, Bn, T, k)
+    llr = torch.empty((T, Bn, prob.N), dtype=torch.float32, device="cuda")
+    tr.forward(w, s_t, e_t, llr)
+    g = tr.backward(w, torch.ones(1, device="cuda"))
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(4).choice(Bn, size=12, replace=False))
+    s = W.unpack_bits(sh.syndromes[idx], prob.M)
+    e = W.unpack_bits(sh.errors[idx], prob.N)
+    _, _, _, rtraj = U.unrolled_grad(U.Tables(prob), s, e, w.cpu().numpy().astype(np.float64))
+    got = llr[:, torch.as_tensor(idx, device="cuda"), :].cpu().numpy()
+    assert np.all(np.abs(got - rtraj) <= 1e-4 * np.maximum(1.0, np.abs(rtraj)))
+    # additivity: the full-batch gradient is the mean of the two half-batch gradients
+    half = []
+    for lo in (0, Bn // 2):
+        th = G.UnrolledTrainer(prob, Bn // 2, T, k)
+        th.forward(w, s_t[lo:lo + Bn // 2].contiguous(), e_t[lo:lo + Bn // 2].contiguous())
+        half.append(th.backward(w, torch.ones(1, device="cuda")))
+        th.close()
+    gh = 0.5 * (half[0] + half[1])
+    assert float((g - gh).abs().max()) <= 1e-5 * float(g.abs().max())
+    # central differences along the gradient
+    u = g / g.norm()
+    hstep = 1e-2
+    lp = float(tr.forward(w + hstep * u, s_t, e_t)[0])
+    lm = float(tr.forward(w - hstep * u, s_t, e_t)[0])
+    assert abs((lp - lm) / (2 * hstep) - float(g.norm())) <= 2e-2 * float(g.norm())
+    tr.close()
