@@ -285,8 +285,8 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
         grp.sync();
 
         // ---- error-node pass (Eqs. 2-4) and syndrome parity; each warp owns
-        // whole 32-column words of e^
-        for (int jb = 32 * grp.warp(); jb < g.N; jb += 32 * grp.nwarps()) {
+        // whole 32-column words of e^ (one column per lane)
+        auto column = [&](int jb) -> uint32_t {
             const int j = jb + lane;
             uint32_t ebit = 0;
             const bool act = (j < g.N) && !((st.mask[jb >> 5] >> lane) & 1u);
@@ -324,10 +324,6 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
                     }
                 }
                 const float lj = __ldg(g.lam + j);
-                float post = lj;                                  // Eq. 3
-#pragma unroll
-                for (int k = 0; k < DV; ++k)
-                    if (k < deg) post = __fadd_rn(post, v[k]);
 #pragma unroll
                 for (int k = 0; k < DV; ++k) {                    // Eq. 2: leave d_i out
                     if (k < deg) {
@@ -338,6 +334,10 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
                         S::st(E, ed[k], fminf(fmaxf(acc, -L), L));
                     }
                 }
+                float post = lj;                                  // Eq. 3
+#pragma unroll
+                for (int k = 0; k < DV; ++k)
+                    if (k < deg) post = __fadd_rn(post, v[k]);
                 st.sumllr[j] = __fadd_rn(st.sumllr[j], post);
                 if (post_out != nullptr && t == max_iters) post_out[j] = post;
                 ebit = (post <= 0.f) ? 1u : 0u;                   // Eq. 4
@@ -348,7 +348,10 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
                     }
                 }
             }
-            const uint32_t bal = __ballot_sync(FULLMASK, ebit);
+            return ebit;
+        };
+        for (int jb = 32 * grp.warp(); jb < g.N; jb += 32 * grp.nwarps()) {
+            const uint32_t bal = __ballot_sync(FULLMASK, column(jb));
             if (lane == 0) st.ehat[jb >> 5] = bal;
         }
         grp.sync();
@@ -450,7 +453,9 @@ __device__ inline void argmin_and_score(const G& grp, const DevGraph& g, const W
 template <int DV, int P, bool W = false, class G = WarpGroup>
 struct GenericEngine {
     using Grp = G;
-    static constexpr int kMinBlocks = 1;
+    // blocks of up to 16 warps: for column degrees up to 6 the kernels fit in
+    // 64 registers, so two such blocks stay resident on an SM
+    static constexpr int kMinBlocks = (G::kBlock && DV <= 6) ? 2 : 1;
     static constexpr int kMaxThreads = G::kBlock ? 512 : 256;
     static constexpr int kPrec = P;
     static constexpr bool kPriorStart = true;   // runs from E(0) need no copy of E(0)
