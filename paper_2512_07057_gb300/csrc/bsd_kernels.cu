@@ -538,6 +538,10 @@ struct SmallEngine {
             const int j = lane + 32 * c;
             if (j >= g.N || ((st.mask[c] >> lane) & 1u)) mb |= 1u << c;
         }
+        // s'_i of the lane's rows in bit 31 (s' is fixed for the whole run)
+        uint32_t sb[RPL];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) sb[r] = (lane + 32 * r < g.M) ? ((st.sp[r] >> lane) & 1u) << 31 : 0u;
         int iters = 0;
         int ok = 0;
         for (int t = 1; t <= max_iters; ++t) {
@@ -577,25 +581,44 @@ struct SmallEngine {
                         x[2 * h] = x2.x;
                         x[2 * h + 1] = x2.y;
                     }
-                    // the two smallest magnitudes m1 <= m2 (m2 = m1 when the
-                    // minimum is attained twice), starting from L_MAX (R3)
-                    float m1 = L, m2 = L;
+                    // the two smallest magnitudes m1 <= m2 of min(|x|, L_MAX)
+                    // (R3; m2 = m1 when the minimum is attained twice): the
+                    // pairs (lo, hi) of edges 2h, 2h + 1; m1 and the runner-up
+                    // among the lo; m2 = min(runner-up, every hi), since a hi
+                    // is never below its own lo
+                    float lo[RD / 2], hi[RD / 2];
+#pragma unroll
+                    for (int h = 0; h < RD / 2; ++h) {
+                        lo[h] = fminf(fabsf(x[2 * h]), fabsf(x[2 * h + 1]));
+                        hi[h] = fmaxf(fabsf(x[2 * h]), fabsf(x[2 * h + 1]));
+                    }
+                    float m1 = fminf(lo[0], lo[1]), m2 = fmaxf(lo[0], lo[1]);
+#pragma unroll
+                    for (int h = 2; h < RD / 2; ++h) {
+                        m2 = fminf(m2, fmaxf(m1, lo[h]));
+                        m1 = fminf(m1, lo[h]);
+                    }
+                    float hm = hi[0];
+#pragma unroll
+                    for (int h = 1; h < RD / 2; ++h) hm = fminf(hm, hi[h]);
+                    m2 = fminf(fminf(m2, hm), L);
+                    m1 = fminf(m1, L);
                     // sign parity in bit 31: a stored message is never -0 (it is
                     // a clamped sum of terms that starts at Lambda_j or the
                     // sentinel), so its sign bit is exactly x < 0
-                    uint32_t nb = ((st.sp[i >> 5] >> (i & 31)) & 1u) << 31;
+                    uint32_t nb = sb[r];
 #pragma unroll
-                    for (int k = 0; k < RD; ++k) {
-                        const float a = fabsf(x[k]);
-                        m2 = fminf(m2, fmaxf(m1, a));
-                        m1 = fminf(m1, a);
-                        nb ^= __float_as_uint(x[k]);
-                    }
+                    for (int k = 0; k < RD; ++k) nb ^= __float_as_uint(x[k]);
                     nb &= 0x80000000u;
                     // D_{i->j} for every edge of the row: alpha * (minimum over the
                     // others), which is m2 for an edge holding the minimum and m1
-                    // otherwise; sign = s'_i xor parity of the others' signs
-                    const float d1 = __fmul_rn(alpha, m1), d2 = __fmul_rn(alpha, m2);
+                    // otherwise; sign = s'_i xor parity of all signs xor the
+                    // edge's own sign.  The row's part of the sign is applied to
+                    // both candidates once (negating a factor negates the
+                    // product exactly), the edge's own per edge.
+                    const float m1s = __uint_as_float(__float_as_uint(m1) | nb);
+                    const float m2s = __uint_as_float(__float_as_uint(m2) | nb);
+                    const float d1 = W ? m1s : __fmul_rn(alpha, m1s), d2 = W ? m2s : __fmul_rn(alpha, m2s);
                     float2* dr = reinterpret_cast<float2*>(st.D + RD * i);
 #pragma unroll
                     for (int h = 0; h < RD / 2; ++h) {
@@ -605,9 +628,9 @@ struct SmallEngine {
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             const int k = 2 * h + u;
-                            const float d = W ? __fmul_rn(u ? w2.y : w2.x, (fabsf(x[k]) == m1) ? m2 : m1)
-                                              : ((fabsf(x[k]) == m1) ? d2 : d1);
-                            dd[u] = __uint_as_float(__float_as_uint(d) ^ ((nb ^ __float_as_uint(x[k])) & 0x80000000u));
+                            const float sel = (fabsf(x[k]) == m1) ? d2 : d1;
+                            const float d = W ? __fmul_rn(u ? w2.y : w2.x, sel) : sel;
+                            dd[u] = __uint_as_float(__float_as_uint(d) ^ (__float_as_uint(x[k]) & 0x80000000u));
                         }
                         dr[h] = make_float2(dd[0], dd[1]);
                     }
@@ -617,8 +640,8 @@ struct SmallEngine {
             // ---- error-node pass (Eqs. 2-4)
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
-                // every column is computed; a masked column stores its sentinel
-                // +L_MAX back and a column beyond N stores nothing
+                // every column is computed; a masked column or one beyond N
+                // stores nothing
                 const bool inr = (lane + 32 * c) < g.N;
                 const bool act = !((mb >> c) & 1u);
                 float v[3];
@@ -633,14 +656,15 @@ struct SmallEngine {
                 // are added in ascending order.  Messages are stored unclamped:
                 // the detector pass reads min(|E|, L_MAX) and the sign, which is
                 // what a clamp at store time (R4) would leave, and |E| stays below
-                // Lambda_j + 3 alpha L_MAX
+                // Lambda_j + 3 alpha L_MAX.  A masked column stores nothing: its
+                // messages hold the sentinel +L_MAX from the moment it was fixed.
                 const float e0 = __fadd_rn(__fadd_rn(l, fminf(v[1], v[2])), fmaxf(v[1], v[2]));
                 const float e1 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[2])), fmaxf(v[0], v[2]));
                 const float e2 = __fadd_rn(__fadd_rn(l, fminf(v[0], v[1])), fmaxf(v[0], v[1]));
-                if (inr) {
-                    S::st(E, ed[0], act ? e0 : L);
-                    S::st(E, ed[1], act ? e1 : L);
-                    S::st(E, ed[2], act ? e2 : L);
+                if (act) {
+                    S::st(E, ed[0], e0);
+                    S::st(E, ed[1], e1);
+                    S::st(E, ed[2], e2);
                 }
                 // Eq. 3 in ascending order: smallest, median, largest
                 const float lo01 = fminf(v[0], v[1]), hi01 = fmaxf(v[0], v[1]);
