@@ -364,6 +364,24 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
             D0[e] = d;
         }
     }
+    // the generic engines' column table: (edge, row) of the k-th edge of column
+    // j at [k][j], (-1, -1) past the column's degree, for degree bounds 3 and 6
+    const int colK = max_col <= 3 ? 3 : max_col <= 6 ? 6 : 0;
+    std::vector<int2> colER((size_t)colK * Npad, make_int2(-1, -1));
+    for (int j = 0; j < N && colK > 0; ++j)
+        for (int k = 0; k < col_ptr[j + 1] - col_ptr[j]; ++k)
+            colER[(size_t)k * Npad + j] = make_int2(col_edge[col_ptr[j] + k], col_row[col_ptr[j] + k]);
+    // E(0) of column j in the storage format (every edge of the column holds it)
+    std::vector<unsigned char> lamEc_st((size_t)Npad * msg_bytes, 0);
+    for (int j = 0; j < N; ++j) {
+        const int e = col_ptr[j + 1] > col_ptr[j] ? col_edge[col_ptr[j]] : -1;
+        if (e >= 0) std::memcpy(&lamEc_st[(size_t)j * msg_bytes], &lamE_st[(size_t)e * msg_bytes], msg_bytes);
+        else {
+            // a column with no edge: its E(0) is never read, but keep the value
+            const float v = store_round(std::fmin(std::fmax(lam[j], -L), L));
+            if (prec == BSD_FP32) std::memcpy(&lamEc_st[(size_t)j * 4], &v, 4);
+        }
+    }
     std::vector<uint32_t> hcol((size_t)N * WM, 0u), acol((size_t)N * (WK > 0 ? WK : 1), 0u);
     for (int i = 0; i < M; ++i)
         for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e)
@@ -384,6 +402,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     gb += align256(sizeof(long long) * N);
     gb += align256(sizeof(float4) * M);
     gb += align256(sizeof(float) * Epad);
+    gb += align256(sizeof(int2) * colER.size());
+    gb += align256(lamEc_st.size());
     if (CUDA_FAILED(cudaMalloc(&dec->graph_mem, gb))) { bsd_destroy(dec); return BSD_ERR_OOM; }
     dec->graph_bytes = gb;
     char* p = (char*)dec->graph_mem;
@@ -398,6 +418,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     long long* d_lamq = carve<long long>(p, N);
     float4* d_rs0 = carve<float4>(p, M);
     float* d_D0 = carve<float>(p, Epad);
+    int2* d_colER = colER.empty() ? nullptr : carve<int2>(p, colER.size());
+    unsigned char* d_lamEc = carve<unsigned char>(p, lamEc_st.size());
     bool ok = !CUDA_FAILED(cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_edge, col_edge.data(), sizeof(int) * E, cudaMemcpyHostToDevice)) &&
@@ -408,7 +430,10 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
               !CUDA_FAILED(cudaMemcpy(d_acol, acol.data(), sizeof(uint32_t) * acol.size(), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_lamq, lamq.data(), sizeof(long long) * N, cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_rs0, rs0.data(), sizeof(float4) * M, cudaMemcpyHostToDevice)) &&
-              !CUDA_FAILED(cudaMemcpy(d_D0, D0.data(), sizeof(float) * Epad, cudaMemcpyHostToDevice));
+              !CUDA_FAILED(cudaMemcpy(d_D0, D0.data(), sizeof(float) * Epad, cudaMemcpyHostToDevice)) &&
+              (colER.empty() ||
+               !CUDA_FAILED(cudaMemcpy(d_colER, colER.data(), sizeof(int2) * colER.size(), cudaMemcpyHostToDevice))) &&
+              !CUDA_FAILED(cudaMemcpy(d_lamEc, lamEc_st.data(), lamEc_st.size(), cudaMemcpyHostToDevice));
     if (!ok) { bsd_destroy(dec); return BSD_ERR_CUDA; }
 
     DevGraph& g = dec->g;
@@ -420,6 +445,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.all_lam_pos = all_pos;
     g.row_ptr = d_row_ptr; g.col_ptr = d_col_ptr; g.col_edge = d_col_edge; g.col_row = d_col_row;
     g.lam = d_lam; g.lamE = d_lamE; g.hcol = d_hcol; g.acol = d_acol; g.lamq = d_lamq; g.rs0 = d_rs0; g.D0 = d_D0;
+    g.colER = d_colER; g.colK = colK; g.lamEc = d_lamEc;
 
     DecCfg& cfg = dec->cfg;
     cfg.max_rounds = params->max_rounds;

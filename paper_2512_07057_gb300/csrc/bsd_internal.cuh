@@ -12,6 +12,8 @@
 //   lamq[N]               Lambda_j on the 2^-16 fixed-point grid (weights)
 //   rs0[M]                the detector records of E(0) (a seed run's first check pass, up to the syndrome)
 //   D0[Epad]              the check messages of E(0) with the scale alpha, before the syndrome sign
+//   colER[colK][Npad]     (edge, row) of the k-th edge of column j, (-1, -1) past its degree
+//   lamEc[Npad]           clamp(Lambda_j) in the storage format (E(0) of every edge of column j)
 //
 // Workspace (one decoder):
 //   seed store, S entries: the snapshot (E, s', mask, vals, e^, record) of
@@ -54,6 +56,9 @@ struct DevGraph {
     const long long* lamq;
     const float4* rs0;     // [M] detector records of E(0): (min1, min2, argmin edge, parity of negatives)
     const float* D0;       // [Epad] check messages of E(0) with scale alpha, before the syndrome sign
+    const int2* colER;     // [colK][Npad] (edge, row) of edge k of column j, (-1, -1) past its degree
+    int colK;              // 3 or 6 (the generic engines' degree bound), 0 when colER is absent
+    const void* lamEc;     // [Npad] E(0) of column j (clamp(Lambda_j)) in the storage format
 };
 
 struct DecCfg {

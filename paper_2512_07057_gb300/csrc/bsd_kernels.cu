@@ -259,7 +259,6 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
         // the sign parity, and E(0) itself (clamp(Lambda), the same on every
         // edge of a column) is read from the graph, not from the candidate
         const bool prior = from_prior && t == 1;
-        const T* const Ein = prior ? reinterpret_cast<const T*>(g.lamE) : E;
         if (prior) {
             for (int i = grp.rank(); i < g.M; i += grp.size()) {
                 const float4 r = __ldg(g.rs0 + i);
@@ -291,19 +290,35 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
             uint32_t ebit = 0;
             const bool act = (j < g.N) && !((st.mask[jb >> 5] >> lane) & 1u);
             if (act) {
-                const int kb = __ldg(g.col_ptr + j);
-                const int deg = __ldg(g.col_ptr + j + 1) - kb;
+                // the column's edges: from the padded (edge, row) table for
+                // degree bounds up to 6 (one coalesced load per slot), else
+                // from the column lists
+                int kb = 0, deg = 0;
+                if constexpr (DV > 6) {
+                    kb = __ldg(g.col_ptr + j);
+                    deg = __ldg(g.col_ptr + j + 1) - kb;
+                }
+                // E(0) is the same on every edge of a column: one load for its sign
+                const bool x0neg = prior && S::ld(reinterpret_cast<const T*>(g.lamEc), j) < 0.f;
                 float v[DV];
                 int ed[DV];
 #pragma unroll
                 for (int k = 0; k < DV; ++k) {
-                    if (k < deg) {
-                        const int e = __ldg(g.col_edge + kb + k);
-                        const int r = __ldg(g.col_row + kb + k);
+                    int e = -1, r = 0;
+                    if constexpr (DV <= 6) {
+                        const int2 er = __ldg(g.colER + (size_t)k * g.Npad + j);
+                        e = er.x;
+                        r = er.y;
+                        deg += (e >= 0) ? 1 : 0;
+                    } else if (k < deg) {
+                        e = __ldg(g.col_edge + kb + k);
+                        r = __ldg(g.col_row + kb + k);
+                    }
+                    if (e >= 0) {
                         const float4 s4 = st.rs[r];
-                        const float xo = S::ld(Ein, e);
+                        const bool xneg = prior ? x0neg : (S::ld(E, e) < 0.f);
                         const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
-                        const uint32_t sg = __float_as_uint(s4.w) ^ ((xo < 0.f) ? 1u : 0u);
+                        const uint32_t sg = __float_as_uint(s4.w) ^ (xneg ? 1u : 0u);
                         const float d = __fmul_rn(W ? __ldg(wt + e) : alpha, m);
                         v[k] = sg ? -d : d;
                         ed[k] = e;
@@ -338,12 +353,13 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
 #pragma unroll
                 for (int k = 0; k < DV; ++k)
                     if (k < deg) post = __fadd_rn(post, v[k]);
-                st.sumllr[j] = __fadd_rn(st.sumllr[j], post);
+                // a run from E(0) starts its sums here (0 + post, as a sum from zero)
+                st.sumllr[j] = __fadd_rn(prior ? 0.f : st.sumllr[j], post);
                 if (post_out != nullptr && t == max_iters) post_out[j] = post;
                 ebit = (post <= 0.f) ? 1u : 0u;                   // Eq. 4
                 if (ebit) {
                     for (int k = 0; k < deg; ++k) {
-                        const int r = __ldg(g.col_row + kb + k);
+                        const int r = DV <= 6 ? __ldg(g.colER + (size_t)k * g.Npad + j).y : __ldg(g.col_row + kb + k);
                         atomicXor(&st.par[r >> 5], 1u << (r & 31));
                     }
                 }
@@ -454,11 +470,13 @@ template <int DV, int P, bool W = false, class G = WarpGroup>
 struct GenericEngine {
     using Grp = G;
     // blocks of up to 16 warps: for column degrees up to 6 the kernels fit in
-    // 64 registers, so two such blocks stay resident on an SM
-    static constexpr int kMinBlocks = (G::kBlock && DV <= 6) ? 2 : 1;
+    // 64 registers, so two such blocks stay resident on an SM; one warp per
+    // candidate: 80 registers, three 8-warp blocks
+    static constexpr int kMinBlocks = (DV <= 6) ? (G::kBlock ? 2 : 3) : 1;
     static constexpr int kMaxThreads = G::kBlock ? 512 : 256;
     static constexpr int kPrec = P;
     static constexpr bool kPriorStart = true;   // runs from E(0) need no copy of E(0)
+    static constexpr bool kPriorSetsSums = true;  // ... nor cleared sums: their first iteration sets them
     G grp;
     __device__ void load_graph(const DevGraph&) {}
     __device__ void clear_sums(const DevGraph& g, const WarpState& st)
@@ -498,6 +516,7 @@ struct SmallEngine {
     static constexpr int kMaxThreads = 256;
     static constexpr int kPrec = P;
     static constexpr bool kPriorStart = !W;  // unweighted runs from E(0) start from the table D0
+    static constexpr bool kPriorSetsSums = false;
     WarpGroup grp;
     using S = Store<P>;
     uint32_t ci[CPL][3];   // (CSR edge id << 16) | row, for column lane + 32 c
@@ -723,7 +742,9 @@ struct SmallEngine {
 };
 
 // write one shot's outputs: e^, A e^, status, iteration count
-template <class G = WarpGroup>
+// (kSparse: A e^ from the set bits of e^, for the seed kernel, where e^ is
+// long and sparse)
+template <class G = WarpGroup, bool kSparse = false>
 __device__ void finalize_shot(const DevGraph& g, const Outputs& out, long long gb, const uint32_t* ehat,
                               uint32_t status, unsigned long long iters, const G& grp = G{})
 {
@@ -732,8 +753,20 @@ __device__ void finalize_shot(const DevGraph& g, const Outputs& out, long long g
     if (out.obs != nullptr) {
         for (int wq = 0; wq < g.WK; ++wq) {
             uint32_t acc = 0;
-            for (int j = grp.rank(); j < g.N; j += grp.size())
-                if ((ehat[j >> 5] >> (j & 31)) & 1u) acc ^= __ldg(g.acol + (size_t)j * g.WK + wq);
+            if constexpr (kSparse) {
+                // over the set bits of e^ only (bits past N are never set)
+                for (int q = grp.rank(); q < g.WN; q += grp.size()) {
+                    uint32_t bits = ehat[q];
+                    while (bits != 0u) {
+                        const int b = __ffs(bits) - 1;
+                        bits &= bits - 1u;
+                        acc ^= __ldg(g.acol + (size_t)(32 * q + b) * g.WK + wq);
+                    }
+                }
+            } else {
+                for (int j = grp.rank(); j < g.N; j += grp.size())
+                    if ((ehat[j >> 5] >> (j & 31)) & 1u) acc ^= __ldg(g.acol + (size_t)j * g.WK + wq);
+            }
             acc = grp.xor_all(acc);
             if (grp.rank() == 0) out.obs[gb * g.WK + wq] = acc;
         }
@@ -910,19 +943,20 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
         // s = 0 with every Lambda_j > 0: D > 0 at t = 1, so e^(1) = 0 and the
         // seed converges after one iteration (exact, no BP needed)
         if (!grp.any(nz != 0u) && cfg.num_results == 1 && g.all_lam_pos) {
-            finalize_shot(g, dp->out, gb, st.ehat, ST_SEED, 1ull, grp);
+            finalize_shot<typename Eng::Grp, true>(g, dp->out, gb, st.ehat, ST_SEED, 1ull, grp);
             grp.sync();
             continue;
         }
         if (!Eng::kPriorStart) group_copy16(grp, st.E, g.lamE, snap_vec16(g));
-        eng.clear_sums(g, st);
+        if (!Eng::kPriorSetsSums) eng.clear_sums(g, st);
         grp.sync();
         int succ = 0;
         const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr, true);
         if (grp.rank() == 0) atomicAdd(&w.stats[0], (unsigned long long)it);
         grp.sync();
         if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
-            finalize_shot(g, dp->out, gb, st.ehat, succ ? ST_SEED : ST_FAILED, (unsigned long long)it, grp);
+            finalize_shot<typename Eng::Grp, true>(g, dp->out, gb, st.ehat, succ ? ST_SEED : ST_FAILED,
+                                                   (unsigned long long)it, grp);
             grp.sync();
             continue;
         }
@@ -1350,7 +1384,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_bp_llr(De
         for (int q = grp.rank(); q < g.WM; q += grp.size()) st.sp[q] = synd[b * g.WM + q];
         for (int q = grp.rank(); q < g.WN; q += grp.size()) { st.mask[q] = 0u; st.vals[q] = 0u; }
         if (!Eng::kPriorStart) group_copy16(grp, st.E, g.lamE, snap_vec16(g));
-        eng.clear_sums(g, st);
+        if (!Eng::kPriorSetsSums) eng.clear_sums(g, st);
         grp.sync();
         int succ;
         eng.run(g, cfg, st, T, false, &succ, llr + b * g.N, true);
@@ -1443,6 +1477,7 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, int group_warp
     else if (g.max_col_deg <= 6) gkind = 1;
     else if (g.max_col_deg <= 16) gkind = 2;
     else return -5;
+    if (gkind < 2 && g.colK != (gkind == 0 ? 3 : 6)) return -5;   // the column table matches the engine
     int skind = -1;                                          // small engine kind, if the code has its layout
     if (small_fits(g, 3, 2)) skind = 3;
     else if (small_fits(g, 5, 3)) skind = 4;
