@@ -561,12 +561,13 @@ struct SmallEngine {
         uint32_t sb[RPL];
 #pragma unroll
         for (int r = 0; r < RPL; ++r) sb[r] = (lane + 32 * r < g.M) ? ((st.sp[r] >> lane) & 1u) << 31 : 0u;
+        const uint32_t spw = lane < RPL ? st.sp[lane] : 0u;
         int iters = 0;
         int ok = 0;
         for (int t = 1; t <= max_iters; ++t) {
             unsigned long long ab_key = 0ull;
             if (ab.key != nullptr && lane == 0) ab_key = *((volatile const unsigned long long*)ab.key);
-            for (int q = lane; q < g.WM; q += 32) st.par[q] = st.sp[q];
+            if (lane < RPL) st.par[lane] = spw;           // the code's M bits fill RPL words
             // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
             const float* wt = W ? cfg.weights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
             // ---- detector pass (Eq. 1); a run from E(0) takes its first check
@@ -706,7 +707,7 @@ struct SmallEngine {
             }
             __syncwarp();
             uint32_t nz = 0;
-            for (int q = lane; q < g.WM; q += 32) nz |= st.par[q];
+            if (lane < RPL) nz = st.par[lane];
             ok = !__any_sync(FULLMASK, nz != 0u);
             iters = t;
             __syncwarp();
