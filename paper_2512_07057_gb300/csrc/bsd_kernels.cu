@@ -233,9 +233,9 @@ __device__ inline unsigned long long fixq(float x)
 // Runs up to max_iters flooding iterations from the messages in st.E.  With
 // stop = true it returns at the first t with H e^(t) = s' (Alg. 2).  On return
 // st.ehat holds e^(t) of the last iteration (masked positions 0), st.sumllr
-// holds the sum over the iterations run of Lambda_j(t).  If post_out is not
-// null, Lambda_j(max_iters) is written there.
-template <int DV, int P, bool W, class G>
+// holds the sum over the iterations run of Lambda_j(t).  With kPostOut,
+// Lambda_j(max_iters) is written to post_out.
+template <int DV, int P, bool W, bool kPostOut, class G>
 __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
                           bool stop, int* success, float* post_out, bool from_prior, const AbortCheck& ab)
 {
@@ -355,7 +355,7 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
                     if (k < deg) post = __fadd_rn(post, v[k]);
                 // a run from E(0) starts its sums here (0 + post, as a sum from zero)
                 st.sumllr[j] = __fadd_rn(prior ? 0.f : st.sumllr[j], post);
-                if (post_out != nullptr && t == max_iters) post_out[j] = post;
+                if (kPostOut && t == max_iters) post_out[j] = post;
                 ebit = (post <= 0.f) ? 1u : 0u;                   // Eq. 4
                 if (ebit) {
                     for (int k = 0; k < deg; ++k) {
@@ -483,10 +483,11 @@ struct GenericEngine {
     {
         for (int j = grp.rank(); j < g.N; j += grp.size()) st.sumllr[j] = 0.f;
     }
+    template <bool kPostOut = false>
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
                        int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
     {
-        return bp_iterate<DV, P, W>(grp, g, cfg, st, max_iters, stop, success, post_out, from_prior, ab);
+        return bp_iterate<DV, P, W, kPostOut>(grp, g, cfg, st, max_iters, stop, success, post_out, from_prior, ab);
     }
     __device__ void argmin_score(const DevGraph& g, const WarpState& st, double guard, int* np, long long* S,
                                  int* tie)
@@ -544,6 +545,7 @@ struct SmallEngine {
 #pragma unroll
         for (int c = 0; c < CPL; ++c) sum[c] = 0.f;
     }
+    template <bool kPostOut = false>
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
                        int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
     {
@@ -693,7 +695,7 @@ struct SmallEngine {
                 const float a1 = fmaxf(lo01, fminf(hi01, v[2]));
                 const float post = __fadd_rn(__fadd_rn(__fadd_rn(l, a0), a1), a2);
                 sum[c] = __fadd_rn(sum[c], post);           // unused for masked columns
-                if (post_out != nullptr && t == max_iters && inr) post_out[lane + 32 * c] = post;
+                if (kPostOut && t == max_iters && inr) post_out[lane + 32 * c] = post;
                 const uint32_t ebit = (act && post <= 0.f) ? 1u : 0u;                // Eq. 4
                 if (ebit) {
 #pragma unroll
@@ -708,9 +710,10 @@ struct SmallEngine {
             __syncwarp();
             uint32_t nz = 0;
             if (lane < RPL) nz = st.par[lane];
+            // (a lane reads and, next iteration, resets only its own word of
+            // par; the other lanes' atomics come after the detector pass sync)
             ok = !__any_sync(FULLMASK, nz != 0u);
             iters = t;
-            __syncwarp();
             if (ok && stop) break;
             if (ab.key != nullptr && __any_sync(FULLMASK, lane == 0 && ab.hit(ab_key))) { ok = 0; break; }
         }
@@ -1388,7 +1391,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_bp_llr(De
         if (!Eng::kPriorSetsSums) eng.clear_sums(g, st);
         grp.sync();
         int succ;
-        eng.run(g, cfg, st, T, false, &succ, llr + b * g.N, true);
+        eng.template run<true>(g, cfg, st, T, false, &succ, llr + b * g.N, true);
         grp.sync();
         if (sum_llr != nullptr) eng.write_sums(g, st, sum_llr + b * g.N);
         grp.sync();
