@@ -385,13 +385,17 @@ def run_reference(args, rank: int):
 def alu_roofline(prof, E: int, dev: int, traffic_case: str):
     """Roofline of the dominant BP kernel from per-kernel event times.
 
-    Algorithmic lane operations of a launch = OPS_PER_UPDATE x the BP
-    iterations it executed (counted on the device) x E; the peak is the
-    lane-operation rate of the chip at its maximum SM clock."""
+    Algorithmic lane operations of a launch = OPS_PER_UPDATE x (the full BP
+    iterations it executed x E + the message updates of first-iteration
+    screens, both counted on the device); the peak is the lane-operation
+    rate of the chip at its maximum SM clock."""
     import torch
     ms_kind = np.sum([pr["ms"] for pr in prof], axis=0)
     launches = np.sum([pr["launches"] for pr in prof], axis=0)
     exec_iters = np.sum([pr["exec_iters"] for pr in prof], axis=0).astype(np.float64)
+    # message updates of seed runs that ended in their first-iteration screen
+    # (the columns next to flipped detectors; counted apart from full iterations)
+    screen = float(sum(pr.get("screen_updates", 0) for pr in prof))
     names = ("k_seed", "k_round", "k_select")
     pk, pk_kind = peaks()
     sm_mhz_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -400,7 +404,7 @@ def alu_roofline(prof, E: int, dev: int, traffic_case: str):
     # the selection kernel runs no BP, so its share is reported but it is never the roofline kernel
     dom = int(np.argmax(ms_kind[:2]))
     dom_iters = exec_iters[dom]
-    dom_updates_per_launch = dom_iters * E / max(1, launches[dom])
+    dom_updates_per_launch = (dom_iters * E + (screen if dom == 0 else 0.0)) / max(1, launches[dom])
     dom_ms_per_launch = ms_kind[dom] / max(1, launches[dom])
     achieved = OPS_PER_UPDATE * dom_updates_per_launch / (dom_ms_per_launch * 1e-3) / 1e12
     roofline = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": alu_peak_tops,
@@ -408,6 +412,9 @@ def alu_roofline(prof, E: int, dev: int, traffic_case: str):
                 "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz (sm_max_mhz {pk_kind})",
                 "ops_per_msg_update": OPS_PER_UPDATE,
                 "msg_updates_per_launch": dom_updates_per_launch, "launch_ms": dom_ms_per_launch,
+                "msg_updates_counted": "full BP iterations x E, plus the edges of first-iteration screens "
+                                       "(seed kernel)",
+                "screen_msg_updates_per_launch": (screen / max(1, launches[0])) if dom == 0 else 0.0,
                 "kernel_share": float(ms_kind[dom] / max(ms_kind.sum(), 1e-9)),
                 "measured_in": "second timed region: same steps, each kernel launched alone between CUDA events "
                                "on the decode stream"}

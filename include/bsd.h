@@ -216,15 +216,20 @@ int bsd_profile_enable(bsd_decoder *dec, int enable);
 /* Synchronise the decode stream, then return and reset, since the previous
  * read: the summed event-timed duration in milliseconds and the launch count
  * of each kernel kind (index 0: seed BP, 1: expand + masked BP of a round,
- * 2: per-shot selection of a round), and the BP iterations executed on the
+ * 2: per-shot selection of a round), the full BP iterations executed on the
  * device (index 0: seed candidates, 1: round candidates, counting children
- * evaluated after a shot's first success), and the number of kernels of this
+ * evaluated after a shot's first success), the number of kernels of this
  * library that ran for this decoder (counted on the device, with or without
- * timing enabled).  While timing is enabled the kernels are launched one by
- * one so that events can bracket them; otherwise each chunk runs as one CUDA
- * graph.  Any pointer may be NULL. */
+ * timing enabled), and the message updates done by first-iteration screens
+ * of seed runs (with every Lambda_j > 0, the scale alpha and one result, a
+ * seed run first forms e^(1) from the columns next to flipped detectors
+ * only, since no other column can flip at t = 1; a run that converges there
+ * ends after that partial iteration, which is counted here and not as a full
+ * iteration).  While timing is enabled the kernels are launched one by one so
+ * that events can bracket them; otherwise each chunk runs as one CUDA graph.
+ * Any pointer may be NULL. */
 int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2],
-                     uint64_t *kernel_launches);
+                     uint64_t *kernel_launches, uint64_t *screen_updates);
 
 /* Kernel kinds timed while timing is enabled: 0..2 as above, then the
  * unrolled decoder's passes (bsd_unrolled_forward / _backward): 3 check pass,

@@ -90,7 +90,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_unrolled_workspace.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
     lib.bsd_unrolled_forward.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, C.c_int64, P]
     lib.bsd_unrolled_backward.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, C.c_int64, P]
-    lib.bsd_profile_read.argtypes = [P, P, P, P, P]
+    lib.bsd_profile_read.argtypes = [P, P, P, P, P, P]
     lib.bsd_profile_read_kinds.argtypes = [P, P, P]
     lib.bsd_autotune.argtypes = [P, P, C.c_int64, P, P, C.c_int32, C.POINTER(C.c_int32)]
     lib.bsd_get_shape.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
@@ -207,15 +207,17 @@ def bsd_profile_enable(dec, enable: bool) -> None:
 
 
 def bsd_profile_read(dec) -> dict:
-    """Kernel times (ms) and launches per kind (seed, round, select), executed iterations."""
+    """Kernel times (ms) and launches per kind (seed, round, select), executed full iterations,
+    kernel launches, message updates of first-iteration screens."""
     import numpy as np
     ms = np.zeros(3, np.float64)
     ln = np.zeros(3, np.int64)
     it = np.zeros(2, np.uint64)
     kl = np.zeros(1, np.uint64)
+    su = np.zeros(1, np.uint64)
     p = lambda a: a.ctypes.data_as(C.c_void_p)
-    check(load().bsd_profile_read(dec, p(ms), p(ln), p(it), p(kl)), "bsd_profile_read")
-    return dict(ms=ms, launches=ln, exec_iters=it, kernel_launches=int(kl[0]))
+    check(load().bsd_profile_read(dec, p(ms), p(ln), p(it), p(kl), p(su)), "bsd_profile_read")
+    return dict(ms=ms, launches=ln, exec_iters=it, kernel_launches=int(kl[0]), screen_updates=int(su[0]))
 
 
 def bsd_profile_read_kinds(dec) -> dict:

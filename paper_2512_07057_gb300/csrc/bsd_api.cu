@@ -393,6 +393,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     // ---- device graph
     size_t gb = 0;
     gb += align256(sizeof(int) * (M + 1));
+    gb += align256(sizeof(int) * E);
     gb += align256(sizeof(int) * (N + 1));
     gb += 2 * align256(sizeof(int) * E);
     gb += align256(sizeof(float) * Npad);
@@ -408,6 +409,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     dec->graph_bytes = gb;
     char* p = (char*)dec->graph_mem;
     int* d_row_ptr = carve<int>(p, M + 1);
+    int* d_row_col = carve<int>(p, E);
     int* d_col_ptr = carve<int>(p, N + 1);
     int* d_col_edge = carve<int>(p, E);
     int* d_col_row = carve<int>(p, E);
@@ -421,6 +423,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     int2* d_colER = colER.empty() ? nullptr : carve<int2>(p, colER.size());
     unsigned char* d_lamEc = carve<unsigned char>(p, lamEc_st.size());
     bool ok = !CUDA_FAILED(cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice)) &&
+              !CUDA_FAILED(cudaMemcpy(d_row_col, H_col_idx, sizeof(int) * E, cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_edge, col_edge.data(), sizeof(int) * E, cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_row, col_row.data(), sizeof(int) * E, cudaMemcpyHostToDevice)) &&
@@ -443,7 +446,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.msg_bytes = msg_bytes; g.prec = prec;
     g.max_col_deg = max_col; g.max_row_deg = max_row;
     g.all_lam_pos = all_pos;
-    g.row_ptr = d_row_ptr; g.col_ptr = d_col_ptr; g.col_edge = d_col_edge; g.col_row = d_col_row;
+    g.row_ptr = d_row_ptr; g.row_col = d_row_col; g.col_ptr = d_col_ptr; g.col_edge = d_col_edge; g.col_row = d_col_row;
     g.lam = d_lam; g.lamE = d_lamE; g.hcol = d_hcol; g.acol = d_acol; g.lamq = d_lamq; g.rs0 = d_rs0; g.D0 = d_D0;
     g.colER = d_colER; g.colK = colK; g.lamEc = d_lamEc;
 
@@ -849,7 +852,7 @@ int bsd_profile_enable(bsd_decoder* dec, int enable)
 }
 
 int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2],
-                     uint64_t* kernel_launches)
+                     uint64_t* kernel_launches, uint64_t* screen_updates)
 {
     if (!dec) return BSD_ERR_INVALID_ARG;
     DeviceGuard dg(dec->device);
@@ -868,6 +871,7 @@ int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64
     }
     if (exec_iters) { exec_iters[0] = st[0]; exec_iters[1] = st[1]; }
     if (kernel_launches) *kernel_launches = st[2];
+    if (screen_updates) *screen_updates = st[3];
     return BSD_OK;
 }
 

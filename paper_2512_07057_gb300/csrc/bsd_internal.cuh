@@ -2,6 +2,7 @@
 //
 // Layout in HBM (all read-only graph tables are tiny and stay L1/L2 resident):
 //   row_ptr[M+1]          CSR of H; CSR edge e of row i lies in [row_ptr[i], row_ptr[i+1])
+//   row_col[E]            column of CSR edge e
 //   col_ptr[N+1]          per error node j, its edges in col_edge/col_row[col_ptr[j] ..)
 //   col_edge[E]           CSR edge id of each (column, k) pair, rows ascending
 //   col_row[E]            detector (row) of that edge
@@ -46,6 +47,7 @@ struct DevGraph {
     int all_lam_pos;       // every Lambda_j > 0 (all p_j < 1/2)
     int det_bytes;         // per-warp detector-side shared memory (set with the engine)
     const int* row_ptr;
+    const int* row_col;    // [E] column of CSR edge e
     const int* col_ptr;
     const int* col_edge;
     const int* col_row;
@@ -133,7 +135,8 @@ struct Work {
     Counters* ctr;
     int* round_ctr;        // 3 * (max_rounds + 2) ints after ctr
     RunDesc* desc;
-    unsigned long long* stats;   // [4]: executed BP iterations (seed, rounds), kernel launches; never reset by a chunk
+    unsigned long long* stats;   // [4]: executed full BP iterations (seed, rounds), kernel launches, message
+                                 // updates of first-iteration screens; never reset by a chunk
 };
 
 // true if e is an error; the error and the source line of the call are then

@@ -237,7 +237,8 @@ __device__ inline unsigned long long fixq(float x)
 // Lambda_j(max_iters) is written to post_out.
 template <int DV, int P, bool W, bool kPostOut, class G>
 __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
-                          bool stop, int* success, float* post_out, bool from_prior, const AbortCheck& ab)
+                          bool stop, int* success, float* post_out, bool from_prior, const AbortCheck& ab,
+                          unsigned* scr)
 {
     using S = Store<P>;
     using T = typename S::T;
@@ -283,6 +284,113 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
         }
         grp.sync();
 
+        // D_{i->j} of column j's edges in ascending order (padding +inf last),
+        // with their CSR edge ids; returns the column's degree
+        auto gather = [&](int j, float (&v)[DV], int (&ed)[DV]) -> int {
+            // the column's edges: from the padded (edge, row) table for degree
+            // bounds up to 6 (one coalesced load per slot), else from the
+            // column lists
+            int kb = 0, deg = 0;
+            if constexpr (DV > 6) {
+                kb = __ldg(g.col_ptr + j);
+                deg = __ldg(g.col_ptr + j + 1) - kb;
+            }
+            // E(0) is the same on every edge of a column: one load for its sign
+            const bool x0neg = prior && S::ld(reinterpret_cast<const T*>(g.lamEc), j) < 0.f;
+#pragma unroll
+            for (int k = 0; k < DV; ++k) {
+                int e = -1, r = 0;
+                if constexpr (DV <= 6) {
+                    const int2 er = __ldg(g.colER + (size_t)k * g.Npad + j);
+                    e = er.x;
+                    r = er.y;
+                    deg += (e >= 0) ? 1 : 0;
+                } else if (k < deg) {
+                    e = __ldg(g.col_edge + kb + k);
+                    r = __ldg(g.col_row + kb + k);
+                }
+                if (e >= 0) {
+                    const float4 s4 = st.rs[r];
+                    const bool xneg = prior ? x0neg : (S::ld(E, e) < 0.f);
+                    const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
+                    const uint32_t sg = __float_as_uint(s4.w) ^ (xneg ? 1u : 0u);
+                    const float d = __fmul_rn(W ? __ldg(wt + e) : alpha, m);
+                    v[k] = sg ? -d : d;
+                    ed[k] = e;
+                } else {
+                    v[k] = INFINITY;
+                    ed[k] = -1;
+                }
+            }
+            // ascending order of value (exchange network)
+#pragma unroll
+            for (int a = 0; a < DV; ++a) {
+#pragma unroll
+                for (int k = 0; k + 1 < DV - a; ++k) {
+                    if (v[k] > v[k + 1]) {
+                        const float tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv;
+                        const int te = ed[k]; ed[k] = ed[k + 1]; ed[k + 1] = te;
+                    }
+                }
+            }
+            return deg;
+        };
+        auto flip_rows = [&](int j, int deg) {                 // s' xor H e^: the rows of column j
+            for (int k = 0; k < deg; ++k) {
+                const int r = DV <= 6 ? __ldg(g.colER + (size_t)k * g.Npad + j).y
+                                      : __ldg(g.col_row + __ldg(g.col_ptr + j) + k);
+                atomicXor(&st.par[r >> 5], 1u << (r & 31));
+            }
+        };
+
+        // ---- screen of a seed run's first iteration: with every Lambda_j > 0
+        // and the scale alpha, D_{i->j}(1) > 0 on every edge whose detector is
+        // not flipped, so a column with no flipped detector keeps e^_j(1) = 0.
+        // e^(1) is formed from the columns next to flipped detectors alone (by
+        // the same operations as below); a run that converges there, most seed
+        // runs, ends without forming E(1) and sum_LLR, which a converged seed
+        // with one result never reads.
+        if (!W && !kPostOut && prior && stop && g.all_lam_pos && cfg.num_results == 1) {
+            uint32_t* seen = st.vals;                          // zero in a seed run
+            for (int q = grp.warp(); q < g.WM; q += grp.nwarps()) {
+                uint32_t word = st.sp[q];
+                while (word != 0u) {
+                    const int i = 32 * q + __ffs(word) - 1;
+                    word &= word - 1u;
+                    const int re = __ldg(g.row_ptr + i + 1);
+                    for (int e = __ldg(g.row_ptr + i) + lane; e < re; e += 32) {
+                        const int j = __ldg(g.row_col + e);
+                        const uint32_t bit = 1u << (j & 31);
+                        if (atomicOr(&seen[j >> 5], bit) & bit) continue;   // another flipped detector has it
+                        float v[DV];
+                        int ed[DV];
+                        const int deg = gather(j, v, ed);
+                        if (scr != nullptr) *scr += (unsigned)deg;
+                        float post = __ldg(g.lam + j);
+#pragma unroll
+                        for (int k = 0; k < DV; ++k)
+                            if (k < deg) post = __fadd_rn(post, v[k]);
+                        if (post <= 0.f) {
+                            atomicOr(&st.ehat[j >> 5], bit);
+                            flip_rows(j, deg);
+                        }
+                    }
+                }
+            }
+            grp.sync();
+            uint32_t nz = 0;
+            for (int q = grp.rank(); q < g.WM; q += grp.size()) nz |= st.par[q];
+            if (!grp.any(nz != 0u)) {
+                ok = 2;                                        // success, by the screen alone
+                iters = 1;
+                break;
+            }
+            // not converged: the full first iteration below forms e^ again
+            for (int q = grp.rank(); q < g.WN; q += grp.size()) seen[q] = 0u;
+            for (int q = grp.rank(); q < g.WM; q += grp.size()) st.par[q] = st.sp[q];
+            grp.sync();
+        }
+
         // ---- error-node pass (Eqs. 2-4) and syndrome parity; each warp owns
         // whole 32-column words of e^ (one column per lane)
         auto column = [&](int jb) -> uint32_t {
@@ -290,54 +398,9 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
             uint32_t ebit = 0;
             const bool act = (j < g.N) && !((st.mask[jb >> 5] >> lane) & 1u);
             if (act) {
-                // the column's edges: from the padded (edge, row) table for
-                // degree bounds up to 6 (one coalesced load per slot), else
-                // from the column lists
-                int kb = 0, deg = 0;
-                if constexpr (DV > 6) {
-                    kb = __ldg(g.col_ptr + j);
-                    deg = __ldg(g.col_ptr + j + 1) - kb;
-                }
-                // E(0) is the same on every edge of a column: one load for its sign
-                const bool x0neg = prior && S::ld(reinterpret_cast<const T*>(g.lamEc), j) < 0.f;
                 float v[DV];
                 int ed[DV];
-#pragma unroll
-                for (int k = 0; k < DV; ++k) {
-                    int e = -1, r = 0;
-                    if constexpr (DV <= 6) {
-                        const int2 er = __ldg(g.colER + (size_t)k * g.Npad + j);
-                        e = er.x;
-                        r = er.y;
-                        deg += (e >= 0) ? 1 : 0;
-                    } else if (k < deg) {
-                        e = __ldg(g.col_edge + kb + k);
-                        r = __ldg(g.col_row + kb + k);
-                    }
-                    if (e >= 0) {
-                        const float4 s4 = st.rs[r];
-                        const bool xneg = prior ? x0neg : (S::ld(E, e) < 0.f);
-                        const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
-                        const uint32_t sg = __float_as_uint(s4.w) ^ (xneg ? 1u : 0u);
-                        const float d = __fmul_rn(W ? __ldg(wt + e) : alpha, m);
-                        v[k] = sg ? -d : d;
-                        ed[k] = e;
-                    } else {
-                        v[k] = INFINITY;
-                        ed[k] = -1;
-                    }
-                }
-                // ascending order of value (exchange network; padding +inf stays last)
-#pragma unroll
-                for (int a = 0; a < DV; ++a) {
-#pragma unroll
-                    for (int k = 0; k + 1 < DV - a; ++k) {
-                        if (v[k] > v[k + 1]) {
-                            const float tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv;
-                            const int te = ed[k]; ed[k] = ed[k + 1]; ed[k + 1] = te;
-                        }
-                    }
-                }
+                const int deg = gather(j, v, ed);
                 const float lj = __ldg(g.lam + j);
 #pragma unroll
                 for (int k = 0; k < DV; ++k) {                    // Eq. 2: leave d_i out
@@ -357,12 +420,7 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
                 st.sumllr[j] = __fadd_rn(prior ? 0.f : st.sumllr[j], post);
                 if (kPostOut && t == max_iters) post_out[j] = post;
                 ebit = (post <= 0.f) ? 1u : 0u;                   // Eq. 4
-                if (ebit) {
-                    for (int k = 0; k < deg; ++k) {
-                        const int r = DV <= 6 ? __ldg(g.colER + (size_t)k * g.Npad + j).y : __ldg(g.col_row + kb + k);
-                        atomicXor(&st.par[r >> 5], 1u << (r & 31));
-                    }
-                }
+                if (ebit) flip_rows(j, deg);
             }
             return ebit;
         };
@@ -485,9 +543,11 @@ struct GenericEngine {
     }
     template <bool kPostOut = false>
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
-                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
+                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{},
+                       unsigned* scr = nullptr)
     {
-        return bp_iterate<DV, P, W, kPostOut>(grp, g, cfg, st, max_iters, stop, success, post_out, from_prior, ab);
+        return bp_iterate<DV, P, W, kPostOut>(grp, g, cfg, st, max_iters, stop, success, post_out, from_prior, ab,
+                                              scr);
     }
     __device__ void argmin_score(const DevGraph& g, const WarpState& st, double guard, int* np, long long* S,
                                  int* tie)
@@ -547,7 +607,8 @@ struct SmallEngine {
     }
     template <bool kPostOut = false>
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
-                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
+                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{},
+                       unsigned* = nullptr)
     {
         const int lane = threadIdx.x & 31;
         const float alpha = cfg.alpha;
@@ -929,6 +990,9 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
     const RunDesc* dp = w.desc;                  // read fields when needed (keeps registers free)
     count_launch(w);
     eng.load_graph(g);
+    unsigned long long seed_iters = 0;           // full BP iterations (group rank 0)
+    unsigned scr = 0;                            // message updates of first-iteration screens (this thread,
+                                                 // flushed before it could wrap)
     for (;;) {
         int b = 0;
         if (grp.rank() == 0) b = atomicAdd(&w.ctr->claim_seed, 1);
@@ -955,8 +1019,9 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
         if (!Eng::kPriorSetsSums) eng.clear_sums(g, st);
         grp.sync();
         int succ = 0;
-        const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr, true);
-        if (grp.rank() == 0) atomicAdd(&w.stats[0], (unsigned long long)it);
+        const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr, true, AbortCheck{}, &scr);
+        if (scr >= (1u << 30)) { atomicAdd(&w.stats[3], (unsigned long long)scr); scr = 0; }
+        if (grp.rank() == 0 && succ != 2) seed_iters += (unsigned long long)it;   // full iterations only
         grp.sync();
         if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
             finalize_shot<typename Eng::Grp, true>(g, dp->out, gb, st.ehat, succ ? ST_SEED : ST_FAILED,
@@ -987,6 +1052,11 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
         }
         grp.sync();
     }
+    if (grp.rank() == 0 && seed_iters != 0ull) atomicAdd(&w.stats[0], seed_iters);
+    unsigned long long ws = scr;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(FULLMASK, ws, o);
+    if ((threadIdx.x & 31) == 0 && ws != 0ull) atomicAdd(&w.stats[3], ws);
 }
 
 // ----------------------------------------------------------------------------

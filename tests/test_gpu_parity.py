@@ -159,6 +159,55 @@ def test_irregular_random_codes(seed):
     _check_workload(prob, params, shots, check_f64=False)
 
 
+@pytest.mark.parametrize("gw", [1, 8])
+def test_priors_above_one_half(gw):
+    """Some p_j above 1/2 (Lambda_j < 0): the zero-syndrome shortcut and the
+    first-iteration screen of seed runs both rest on every Lambda_j > 0 and
+    must stay off; the outputs equal the oracle's bit for bit, on a random
+    code (one warp or a block of 8 per candidate) and including all-zero
+    syndromes."""
+    rng = np.random.default_rng(11)
+    prob = W.random_ldpc(40, 80, 3, 0.05, 21, K=3)
+    prob.priors = rng.uniform(0.01, 0.15, size=prob.N)
+    prob.priors[rng.choice(prob.N, size=6, replace=False)] = rng.uniform(0.55, 0.7, size=6)
+    shots = W.sample_shots(prob, 2_000, "above_half")
+    synd = shots.syndromes.copy()
+    synd[:50] = 0
+    params = D.make_params(max_rounds=5, beam_width=4, initial_iters=15, iters_per_round=8, ms_scale=0.625,
+                           group_warps=gw)
+    gpu = _gpu_decode(prob, params, synd)
+    ref32 = oracle.Graph(prob, "f32").decode_batch(synd, _oracle_params(params), nthreads=8)
+    _assert_bit_exact(gpu, ref32, prob.K)
+
+
+def test_first_iteration_screen_accounting():
+    """Seed runs on the phenomenological DEM (every Lambda_j > 0, one result):
+    a run that converges at t = 1 ends in the first-iteration screen, so the
+    device counts its screened message updates and no full iteration for it.
+    The full seed iterations are then those of the seeds that converged after
+    more than one iteration plus initial_iters for each seed that did not."""
+    prob = W.bb_phenomenological(12, 6, 12, 1e-3, 1e-3)
+    shots = W.sample_shots(prob, 4_000, "screen_accounting")
+    params = D.make_params("beam64_640iters", ms_scale=0.625, group_warps=8)
+    dec = D.BeamSearchDecoder(prob, params)
+    dec.profile(True)
+    dec.profile_read()
+    out = dec.decode(D.to_torch_words(shots.syndromes))
+    torch.cuda.synchronize()
+    rd = dec.profile_read()
+    st = D.from_torch_words(out.status) & 7
+    it = D.from_torch_words(out.iters).astype(np.int64)
+    dec.close()
+    seed = st == 1
+    assert seed.mean() > 0.99
+    assert rd["screen_updates"] > 0
+    want = int(it[seed & (it > 1)].sum()) + params.initial_iters * int((~seed).sum())
+    assert int(rd["exec_iters"][0]) == want
+    ref = oracle.Graph(prob, "f32").decode_batch(shots.syndromes, _oracle_params(params), nthreads=8)
+    assert np.array_equal(D.from_torch_words(out.corrections), ref["corrections"])
+    assert np.array_equal(D.from_torch_words(out.iters), ref["iters"])
+
+
 def test_edge_cases_small_problems():
     prob = W.bb72_code_capacity(0.08)
     rng = np.random.default_rng(5)
