@@ -102,7 +102,7 @@ struct Counters {
     int claim_seed;
     int n_active;          // seed-store entries written by k_seed
     int err;
-    int pad;
+    int n_queue;           // shots the first-iteration screen passed on to the seed BP
     // followed by 3 * (max_rounds + 2) ints for the current pass:
     // claim_round[r], claim_select[r], work_count[r] (reset by k_pass_end)
 };
@@ -111,6 +111,7 @@ struct Work {
     long long S;           // shots per chunk = seed-store entries
     long long A;           // active entries per beam pass
     int SB;                // words per slot bit record: sp[WM] mask[WN] vals[WN] ehat[WN]
+    int* queue;            // [S] chunk-local shots the screen passed on to the seed BP
     // seed store [S]
     unsigned char* seedE;  // [S][Epad] messages in the storage format
     uint32_t* seedBits;    // [S][SB]
@@ -156,6 +157,10 @@ struct LaunchShape {
     int group_warps;       // warps per BP candidate: 1 (a warp) or the whole block
     int select_warps;      // block size of the selection kernel, in warps (<= 8)
     int grid_seed, grid_round, grid_select;
+    int screen;            // a first-iteration screen kernel runs before the seed BP
+    int grid_screen;       // its blocks of 8 warps (one shot per warp)
+    int dv_screen;         // its column degree bound: 0 -> 3, 1 -> 6, 2 -> 16
+    size_t smem_screen;
     size_t smem_bp;        // dynamic shared memory of the seed / round kernels
     size_t smem_select;
     int dv;                // engine id

@@ -8,7 +8,11 @@
 //
 // Kernels (all persistent: warps claim work with one atomic per item and
 // exit when the item counter runs out, so uneven iteration counts balance):
-//   k_seed<DV>    the seed BP of every shot in a chunk (Alg. 3, first BP run)
+//   k_screen<DV>  (generic engines, every Lambda_j > 0, one result) a warp per
+//                 shot forms e^(1) from the columns next to flipped detectors;
+//                 finalises the shots that converge there, queues the rest
+//   k_seed<DV>    the seed BP of every shot in a chunk, or of the queued ones
+//                 (Alg. 3, first BP run)
 //   k_round<DV>   expand + masked BP for every child of round r (Alg. 2)
 //   k_select      per shot: first success in visit order, results, top-w
 //                 pruning and the work list of round r + 1 (Alg. 3, App. B)
@@ -237,8 +241,7 @@ __device__ inline unsigned long long fixq(float x)
 // Lambda_j(max_iters) is written to post_out.
 template <int DV, int P, bool W, bool kPostOut, class G>
 __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters,
-                          bool stop, int* success, float* post_out, bool from_prior, const AbortCheck& ab,
-                          unsigned* scr)
+                          bool stop, int* success, float* post_out, bool from_prior, const AbortCheck& ab)
 {
     using S = Store<P>;
     using T = typename S::T;
@@ -342,54 +345,6 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
                 atomicXor(&st.par[r >> 5], 1u << (r & 31));
             }
         };
-
-        // ---- screen of a seed run's first iteration: with every Lambda_j > 0
-        // and the scale alpha, D_{i->j}(1) > 0 on every edge whose detector is
-        // not flipped, so a column with no flipped detector keeps e^_j(1) = 0.
-        // e^(1) is formed from the columns next to flipped detectors alone (by
-        // the same operations as below); a run that converges there, most seed
-        // runs, ends without forming E(1) and sum_LLR, which a converged seed
-        // with one result never reads.
-        if (!W && !kPostOut && prior && stop && g.all_lam_pos && cfg.num_results == 1) {
-            uint32_t* seen = st.vals;                          // zero in a seed run
-            for (int q = grp.warp(); q < g.WM; q += grp.nwarps()) {
-                uint32_t word = st.sp[q];
-                while (word != 0u) {
-                    const int i = 32 * q + __ffs(word) - 1;
-                    word &= word - 1u;
-                    const int re = __ldg(g.row_ptr + i + 1);
-                    for (int e = __ldg(g.row_ptr + i) + lane; e < re; e += 32) {
-                        const int j = __ldg(g.row_col + e);
-                        const uint32_t bit = 1u << (j & 31);
-                        if (atomicOr(&seen[j >> 5], bit) & bit) continue;   // another flipped detector has it
-                        float v[DV];
-                        int ed[DV];
-                        const int deg = gather(j, v, ed);
-                        if (scr != nullptr) *scr += (unsigned)deg;
-                        float post = __ldg(g.lam + j);
-#pragma unroll
-                        for (int k = 0; k < DV; ++k)
-                            if (k < deg) post = __fadd_rn(post, v[k]);
-                        if (post <= 0.f) {
-                            atomicOr(&st.ehat[j >> 5], bit);
-                            flip_rows(j, deg);
-                        }
-                    }
-                }
-            }
-            grp.sync();
-            uint32_t nz = 0;
-            for (int q = grp.rank(); q < g.WM; q += grp.size()) nz |= st.par[q];
-            if (!grp.any(nz != 0u)) {
-                ok = 2;                                        // success, by the screen alone
-                iters = 1;
-                break;
-            }
-            // not converged: the full first iteration below forms e^ again
-            for (int q = grp.rank(); q < g.WN; q += grp.size()) seen[q] = 0u;
-            for (int q = grp.rank(); q < g.WM; q += grp.size()) st.par[q] = st.sp[q];
-            grp.sync();
-        }
 
         // ---- error-node pass (Eqs. 2-4) and syndrome parity; each warp owns
         // whole 32-column words of e^ (one column per lane)
@@ -543,11 +498,9 @@ struct GenericEngine {
     }
     template <bool kPostOut = false>
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
-                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{},
-                       unsigned* scr = nullptr)
+                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
     {
-        return bp_iterate<DV, P, W, kPostOut>(grp, g, cfg, st, max_iters, stop, success, post_out, from_prior, ab,
-                                              scr);
+        return bp_iterate<DV, P, W, kPostOut>(grp, g, cfg, st, max_iters, stop, success, post_out, from_prior, ab);
     }
     __device__ void argmin_score(const DevGraph& g, const WarpState& st, double guard, int* np, long long* S,
                                  int* tie)
@@ -607,8 +560,7 @@ struct SmallEngine {
     }
     template <bool kPostOut = false>
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
-                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{},
-                       unsigned* = nullptr)
+                       int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
     {
         const int lane = threadIdx.x & 31;
         const float alpha = cfg.alpha;
@@ -919,6 +871,7 @@ __global__ void k_begin_chunk(Work w, int n_round_ints, const uint32_t* synd, Ou
     if (threadIdx.x == 0) {
         w.ctr->claim_seed = 0;
         w.ctr->n_active = 0;
+        w.ctr->n_queue = 0;
         w.ctr->err = 0;
         RunDesc d;
         d.synd = synd;
@@ -977,10 +930,191 @@ __global__ void k_round_end(Work w, int max_rounds, cudaGraphConditionalHandle c
 }
 
 // ----------------------------------------------------------------------------
+// first-iteration screen of the seed runs (generic engines)
+// ----------------------------------------------------------------------------
+// With every Lambda_j > 0, the scale alpha and one result, E(0) carries no
+// negative sign, so at t = 1 a detector i with s_i = 0 sends
+// D_{i->j}(1) = alpha min_{j' != j} Lambda_{j'} > 0 to every neighbour, and a
+// column none of whose detectors is flipped has Lambda_j(1) > 0, e^_j(1) = 0.
+// One warp per shot forms e^(1) from the columns next to flipped detectors
+// (each once), by the operations and in the order of the seed BP's first
+// iteration (bp_iterate with the E(0) records), and tests H e^(1) = s.  A shot
+// that converges (or has s = 0) is finalised here: its seed BP would stop at
+// t = 1 with this e^, and a converged seed with one result reads neither E(1)
+// nor sum_LLR.  The others go to the seed BP through the queue.  The state of
+// a warp is four bit vectors, so many shots are in flight per SM.
+constexpr int kScreenWarps = 8;
+constexpr int kMaxFlip = 128;
+
+__host__ __device__ inline size_t screen_warp_words(const DevGraph& g)
+{
+    return 2 * (size_t)g.WN + 2 * (size_t)g.WM + 2 * (size_t)kMaxFlip;
+}
+
+template <int DV>
+__global__ void k_screen(DevGraph g, DecCfg cfg, Work w)
+{
+    extern __shared__ __align__(16) uint32_t ssm[];
+    const int lane = threadIdx.x & 31;
+    uint32_t* seen = ssm + (size_t)(threadIdx.x >> 5) * screen_warp_words(g);
+    uint32_t* eh = seen + g.WN;
+    uint32_t* sp = eh + g.WN;
+    uint32_t* par = sp + g.WM;
+    int* fst = reinterpret_cast<int*>(par + g.WM);    // [kMaxFlip] flipped detectors, then their first edges
+    int* foff = fst + kMaxFlip;                       // [kMaxFlip] their edges' offsets in the shot's list
+    count_launch(w);
+    const RunDesc* dp = w.desc;
+    const long long n = dp->chunk_n;
+    const long long nw = (long long)gridDim.x * kScreenWarps;
+    const float alpha = cfg.alpha;
+    unsigned long long upd = 0;                  // message updates formed (lane)
+    for (long long b = (long long)blockIdx.x * kScreenWarps + (threadIdx.x >> 5); b < n; b += nw) {
+        const long long gb = dp->chunk_base + b;
+        const uint32_t* s = dp->synd + gb * g.WM;
+        uint32_t nz = 0;
+        for (int q = lane; q < g.WM; q += 32) {
+            const uint32_t x = s[q];
+            sp[q] = x;
+            par[q] = x;
+            nz |= x;
+        }
+        for (int q = lane; q < g.WN; q += 32) { seen[q] = 0u; eh[q] = 0u; }
+        __syncwarp();
+        bool conv = !__any_sync(FULLMASK, nz != 0u);
+        if (!conv) {
+            // the flipped detectors, in order (a shot with more than kMaxFlip
+            // goes to the seed BP unscreened)
+            int nflip = 0;
+            for (int q0 = 0; q0 < g.WM; q0 += 32) {
+                const int q = q0 + lane;
+                const uint32_t word = q < g.WM ? sp[q] : 0u;
+                const int c = __popc(word);
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULLMASK, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int k = nflip + incl - c;
+                if (k + c <= kMaxFlip) {
+                    for (uint32_t w2 = word; w2 != 0u; w2 &= w2 - 1u) fst[k++] = 32 * q + __ffs(w2) - 1;
+                }
+                nflip += __shfl_sync(FULLMASK, incl, 31);
+            }
+            if (nflip <= kMaxFlip) {
+                __syncwarp();
+                // each flipped detector's first edge and its edges' offset in
+                // the shot's list of (detector, edge) pairs
+                int tot = 0;
+                for (int k0 = 0; k0 < nflip; k0 += 32) {
+                    const int k = k0 + lane;
+                    int rb = 0, d = 0;
+                    if (k < nflip) {
+                        const int i = fst[k];
+                        rb = __ldg(g.row_ptr + i);
+                        d = __ldg(g.row_ptr + i + 1) - rb;
+                    }
+                    int incl = d;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(FULLMASK, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    if (k < nflip) {
+                        fst[k] = rb;
+                        foff[k] = tot + incl - d;
+                    }
+                    tot += __shfl_sync(FULLMASK, incl, 31);
+                }
+                __syncwarp();
+                // one (detector, edge) pair per lane: the column on the edge
+                for (int t = lane; t < tot; t += 32) {
+                    int lo = 0, hi = nflip - 1;                    // last detector with foff <= t
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (foff[mid] <= t) lo = mid; else hi = mid - 1;
+                    }
+                    const int e0 = fst[lo] + (t - foff[lo]);
+                    const int j = __ldg(g.row_col + e0);
+                    const uint32_t bit = 1u << (j & 31);
+                    if (atomicOr(&seen[j >> 5], bit) & bit) continue;   // another flipped detector has it
+                    // D_{i'->j}(1) on the column's edges from the E(0) records
+                    // with the syndrome bit folded into the sign parity
+                    int kb = 0, deg = 0;
+                    if constexpr (DV > 6) {
+                        kb = __ldg(g.col_ptr + j);
+                        deg = __ldg(g.col_ptr + j + 1) - kb;
+                    }
+                    float v[DV];
+#pragma unroll
+                    for (int k = 0; k < DV; ++k) {
+                        int e = -1, r = 0;
+                        if constexpr (DV <= 6) {
+                            const int2 er = __ldg(g.colER + (size_t)k * g.Npad + j);
+                            e = er.x;
+                            r = er.y;
+                            deg += (e >= 0) ? 1 : 0;
+                        } else if (k < deg) {
+                            e = __ldg(g.col_edge + kb + k);
+                            r = __ldg(g.col_row + kb + k);
+                        }
+                        if (e >= 0) {
+                            const float4 s4 = __ldg(g.rs0 + r);
+                            const uint32_t si = (sp[r >> 5] >> (r & 31)) & 1u;
+                            const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
+                            const uint32_t sg = __float_as_uint(s4.w) ^ si;   // E(0) > 0 on every edge
+                            const float d = __fmul_rn(alpha, m);
+                            v[k] = sg ? -d : d;
+                        } else {
+                            v[k] = INFINITY;
+                        }
+                    }
+#pragma unroll
+                    for (int a = 0; a < DV; ++a) {
+#pragma unroll
+                        for (int k = 0; k + 1 < DV - a; ++k) {
+                            if (v[k] > v[k + 1]) { const float tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv; }
+                        }
+                    }
+                    float post = __ldg(g.lam + j);               // Eq. 3 in ascending order
+#pragma unroll
+                    for (int k = 0; k < DV; ++k)
+                        if (k < deg) post = __fadd_rn(post, v[k]);
+                    upd += (unsigned long long)deg;
+                    if (post <= 0.f) {                            // Eq. 4
+                        atomicOr(&eh[j >> 5], bit);
+                        for (int k = 0; k < deg; ++k) {
+                            const int r = DV <= 6 ? __ldg(g.colER + (size_t)k * g.Npad + j).y
+                                                  : __ldg(g.col_row + kb + k);
+                            atomicXor(&par[r >> 5], 1u << (r & 31));
+                        }
+                    }
+                }
+                __syncwarp();
+                nz = 0;
+                for (int q = lane; q < g.WM; q += 32) nz |= par[q];
+                conv = !__any_sync(FULLMASK, nz != 0u);
+            }
+        }
+        if (conv) {
+            finalize_shot<WarpGroup, true>(g, dp->out, gb, eh, ST_SEED, 1ull);
+        } else if (lane == 0) {
+            const int k = atomicAdd(&w.ctr->n_queue, 1);
+            w.queue[k] = (int)b;
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) upd += __shfl_xor_sync(FULLMASK, upd, o);
+    if (lane == 0 && upd != 0ull) atomicAdd(&w.stats[3], upd);
+}
+
+// ----------------------------------------------------------------------------
 // seed BP
 // ----------------------------------------------------------------------------
 template <class Eng>
-__global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevGraph g, DecCfg cfg, Work w)
+__global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevGraph g, DecCfg cfg, Work w,
+                                                                             int screened)
 {
     extern __shared__ __align__(16) char smem[];
     Eng eng;
@@ -990,12 +1124,14 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
     const RunDesc* dp = w.desc;                  // read fields when needed (keeps registers free)
     count_launch(w);
     eng.load_graph(g);
-    unsigned long long seed_iters = 0;           // full BP iterations (group rank 0)
-    unsigned scr = 0;                            // message updates of first-iteration screens (this thread,
-                                                 // flushed before it could wrap)
+    unsigned long long seed_iters = 0;           // BP iterations (group rank 0)
     for (;;) {
         int b = 0;
-        if (grp.rank() == 0) b = atomicAdd(&w.ctr->claim_seed, 1);
+        if (grp.rank() == 0) {
+            // after a screen, the shots it passed on; else every shot of the chunk
+            const int k = atomicAdd(&w.ctr->claim_seed, 1);
+            b = !screened ? k : (k < *((volatile int*)&w.ctr->n_queue) ? w.queue[k] : (int)dp->chunk_n);
+        }
         b = grp.bcast(b);
         if (b >= dp->chunk_n) break;
         const long long gb = dp->chunk_base + b;
@@ -1019,9 +1155,8 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
         if (!Eng::kPriorSetsSums) eng.clear_sums(g, st);
         grp.sync();
         int succ = 0;
-        const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr, true, AbortCheck{}, &scr);
-        if (scr >= (1u << 30)) { atomicAdd(&w.stats[3], (unsigned long long)scr); scr = 0; }
-        if (grp.rank() == 0 && succ != 2) seed_iters += (unsigned long long)it;   // full iterations only
+        const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr, true);
+        if (grp.rank() == 0) seed_iters += (unsigned long long)it;
         grp.sync();
         if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
             finalize_shot<typename Eng::Grp, true>(g, dp->out, gb, st.ehat, succ ? ST_SEED : ST_FAILED,
@@ -1053,10 +1188,6 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
         grp.sync();
     }
     if (grp.rank() == 0 && seed_iters != 0ull) atomicAdd(&w.stats[0], seed_iters);
-    unsigned long long ws = scr;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(FULLMASK, ws, o);
-    if ((threadIdx.x & 31) == 0 && ws != 0ull) atomicAdd(&w.stats[3], ws);
 }
 
 // ----------------------------------------------------------------------------
@@ -1617,10 +1748,43 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, int group_warp
                                                                   ls->smem_select)))
         return -2;
     if (bps_bp < 1 || bps_sel < 1) return -5;
+    // the first-iteration screen: generic engines, the scale alpha, every
+    // Lambda_j > 0, one result
+    ls->screen = 0;
+    ls->grid_screen = 0;
+    ls->smem_screen = sizeof(uint32_t) * screen_warp_words(g) * kScreenWarps;
+    if (eng < 9 || eng >= kBlockEngine) {                   // not a small engine
+        if (!weighted && g.all_lam_pos && cfg.num_results == 1 && ls->smem_screen <= (size_t)max_optin) {
+            void* kf = gkind == 0 ? (void*)k_screen<3> : gkind == 1 ? (void*)k_screen<6> : (void*)k_screen<16>;
+            int bps_scr = 0;
+            if (CUDA_FAILED(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) ||
+                CUDA_FAILED(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_scr, kf, 32 * kScreenWarps,
+                                                                          ls->smem_screen)))
+                return -2;
+            if (bps_scr >= 1) {
+                ls->screen = 1;
+                ls->grid_screen = sms * bps_scr;
+                ls->dv_screen = gkind;
+            }
+        }
+    }
     ls->grid_seed = sms * bps_bp;
     ls->grid_round = sms * bps_bp;
     ls->grid_select = sms * bps_sel;
     return 0;
+}
+
+static void* screen_func(const LaunchShape& ls)
+{
+    return ls.dv_screen == 0 ? (void*)k_screen<3> : ls.dv_screen == 1 ? (void*)k_screen<6> : (void*)k_screen<16>;
+}
+
+static void launch_screen(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls, cudaStream_t s)
+{
+    const dim3 grid((unsigned)ls.grid_screen), block(32 * kScreenWarps);
+    if (ls.dv_screen == 0) k_screen<3><<<grid, block, ls.smem_screen, s>>>(g, cfg, w);
+    else if (ls.dv_screen == 1) k_screen<6><<<grid, block, ls.smem_screen, s>>>(g, cfg, w);
+    else k_screen<16><<<grid, block, ls.smem_screen, s>>>(g, cfg, w);
 }
 
 template <class Eng>
@@ -1633,8 +1797,13 @@ static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, c
     k_begin_chunk<<<1, 128, 0, s>>>(w, nri, synd, out, base, n);
     if (CUDA_FAILED(cudaGetLastError())) return -2;
     if (gx != nullptr) return !CUDA_FAILED(cudaGraphLaunch(gx, s)) ? 0 : -2;
+    if (ls.screen) {
+        if (hk) hk->before(hk->ctx, 0);
+        launch_screen(g, cfg, w, ls, s);
+        if (hk) hk->after(hk->ctx, 0);
+    }
     if (hk) hk->before(hk->ctx, 0);
-    k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w);
+    k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, ls.screen);
     if (hk) hk->after(hk->ctx, 0);
     if (CUDA_FAILED(cudaGetLastError())) return -2;
     if (cfg.max_rounds == 0) return 0;
@@ -1698,9 +1867,16 @@ static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0,
     cudaGraph_t graph = nullptr;
     if (CUDA_FAILED(cudaGraphCreate(&graph, 0))) return -2;
     int rc = 0;
-    cudaGraphNode_t seed;
-    void* sargs[] = {&g, &cfg, &w};
-    rc = add_kernel(graph, &seed, nullptr, (void*)k_seed<Eng>, ls.grid_seed, threads, ls.smem_bp, sargs);
+    cudaGraphNode_t seed, scr;
+    int screened = ls.screen;
+    void* sargs[] = {&g, &cfg, &w, &screened};
+    void* cargs[] = {&g, &cfg, &w};
+    if (ls.screen)
+        rc = add_kernel(graph, &scr, nullptr, screen_func(ls), ls.grid_screen, 32 * kScreenWarps, ls.smem_screen,
+                        cargs);
+    if (!rc)
+        rc = add_kernel(graph, &seed, ls.screen ? &scr : nullptr, (void*)k_seed<Eng>, ls.grid_seed, threads,
+                        ls.smem_bp, sargs);
     // seed, then WHILE (a window of active shots left) { round 1, WHILE (the
     // next round has children) { round r, selection, round end }, pass end }:
     // a chunk runs exactly the passes and rounds it needs
@@ -1819,6 +1995,7 @@ size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long 
     v.seedBits = (uint32_t*)take(sizeof(uint32_t) * (size_t)S * SB);
     v.seedMeta = (SlotMeta*)take(sizeof(SlotMeta) * (size_t)S);
     v.seed_shot = (int*)take(sizeof(int) * (size_t)S);
+    v.queue = (int*)take(sizeof(int) * (size_t)S);
     v.slotE = (unsigned char*)take(2 * (size_t)A * W2 * snap_bytes(g));
     v.slotBits = (uint32_t*)take(sizeof(uint32_t) * 2 * (size_t)A * W2 * SB);
     v.slotMeta = (SlotMeta*)take(sizeof(SlotMeta) * 2 * (size_t)A * W2);

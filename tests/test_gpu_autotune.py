@@ -81,3 +81,27 @@ def test_graph_runs_only_the_rounds_a_chunk_needs():
     rounds = (launches - 3 - 2) // 3
     assert launches == 3 + 1 + 3 * rounds + 1 and 1 <= rounds <= 10
     dec.close()
+
+
+@pytest.mark.parametrize("gw", [1, 8])
+def test_screen_kernel_runs_before_the_seed_on_dems(gw):
+    """A generic-engine decoder with every Lambda_j > 0 and one result runs the
+    first-iteration screen before the seed BP: 4 kernels for a seed-only chunk
+    (set-up, screen, seed, pass gate).  With per-edge weights the screen is
+    off (3 kernels), and so it is with two results (shown without beam
+    rounds: set-up and seed only)."""
+    prob = W.bb_phenomenological(6, 6, 3, 0.01, 0.01)
+    zero = torch.zeros((64, (prob.M + 31) // 32), dtype=torch.int32, device="cuda")
+    for nr, rounds, weights, want in ((1, 3, False, 4), (1, 3, True, 3), (2, 0, False, 2), (1, 0, False, 3)):
+        dec = D.BeamSearchDecoder(prob, D.make_params(max_rounds=rounds, beam_width=4, initial_iters=10,
+                                                      iters_per_round=5, num_results=nr, ms_scale=0.625,
+                                                      group_warps=gw))
+        if weights:
+            dec.set_weights(np.full((2, prob.n_edges), 0.625, np.float32))
+        dec.profile_read()
+        out = dec.decode(zero)
+        torch.cuda.synchronize()
+        assert dec.profile_read()["kernel_launches"] == want, (nr, rounds, weights)
+        assert np.all(D.from_torch_words(out.status) == 1)
+        assert not D.from_torch_words(out.corrections).any()
+        dec.close()
