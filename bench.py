@@ -382,7 +382,7 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
-def alu_roofline(prof, E: int, dev: int, traffic_case: str):
+def alu_roofline(prof, E: int, dev: int, traffic_case: str, shots: int = 0, msg_bytes: int = 4):
     """Roofline of the dominant BP kernel from per-kernel event times.
 
     Algorithmic lane operations of a launch = OPS_PER_UPDATE x (the full BP
@@ -421,11 +421,18 @@ def alu_roofline(prof, E: int, dev: int, traffic_case: str):
     # DRAM bytes per candidate-iteration from an ncu capture of a smaller case
     # (profiles/), scaled to this run's average launch; null once the kernel
     # sources differ from the ones that were captured
-    tr = _traffic_record(names[dom], E)
+    tr = _traffic_record(names[dom], E, msg_bytes)
     if tr is not None:
-        roofline["traffic"] = tr * (dom_iters / max(1, launches[dom]))
-        roofline["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum on a {traffic_case}, " \
-                                     "scaled by candidate-iterations"
+        per, unit = tr
+        if unit == "shot" and shots > 0:
+            # the seed stage (screen and seed BP) moves its bytes per shot
+            roofline["traffic"] = per * shots / max(1, launches[dom])
+            roofline["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum of the seed stage on " \
+                                         f"a {traffic_case}, per shot, scaled by the shots of a launch"
+        elif unit == "candidate_iteration":
+            roofline["traffic"] = per * (dom_iters / max(1, launches[dom]))
+            roofline["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum on a {traffic_case}, " \
+                                         "scaled by candidate-iterations"
     return roofline, exec_iters
 
 
@@ -638,7 +645,9 @@ def run_precision(args, rank: int, world: int, local_rank: int):
             t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_total = float(t.item())
-        roofline, exec_iters = alu_roofline(prof, E, dev, "small case of the same DEM")
+        roofline, exec_iters = alu_roofline(prof, E, dev, "small case of the same DEM",
+                                            shots=shots_per_step * args.steps,
+                                            msg_bytes=4 if prec == B.BSD_FP32 else 2)
         per_p = {}
         for (p, prob, sh), o in zip(work, outs):
             st = D.from_torch_words(o.status)
@@ -808,9 +817,9 @@ def run_unrolled(args, rank: int, world: int, local_rank: int):
                 "kernel_share": float(prof["ms"][dom] / max(prof["ms"][3:7].sum(), 1e-9)),
                 "peak_source": f"hbm_gbs ({pk_kind})",
                 "measured_in": "second timed region: same steps, each pass launched between CUDA events"}
-    tr_bytes = _traffic_record(names[dom], E)
-    if tr_bytes is not None:
-        roofline["traffic"] = tr_bytes
+    tr_rec = _traffic_record(names[dom], E)
+    if tr_rec is not None and tr_rec[1] == "launch":
+        roofline["traffic"] = tr_rec[0]
         roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, averaged over " \
                                      "the launches of one training step of this workload"
     steps_s = ms_total * 1e-3
@@ -991,7 +1000,8 @@ def run_synthetic(args, rank: int, world: int, local_rank: int):
         t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
-    roofline, exec_iters = alu_roofline(prof, prob.n_edges, dev, "small case of the same DEM")
+    roofline, exec_iters = alu_roofline(prof, prob.n_edges, dev, "small case of the same DEM",
+                                        shots=len(decs) * sh.B * args.steps)
     per_w = {}
     for preset, o, pr in zip(SYN_PRESETS, outs, prof):
         st = D.from_torch_words(o.status)
@@ -1352,25 +1362,29 @@ def e2e_host(decs, work, args, dev):
             "d2h_bytes_per_step": int(d2h), "api": "bsd_decode_host (pinned host buffers)"}
 
 
-def _traffic_record(kernel: str, edges: int):
-    """bytes per unit of work recorded for `kernel` on a problem with `edges`
-    edges, if the kernel sources the record names are unchanged since the
-    capture (per candidate-iteration for the decoder kernels, per launch for
-    the unrolled passes)."""
+def _traffic_record(kernel: str, edges: int, msg_bytes: int = 0):
+    """(bytes per unit of work, unit) recorded for `kernel` on a problem with
+    `edges` edges (and, where the record names it, `msg_bytes` bytes per
+    stored message), if the kernel sources the record names are unchanged
+    since the capture; the unit is a candidate-iteration (decoder kernels), a
+    launch (the unrolled passes) or a shot (the seed stage)."""
     import glob
     import re
     for path in glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_traffic_*.md")):
         txt = open(path).read()
         h = re.search(r"^source_hash: (\w+)$", txt, re.M)
         k = re.search(r"^kernel: (\w+)$", txt, re.M)
-        b = re.search(r"^bytes_per_(?:candidate_iteration|launch): ([0-9.]+)$", txt, re.M)
+        b = re.search(r"^bytes_per_(candidate_iteration|launch|shot): ([0-9.]+)$", txt, re.M)
         e = re.search(r"^edges: (\d+)$", txt, re.M)
+        mb = re.search(r"^msg_bytes: (\d+)$", txt, re.M)
         src = re.search(r"^sources: (.+)$", txt, re.M)
         if e is not None and int(e.group(1)) != edges:
             continue
+        if mb is not None and msg_bytes and int(mb.group(1)) != msg_bytes:
+            continue
         files = src.group(1).split() if src else None
         if h and k and b and k.group(1) == kernel and h.group(1) == _source_hash(files):
-            return float(b.group(1))
+            return float(b.group(2)), b.group(1)
     return None
 
 
