@@ -1125,14 +1125,22 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
     count_launch(w);
     eng.load_graph(g);
     unsigned long long seed_iters = 0;           // BP iterations (group rank 0)
+    // a warp claims its shots kBatch at a time (one atomic per batch on the
+    // chunk's counter, which a million one-iteration seeds would otherwise
+    // hit a million times); a block candidate one at a time
+    constexpr int kBatch = Eng::Grp::kBlock ? 1 : 4;
+    const int nq = screened ? *((volatile int*)&w.ctr->n_queue) : 0;
+    int kcur = 0, kend = 0;                      // claimed slots [kcur, kend), the same in the whole group
     for (;;) {
-        int b = 0;
-        if (grp.rank() == 0) {
-            // after a screen, the shots it passed on; else every shot of the chunk
-            const int k = atomicAdd(&w.ctr->claim_seed, 1);
-            b = !screened ? k : (k < *((volatile int*)&w.ctr->n_queue) ? w.queue[k] : (int)dp->chunk_n);
+        if (kcur >= kend) {
+            int base = 0;
+            if (grp.rank() == 0) base = atomicAdd(&w.ctr->claim_seed, kBatch);
+            kcur = grp.bcast(base);
+            kend = kcur + kBatch;
         }
-        b = grp.bcast(b);
+        const int k = kcur++;
+        // after a screen, the shots it passed on; else every shot of the chunk
+        const int b = !screened ? k : (k < nq ? w.queue[k] : (int)dp->chunk_n);
         if (b >= dp->chunk_n) break;
         const long long gb = dp->chunk_base + b;
         const uint32_t* s = dp->synd + gb * g.WM;

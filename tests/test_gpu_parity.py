@@ -145,6 +145,26 @@ def test_chunked_batches_match_single_pass():
     _assert_bit_exact(a, ref32, prob.K)
 
 
+@pytest.mark.parametrize("gw", [1, 8])
+def test_chunked_dem_with_screen_matches_single_pass(gw):
+    """The phenomenological DEM (first-iteration screen on) in several chunks
+    with a ragged tail: every chunk restarts the screen's queue, and the
+    outputs equal one pass over the batch and the oracle, bit for bit."""
+    prob = W.bb_phenomenological(6, 6, 4, 0.01, 0.01)
+    shots = W.sample_shots(prob, 5_003, "phenom_chunks")
+    base = dict(max_rounds=4, beam_width=8, initial_iters=20, iters_per_round=10, ms_scale=0.625, group_warps=gw)
+    small = D.make_params(workspace_bytes=24 << 20, **base)
+    big = D.make_params(**base)
+    a = _gpu_decode(prob, small, shots.syndromes)
+    assert a["info"]["chunk_shots"] < shots.B and shots.B % a["info"]["chunk_shots"] != 0
+    b = _gpu_decode(prob, big, shots.syndromes)
+    for k in ("corrections", "obs", "status", "iters"):
+        assert np.array_equal(a[k], b[k]), k
+    ref32 = oracle.Graph(prob, "f32").decode_batch(shots.syndromes, _oracle_params(big), nthreads=8)
+    _assert_bit_exact(a, ref32, prob.K)
+    assert (a["status"] & 7 == 2).any()                # some shots reached the beam
+
+
 # ----------------------------------------------------------------------------
 # edge cases
 # ----------------------------------------------------------------------------
