@@ -1344,10 +1344,15 @@ __global__ void __launch_bounds__(256) k_select(DevGraph g, DecCfg cfg, Work w, 
     const RunDesc d = *w.desc;
     int* rc = round_ctr(w, r);
     const int cb = r & 1;
+    int acur = 0, aend = 0;                      // window entries claimed four at a time
     for (;;) {
-        int a = 0;
-        if (lane == 0) a = atomicAdd(&rc[1], 1);
-        a = __shfl_sync(FULLMASK, a, 0);
+        if (acur >= aend) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&rc[1], 4);
+            acur = __shfl_sync(FULLMASK, base, 0);
+            aend = acur + 4;
+        }
+        const int a = acur++;
         if (a >= cnt) break;
         if (r == 1) {
             // a new window entry: the seed path is its only path (Alg. 3)
