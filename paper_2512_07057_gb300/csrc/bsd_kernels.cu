@@ -276,11 +276,14 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
             float m1 = L, m2 = L;
             int id = -1;
             uint32_t neg = (st.sp[i >> 5] >> (i & 31)) & 1u;
+            // branch-free: the runner-up is min(m2, max(m1, a)); the argmin
+            // moves only on a strictly smaller value (first index on ties)
             for (int e = rb; e < re; ++e) {
                 const float x = S::ld(E, e);
                 const float a = fabsf(x);
-                if (a < m1) { m2 = m1; m1 = a; id = e; }
-                else if (a < m2) { m2 = a; }
+                m2 = fminf(m2, fmaxf(m1, a));
+                id = (a < m1) ? e : id;
+                m1 = fminf(m1, a);
                 neg ^= (x < 0.f) ? 1u : 0u;
             }
             st.rs[i] = make_float4(m1, m2, __int_as_float(id), __uint_as_float(neg));
