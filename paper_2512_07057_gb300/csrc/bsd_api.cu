@@ -119,7 +119,9 @@ LaunchShape small_shape(const LaunchShape& ls, const DecCfg& cfg, int n)
     const long long per_block = ls.group_warps >= 2 ? 1 : ls.warps_per_block;
     auto cap = [](long long v, int full) { return (int)(v < 1 ? 1 : (v < full ? v : full)); };
     s.grid_seed = cap((n + per_block - 1) / per_block, ls.grid_seed);
-    if (ls.screen) s.grid_screen = cap((n + 7) / 8, ls.grid_screen);   // eight shots per screen block
+    // no first-iteration screen: for a few shots its extra launch costs more
+    // latency than it saves
+    s.screen = 0;
     s.grid_round = cap(((long long)n * 2 * cfg.w + per_block - 1) / per_block, ls.grid_round);
     s.grid_select = cap((n + ls.select_warps - 1) / ls.select_warps, ls.grid_select);
     return s;
