@@ -25,12 +25,18 @@ def _arrays(out):
     return {k: D.from_torch_words(getattr(out, k)).copy() for k in ("corrections", "obs_flips", "status", "iters")}
 
 
-@pytest.mark.parametrize("case", ["bb144_beam32", "bb72_32res"])
+@pytest.mark.parametrize("case", ["bb144_beam32", "bb72_32res", "phenom_screen"])
 def test_noalloc_matches_decode_on_two_calls(case):
     if case == "bb144_beam32":
         prob = W.bb144_code_capacity(0.05)
         params = D.make_params("beam32_340iters", ms_scale=0.625)
         shots = W.sample_shots(prob, 3_000, "noalloc_bb144")
+    elif case == "phenom_screen":
+        # a generic-engine DEM: the first-iteration screen and its queue run
+        # in the static array too, over several chunks
+        prob = W.bb_phenomenological(6, 6, 4, 0.01, 0.01)
+        params = D.make_params(max_rounds=4, beam_width=8, initial_iters=20, iters_per_round=10, ms_scale=0.625)
+        shots = W.sample_shots(prob, 4_000, "noalloc_phenom")
     else:
         prob = W.bb72_code_capacity(0.05)
         params = D.make_params("beam64_32res_640iters", ms_scale=0.625)
