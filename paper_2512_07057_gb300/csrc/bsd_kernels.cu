@@ -226,9 +226,12 @@ __device__ inline WarpState carve(char* base, const DevGraph& g)
     return s;
 }
 
+// round(x * 2^16) to the nearest integer, ties to even: scaling a float by a
+// power of two is exact, so single precision gives the value double would
+// (GB300's double-precision pipe is narrow)
 __device__ inline unsigned long long fixq(float x)
 {
-    return (unsigned long long)__double2ll_rn((double)x * kFixScale);
+    return (unsigned long long)__float2ll_rn(__fmul_rn(x, (float)kFixScale));
 }
 
 // ----------------------------------------------------------------------------
