@@ -200,6 +200,27 @@ def test_priors_above_one_half(gw):
     _assert_bit_exact(gpu, ref32, prob.K)
 
 
+def test_screen_with_many_flipped_detectors():
+    """Dense syndromes on a DEM: shots with more than 128 flipped detectors go
+    to the seed BP unscreened, others are screened; all-ones, random dense,
+    sampled and single-detector syndromes, bit-exact against the oracle."""
+    prob = W.bb_phenomenological(12, 6, 4, 0.01, 0.01)         # 360 detectors
+    rng = np.random.default_rng(8)
+    n = 40
+    bits = np.zeros((n, prob.M), np.uint8)
+    bits[0] = 1                                                   # every detector flipped
+    bits[1:20] = (rng.random((19, prob.M)) < 0.5)                 # about M/2 flipped
+    bits[20:30] = W.unpack_bits(W.sample_shots(prob, 10, "dense_real").syndromes, prob.M)   # sampled errors
+    for k in range(30, n):
+        bits[k, rng.integers(prob.M)] = 1                         # a single detector
+    synd = W.pack_bits(bits)
+    params = D.make_params(max_rounds=2, beam_width=2, initial_iters=6, iters_per_round=3, ms_scale=0.625)
+    gpu = _gpu_decode(prob, params, synd)
+    ref32 = oracle.Graph(prob, "f32").decode_batch(synd, _oracle_params(params), nthreads=8)
+    _assert_bit_exact(gpu, ref32, prob.K)
+    assert (bits.sum(1) > 128).sum() >= 20
+
+
 def test_first_iteration_screen_accounting():
     """Seed runs on the phenomenological DEM (every Lambda_j > 0, one result):
     a run that converges at t = 1 ends in the first-iteration screen, so the
