@@ -1,0 +1,74 @@
+"""Host-side helpers of bench.py (CPU): the traffic records read from the
+profile summaries.
+
+A record names the kernel, the problem's edge count, optionally the stored
+message size, its unit of work (a candidate-iteration, a launch or a shot)
+and the hash of the kernel sources it was captured with; a record whose
+sources have changed since, or that belongs to another problem, is not
+used, so the benchmark line reports null traffic instead of a stale figure.
+"""
+import os
+
+import pytest
+
+import bench
+
+
+def _tree(tmp_path, src_text):
+    csrc = tmp_path / "paper_2512_07057_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "bsd_internal.cuh").write_text("// header\n")
+    (csrc / "bsd_kernels.cu").write_text(src_text)
+    (tmp_path / "profiles").mkdir()
+    return tmp_path
+
+
+def _record(root, name, kernel, unit, value, edges, msg_bytes=None):
+    h = bench._source_hash(["bsd_internal.cuh", "bsd_kernels.cu"])
+    lines = [f"# {kernel} traffic", "", "sources: bsd_internal.cuh bsd_kernels.cu", f"source_hash: {h}",
+             f"kernel: {kernel}", f"edges: {edges}"]
+    if msg_bytes is not None:
+        lines.append(f"msg_bytes: {msg_bytes}")
+    lines.append(f"bytes_per_{unit}: {value}")
+    (root / "profiles" / name).write_text("\n".join(lines) + "\n")
+
+
+@pytest.fixture
+def tree(tmp_path, monkeypatch):
+    root = _tree(tmp_path, "// kernels v1\n")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    return root
+
+
+def test_record_units_and_filters(tree):
+    _record(tree, "k_round_traffic_a.md", "k_round", "candidate_iteration", 44.13, 432)
+    _record(tree, "k_seed_traffic_a4.md", "k_seed", "shot", 180.8, 6912, msg_bytes=4)
+    _record(tree, "k_seed_traffic_a2.md", "k_seed", "shot", 179.9, 6912, msg_bytes=2)
+    _record(tree, "k_u_var_traffic_a.md", "k_u_var", "launch", 197014355, 6912)
+    assert bench._traffic_record("k_round", 432) == (44.13, "candidate_iteration")
+    assert bench._traffic_record("k_round", 6912) is None                 # another problem
+    assert bench._traffic_record("k_seed", 6912, 4) == (180.8, "shot")
+    assert bench._traffic_record("k_seed", 6912, 2) == (179.9, "shot")
+    assert bench._traffic_record("k_u_var", 6912) == (197014355.0, "launch")
+    assert bench._traffic_record("k_select", 432) is None                 # no record
+
+
+def test_record_goes_stale_when_the_sources_change(tree):
+    _record(tree, "k_round_traffic_a.md", "k_round", "candidate_iteration", 44.13, 432)
+    assert bench._traffic_record("k_round", 432) is not None
+    (tree / "paper_2512_07057_gb300" / "csrc" / "bsd_kernels.cu").write_text("// kernels v2\n")
+    assert bench._traffic_record("k_round", 432) is None
+
+
+def test_committed_records_parse():
+    """Every traffic record under profiles/ names its kernel, sources, hash,
+    edges and exactly one unit of work."""
+    import re
+    prof = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles")
+    names = [n for n in os.listdir(prof) if "_traffic_" in n]
+    assert names
+    for n in names:
+        txt = open(os.path.join(prof, n)).read()
+        for key in ("kernel", "sources", "source_hash", "edges"):
+            assert re.search(rf"^{key}: \S+", txt, re.M), (n, key)
+        assert len(re.findall(r"^bytes_per_(candidate_iteration|launch|shot): [0-9.]+$", txt, re.M)) == 1, n
