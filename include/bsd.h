@@ -174,6 +174,11 @@ int bsd_decode_host(bsd_decoder *dec, const uint32_t *h_syndromes, int64_t B,
  *   The first call on a device looks up the array's device address on that
  *   device (cudaGetSymbolAddress); make that first call before any stream
  *   capture on the device.
+ *   Unlike bsd_decode, the call is not fully asynchronous: with max_rounds
+ *   > 0, after the seed pass of each chunk it copies the chunk's count of
+ *   shots that need beam rounds to the host and synchronises the stream to
+ *   read it, so the calling thread waits for each chunk's seed pass (the
+ *   beam rounds of the last chunk are still in flight when it returns).
  *   All calls on a device share the one array, and it keeps the contents the
  *   last call left: each call clears the counters it needs zeroed, but calls
  *   whose work overlaps on the GPU (two streams, two host threads, two

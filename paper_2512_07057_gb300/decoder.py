@@ -89,6 +89,33 @@ class BeamSearchDecoder:
         except Exception:
             pass
 
+    # The kernels index every buffer by shot and word with no bounds of their
+    # own, so a tensor of the wrong size, type or device would be read or
+    # written out of bounds: every tensor is checked before the call.
+    def _check_tensor(self, t, name: str, shape: tuple) -> None:
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {shape}")
+        if t.element_size() != 4 or t.dtype.is_floating_point:
+            raise ValueError(f"{name}: dtype {t.dtype}, expected 32-bit integer words")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: not contiguous")
+        if not t.is_cuda or t.device.index != self.device:
+            raise ValueError(f"{name}: on {t.device}, expected cuda:{self.device}")
+
+    def _check_syndromes(self, syndromes) -> int:
+        if syndromes.dim() != 2:
+            raise ValueError(f"syndromes: {syndromes.dim()} dimensions, expected [B, {_words(self.M)}]")
+        nb = int(syndromes.shape[0])
+        self._check_tensor(syndromes, "syndromes", (nb, _words(self.M)))
+        return nb
+
+    def _check_outputs(self, out: DecodeResult, nb: int) -> None:
+        self._check_tensor(out.corrections, "corrections", (nb, _words(self.N)))
+        self._check_tensor(out.obs_flips, "obs_flips", (nb, max(_words(self.K), 1)))
+        self._check_tensor(out.status, "status", (nb,))
+        if out.iters is not None:
+            self._check_tensor(out.iters, "iters", (nb,))
+
     def _stream(self, stream):
         import torch
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -105,23 +132,24 @@ class BeamSearchDecoder:
 
     def decode(self, syndromes, out: DecodeResult | None = None, stream=None, with_iters: bool = True) -> DecodeResult:
         """syndromes: CUDA tensor [B, ceil(M/32)] of 32-bit words (int32 or uint32 bits)."""
-        import torch
-        assert syndromes.is_cuda and syndromes.is_contiguous() and syndromes.element_size() == 4
-        assert syndromes.shape[1] == _words(self.M)
-        nb = syndromes.shape[0]
+        nb = self._check_syndromes(syndromes)
         if out is None:
             out = self.alloc_outputs(nb)
+        self._check_outputs(out, nb)
         B.bsd_decode(self.h, C.c_void_p(syndromes.data_ptr()), nb, C.c_void_p(out.corrections.data_ptr()),
                      C.c_void_p(out.obs_flips.data_ptr()), C.c_void_p(out.status.data_ptr()),
-                     C.c_void_p(out.iters.data_ptr()) if with_iters else None, self._stream(stream))
+                     C.c_void_p(out.iters.data_ptr()) if with_iters and out.iters is not None else None,
+                     self._stream(stream))
         return out
 
     def decode_noalloc(self, syndromes, out: DecodeResult, stream=None) -> int:
         """bsd_decode_noalloc into caller-allocated outputs; returns the C return code."""
-        assert syndromes.is_cuda and syndromes.is_contiguous() and syndromes.element_size() == 4
-        return B.bsd_decode_noalloc(self.h, C.c_void_p(syndromes.data_ptr()), syndromes.shape[0],
+        nb = self._check_syndromes(syndromes)
+        self._check_outputs(out, nb)
+        return B.bsd_decode_noalloc(self.h, C.c_void_p(syndromes.data_ptr()), nb,
                                     C.c_void_p(out.corrections.data_ptr()), C.c_void_p(out.obs_flips.data_ptr()),
-                                    C.c_void_p(out.status.data_ptr()), C.c_void_p(out.iters.data_ptr()),
+                                    C.c_void_p(out.status.data_ptr()),
+                                    C.c_void_p(out.iters.data_ptr()) if out.iters is not None else None,
                                     self._stream(stream))
 
     def decode_host(self, syndromes: np.ndarray, stream=None) -> dict:

@@ -85,3 +85,64 @@ def test_create_rejects_invalid_input_before_touching_the_device():
     lib = B.load()
     assert lib.bsd_decode(None, None, 1, None, None, None, None, None) == B.BSD_ERR_INVALID_ARG
     assert lib.bsd_sync_error(None) == B.BSD_ERR_INVALID_ARG
+
+
+def _unbound_decoder(M=72, N=144, K=12, device=0):
+    """A BeamSearchDecoder shell with sizes but no handle: its checks run on
+    the host, so a rejection here happens before any library call."""
+    from paper_2512_07057_gb300 import decoder as D
+
+    class _NoCall:
+        def __getattr__(self, name):
+            raise AssertionError(f"the library was called ({name}) despite a bad tensor")
+
+    dec = D.BeamSearchDecoder.__new__(D.BeamSearchDecoder)
+    dec.M, dec.N, dec.K, dec.device, dec.h = M, N, K, device, None
+    return dec, _NoCall()
+
+
+def _good_io(torch, nb=5, M=72, N=144, K=12):
+    from paper_2512_07057_gb300 import decoder as D
+    w = lambda n: (n + 31) // 32
+    synd = torch.zeros((nb, w(M)), dtype=torch.int32)
+    out = D.DecodeResult(corrections=torch.zeros((nb, w(N)), dtype=torch.int32),
+                         obs_flips=torch.zeros((nb, max(w(K), 1)), dtype=torch.int32),
+                         status=torch.zeros(nb, dtype=torch.int32), iters=torch.zeros(nb, dtype=torch.int32))
+    return synd, out
+
+
+@pytest.mark.parametrize("bad", ["synd_words", "synd_1d", "corr_rows", "corr_words", "obs_words", "status_rows",
+                                 "iters_rows", "corr_dtype", "status_float", "corr_noncontig", "host_tensors"])
+@pytest.mark.parametrize("call", ["decode", "decode_noalloc"])
+def test_decoder_rejects_mis_sized_tensors_before_any_launch(bad, call, monkeypatch):
+    torch = pytest.importorskip("torch")
+    from paper_2512_07057_gb300 import decoder as D
+    dec, trap = _unbound_decoder()
+    monkeypatch.setattr(D, "B", trap)
+    synd, out = _good_io(torch)
+    if bad == "synd_words":
+        synd = torch.zeros((5, 2), dtype=torch.int32)
+    elif bad == "synd_1d":
+        synd = torch.zeros(15, dtype=torch.int32)
+    elif bad == "corr_rows":
+        out.corrections = torch.zeros((4, 5), dtype=torch.int32)
+    elif bad == "corr_words":
+        out.corrections = torch.zeros((5, 4), dtype=torch.int32)
+    elif bad == "obs_words":
+        out.obs_flips = torch.zeros((5, 0), dtype=torch.int32)
+    elif bad == "status_rows":
+        out.status = torch.zeros(4, dtype=torch.int32)
+    elif bad == "iters_rows":
+        out.iters = torch.zeros(6, dtype=torch.int32)
+    elif bad == "corr_dtype":
+        out.corrections = torch.zeros((5, 5), dtype=torch.int64)
+    elif bad == "status_float":
+        out.status = torch.zeros(5, dtype=torch.float32)
+    elif bad == "corr_noncontig":
+        out.corrections = torch.zeros((5, 10), dtype=torch.int32)[:, ::2]
+    # "host_tensors": every size is right, but nothing is on the decoder's device
+    with pytest.raises(ValueError):
+        if call == "decode":
+            dec.decode(synd, out)
+        else:
+            dec.decode_noalloc(synd, out)

@@ -70,3 +70,35 @@ def test_noalloc_rejects_a_shot_larger_than_the_scratch():
     assert dec.decode_noalloc(synd, out) == B.BSD_ERR_SCRATCH
     assert "scratch" in B.bsd_error_string(B.BSD_ERR_SCRATCH)
     dec.close()
+
+
+def test_noalloc_16bit_messages():
+    """16-bit message storage: a decoder that re-runs near-tie shots in single
+    precision needs a second decoder's buffers, so the allocation-free call
+    refuses it; with the re-runs switched off it returns what bsd_decode
+    returns, on two calls in a row."""
+    prob = W.bb144_code_capacity(0.05)
+    shots = W.sample_shots(prob, 2_000, "noalloc_fp16")
+    synd = D.to_torch_words(shots.syndromes)
+    with_reruns = D.BeamSearchDecoder(prob, D.make_params("beam32_340iters", ms_scale=0.625,
+                                                          msg_precision=B.BSD_FP16, tie_guard_rel=1e-3))
+    out = with_reruns.alloc_outputs(shots.B)
+    assert with_reruns.decode_noalloc(synd, out) == B.BSD_ERR_UNSUPPORTED
+    with_reruns.close()
+    dec = D.BeamSearchDecoder(prob, D.make_params("beam32_340iters", ms_scale=0.625,
+                                                  msg_precision=B.BSD_FP16, tie_guard_rel=-1.0))
+    ref = _arrays(dec.decode(synd))
+    torch.cuda.synchronize()
+    assert (ref["status"] & 24).sum() == 0        # no near-tie flag, no re-run
+    for call in range(2):
+        out = dec.alloc_outputs(shots.B)
+        for t in (out.corrections, out.obs_flips, out.status, out.iters):
+            t.fill_(-1)
+        rc = dec.decode_noalloc(synd, out)
+        assert rc == B.BSD_OK, B.bsd_error_string(rc)
+        torch.cuda.synchronize()
+        got = _arrays(out)
+        for k in ref:
+            assert np.array_equal(got[k], ref[k]), f"call {call}: {k} differs"
+    assert (ref["status"] == 2).sum() > 0
+    dec.close()
