@@ -49,6 +49,16 @@ class _Trace(C.Structure):
          ("ret_round", C.c_int32), ("ret_canon", C.c_int32)]
 
 
+class _DLog(C.Structure):
+    _fields_ = [("cap", C.c_int32), ("n", C.c_int32)] + \
+        [(nm, C.POINTER(C.c_int32)) for nm in ("call", "round", "t", "kind", "nties")] + \
+        [("key", C.POINTER(C.c_uint64)), ("gap", C.POINTER(C.c_double))]
+
+
+# kinds of decision-log records
+LOG_ITER, LOG_ARGMIN, LOG_PRUNE, LOG_RESULT = 0, 1, 2, 3
+
+
 @dataclass
 class Params:
     """Beam search parameters (Alg. 3) plus the readings' constants."""
@@ -89,6 +99,14 @@ def _lib(precision: str) -> C.CDLL:
     if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(src):
         from . import build_oracle
         build_oracle.build()
+    _LIBS[precision] = load_library(path, precision)
+    return _LIBS[precision]
+
+
+def load_library(path: str, precision: str) -> C.CDLL:
+    """Load a build of bsd_oracle.c at `path` (the packaged ones, or a copy
+    compiled elsewhere, e.g. by a test that checks the pins catch a planted
+    mistake) and declare its entry points."""
     lib = C.CDLL(path)
     rt = C.c_double if precision == "f64" else C.c_float
     P = C.c_void_p
@@ -97,6 +115,8 @@ def _lib(precision: str) -> C.CDLL:
     lib.oracle_graph_destroy.argtypes = [P]
     lib.oracle_decode.argtypes = [P, C.POINTER(_Params), P, P, P, P, P, P, C.POINTER(_Trace)]
     lib.oracle_decode_batch.argtypes = [P, C.POINTER(_Params), P, C.c_int64, P, P, P, P, P, P, C.c_int]
+    lib.oracle_decode_logged.argtypes = [P, C.POINTER(_Params), P, P, P, P, P, P, C.POINTER(_DLog)]
+    lib.oracle_decode_logged.restype = C.c_int
     lib.oracle_masked_bp.argtypes = [P, C.POINTER(_Params), P, P, P, P, C.c_int, C.c_int,
                                      P, P, P, P, P, P]
     lib.oracle_masked_bp.restype = C.c_int
@@ -105,7 +125,6 @@ def _lib(precision: str) -> C.CDLL:
     lib.oracle_round_storage.argtypes = [P, C.c_int, C.c_int]
     lib._real = rt
     lib._np_real = np.float64 if precision == "f64" else np.float32
-    _LIBS[precision] = lib
     return lib
 
 
@@ -116,8 +135,8 @@ def _ptr(a: np.ndarray):
 class Graph:
     """The oracle's own copy of (H, A, p)."""
 
-    def __init__(self, prob, precision: str = "f64"):
-        self.lib = _lib(precision)
+    def __init__(self, prob, precision: str = "f64", lib: C.CDLL | None = None):
+        self.lib = lib if lib is not None else _lib(precision)
         self.precision = precision
         self.M, self.N, self.K = int(prob.M), int(prob.N), int(prob.K)
         self._keep = [np.ascontiguousarray(prob.H_row_ptr, np.int32),
@@ -189,6 +208,39 @@ class Graph:
         return dict(ehat=e, status=int(st[0]), iters=int(it[0]), min_gap=float(gap[0]), ties=int(nt[0]),
                     trace=trace)
 
+    def decode_log(self, s_bits: np.ndarray, params: Params, cap: int = 1 << 16) -> dict:
+        """One syndrome (M bytes) with its decision log: one record per BP
+        iteration (kind 0: signs of the messages and of e^(t)), per next_pos
+        (kind 1), per kept set of a round (kind 2) and per choice among
+        results (kind 3), in the sequential algorithm's order.  Each record
+        has the call (0 = seed BP, then children in visit order), round,
+        iteration, a key of its outcome, its smallest nonzero relative margin
+        and its number of exact ties."""
+        s = np.ascontiguousarray(s_bits, np.uint8).reshape(self.M)
+        e = np.zeros(self.N, np.uint8)
+        st = np.zeros(1, np.int32)
+        it = np.zeros(1, np.int64)
+        gap = np.zeros(1, np.float64)
+        nt = np.zeros(1, np.int32)
+        ints = {nm: np.zeros(cap, np.int32) for nm in ("call", "round", "t", "kind", "nties")}
+        key = np.zeros(cap, np.uint64)
+        lg = np.zeros(cap, np.float64)
+        d = _DLog()
+        d.cap = cap
+        for nm, a in ints.items():
+            setattr(d, nm, a.ctypes.data_as(C.POINTER(C.c_int32)))
+        d.key = key.ctypes.data_as(C.POINTER(C.c_uint64))
+        d.gap = lg.ctypes.data_as(C.POINTER(C.c_double))
+        p = params._c()
+        full = self.lib.oracle_decode_logged(self.h, C.byref(p), _ptr(s), _ptr(e), _ptr(st), _ptr(it), _ptr(gap),
+                                             _ptr(nt), C.byref(d))
+        if full:
+            raise RuntimeError("decision log capacity exceeded")
+        n = d.n
+        log = {nm: a[:n].copy() for nm, a in ints.items()}
+        log.update(key=key[:n].copy(), gap=lg[:n].copy())
+        return dict(ehat=e, status=int(st[0]), iters=int(it[0]), min_gap=float(gap[0]), ties=int(nt[0]), log=log)
+
     # ------------------------------------------------------------- masked BP
     def masked_bp(self, E_in, masked, val, s_bits, max_iters: int, params: Params,
                   stop_on_success: bool = True, record: bool = False) -> dict:
@@ -235,6 +287,25 @@ def round_storage(x: np.ndarray, mode: int) -> np.ndarray:
 
 
 STATUS_NEAR_TIE = 8
+
+
+def first_divergence(log_a: dict, log_b: dict) -> int:
+    """Index of the first record where two decision logs of the same shot
+    differ (call, kind, iteration or outcome key), or the length of the
+    shorter one when one is a prefix of the other, or -1 when they are equal."""
+    n = min(len(log_a["key"]), len(log_b["key"]))
+    for k in range(n):
+        if (log_a["call"][k] != log_b["call"][k] or log_a["kind"][k] != log_b["kind"][k]
+                or log_a["t"][k] != log_b["t"][k] or log_a["key"][k] != log_b["key"][k]):
+            return k
+    return -1 if len(log_a["key"]) == len(log_b["key"]) else n
+
+
+def near_tie_before(log: dict, upto: int, threshold: float) -> bool:
+    """Does the log hold a decision with an exact tie or a relative margin
+    below threshold among its records 0..upto (inclusive)?"""
+    hi = len(log["key"]) if upto < 0 else min(upto + 1, len(log["key"]))
+    return bool((log["nties"][:hi] > 0).any() or (log["gap"][:hi] < threshold).any())
 
 
 # Table I of the paper: (max_rounds, beam_width, initial_iters, iters_per_round, num_results)

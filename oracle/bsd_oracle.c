@@ -54,6 +54,16 @@
  *       any precision
  *   R17 weighted min-sum: a weight w[t'][e] per edge in place of alpha, with
  *       t' = min(t, T) - 1 and t counted from 1 in every BP call
+ *   R19 near-tie log (every build): each decision taken in floating point is
+ *       logged with its relative margin -- the sign of every Lambda_j(t) and
+ *       E_{j->i}(t) formed (|sum| / max(1, sum of |terms|)), every argmin
+ *       (second smallest minus smallest over max(1, second)), the order of
+ *       each round's kept set and, before the last round, the boundary
+ *       between the last kept and the first dropped child ((a - b) /
+ *       max(1, |a|)), and the choice of minimum weight among results; a
+ *       margin of exactly 0 is an exact tie.  Per shot: the smallest nonzero
+ *       margin and the number of exact ties, and on request the decision log
+ *       (oracle_decode_logged) that places each one in the run
  *   Score and weight arithmetic:
  *     double build: score = (sum over U of |sum_LLR[j]| added in ascending
  *                   order) / iters; weight = sum of Lambda_j over the support
@@ -279,17 +289,72 @@ typedef struct {
    a score order, a weight order): the smallest nonzero relative margin, and
    the number of exact ties (margin 0).  R5 and R7 settle an exact tie the
    same way in any precision only when both precisions compute equal values;
-   a lower precision can also split an exact tie of this build. */
+   a lower precision can also split an exact tie of this build.
+
+   The relative margin of a sign decision on a sum is |sum| / max(1, sum of
+   the magnitudes of its terms); of an order decision between a > b it is
+   (a - b) / max(1, |a|). */
 static int g_ties_tls_dummy;
 static _Thread_local int *g_tie_counter = &g_ties_tls_dummy;
 
-static void gap_update(double *g, double value, double scale)
+static void margin_note(double *g, int *nties, double value, double scale)
 {
     double s = scale > 1.0 ? scale : 1.0;
     double r = fabs(value) / s;
-    if (r == 0) { ++*g_tie_counter; return; }
+    if (r == 0) { ++*nties; return; }
     if (r < *g) *g = r;
 }
+
+static void gap_update(double *g, double value, double scale)
+{
+    margin_note(g, g_tie_counter, value, scale);
+}
+
+/* Decision log (optional, one shot at a time): one record per decision
+   group, in the order the sequential algorithm takes them, so that two runs
+   of the same shot (double and single precision) can be compared record by
+   record up to their first different outcome.
+     kind 0  BP iteration t of a call: key = hash of the signs of every
+             stored E_{j->i}(t) and of e^(t); margins of the signs of every
+             Lambda_j(t) and E_{j->i}(t) formed (Eqs. 2-4)
+     kind 1  next_pos of a call (Alg. 3 argmin): key = next_pos; margin
+             between the smallest and second smallest |sum_LLR|
+     kind 2  the kept set of a round (Alg. 3 pruning, App. B): key = hash of
+             the kept canonical indices in rank order; margins between
+             consecutive kept scores and, before the last round, between the
+             last kept and the first dropped child
+     kind 3  the returned element of results (App. B minimum weight): key =
+             its index; margins between its weight and every other
+   Calls are numbered in visit order: 0 the seed BP, then every child. */
+typedef struct {
+    int32_t cap, n;
+    int32_t *call, *round, *t, *kind, *nties;
+    uint64_t *key;
+    double *gap;             /* smallest nonzero relative margin of the record (inf if none) */
+} oracle_dlog;
+
+static _Thread_local oracle_dlog *g_dlog = NULL;
+static _Thread_local int g_call = 0, g_round = 0;
+
+static void log_push(int kind, int t, uint64_t key, double gap, int nties)
+{
+    oracle_dlog *d = g_dlog;
+    if (!d || d->n >= d->cap) return;
+    const int k = d->n++;
+    d->call[k] = g_call; d->round[k] = g_round; d->t[k] = t; d->kind[k] = kind;
+    d->key[k] = key; d->gap[k] = gap; d->nties[k] = nties;
+}
+
+/* 64-bit FNV-1a over a sequence of small values */
+static uint64_t fnv_add(uint64_t h, uint64_t v)
+{
+    for (int b = 0; b < 8; ++b) {
+        h ^= (v >> (8 * b)) & 0xffu;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+#define FNV_INIT 14695981039346656037ull
 
 static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *c, bp_work *w)
 {
@@ -342,6 +407,8 @@ static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *
             }
         }
         /* Eqs. 2-3 for unmasked nodes, summing in ascending order (R5) */
+        double it_gap = INFINITY;
+        int it_ties = 0;
         for (int j = 0; j < N; ++j) {
             if (c->masked[j]) { w->post[j] = 0; continue; }
             int deg = g->col_ptr[j + 1] - g->col_ptr[j];
@@ -364,7 +431,7 @@ static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *
                 scale += fabs((double)w->vbuf[k]);
             }
             w->post[j] = post;                       /* Eq. 3 */
-            gap_update(&c->min_gap, (double)post, scale);
+            margin_note(&it_gap, &it_ties, (double)post, scale);
             for (int k = 0; k < deg; ++k) {          /* Eq. 2: leave d_i out */
                 real acc = g->lam[j];
                 double sc = fabs((double)g->lam[j]);
@@ -373,7 +440,7 @@ static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *
                     acc += w->vbuf[k2];
                     sc += fabs((double)w->vbuf[k2]);
                 }
-                gap_update(&c->min_gap, (double)acc, sc);
+                margin_note(&it_gap, &it_ties, (double)acc, sc);
                 if (acc > LMAX) acc = LMAX;          /* R4 */
                 if (acc < -LMAX) acc = -LMAX;
                 Em[w->ebuf[k]] = store_msg(prm, acc);
@@ -385,6 +452,14 @@ static void masked_bp(const oracle_graph *g, const oracle_params *prm, bp_call *
             c->ehat[j] = c->masked[j] ? 0 : (uint8_t)(w->post[j] <= 0);
         if (c->llr_traj)
             for (int j = 0; j < N; ++j) c->llr_traj[(size_t)(t - 1) * N + j] = w->post[j];
+        if (it_gap < c->min_gap) c->min_gap = it_gap;
+        *g_tie_counter += it_ties;
+        if (g_dlog) {
+            uint64_t h = FNV_INIT;
+            for (int e = 0; e < E; ++e) h = fnv_add(h, Em[e] < 0);
+            for (int j = 0; j < N; ++j) h = fnv_add(h, c->ehat[j]);
+            log_push(0, t, h, it_gap, it_ties);
+        }
         c->iters = t;
         /* stopping rule: H e(t) = s' */
         int ok = 1;
@@ -578,10 +653,11 @@ static void tie_check(dec_ctx *x, double gap_rel)
 }
 
 /* margin at the pruning boundary of a round: the relative score gap between
-   the last kept child (rank w-1) and the first dropped one (rank w) */
-static void pruning_margin(dec_ctx *x, int w)
+   the last kept child (rank w-1) and the first dropped one (rank w); inf when
+   the round has no more than w children (nothing is dropped) */
+static double pruning_margin(dec_ctx *x, int w)
 {
-    if (x->nr <= w) return;
+    if (x->nr <= w) return INFINITY;
     /* rank the round's children by (score desc, canonical index asc) */
     for (int a = 1; a < x->nr; ++a)
         for (int k = a; k > 0; --k) {
@@ -593,7 +669,7 @@ static void pruning_margin(dec_ctx *x, int w)
         }
     const double s0 = x->rscore[w - 1], s1 = x->rscore[w];
     const double den = fabs(s0) > 1.0 ? fabs(s0) : 1.0;
-    tie_check(x, (s0 - s1) / den);
+    return (s0 - s1) / den;
 }
 
 static void ctx_free(dec_ctx *x)
@@ -629,11 +705,15 @@ static int results_best(dec_ctx *x, double *min_gap)
     int best = 0;
     for (int r = 1; r < x->nres; ++r)
         if (x->res_w[r] < x->res_w[best]) best = r;
-    if (min_gap) {
-        for (int r = 0; r < x->nres; ++r) {
-            if (r == best || x->res_w[r] == x->res_w[best]) continue;
-            gap_update(min_gap, x->res_w[r] - x->res_w[best], fabs(x->res_w[best]));
-        }
+    if (x->nres > 1) {
+        /* an equal weight is an exact tie, settled by the order found (R11) */
+        double g = INFINITY;
+        int nt = 0;
+        for (int r = 0; r < x->nres; ++r)
+            if (r != best) margin_note(&g, &nt, x->res_w[r] - x->res_w[best], fabs(x->res_w[best]));
+        if (min_gap && g < *min_gap) *min_gap = g;
+        *g_tie_counter += nt;
+        log_push(3, 0, (uint64_t)best, g, nt);
     }
     return best;
 }
@@ -673,6 +753,8 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
 {
     int ties = 0;
     g_tie_counter = &ties;
+    g_call = 0;
+    g_round = 0;
     const oracle_graph *g = x->g;
     const oracle_params *prm = x->prm;
     const int N = g->N, E = g->E;
@@ -706,6 +788,7 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
     seed->next_pos = least_reliable(g, x->sum_llr, x->cmask, &agap);
     if (agap == 0) ++*g_tie_counter;
     else if (agap < gap) gap = agap;
+    log_push(1, 0, (uint64_t)(int64_t)seed->next_pos, agap == 0 ? INFINITY : agap, agap == 0);
     seed->score = 0;
     seed->canon = 0;
     memset(seed->masked, 0, (size_t)N);
@@ -725,6 +808,7 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
     for (int r = 1; r <= prm->max_rounds && !done; ++r) {
         x->nnxt = 0;
         x->nr = 0;
+        g_round = r;
         for (int pr = 0; pr < x->ncur && !done; ++pr) {
             path_t *par = &x->cur[pr];
             if (par->next_pos < 0) continue;                       /* R9 */
@@ -740,6 +824,7 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
                 c->E_in = par->E; c->masked = x->cmask; c->val = x->cval; c->s = s;
                 c->max_iters = prm->iters_per_round; c->stop_on_success = 1;
                 c->E_out = ch->E; c->sum_llr = x->sum_llr; c->ehat = ch->ehat; c->llr_traj = NULL;
+                ++g_call;
                 masked_bp(g, prm, c, &x->w);
                 if (c->min_gap < gap) gap = c->min_gap;
                 total += c->iters;
@@ -749,6 +834,8 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
                 ch->next_pos = least_reliable(g, x->sum_llr, x->cmask, &agap);
                 if (ch->next_pos >= 0 && agap == 0) ++*g_tie_counter;
                 else if (ch->next_pos >= 0 && agap < gap) gap = agap;
+                log_push(1, 0, (uint64_t)(int64_t)ch->next_pos, agap == 0 ? INFINITY : agap,
+                         ch->next_pos >= 0 && agap == 0);
                 ch->score = path_score(g, x->sum_llr, x->cmask, c->iters, x->tmp);
                 ch->canon = canon;
                 if (ch->next_pos >= 0) tie_check(x, agap);
@@ -780,12 +867,29 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
             }
         }
         if (done) break;
-        if (r < prm->max_rounds) pruning_margin(x, w);
+        /* the round's pruning decisions: the boundary between kept and
+           dropped (before the last round; it flags a near tie, R16) and the
+           order of the kept set (the visit order of the next round, and in
+           the last round the path R10 falls back to) */
+        double pg = INFINITY;
+        int pties = 0;
+        if (r < prm->max_rounds) {
+            const double bm = pruning_margin(x, w);
+            tie_check(x, bm);
+            if (bm < INFINITY) margin_note(&pg, &pties, bm, 1.0);
+        }
         /* the new set, explored next round in descending score (App. B) */
         sort_paths(x->nxt, x->nnxt);
         if (prm->prune_mode == 1 && x->nnxt > w) x->nnxt = w;     /* Alg. 3: keep the top beam_width */
         for (int k = 0; k + 1 < x->nnxt; ++k)
-            gap_update(&gap, x->nxt[k].score - x->nxt[k + 1].score, fabs(x->nxt[k].score));
+            margin_note(&pg, &pties, x->nxt[k].score - x->nxt[k + 1].score, fabs(x->nxt[k].score));
+        if (pg < gap) gap = pg;
+        *g_tie_counter += pties;
+        if (g_dlog) {
+            uint64_t h = FNV_INIT;
+            for (int k = 0; k < x->nnxt; ++k) h = fnv_add(h, (uint64_t)x->nxt[k].canon);
+            log_push(2, 0, h, pg, pties);
+        }
         if (tr)
             for (int k = 0; k < x->nnxt; ++k)
                 if (x->nxt[k].trace_idx >= 0) tr->kept[x->nxt[k].trace_idx] = k;
@@ -811,6 +915,21 @@ static void decode_one(dec_ctx *x, const uint8_t *s, uint8_t *out_e, int32_t *st
     if (min_gap) *min_gap = gap;
     if (n_ties) *n_ties = ties;
     g_tie_counter = &g_ties_tls_dummy;
+}
+
+/* One syndrome with its decision log (see oracle_dlog); the outputs are
+   those of oracle_decode.  Returns 0, or 1 if the log ran out of room. */
+int oracle_decode_logged(const oracle_graph *g, const oracle_params *prm, const uint8_t *s,
+                         uint8_t *ehat, int32_t *status, int64_t *iters, double *min_gap,
+                         int32_t *n_ties, oracle_dlog *log)
+{
+    dec_ctx *x = ctx_new(g, prm);
+    log->n = 0;
+    g_dlog = log;
+    decode_one(x, s, ehat, status, iters, min_gap, n_ties, NULL);
+    g_dlog = NULL;
+    ctx_free(x);
+    return log->n >= log->cap ? 1 : 0;
 }
 
 /* ------------------------------------------------------------------------- */

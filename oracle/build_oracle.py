@@ -21,6 +21,13 @@ CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-s
           "-Wall", "-Wno-unused-function"]
 
 
+def compile_library(src: str, out: str, single: bool = False) -> None:
+    """Compile one build of an oracle source file (double, or single with
+    single=True) into the shared library `out`."""
+    cmd = ["gcc", *CFLAGS, *(["-DORACLE_FP32"] if single else []), "-o", out, src, "-lm", "-lpthread"]
+    subprocess.run(cmd, check=True)
+
+
 def _needs(out: str) -> bool:
     return not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC)
 
@@ -32,8 +39,7 @@ def build(force: bool = False) -> None:
         if not force and not _needs(out):
             return
         tmp = out + f".tmp{os.getpid()}"
-        cmd = ["gcc", *CFLAGS, *extra, "-o", tmp, SRC, "-lm", "-lpthread"]
-        subprocess.run(cmd, check=True)
+        compile_library(SRC, tmp, single=bool(extra))
         os.replace(tmp, out)
 
     with ThreadPoolExecutor(len(TARGETS)) as ex:

@@ -17,6 +17,7 @@ import oracle  # noqa: E402
 from paper_2512_07057_gb300 import binding as B  # noqa: E402
 from paper_2512_07057_gb300 import decoder as D  # noqa: E402
 from paper_2512_07057_gb300 import workloads as W  # noqa: E402
+from parity_f64 import check_against_f64  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -179,6 +180,7 @@ def test_full_size_phenomenological_sampled(prec):
                     ms_scale=0.625, llr_clamp=1e4)
         exp = oracle.Graph(prob, "f32").decode_batch(shots.syndromes[idx], oracle.Params(**base), nthreads=16)
         exp = {k: exp[k] for k in ("corrections", "obs", "status", "iters")}
+        check_against_f64(prob, oracle.Params(**base), shots.syndromes[idx], sub, nthreads=16)
     else:
         exp, _ = _expected(prob, params, shots.syndromes[idx], prec)
     _check(sub, exp, prob.K)

@@ -464,3 +464,204 @@ def test_near_tie_flags(oracle_mod):
     for k in ("corrections", "iters"):
         assert np.array_equal(r0[k], r2[k])
     assert np.array_equal(r0["status"], r2["status"] & ~np.uint32(8))
+
+
+# ----------------------------------------------------------------------------
+# Near-tie logging: hand-worked margins, exact ties and status bit 8
+# ----------------------------------------------------------------------------
+def _priors(lam):
+    """Priors whose Lambda_j = log((1-p_j)/p_j) are the given values."""
+    return 1.0 / (1.0 + np.exp(np.asarray(lam, np.float64)))
+
+
+def _golden_params(oracle_mod, q, guard=0.0):
+    return oracle_mod.Params(max_rounds=q["max_rounds"], beam_width=q["beam_width"],
+                             initial_iters=q["initial_iters"], iters_per_round=q["iters_per_round"],
+                             num_results=1, ms_scale=q["alpha"], llr_clamp=q["llr_clamp"], tie_guard=guard)
+
+
+def _close(a, b, rel):
+    if b == "inf":
+        return a == np.inf
+    return abs(a - b) <= rel * abs(b)
+
+
+def _near_tie_sign_margins(oracle_mod, G_for, rel):
+    g = _golden("near_tie_sign_margins.json")
+    pr = g["problem"]
+    for name, case in g["cases"].items():
+        G = G_for(_dense_problem(pr["H"], _priors(case["Lambda"])))
+        r = G.decode_log(np.array(pr["syndrome"]), _golden_params(oracle_mod, pr["params"]))
+        exp = case["expected"]
+        assert r["status"] == exp["status"] and list(r["ehat"]) == exp["ehat"] and r["iters"] == exp["iters"], name
+        assert _close(r["min_gap"], exp["min_gap"], rel), (name, r["min_gap"])
+        assert r["ties"] == exp["ties"], (name, r["ties"])
+        lg = r["log"]
+        for k, rec in enumerate(exp.get("records", [])):
+            assert (lg["kind"][k], lg["call"][k], lg["t"][k], lg["nties"][k]) == \
+                (rec["kind"], rec["call"], rec["t"], rec["nties"]), (name, k)
+            assert _close(lg["gap"][k], rec["gap"], rel), (name, k, lg["gap"][k])
+            if "key" in rec:
+                assert int(lg["key"][k]) == rec["key"]
+
+
+def _near_tie_argmin(oracle_mod, G_for, rel):
+    g = _golden("near_tie_argmin.json")
+    pr = g["problem"]
+    G = G_for(_dense_problem(pr["H"], _priors(pr["Lambda"])))
+    exp = g["expected"]
+    for guard, st in exp["status_by_guard"].items():
+        r = G.decode_log(np.array(pr["syndrome"]), _golden_params(oracle_mod, pr["params"], float(guard)))
+        assert r["status"] == st, (guard, r["status"])
+        assert list(r["ehat"]) == exp["ehat"] and r["iters"] == exp["iters"]
+        assert _close(r["min_gap"], exp["min_gap"], rel), r["min_gap"]
+        assert r["ties"] == exp["ties"], r["ties"]
+        lg = r["log"]
+        am = np.nonzero(lg["kind"] == oracle_mod.LOG_ARGMIN)[0]
+        assert len(am) == len(exp["argmin_records"])
+        for k, rec in zip(am, exp["argmin_records"]):
+            assert lg["call"][k] == rec["call"] and int(lg["key"][k]) == rec["key"]
+            assert _close(lg["gap"][k], rec["gap"], rel), (k, lg["gap"][k])
+        # the iteration records of every call: t = 1..iters in order
+        it = lg["kind"] == oracle_mod.LOG_ITER
+        assert list(lg["t"][it]) == [1, 2, 3, 4, 1, 2, 3, 1, 2, 3]
+
+
+def _near_tie_pruning(oracle_mod, G_for, rel):
+    g = _golden("near_tie_pruning.json")
+    pr = g["problem"]
+    G = G_for(_dense_problem(pr["H"], _priors(pr["Lambda"])))
+    exp = g["expected"]
+    for guard, st in exp["status_by_guard"].items():
+        r = G.decode_log(np.array(pr["syndrome"]), _golden_params(oracle_mod, pr["params"], float(guard)))
+        assert r["status"] == st, (guard, r["status"])
+        assert list(r["ehat"]) == exp["ehat"] and r["iters"] == exp["iters"]
+        assert _close(r["min_gap"], exp["min_gap"], rel), r["min_gap"]
+        assert r["ties"] == exp["ties"], r["ties"]
+        lg = r["log"]
+        pk = np.nonzero(lg["kind"] == oracle_mod.LOG_PRUNE)[0]
+        assert len(pk) == len(exp["prune_records"])
+        for k, rec in zip(pk, exp["prune_records"]):
+            assert lg["round"][k] == rec["round"] and lg["nties"][k] == rec["nties"]
+            assert _close(lg["gap"][k], rec["gap"], rel), (rec["round"], lg["gap"][k])
+        am = lg["kind"] == oracle_mod.LOG_ARGMIN
+        assert [int(x) for x in lg["key"][am]] == exp["argmin_records"]["keys"]
+        assert list(lg["nties"][am]) == exp["argmin_records"]["nties"]
+        it = np.nonzero(lg["kind"] == oracle_mod.LOG_ITER)[0]
+        assert len(it) == len(exp["iteration_gaps"])
+        for k, gv in zip(it, exp["iteration_gaps"]):
+            assert _close(lg["gap"][k], gv, rel) and lg["nties"][k] == 0, (k, lg["gap"][k])
+
+
+_NEAR_TIE_PINS = (_near_tie_sign_margins, _near_tie_argmin, _near_tie_pruning)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("pin", _NEAR_TIE_PINS, ids=lambda f: f.__name__[1:])
+def test_near_tie_hand_worked(oracle_mod, precision, pin):
+    """Sign margins and exact ties (Eqs. 2-4), the argmin runner-up margin
+    (Alg. 3), the pruning margin between ranks w-1 and w (App. B), the
+    smallest margin, the tie count and status bit 8 against hand-worked
+    values; the single-precision build within its rounding (scores on the
+    2^-16 grid)."""
+    rel = 1e-9 if precision == "f64" else 2e-3
+    pin(oracle_mod, lambda prob: oracle_mod.Graph(prob, precision), rel)
+
+
+# planted mistakes in the near-tie logic: (description, original text, replacement)
+_MUTANTS = [
+    ("pruning margin between ranks w and w+1",
+     "const double s0 = x->rscore[w - 1], s1 = x->rscore[w];",
+     "const double s0 = x->rscore[w], s1 = x->rscore[w + 1];"),
+    ("pruning margin between ranks w-2 and w-1",
+     "const double s0 = x->rscore[w - 1], s1 = x->rscore[w];",
+     "const double s0 = x->rscore[w - 2], s1 = x->rscore[w - 1];"),
+    ("argmin margin relative to the smallest instead of the runner-up",
+     "double s = fabs((double)second) > 1.0 ? fabs((double)second) : 1.0;",
+     "double s = fabs((double)bv) > 1.0 ? fabs((double)bv) : 1.0;"),
+    ("runner-up = first node seen after the smallest",
+     "} else if (!have_second || v < second) {",
+     "} else if (!have_second) {"),
+    ("sign margin without the message terms in its scale",
+     "                scale += fabs((double)w->vbuf[k]);\n",
+     ""),
+    ("exact ties flagged as near ties",
+     "if (x->prm->tie_guard > 0 && gap_rel > 0 && gap_rel < x->prm->tie_guard)",
+     "if (x->prm->tie_guard > 0 && gap_rel >= 0 && gap_rel < x->prm->tie_guard)"),
+    ("pruning margin not flagged",
+     "            tie_check(x, bm);\n",
+     ""),
+]
+
+
+@pytest.mark.parametrize("mutant", _MUTANTS, ids=[m[0] for m in _MUTANTS])
+def test_near_tie_pins_catch_planted_mistakes(oracle_mod, tmp_path, mutant):
+    """Each planted mistake in the oracle's near-tie logic (a copy of the
+    source compiled here, on the CPU) makes at least one hand-worked pin fail."""
+    from oracle import build_oracle
+    _, old, new = mutant
+    src = open(build_oracle.SRC).read()
+    assert src.count(old) == 1, "the planted mistake no longer matches the source"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    lib_path = str(tmp_path / "libmutant.so")
+    build_oracle.compile_library(str(path), lib_path)
+    lib = oracle_mod.load_library(lib_path, "f64")
+    failed = 0
+    for pin in _NEAR_TIE_PINS:
+        try:
+            pin(oracle_mod, lambda prob: oracle_mod.Graph(prob, "f64", lib=lib), 1e-9)
+        except AssertionError:
+            failed += 1
+    assert failed > 0
+
+
+def test_decision_log_summarises_the_run(oracle_mod):
+    """The decision log's records reproduce the run's near-tie summary (the
+    smallest nonzero margin and the tie count), leave its outputs unchanged,
+    and two runs of the same build have equal logs."""
+    prob, sh = _bb_shots(0.05, 60, "dlog")
+    prm = oracle_mod.Params(max_rounds=10, beam_width=8, initial_iters=50, iters_per_round=20, ms_scale=0.625)
+    s_all = W.unpack_bits(sh.syndromes, prob.M)
+    for precision in ("f64", "f32"):
+        G = oracle_mod.Graph(prob, precision)
+        for b in range(sh.B):
+            r = G.decode_log(s_all[b], prm)
+            r0 = G.decode_one(s_all[b], prm)
+            assert (r["status"], r["iters"], list(r["ehat"])) == (r0["status"], r0["iters"], list(r0["ehat"]))
+            lg = r["log"]
+            assert r["ties"] == r0["ties"] == int(lg["nties"].sum())
+            assert r["min_gap"] == r0["min_gap"] == float(lg["gap"].min())
+            assert oracle_mod.first_divergence(lg, G.decode_log(s_all[b], prm)["log"]) == -1
+            # records: the seed's iterations, its argmin, then per child its
+            # iterations and argmin, a kept set per finished round
+            assert lg["call"][0] == 0 and lg["kind"][0] == oracle_mod.LOG_ITER and lg["t"][0] == 1
+            assert np.all(np.diff(lg["call"]) >= 0)
+
+
+def test_f64_parity_rule_on_the_single_precision_build(oracle_mod):
+    """The rule the GPU tests apply against double precision, checked with the
+    oracle's single-precision build in the GPU's place: it holds on the
+    [[72,12,6]] workload, and it rejects a mismatch planted on a shot whose
+    double-precision run has no near tie."""
+    import parity_f64
+    prob = W.bb72_code_capacity(0.03)
+    sh = W.sample_shots(prob, 10_000, "bb72_cc_p0.03")
+    prm = oracle_mod.Params(max_rounds=10, beam_width=8, initial_iters=50, iters_per_round=20, ms_scale=0.625)
+    r32 = oracle_mod.Graph(prob, "f32").decode_batch(sh.syndromes, prm, nthreads=8)
+    counts, r64 = parity_f64.check_against_f64(prob, prm, sh.syndromes, r32, nthreads=8)
+    assert counts["mismatches"] == counts["near_tie_1e4"]
+    calm = np.nonzero((r64["min_gap"] > 1e-3) & (r64["ties"] == 0) & (r64["status"] == 2))[0]
+    planted = {k: v.copy() for k, v in r32.items()}
+    planted["corrections"][calm[0], 0] ^= 1
+    with pytest.raises(AssertionError, match="no near tie"):
+        parity_f64.check_against_f64(prob, prm, sh.syndromes, planted, ref64=r64)
+    # the divergence search itself
+    a = dict(call=np.array([0, 0, 1]), kind=np.array([0, 1, 0]), t=np.array([1, 0, 1]),
+             key=np.array([5, 7, 9], np.uint64), gap=np.array([0.5, 1e-5, 0.3]), nties=np.array([0, 0, 0]))
+    b = {k: v.copy() for k, v in a.items()}
+    assert oracle_mod.first_divergence(a, b) == -1
+    b["key"][2] = 10
+    assert oracle_mod.first_divergence(a, b) == 2
+    assert oracle_mod.near_tie_before(a, 0, 1e-4) is False
+    assert oracle_mod.near_tie_before(a, 1, 1e-4) is True and oracle_mod.near_tie_before(a, 1, 1e-6) is False
