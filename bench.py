@@ -36,11 +36,15 @@ PS = (0.01, 0.03, 0.05)
 PRESET = "beam32_340iters"
 ALPHA = 0.625
 WORKLOAD = "bb144_code_capacity beam32_340iters alpha=0.625 p={0.01,0.03,0.05}"
-# algorithmic lane operations per message update of min-sum (Eqs. 1-3):
-# check side |x|, min1 and min2 compares, sign parity, select, sign, scale (7);
-# error side add into the posterior, extrinsic add, two-sided clamp (4);
-# per-node posterior bookkeeping amortised over the edges (1)
-OPS_PER_UPDATE = 12
+# algorithmic ALU operations per message update of min-sum (Eqs. 1-3), the
+# count of the algorithm and not of any kernel: on the check side, folding
+# |E_{j->i}| into the row's two smallest magnitudes (a compare-exchange: 2)
+# and its sign into the row's sign parity (1), then selecting the outgoing
+# magnitude (min1, or min2 on the argmin edge) with its sign (1); on the
+# error side, adding D_{i->j} into Lambda_j(t) (1) and forming the extrinsic
+# E_{j->i} = Lambda_j(t) - D_{i->j} (1).  The per-row scale and the per-node
+# hard decision are amortised over the edges and left out.
+OPS_PER_UPDATE = 6
 LANES_PER_SM = 128          # FP32/INT32 lanes per Blackwell SM
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # phenomenological DEM of the [[144,12,12]] code (12 noisy rounds + 1 perfect, 936 x 2592, 6912 edges)
@@ -93,6 +97,12 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shapes (for profiler runs, where tuning timings "
                          "are distorted)")
+    ap.add_argument("--no-side-by-side", action="store_true",
+                    help="headline only: skip the phenomenological-DEM precision forms and the synthetic-DEM widths "
+                         "that the default run adds to its line")
+    ap.add_argument("--side-steps", type=int, default=3, help="timed steps of each side-by-side workload")
+    ap.add_argument("--side-cpu-seconds", type=float, default=6.0,
+                    help="target CPU time of each side-by-side workload's oracle baseline")
     ap.add_argument("--train-steps", type=int, default=300, help="unrolled_training: steps before the LER judgement")
     ap.add_argument("--judge-shots", type=int, default=1_000_000, help="unrolled_training: held-out shots")
     a = ap.parse_args()
@@ -204,26 +214,51 @@ def ler_of(prob, shots, obs, status):
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline line and reference arm)
 # ----------------------------------------------------------------------------
-def oracle_rate(work, target_s: float, nthreads: int, preset: str = PRESET):
+def oracle_run(work, target_s: float, nthreads: int, preset: str = PRESET, n_min: int = 1000,
+               calib: int = 2000) -> dict:
     """Oracle (double precision) on a bounded prefix of each p batch, sized
-    from a short calibration run so the whole sample takes about target_s."""
+    from a short calibration run so the whole sample takes about target_s;
+    returns the rate, the prefix size, the time and the outputs per batch."""
     import oracle
     per = []
     for p, prob, sh in work:
         g = oracle.Graph(prob, "f64")
         prm = oracle.preset(preset, ms_scale=ALPHA)
-        n0 = min(2000, sh.B)
+        n0 = min(calib, sh.B)
         t0 = time.perf_counter()
         g.decode_batch(sh.syndromes[:n0], prm, nthreads=nthreads)
         per.append((g, prm, sh, (time.perf_counter() - t0) / n0))
     # equal shot counts per p (the workload mixes the three p equally)
     sec_per_mix = sum(x[3] for x in per)
-    n = int(max(1000, min(work[0][2].B, target_s / max(sec_per_mix, 1e-9))))
+    n = int(max(n_min, min(work[0][2].B, target_s / max(sec_per_mix, 1e-9))))
+    outs = []
     t0 = time.perf_counter()
     for g, prm, sh, _ in per:
-        g.decode_batch(sh.syndromes[:n], prm, nthreads=nthreads)
+        outs.append(g.decode_batch(sh.syndromes[:n], prm, nthreads=nthreads))
     dt = time.perf_counter() - t0
-    return len(work) * n / dt, n, dt
+    return dict(rate=len(work) * n / dt, n=n, dt=dt, outputs=outs, params=per[0][1])
+
+
+def oracle_rate(work, target_s: float, nthreads: int, preset: str = PRESET):
+    r = oracle_run(work, target_s, nthreads, preset)
+    return r["rate"], r["n"], r["dt"]
+
+
+def cpu_baseline_of(work, target_s: float, preset: str, single_s: float = 4.0) -> tuple[dict, dict]:
+    """The cpu_baseline object: the double-precision oracle on all host
+    threads and, beside it, on one thread (the paper times one core), each on
+    a bounded prefix of every batch; also returns the all-thread run."""
+    nth = cores()
+    r = oracle_run(work, target_s, nth, preset)
+    r1 = oracle_run(work, single_s, 1, preset, n_min=50, calib=200)
+    k = len(work)
+    obj = {"value": r["rate"], "unit": "syndromes/s", "cores": nth, "kind": "oracle",
+           "sample": f"first {r['n']} shots of each of the {k} batches, double-precision oracle, "
+                     f"{r['dt']:.1f} s on {nth} host threads",
+           "single_core": {"value": r1["rate"], "unit": "syndromes/s", "cores": 1,
+                           "sample": f"first {r1['n']} shots of each of the {k} batches, {r1['dt']:.1f} s "
+                                     f"on one host thread"}}
+    return obj, r
 
 
 def cores() -> int:
@@ -433,6 +468,17 @@ def alu_roofline(prof, E: int, dev: int, traffic_case: str, shots: int = 0, msg_
             roofline["traffic"] = per * (dom_iters / max(1, launches[dom]))
             roofline["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum on a {traffic_case}, " \
                                          "scaled by candidate-iterations"
+    # measured DRAM throughput and L2 hit rate of one launch (ncu), against the measured copy bandwidth
+    mr = _memory_record(names[dom], E, msg_bytes)
+    if mr is not None:
+        hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+        roofline["dram_gbs"] = mr["dram_gbs"]
+        roofline["l2_hit"] = mr["l2_hit"]
+        roofline["dram_frac_of_peak"] = mr["dram_gbs"] / hbm_peak
+        roofline["dram_measured"] = {k: mr[k] for k in ("dram_bytes_per_launch", "launch_us_under_ncu", "case",
+                                                       "record")}
+    else:
+        roofline["dram_gbs"] = roofline["l2_hit"] = roofline["dram_frac_of_peak"] = None
     return roofline, exec_iters
 
 
@@ -560,6 +606,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     msg_alg = alg_iters_step * E * world / (steps_total_s / args.steps)
     msg_exec = float(exec_iters.sum()) * E * world / steps_total_s
     # the survey's streaming model: 14.7 B per update if every iteration moved its state through HBM
+    # (context only: the state of this code stays on chip; the measured figure is the roofline's dram_gbs)
     stream_bytes = 2 * 4 * E + 2 * (2 * 4 + 4) * 72 + 8 * 144
     line = {
         "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world, "steps": args.steps,
@@ -572,8 +619,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / args.steps, "round": float(exec_iters[1]) / args.steps},
         "msg_updates_per_s": {"algorithmic": msg_alg, "executed": msg_exec,
                               "executed_per_algorithmic": float(exec_iters.sum() / args.steps / max(alg_iters_step, 1)),
-                              "pct_hbm_peak_streaming_model": 100 * msg_alg * (stream_bytes / E) / (hbm_peak * 1e9 * world),
-                              "streaming_bytes_per_update": stream_bytes / E},
+                              "streaming_model_bytes_per_update": stream_bytes / E},
+        "hbm": {"dram_gbs": roofline["dram_gbs"], "pct_of_peak": (100 * roofline["dram_frac_of_peak"]
+                                                                 if roofline["dram_frac_of_peak"] is not None
+                                                                 else None),
+                "l2_hit": roofline["l2_hit"], "peak_gbs": hbm_peak, "kernel": roofline["kernel"],
+                "source": "ncu on one launch of the dominant kernel (profiles/); null when its sources changed"},
         "roofline": roofline,
         "gpu_launches": int(sum(pr["kernel_launches"] for pr in prof_graph)),
         "profiled_ms_per_step": float(sum(ms_steps_p)) / args.steps,
@@ -584,36 +635,51 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_host(decs, work, args, dev)
     if rank == 0 and not args.no_cpu_baseline:
-        rate, n, dt = oracle_rate(work, args.cpu_seconds, cores())
-        line["cpu_baseline"] = {"value": rate, "unit": "syndromes/s", "cores": cores(), "kind": "oracle",
-                                "sample": f"first {n} shots of each p batch (3 x {n}), double-precision oracle, "
-                                          f"{dt:.1f} s on {cores()} host threads"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+        line["cpu_baseline"], _ = cpu_baseline_of(work, args.cpu_seconds, PRESET)
     for d in decs:
         d.close()
+    if world == 1 and not args.no_side_by_side:
+        line["side_by_side"] = side_by_side(args, dev)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
-def run_precision(args, rank: int, world: int, local_rank: int):
+def side_by_side(args, dev) -> dict:
+    """The metric's comparison in the same run: the phenomenological DEM with
+    the plain FP32 path beside FP16 and BF16 message storage (10^5 shots at
+    each p = q), and the synthetic 936 x 8800 DEM at beam widths 8, 32 and 64
+    (10^6 shots), each with its own roofline, LER and CPU oracle baseline;
+    fewer timed steps than the headline (same timing rules)."""
+    from paper_2512_07057_gb300 import workloads as W
+    t0 = time.perf_counter()
+    steps, warm = args.side_steps, max(3, min(args.warmup, 3))
+    cpu_s = None if args.no_cpu_baseline else args.side_cpu_seconds
+    phen = precision_forms(make_phen_workload(0, PHEN_SHOTS), dev, steps, warm, 1, 0, args.workspace_gb, cpu_s)
+    phen.pop("e2e", None)
+    phen.update(workload=PHEN_WORKLOAD, steps=steps, warmup=warm,
+                fp16_vs_plain_fp32=phen["forms"]["fp16"]["value"] / phen["forms"]["fp32"]["value"],
+                bf16_vs_plain_fp32=phen["forms"]["bf16"]["value"] / phen["forms"]["fp32"]["value"])
+    prob = W.synthetic_dem()
+    sh = W.sample_shots(prob, SYN_SHOTS, W.shot_seed("synthetic_dem", 0))
+    syn = synthetic_widths(prob, sh, dev, steps, warm, 1, 0, args.workspace_gb, cpu_s)
+    syn.update(workload=SYN_WORKLOAD, steps=steps, warmup=warm)
+    return {"phenomenological_dem": phen, "synthetic_dem": syn, "wall_s": time.perf_counter() - t0}
+
+
+def precision_forms(work, dev, steps: int, warmup: int, world: int, rank: int, workspace_gb: float,
+                    cpu_seconds: float | None, e2e_args=None) -> dict:
     """The phenomenological DEM decoded with FP32 (the plain path), FP16 and
-    BF16 message storage, side by side; the line's value is the FP16 form.
-    The cpu_baseline leg decodes a bounded prefix with the double-precision
-    oracle and states, per form, how many decisions differ from it."""
+    BF16 message storage, each timed on the same syndromes: per form the
+    throughput, its roofline, LER and re-run shares per p.  With cpu_seconds,
+    the double-precision oracle on a bounded prefix gives the cpu_baseline
+    (shared by the three forms) and, per form, the decisions that differ from
+    it under the parity rule (a near tie of the double-precision run at or
+    before the first divergent decision excuses a difference)."""
     import torch
     import torch.distributed as dist
 
-    from __graft_entry__ import build
     from paper_2512_07057_gb300 import binding as B
     from paper_2512_07057_gb300 import decoder as D
-
-    torch.cuda.set_device(local_rank)
-    dev = local_rank
-    if rank == 0:
-        build()
-    if world > 1:
-        dist.barrier()
-        build()
-    work = make_phen_workload(rank, args.shots, args.ps)
     synd = [D.to_torch_words(sh.syndromes, dev) for _, _, sh in work]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
     stream = torch.cuda.current_stream(dev)
@@ -624,7 +690,7 @@ def run_precision(args, rank: int, world: int, local_rank: int):
         decs, outs = [], []
         for p, prob, sh in work:
             params = D.make_params(PHEN_PRESET, ms_scale=ALPHA, msg_precision=prec,
-                                   workspace_bytes=int(args.workspace_gb * (1 << 30)))
+                                   workspace_bytes=int(workspace_gb * (1 << 30)))
             decs.append(D.BeamSearchDecoder(prob, params, device=dev))
             outs.append(decs[-1].alloc_outputs(sh.B))
             tuned.setdefault(name, {})[str(p)] = autotune(decs[-1], synd[len(decs) - 1])
@@ -633,11 +699,11 @@ def run_precision(args, rank: int, world: int, local_rank: int):
             for d, s, o in zip(decs, synd, outs):
                 d.decode(s, o, stream=stream)
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             flush.fill_(1.0)
             step()
         torch.cuda.synchronize(dev)
-        tr_args = (decs, step, flush, stream, dev, args.steps, world, rank)
+        tr_args = (decs, step, flush, stream, dev, steps, world, rank)
         ms_steps, _, clocks, prof_graph = timed_region(*tr_args, profiled=False, sample_clocks=True)
         _, _, _, prof = timed_region(*tr_args, profiled=True, sample_clocks=False)
         ms_total = float(sum(ms_steps))
@@ -646,7 +712,7 @@ def run_precision(args, rank: int, world: int, local_rank: int):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_total = float(t.item())
         roofline, exec_iters = alu_roofline(prof, E, dev, "small case of the same DEM",
-                                            shots=shots_per_step * args.steps,
+                                            shots=shots_per_step * steps,
                                             msg_bytes=4 if prec == B.BSD_FP32 else 2)
         per_p = {}
         for (p, prob, sh), o in zip(work, outs):
@@ -661,16 +727,76 @@ def run_precision(args, rank: int, world: int, local_rank: int):
                              "mean_alg_iters": float(it.mean())}
             host_out[(name, p)] = (D.from_torch_words(o.corrections).copy(), st.copy())
         steps_s = ms_total * 1e-3
-        forms[name] = {"value": world * shots_per_step * args.steps / steps_s, "unit": "syndromes/s",
-                       "ms_per_step": ms_total / args.steps, "msg_bytes": 4 if prec == B.BSD_FP32 else 2,
-                       "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / args.steps,
-                                                  "round": float(exec_iters[1]) / args.steps},
+        forms[name] = {"value": world * shots_per_step * steps / steps_s, "unit": "syndromes/s",
+                       "ms_per_step": ms_total / steps, "msg_bytes": 4 if prec == B.BSD_FP32 else 2,
+                       "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / steps,
+                                                  "round": float(exec_iters[1]) / steps},
                        "roofline": roofline, "gpu_launches": int(sum(pr["kernel_launches"] for pr in prof_graph)),
                        "clocks": clocks, "per_p": per_p}
-        if name == "fp16" and rank == 0 and not args.no_e2e:
-            e2e = e2e_host(decs, work, args, dev)
+        if name == "fp16" and e2e_args is not None:
+            e2e = e2e_host(decs, work, e2e_args, dev)
         for d in decs:
             d.close()
+    res = {"forms": forms, "launch_shapes": tuned, "e2e": e2e}
+    if cpu_seconds:
+        import oracle
+        base, run = cpu_baseline_of(work, cpu_seconds, PHEN_PRESET)
+        res["cpu_baseline"] = base
+        # the same prefix decoded by the double-precision oracle: decisions of
+        # each form that differ, and how many a near tie before the first
+        # divergent decision explains (threshold 1e-6 and the 1e-4 guard band)
+        n = run["n"]
+        agree = {}
+        for (p, prob, sh), r in zip(work, run["outputs"]):
+            g64, g32 = oracle.Graph(prob, "f64"), oracle.Graph(prob, "f32")
+            s_bits = None
+            for name in forms:
+                corr, st = host_out[(name, p)]
+                diff = np.nonzero((corr[:n] != r["corrections"]).any(1) | ((st[:n] & 7) != r["status"]))[0]
+                n6 = n4 = 0
+                if len(diff):
+                    from paper_2512_07057_gb300 import workloads as W
+                    if s_bits is None:
+                        s_bits = W.unpack_bits(sh.syndromes[:n], prob.M)
+                    import dataclasses
+                    prm = run["params"]
+                    for b in diff[:50]:
+                        # the single-precision build with the form's storage (a
+                        # re-run shot: single-precision messages)
+                        ms = 0 if (st[b] & B.BSD_STATUS_FP32_RERUN) else {"fp32": 0, "fp16": 1, "bf16": 2}[name]
+                        l64 = g64.decode_log(s_bits[b], prm)["log"]
+                        l32 = g32.decode_log(s_bits[b], dataclasses.replace(prm, msg_storage=ms))["log"]
+                        k = oracle.first_divergence(l64, l32)
+                        n6 += int(k >= 0 and oracle.near_tie_before(l64, k, 1e-6))
+                        n4 += int(k >= 0 and oracle.near_tie_before(l64, k, 1e-4))
+                agree.setdefault(name, {})[str(p)] = {
+                    "shots": int(n), "differ": int(len(diff)), "examined": int(min(len(diff), 50)),
+                    "near_tie_before_divergence_1e-6": n6, "near_tie_before_divergence_1e-4": n4}
+        res["fp64_agreement"] = agree
+    return res
+
+
+def run_precision(args, rank: int, world: int, local_rank: int):
+    """The phenomenological DEM with FP32, FP16 and BF16 message storage side
+    by side; the line's value is the FP16 form."""
+    import torch
+    import torch.distributed as dist
+
+    from __graft_entry__ import build
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+        build()
+    work = make_phen_workload(rank, args.shots, args.ps)
+    shots_per_step = sum(sh.B for _, _, sh in work)
+    res = precision_forms(work, dev, args.steps, args.warmup, world, rank, args.workspace_gb,
+                          None if (rank != 0 or args.no_cpu_baseline) else args.cpu_seconds,
+                          e2e_args=args if (rank == 0 and not args.no_e2e) else None)
+    forms = res["forms"]
     main_form = forms["fp16"]
     line = {
         "metric": METRIC, "value": main_form["value"], "unit": "syndromes/s", "n_gpus": world,
@@ -680,36 +806,17 @@ def run_precision(args, rank: int, world: int, local_rank: int):
         "config": {"workload": PHEN_WORKLOAD, "code": "[[144,12,12]] phenomenological DEM, 936 x 2592, 6912 edges",
                    "shots_per_p_per_gpu": args.shots, "syndromes_per_step_per_gpu": shots_per_step,
                    "l2": "flushed before every timed step (256 MiB write outside the step events)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "launch_shapes": tuned},
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "launch_shapes": res["launch_shapes"]},
         "roofline": main_form["roofline"], "gpu_launches": main_form["gpu_launches"], "clocks": main_form["clocks"],
         "forms": forms,
         "fp16_vs_plain_fp32": main_form["value"] / forms["fp32"]["value"],
     }
-    if e2e is not None:
-        line["e2e"] = e2e
-    if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        nth = cores()
-        rate, n, dt = oracle_rate(work, args.cpu_seconds, nth, PHEN_PRESET)
-        line["cpu_baseline"] = {"value": rate, "unit": "syndromes/s", "cores": nth, "kind": "oracle",
-                                "sample": f"first {n} shots of each p batch, double-precision oracle, "
-                                          f"{dt:.1f} s on {nth} host threads"}
-        # the same prefix decoded by the double-precision oracle: decisions of each form that differ
-        agree = {}
-        for p, prob, sh in work:
-            r = oracle.Graph(prob, "f64").decode_batch(sh.syndromes[:n], oracle.preset(PHEN_PRESET, ms_scale=ALPHA),
-                                                       nthreads=nth)
-            near = (r["min_gap"] > 0) & (r["min_gap"] < 1e-4)      # a margin in (0, 1e-4) relative
-            exact = r["ties"] > 0                                      # an exact tie decided by R5 / R7 / R8
-            for name in forms:
-                corr, st = host_out[(name, p)]
-                diff = (corr[:n] != r["corrections"]).any(1) | ((st[:n] & 7) != r["status"])
-                agree.setdefault(name, {})[str(p)] = {
-                    "shots": int(n), "differ": int(diff.sum()),
-                    "differ_on_fp64_near_tie": int((diff & near).sum()),
-                    "differ_on_fp64_exact_tie": int((diff & exact & ~near).sum()),
-                    "fp64_near_tie_shots": int(near.sum()), "fp64_exact_tie_shots": int(exact.sum())}
-        line["fp64_agreement"] = agree
+    if res["e2e"] is not None:
+        line["e2e"] = res["e2e"]
+    if "cpu_baseline" in res:
+        line["cpu_baseline"] = res["cpu_baseline"]
+        line["fp64_agreement"] = res["fp64_agreement"]
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -954,6 +1061,85 @@ def _unrolled_cpu_baseline(prob, T, target_s):
                                         f"reference, {dt:.1f} s"}
 
 
+def synthetic_widths(prob, sh, dev, steps: int, warmup: int, world: int, rank: int, workspace_gb: float,
+                     cpu_seconds: float | None, e2e_args=None) -> dict:
+    """The 936 x 8800 synthetic DEM decoded with beam widths 8, 32 and 64 (the
+    matching Table I presets) on the same syndromes: the throughput over the
+    three, each width's kernel times, LER and roofline; with cpu_seconds the
+    double-precision oracle on a bounded prefix per width."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2512_07057_gb300 import decoder as D
+    synd = D.to_torch_words(sh.syndromes, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream(dev)
+    res = {"per_width": {}, "launch_shapes": {}}
+    decs, outs = [], []
+    for preset in SYN_PRESETS:
+        d = D.BeamSearchDecoder(prob, D.make_params(preset, ms_scale=ALPHA,
+                                                    workspace_bytes=int(workspace_gb * (1 << 30))), device=dev)
+        decs.append(d)
+        outs.append(d.alloc_outputs(sh.B))
+        res["launch_shapes"][preset] = autotune(d, synd, 16384)
+
+    def run_region(ds, os_):
+        def step():
+            for d, o in zip(ds, os_):
+                d.decode(synd, o, stream=stream)
+        for _ in range(warmup):
+            flush.fill_(1.0)
+            step()
+        torch.cuda.synchronize(dev)
+        tr_args = (ds, step, flush, stream, dev, steps, world, rank)
+        ms_steps, _, clocks, prof_graph = timed_region(*tr_args, profiled=False, sample_clocks=True)
+        _, _, _, prof = timed_region(*tr_args, profiled=True, sample_clocks=False)
+        ms_total = float(sum(ms_steps))
+        if world > 1:
+            t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_total = float(t.item())
+        return ms_total, clocks, prof_graph, prof
+
+    # all three widths in one step (the headline of this workload)
+    ms_total, clocks, prof_graph, prof = run_region(decs, outs)
+    roofline, exec_iters = alu_roofline(prof, prob.n_edges, dev, "small case of the same DEM",
+                                        shots=len(decs) * sh.B * steps)
+    for preset, d, o, pr in zip(SYN_PRESETS, decs, outs, prof):
+        st = D.from_torch_words(o.status)
+        it = D.from_torch_words(o.iters).astype(np.int64)
+        res["per_width"][preset] = {
+            "ler": ler_of(prob, sh, D.from_torch_words(o.obs_flips), st & 7),
+            "seed_converged": float(((st & 7) == 1).mean()), "beam_converged": float(((st & 7) == 2).mean()),
+            "failed": float(((st & 7) == 4).mean()), "mean_alg_iters": float(it.mean()),
+            "kernel_ms_per_step": {n: float(x) / steps for n, x in zip(("k_seed", "k_round", "k_select"), pr["ms"])}}
+    steps_s = ms_total * 1e-3
+    res.update(value=world * len(decs) * sh.B * steps / steps_s, ms_per_step=ms_total / steps, clocks=clocks,
+               roofline=roofline, gpu_launches=int(sum(pr["kernel_launches"] for pr in prof_graph)),
+               exec_bp_iters_per_step={"seed": float(exec_iters[0]) / steps, "round": float(exec_iters[1]) / steps})
+    # each width timed alone, with its own roofline
+    for preset, d, o in zip(SYN_PRESETS, decs, outs):
+        ms_w, _, _, prof_w = run_region([d], [o])
+        rl, _ = alu_roofline(prof_w, prob.n_edges, dev, "small case of the same DEM", shots=sh.B * steps)
+        res["per_width"][preset].update(value=world * sh.B * steps / (ms_w * 1e-3), ms_per_step=ms_w / steps,
+                                        roofline=rl)
+    if e2e_args is not None:
+        res["e2e"] = e2e_host(decs, [(w, prob, sh) for w in SYN_PRESETS], e2e_args, dev)
+    for d in decs:
+        d.close()
+    if cpu_seconds:
+        tot_n = tot_t = 0.0
+        for preset in SYN_PRESETS:
+            base, run = cpu_baseline_of([(preset, prob, sh)], cpu_seconds / 3, preset, single_s=1.5)
+            res["per_width"][preset]["cpu_baseline"] = base
+            tot_n += run["n"]
+            tot_t += run["dt"]
+        res["cpu_baseline"] = {"value": tot_n / tot_t, "unit": "syndromes/s", "cores": cores(), "kind": "oracle",
+                               "sample": "the per-width samples together (per_width.*.cpu_baseline), "
+                                         "double-precision oracle"}
+    return res
+
+
 def run_synthetic(args, rank: int, world: int, local_rank: int):
     """The 936 x 8800 synthetic DEM decoded with beam widths 8, 32 and 64 (the
     matching Table I presets), 10^6 seeded shots each per step."""
@@ -961,7 +1147,6 @@ def run_synthetic(args, rank: int, world: int, local_rank: int):
     import torch.distributed as dist
 
     from __graft_entry__ import build
-    from paper_2512_07057_gb300 import decoder as D
     from paper_2512_07057_gb300 import workloads as W
 
     torch.cuda.set_device(local_rank)
@@ -973,74 +1158,28 @@ def run_synthetic(args, rank: int, world: int, local_rank: int):
         build()
     prob = W.synthetic_dem()
     sh = W.sample_shots(prob, args.shots, W.shot_seed("synthetic_dem", rank))
-    synd = D.to_torch_words(sh.syndromes, dev)
-    decs, outs, tuned = [], [], {}
-    for preset in SYN_PRESETS:
-        d = D.BeamSearchDecoder(prob, D.make_params(preset, ms_scale=ALPHA,
-                                                    workspace_bytes=int(args.workspace_gb * (1 << 30))), device=dev)
-        decs.append(d)
-        outs.append(d.alloc_outputs(sh.B))
-        tuned[preset] = autotune(d, synd, 16384)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
-    stream = torch.cuda.current_stream(dev)
-
-    def step():
-        for d, o in zip(decs, outs):
-            d.decode(synd, o, stream=stream)
-
-    for _ in range(args.warmup):
-        flush.fill_(1.0)
-        step()
-    torch.cuda.synchronize(dev)
-    tr_args = (decs, step, flush, stream, dev, args.steps, world, rank)
-    ms_steps, _, clocks, prof_graph = timed_region(*tr_args, profiled=False, sample_clocks=True)
-    _, _, _, prof = timed_region(*tr_args, profiled=True, sample_clocks=False)
-    ms_total = float(sum(ms_steps))
-    if world > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    roofline, exec_iters = alu_roofline(prof, prob.n_edges, dev, "small case of the same DEM",
-                                        shots=len(decs) * sh.B * args.steps)
-    per_w = {}
-    for preset, o, pr in zip(SYN_PRESETS, outs, prof):
-        st = D.from_torch_words(o.status)
-        it = D.from_torch_words(o.iters).astype(np.int64)
-        per_w[preset] = {"ler": ler_of(prob, sh, D.from_torch_words(o.obs_flips), st & 7),
-                         "seed_converged": float(((st & 7) == 1).mean()),
-                         "beam_converged": float(((st & 7) == 2).mean()),
-                         "failed": float(((st & 7) == 4).mean()), "mean_alg_iters": float(it.mean()),
-                         "kernel_ms_per_step": {n: float(x) / args.steps
-                                                for n, x in zip(("k_seed", "k_round", "k_select"), pr["ms"])}}
-    steps_s = ms_total * 1e-3
+    res = synthetic_widths(prob, sh, dev, args.steps, args.warmup, world, rank, args.workspace_gb,
+                           None if (rank != 0 or args.no_cpu_baseline) else args.cpu_seconds,
+                           e2e_args=args if (rank == 0 and not args.no_e2e) else None)
     line = {
-        "metric": METRIC, "value": world * len(decs) * sh.B * args.steps / steps_s, "unit": "syndromes/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+        "metric": METRIC, "value": res["value"], "unit": "syndromes/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": SYN_WORKLOAD, "code": f"synthetic DEM {prob.M} x {prob.N}, {prob.n_edges} edges",
-                   "shots_per_width_per_gpu": sh.B, "syndromes_per_step_per_gpu": len(decs) * sh.B,
+                   "shots_per_width_per_gpu": sh.B, "syndromes_per_step_per_gpu": len(SYN_PRESETS) * sh.B,
                    "l2": "flushed before every timed step (256 MiB write outside the step events)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "launch_shapes": tuned},
-        "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / args.steps,
-                                   "round": float(exec_iters[1]) / args.steps},
-        "roofline": roofline, "gpu_launches": int(sum(pr["kernel_launches"] for pr in prof_graph)),
-        "per_width": per_w, "clocks": clocks,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "launch_shapes": res["launch_shapes"]},
+        "exec_bp_iters_per_step": res["exec_bp_iters_per_step"],
+        "roofline": res["roofline"], "gpu_launches": res["gpu_launches"],
+        "per_width": res["per_width"], "clocks": res["clocks"],
     }
-    if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e_host(decs, [(w, prob, sh) for w in SYN_PRESETS], args, dev)
-    if rank == 0 and not args.no_cpu_baseline:
-        rates = []
-        for preset in SYN_PRESETS:
-            r, n, dt = oracle_rate([(preset, prob, sh)], args.cpu_seconds / 3, cores(), preset)
-            rates.append((r, n, dt))
-        tot = sum(n for _, n, _ in rates) / sum(n / r for r, n, _ in rates)
-        line["cpu_baseline"] = {"value": tot, "unit": "syndromes/s", "cores": cores(), "kind": "oracle",
-                                "sample": "first " + "/".join(str(n) for _, n, _ in rates) +
-                                          " shots for the three widths, double-precision oracle"}
+    if "e2e" in res:
+        line["e2e"] = res["e2e"]
+    if "cpu_baseline" in res:
+        line["cpu_baseline"] = res["cpu_baseline"]
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for d in decs:
-        d.close()
 
 
 def run_xyz(args, rank: int, world: int, local_rank: int):
@@ -1385,6 +1524,30 @@ def _traffic_record(kernel: str, edges: int, msg_bytes: int = 0):
         files = src.group(1).split() if src else None
         if h and k and b and k.group(1) == kernel and h.group(1) == _source_hash(files):
             return float(b.group(2)), b.group(1)
+    return None
+
+
+def _memory_record(kernel: str, edges: int, msg_bytes: int = 0):
+    """The DRAM throughput and L2 hit rate that ncu measured for one launch of
+    `kernel` (profiles/<kernel>_memory_*.md) on a problem with `edges` edges,
+    if the kernel sources the record names are unchanged since the capture."""
+    import glob
+    import re
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_memory_*.md"))):
+        txt = open(path).read()
+        f = {m.group(1): m.group(2).strip() for m in re.finditer(r"^(\w+): (.+)$", txt, re.M)}
+        if f.get("kernel") != kernel or "dram_bytes" not in f or "duration_us" not in f:
+            continue
+        if "edges" in f and int(f["edges"]) != edges:
+            continue
+        if "msg_bytes" in f and msg_bytes and int(f["msg_bytes"]) != msg_bytes:
+            continue
+        if f.get("source_hash") != _source_hash(f["sources"].split() if "sources" in f else None):
+            continue
+        dram_b, dur = float(f["dram_bytes"]), float(f["duration_us"]) * 1e-6
+        return {"dram_gbs": dram_b / dur / 1e9, "l2_hit": float(f["l2_hit_pct"]) / 100.0,
+                "dram_bytes_per_launch": dram_b, "launch_us_under_ncu": dur * 1e6, "case": f.get("case", ""),
+                "record": os.path.relpath(path, ROOT)}
     return None
 
 

@@ -72,3 +72,33 @@ def test_committed_records_parse():
         for key in ("kernel", "sources", "source_hash", "edges"):
             assert re.search(rf"^{key}: \S+", txt, re.M), (n, key)
         assert len(re.findall(r"^bytes_per_(candidate_iteration|launch|shot): [0-9.]+$", txt, re.M)) == 1, n
+
+
+def _memory(root, name, kernel, edges, dram_bytes, duration_us, l2_hit_pct):
+    h = bench._source_hash(["bsd_internal.cuh", "bsd_kernels.cu"])
+    lines = [f"# {kernel} memory", "", "sources: bsd_internal.cuh bsd_kernels.cu", f"source_hash: {h}",
+             f"kernel: {kernel}", f"edges: {edges}", "case: 200000 shots, p = 0.05",
+             f"dram_bytes: {dram_bytes}", f"duration_us: {duration_us}", f"l2_hit_pct: {l2_hit_pct}"]
+    (root / "profiles" / name).write_text("\n".join(lines) + "\n")
+
+
+def test_memory_record_gives_dram_throughput_and_l2_hit(tree):
+    """The measured DRAM throughput of one launch is its DRAM bytes over its
+    duration; the L2 hit rate is passed through as a fraction; the record
+    goes stale with the sources and is not used for another problem."""
+    _memory(tree, "k_round_memory_a.md", "k_round", 432, 2.0e8, 500.0, 61.5)
+    r = bench._memory_record("k_round", 432)
+    assert abs(r["dram_gbs"] - 400.0) < 1e-9 and abs(r["l2_hit"] - 0.615) < 1e-12
+    assert r["record"] == os.path.join("profiles", "k_round_memory_a.md")
+    assert bench._memory_record("k_round", 6912) is None
+    assert bench._memory_record("k_seed", 432) is None
+    (tree / "paper_2512_07057_gb300" / "csrc" / "bsd_kernels.cu").write_text("// kernels v2\n")
+    assert bench._memory_record("k_round", 432) is None
+
+
+def test_ops_per_update_is_the_algorithmic_count():
+    """Six ALU operations per message update: two for the compare-exchange
+    into the row's two smallest magnitudes, one sign XOR, one signed select
+    of the outgoing magnitude, one add into the posterior, one extrinsic
+    subtraction."""
+    assert bench.OPS_PER_UPDATE == 2 + 1 + 1 + 1 + 1
