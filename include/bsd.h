@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define BSD_PARAMS_VERSION 2u
+#define BSD_PARAMS_VERSION 3u
 
 /* return codes */
 #define BSD_OK               0
@@ -103,6 +103,12 @@ typedef struct {
     int32_t  small_batch;      /* chunks of at most this many shots launch a second graph whose
                                   grids are sized to them (low latency for single syndromes):
                                   0 the default 32, -1 never, else 1..65536 */
+    int32_t  batch_slots;      /* codes without the small engine's layout (detector error models),
+                                  with the scale alpha and num_results = 1: the seed BP of many
+                                  shots runs at once over this many slots, messages streamed
+                                  through device memory with the shots contiguous; 0 or -1 never,
+                                  else 256..65536 (rounded down to a multiple of 256, capped by a
+                                  quarter of the workspace); results do not depend on it */
 } bsd_params;
 
 /* Fill *out with the library defaults: beam8_230iters, ms_scale 1,
@@ -212,6 +218,12 @@ int bsd_sync_error(bsd_decoder *dec);
 int bsd_get_info(const bsd_decoder *dec, int32_t *M, int32_t *N, int32_t *K, int32_t *n_edges,
                  int64_t *chunk_shots, int64_t *workspace_bytes);
 
+/* The batched seed BP of a decoder (the paper has no counterpart: it is how
+ * this library runs the first BP run of Alg. 3 for many syndromes at once):
+ * *slots = the slots of its workspace (0: none), *active = 1 if the current
+ * launch shape uses them.  Any pointer may be NULL. */
+int bsd_get_batch(const bsd_decoder *dec, int32_t *slots, int32_t *active);
+
 /* Opt-in timing of this library's kernels (not part of the method): while
  * enabled, every kernel launch made by bsd_decode / bsd_decode_host is
  * bracketed by two CUDA events recorded on the decode stream.  Enabling costs
@@ -223,7 +235,8 @@ int bsd_profile_enable(bsd_decoder *dec, int enable);
  * of each kernel kind (index 0: seed BP, 1: expand + masked BP of a round,
  * 2: per-shot selection of a round), the full BP iterations executed on the
  * device (index 0: seed candidates, 1: round candidates, counting children
- * evaluated after a shot's first success), the number of kernels of this
+ * evaluated after a shot's first success, 2: the part of index 0 run by the
+ * batched seed BP of bsd_params.batch_slots), the number of kernels of this
  * library that ran for this decoder (counted on the device, with or without
  * timing enabled), and the message updates done by first-iteration screens
  * of seed runs (with every Lambda_j > 0, the scale alpha and one result, a
@@ -233,14 +246,16 @@ int bsd_profile_enable(bsd_decoder *dec, int enable);
  * iteration).  While timing is enabled the kernels are launched one by one so
  * that events can bracket them; otherwise each chunk runs as one CUDA graph.
  * Any pointer may be NULL. */
-int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2],
+int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64_t exec_iters[3],
                      uint64_t *kernel_launches, uint64_t *screen_updates);
 
-/* Kernel kinds timed while timing is enabled: 0..2 as above, then the
- * unrolled decoder's passes (bsd_unrolled_forward / _backward): 3 check pass,
- * 4 error-node pass, 5 error-node adjoint, 6 check adjoint, 7 its other
- * kernels (bit planes, initial messages, loss and gradient reductions). */
-#define BSD_PROFILE_KINDS 8
+/* Kernel kinds timed while timing is enabled: 0..2 as above (0 also the
+ * first-iteration screen), then the unrolled decoder's passes
+ * (bsd_unrolled_forward / _backward): 3 check pass, 4 error-node pass,
+ * 5 error-node adjoint, 6 check adjoint, 7 its other kernels (bit planes,
+ * initial messages, loss and gradient reductions), then the batched seed BP:
+ * 8 its check pass, 9 its error-node pass, 10 its stopping test and refill. */
+#define BSD_PROFILE_KINDS 11
 
 /* Synchronise the stream of the last timed launch, then return and reset the
  * summed event-timed milliseconds and launch counts of every kind. */

@@ -12,7 +12,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbsd.so")
 
-BSD_PARAMS_VERSION = 2
+BSD_PARAMS_VERSION = 3
 BSD_OK = 0
 BSD_ERR_INVALID_ARG = -1
 BSD_ERR_CUDA = -2
@@ -31,12 +31,12 @@ BSD_STATUS_FAILED = 4
 
 # every symbol include/bsd.h declares
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
-           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_profile_enable", "bsd_profile_read",
+           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_get_batch", "bsd_profile_enable", "bsd_profile_read",
            "bsd_decode_noalloc", "bsd_set_weights", "bsd_unrolled_workspace", "bsd_unrolled_forward",
            "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_autotune", "bsd_get_shape", "bsd_dem_parse",
            "bsd_dem_sizes", "bsd_dem_fill", "bsd_dem_free",
            "bsd_error_string", "bsd_last_cuda_error", "bsd_destroy")
-BSD_PROFILE_KINDS = 8
+BSD_PROFILE_KINDS = 11
 BSD_DEM_MERGE = 1
 BSD_ERR_SCRATCH = -7
 
@@ -46,7 +46,7 @@ class bsd_params(C.Structure):
                 ("initial_iters", C.c_int32), ("iters_per_round", C.c_int32), ("num_results", C.c_int32),
                 ("ms_scale", C.c_float), ("llr_clamp", C.c_float), ("msg_precision", C.c_int32),
                 ("tie_guard_rel", C.c_float), ("workspace_bytes", C.c_int64), ("group_warps", C.c_int32),
-                ("small_batch", C.c_int32)]
+                ("small_batch", C.c_int32), ("batch_slots", C.c_int32)]
 
 
 class bsd_shape_timing(C.Structure):
@@ -84,6 +84,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_bp_llr.argtypes = [P, P, C.c_int64, C.c_int32, P, P, P]
     lib.bsd_sync_error.argtypes = [P]
     lib.bsd_get_info.argtypes = [P] + [C.POINTER(C.c_int32)] * 4 + [C.POINTER(C.c_int64)] * 2
+    lib.bsd_get_batch.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.bsd_decode_noalloc.argtypes = [P, P, C.c_int64, P, P, P, P, P]
     lib.bsd_profile_enable.argtypes = [P, C.c_int]
     lib.bsd_set_weights.argtypes = [P, P, C.c_int32]
@@ -179,6 +180,13 @@ def bsd_get_info(dec) -> dict:
     return dict(M=M.value, N=N.value, K=K.value, n_edges=E.value, chunk_shots=cs.value, workspace_bytes=wb.value)
 
 
+def bsd_get_batch(dec) -> dict:
+    """Slots of the decoder's batched seed BP (0: none) and whether its launch shape uses them."""
+    sl, ac = C.c_int32(), C.c_int32()
+    check(load().bsd_get_batch(dec, C.byref(sl), C.byref(ac)), "bsd_get_batch")
+    return dict(slots=sl.value, active=bool(ac.value))
+
+
 def bsd_set_weights(dec, h_weights, T: int) -> None:
     """h_weights: host address of float32 [T][E] (CSR edge order), or None with T = 0."""
     check(load().bsd_set_weights(dec, h_weights, int(T)), "bsd_set_weights")
@@ -212,7 +220,7 @@ def bsd_profile_read(dec) -> dict:
     import numpy as np
     ms = np.zeros(3, np.float64)
     ln = np.zeros(3, np.int64)
-    it = np.zeros(2, np.uint64)
+    it = np.zeros(3, np.uint64)
     kl = np.zeros(1, np.uint64)
     su = np.zeros(1, np.uint64)
     p = lambda a: a.ctypes.data_as(C.c_void_p)

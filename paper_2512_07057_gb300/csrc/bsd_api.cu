@@ -98,6 +98,8 @@ int validate_params(const bsd_params* p)
     if (p->workspace_bytes < 0) return BSD_ERR_INVALID_ARG;
     if (p->group_warps < 0 || p->group_warps > 16 || p->small_batch < -1 || p->small_batch > 65536)
         return BSD_ERR_INVALID_ARG;
+    if (p->batch_slots < -1 || (p->batch_slots > 0 && p->batch_slots < kBsChunk) || p->batch_slots > 65536)
+        return BSD_ERR_INVALID_ARG;
     return BSD_OK;
 }
 
@@ -119,9 +121,10 @@ LaunchShape small_shape(const LaunchShape& ls, const DecCfg& cfg, int n)
     const long long per_block = ls.group_warps >= 2 ? 1 : ls.warps_per_block;
     auto cap = [](long long v, int full) { return (int)(v < 1 ? 1 : (v < full ? v : full)); };
     s.grid_seed = cap((n + per_block - 1) / per_block, ls.grid_seed);
-    // no first-iteration screen: for a few shots its extra launch costs more
-    // latency than it saves
+    // no first-iteration screen and no batched seed BP: for a few shots their
+    // extra launches cost more latency than they save
     s.screen = 0;
+    s.batch = 0;
     s.grid_round = cap(((long long)n * 2 * cfg.w + per_block - 1) / per_block, ls.grid_round);
     s.grid_select = cap((n + ls.select_warps - 1) / ls.select_warps, ls.grid_select);
     return s;
@@ -479,7 +482,22 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     const double seed_b = (double)msg_bytes * Epad + sizeof(uint32_t) * (double)SB + sizeof(SlotMeta) + 4.0;
     const double win_b = 2.0 * W2 * ((double)msg_bytes * Epad + sizeof(uint32_t) * (double)SB + sizeof(SlotMeta)) +
                          12.0 + cfg.w + 8.0 + NR * (4.0 * WN + 12.0) + 4.0 + 2.0 * W2 * sizeof(int2);
-    const long long budget = params->workspace_bytes > 0 ? params->workspace_bytes : (4ll << 30);
+    long long budget = params->workspace_bytes > 0 ? params->workspace_bytes : (4ll << 30);
+    // the batched seed BP's slots: the requested count (at most a quarter of
+    // the workspace)
+    int bs_slots = 0;
+    if (dec->ls.batch && params->batch_slots > 0) {
+        const long long cap = budget / 4;
+        const int fit = batch_slots_for(g, cap);
+        const int want = params->batch_slots / kBsChunk * kBsChunk;
+        bs_slots = want < fit ? want : fit;
+        if (bs_slots > 0) {
+            Work probe{};
+            const size_t with = work_layout(g, cfg, 1, 1, nullptr, &probe, bs_slots);
+            const size_t without = work_layout(g, cfg, 1, 1, nullptr, nullptr);
+            budget -= (long long)(with - without);
+        }
+    }
     long long A = (long long)(0.8 * (double)budget / win_b);
     if (A < 1) A = 1;
     long long S = (long long)(((double)budget - (double)A * win_b) / seed_b);
@@ -487,7 +505,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     if (S < A) S = A;
     if (A > (1ll << 22)) A = 1ll << 22;
     for (;;) {
-        const size_t wb = work_layout(g, cfg, S, A, nullptr, nullptr);
+        const size_t wb = work_layout(g, cfg, S, A, nullptr, nullptr, bs_slots);
         if (cudaMalloc(&dec->work_mem, wb) == cudaSuccess) { dec->work_bytes = wb; break; }
         cudaGetLastError();
         dec->work_mem = nullptr;
@@ -496,7 +514,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
         A = A > 1 ? A / 2 : 1;
     }
     Work& w = dec->w;
-    work_layout(g, cfg, S, A, (char*)dec->work_mem, &w);
+    work_layout(g, cfg, S, A, (char*)dec->work_mem, &w, bs_slots);
     dec->ctr_bytes = work_head_bytes(cfg);
     if (CUDA_FAILED(cudaMemset(dec->work_mem, 0, dec->ctr_bytes)) ||
         CUDA_FAILED(cudaMallocHost(&dec->h_nactive, sizeof(int)))) {
@@ -854,7 +872,7 @@ int bsd_profile_enable(bsd_decoder* dec, int enable)
     return BSD_OK;
 }
 
-int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64_t exec_iters[2],
+int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64_t exec_iters[3],
                      uint64_t* kernel_launches, uint64_t* screen_updates)
 {
     if (!dec) return BSD_ERR_INVALID_ARG;
@@ -862,7 +880,7 @@ int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64
     if (!dg.ok) return BSD_ERR_CUDA;
     if (CUDA_FAILED(cudaStreamSynchronize(dec->last_stream))) return BSD_ERR_CUDA;
     prof_collect(dec);
-    unsigned long long st[4] = {0, 0, 0, 0};
+    unsigned long long st[kStats] = {};
     if (CUDA_FAILED(cudaMemcpy(st, dec->w.stats, sizeof(st), cudaMemcpyDeviceToHost)) ||
         CUDA_FAILED(cudaMemset(dec->w.stats, 0, sizeof(st))))
         return BSD_ERR_CUDA;
@@ -872,7 +890,7 @@ int bsd_profile_read(bsd_decoder* dec, double ms[3], int64_t launches[3], uint64
         dec->ms[k] = 0;
         dec->launches[k] = 0;
     }
-    if (exec_iters) { exec_iters[0] = st[0]; exec_iters[1] = st[1]; }
+    if (exec_iters) { exec_iters[0] = st[0]; exec_iters[1] = st[1]; exec_iters[2] = st[4]; }
     if (kernel_launches) *kernel_launches = st[2];
     if (screen_updates) *screen_updates = st[3];
     return BSD_OK;
@@ -941,6 +959,14 @@ int bsd_get_info(const bsd_decoder* dec, int32_t* M, int32_t* N, int32_t* K, int
     if (n_edges) *n_edges = dec->g.E;
     if (chunk_shots) *chunk_shots = dec->w.S;
     if (workspace_bytes) *workspace_bytes = (int64_t)dec->work_bytes;
+    return BSD_OK;
+}
+
+int bsd_get_batch(const bsd_decoder* dec, int32_t* slots, int32_t* active)
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    if (slots) *slots = dec->w.bs_slots;
+    if (active) *active = (dec->ls.batch && dec->w.bs_slots > 0) ? 1 : 0;
     return BSD_OK;
 }
 

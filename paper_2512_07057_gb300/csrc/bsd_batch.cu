@@ -1,0 +1,465 @@
+// bsd_batch.cu -- the seed BP of many shots at once, messages streamed
+// through HBM with the shots contiguous.
+//
+// The seed BP of a shot (Alg. 3, first BP run: Eqs. 1-4 from E(0) = Lambda
+// with the stopping rule) reads the same graph for every shot.  Here Bs slots
+// each hold one shot and every pass walks the graph once for all of them: the
+// messages live in [Epad][Bs] (edge e of slot b at e * Bs + b), so the 32
+// threads of a warp -- 32 slots of one row or one column -- read and write 32
+// consecutive messages, and every graph table entry is one broadcast load for
+// the whole warp.  Per iteration:
+//   k_bs_check   per (row i, slot): the two smallest magnitudes of the row's
+//                messages (capped at L_MAX) and the parity of their signs with
+//                s_i, written as the record (min1, min2) with the parity in
+//                both sign bits (Eq. 1 before the per-edge selection);
+//   k_bs_var     per (column j, slot): D_{i->j} from the record and the edge's
+//                own message (min2 where |E_{j->i}| = min1, else min1; the
+//                parity without the edge's own sign; times alpha), then
+//                Eqs. 2-3 in ascending order and Eq. 4; a column with
+//                e^_j(t) = 1 is added to the slot's list;
+//   k_bs_retire  per slot: H e^(t) = s from the listed columns (a stopping
+//                test needs only the few ones of e^); a converged shot gets
+//                its outputs, a shot at initial_iters without convergence (or
+//                with more ones than the list holds) goes to the list of shots
+//                the per-candidate seed kernel decodes again from scratch
+//                (its snapshot and sum_LLR feed the beam); a finished slot
+//                takes the next queued shot.
+// A slot's first iteration reads the precomputed records of E(0) and E(0)
+// itself from the graph tables, as the per-candidate engines do.  Every
+// operation is the one the per-candidate generic engine performs on the same
+// values in the same order (minimum with the lowest-index rule replaced by the
+// equivalent magnitude test, since a tie for the minimum makes min2 = min1),
+// so outputs and iteration counts are bit-identical.  Messages are stored
+// clamped to [-L_MAX, L_MAX] in the decoder's storage format.
+#include "bsd_device.cuh"
+#include "bsd_internal.cuh"
+
+namespace bsd {
+
+namespace {
+
+__device__ __forceinline__ bool batch_running(const Work& w)
+{
+    return *((volatile const int*)&w.ctr->bs_run) != 0;
+}
+
+// the slots of a block and the contiguous range of items (rows or columns) it covers
+struct BsRange {
+    int b;            // this thread's slot
+    int lo, hi;       // items [lo, hi)
+};
+
+__device__ __forceinline__ BsRange bs_range(const Work& w, int items)
+{
+    const int nch = w.bs_slots / kBsChunk;
+    const int groups = (gridDim.x + nch - 1) / nch;      // item groups
+    const int c = blockIdx.x % nch, grp = blockIdx.x / nch;
+    const int per = (items + groups - 1) / groups;
+    BsRange r;
+    r.b = c * kBsChunk + threadIdx.x;
+    r.lo = grp * per;
+    r.hi = min(items, r.lo + per);
+    return r;
+}
+
+}  // namespace
+
+// fill the slots with the first queued shots (every shot of the chunk when no
+// screen ran) and open the loop
+__global__ void k_bs_begin(Work w, int screened, cudaGraphConditionalHandle cond, int use_cond)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.stats[2], 1ull);
+    const long long chunk_n = w.desc->chunk_n;
+    const int nq = screened ? *((volatile int*)&w.ctr->n_queue) : (int)chunk_n;
+    const int Bs = w.bs_slots;
+    for (int b = threadIdx.x; b < Bs; b += blockDim.x) {
+        w.bs_shot[b] = b < nq ? (screened ? w.queue[b] : b) : -1;
+        w.bs_t[b] = 0;
+        w.bs_nl[b] = 0;
+    }
+    if (threadIdx.x == 0) {
+        const int n0 = nq < Bs ? nq : Bs;
+        w.ctr->bs_claim = n0;
+        w.ctr->bs_run = n0 > 0 ? 1 : 0;
+        w.ctr->bs_active_next = 0;
+        w.ctr->bs_done_blocks = 0;
+        w.ctr->n_fail = 0;
+        if (use_cond) cudaGraphSetConditional(cond, n0 > 0 ? 1u : 0u);
+    }
+}
+
+// Eq. 1, first half: the record of every (row, slot)
+template <int P>
+__global__ void __launch_bounds__(kBsChunk) k_bs_check(DevGraph g, DecCfg cfg, Work w)
+{
+    if (!batch_running(w)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.stats[2], 1ull);
+    using S = Store<P>;
+    using T = typename S::T;
+    const BsRange rg = bs_range(w, g.M);
+    const int b = rg.b;
+    const int Bs = w.bs_slots;
+    const int shot = w.bs_shot[b];
+    if (shot < 0) return;
+    const bool fresh = w.bs_t[b] == 0;
+    const uint32_t* s = w.desc->synd + (w.desc->chunk_base + shot) * (long long)g.WM;
+    const T* E = reinterpret_cast<const T*>(w.bsE);
+    const float L = cfg.L;
+    uint32_t sw = 0;
+    int sq = -1;
+    for (int i = rg.lo; i < rg.hi; ++i) {
+        if ((i >> 5) != sq) { sq = i >> 5; sw = __ldg(s + sq); }
+        uint32_t nb = (sw >> (i & 31)) & 1u;
+        float m1, m2;
+        if (fresh) {
+            const float4 r = __ldg(g.rs0 + i);
+            m1 = r.x;
+            m2 = r.y;
+            nb ^= __float_as_uint(r.w) & 1u;
+        } else {
+            // branch-free running pair of smallest magnitudes, capped at L_MAX (R3)
+            m1 = L;
+            m2 = L;
+            const int rb = __ldg(g.row_ptr + i), re = __ldg(g.row_ptr + i + 1);
+            for (int e = rb; e < re; ++e) {
+                const float x = S::ld(E, (size_t)e * Bs + b);
+                const float a = fabsf(x);
+                m2 = fminf(m2, fmaxf(m1, a));
+                m1 = fminf(m1, a);
+                nb ^= (x < 0.f) ? 1u : 0u;
+            }
+        }
+        const uint32_t sb = nb << 31;
+        w.bsR[(size_t)i * Bs + b] = make_float2(__uint_as_float(__float_as_uint(m1) | sb),
+                                                __uint_as_float(__float_as_uint(m2) | sb));
+    }
+}
+
+// Eq. 1 per edge, Eqs. 2-4 per (column, slot)
+template <int DV, int P>
+__global__ void __launch_bounds__(kBsChunk) k_bs_var(DevGraph g, DecCfg cfg, Work w)
+{
+    if (!batch_running(w)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.stats[2], 1ull);
+    using S = Store<P>;
+    using T = typename S::T;
+    const BsRange rg = bs_range(w, g.N);
+    const int b = rg.b;
+    const int Bs = w.bs_slots;
+    const int shot = w.bs_shot[b];
+    if (shot < 0) return;
+    const bool fresh = w.bs_t[b] == 0;
+    T* const E = reinterpret_cast<T*>(w.bsE);
+    const float alpha = cfg.alpha, L = cfg.L;
+    for (int j = rg.lo; j < rg.hi; ++j) {
+        int kb = 0, deg = 0;
+        if constexpr (DV > 6) {
+            kb = __ldg(g.col_ptr + j);
+            deg = __ldg(g.col_ptr + j + 1) - kb;
+        }
+        // E(0) of a fresh slot: the same on every edge of the column
+        const float x0 = fresh ? S::ld(reinterpret_cast<const T*>(g.lamEc), j) : 0.f;
+        float v[DV];
+        int ed[DV];
+#pragma unroll
+        for (int k = 0; k < DV; ++k) {
+            int e = -1, r = 0;
+            if constexpr (DV <= 6) {
+                const int2 er = __ldg(g.colER + (size_t)k * g.Npad + j);
+                e = er.x;
+                r = er.y;
+                deg += (e >= 0) ? 1 : 0;
+            } else if (k < deg) {
+                e = __ldg(g.col_edge + kb + k);
+                r = __ldg(g.col_row + kb + k);
+            }
+            if (e >= 0) {
+                const float2 rec = w.bsR[(size_t)r * Bs + b];
+                const float xo = fresh ? x0 : S::ld(E, (size_t)e * Bs + b);
+                // the minimum over the row's other edges: min2 on an edge
+                // holding the minimum (a tie makes min2 = min1), min1 elsewhere
+                const float m = (fabsf(xo) == fabsf(rec.x)) ? rec.y : rec.x;
+                // sign: the row's parity (in m) without the edge's own sign
+                const float d = __fmul_rn(alpha, m);
+                v[k] = __uint_as_float(__float_as_uint(d) ^ (__float_as_uint(xo) & 0x80000000u));
+                ed[k] = e;
+            } else {
+                v[k] = INFINITY;
+                ed[k] = -1;
+            }
+        }
+        // ascending order of value (the exchange network of the per-candidate engines)
+#pragma unroll
+        for (int a = 0; a < DV; ++a) {
+#pragma unroll
+            for (int k = 0; k + 1 < DV - a; ++k) {
+                if (v[k] > v[k + 1]) {
+                    const float tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv;
+                    const int te = ed[k]; ed[k] = ed[k + 1]; ed[k + 1] = te;
+                }
+            }
+        }
+        const float lj = __ldg(g.lam + j);
+#pragma unroll
+        for (int k = 0; k < DV; ++k) {                        // Eq. 2: leave d_i out
+            if (k < deg) {
+                float acc = lj;
+#pragma unroll
+                for (int k2 = 0; k2 < DV; ++k2)
+                    if (k2 != k && k2 < deg) acc = __fadd_rn(acc, v[k2]);
+                S::st(E, (size_t)ed[k] * Bs + b, fminf(fmaxf(acc, -L), L));
+            }
+        }
+        float post = lj;                                      // Eq. 3
+#pragma unroll
+        for (int k = 0; k < DV; ++k)
+            if (k < deg) post = __fadd_rn(post, v[k]);
+        if (post <= 0.f) {                                    // Eq. 4
+            const int q = atomicAdd(&w.bs_nl[b], 1);
+            if (q < kBsList) w.bs_list[(size_t)q * Bs + b] = j;
+        }
+    }
+}
+
+// stopping rule, outputs of converged shots, hand-off of the others, refill
+__global__ void __launch_bounds__(256) k_bs_retire(DevGraph g, DecCfg cfg, Work w, int screened,
+                                                  cudaGraphConditionalHandle cond, int use_cond)
+{
+    if (!batch_running(w)) {
+        // (the loop flag and the graph's condition are always set together;
+        // should they ever disagree, the loop still ends here)
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.stats[2], 1ull);
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31;
+    const int Bs = w.bs_slots;
+    const RunDesc* dp = w.desc;
+    const long long chunk_n = dp->chunk_n;
+    const int nq = screened ? *((volatile int*)&w.ctr->n_queue) : (int)chunk_n;
+    unsigned long long ran = 0;                   // slot-iterations of this launch (lane 0 of each warp)
+    int active = 0;                               // slots holding a shot for the next iteration
+    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < Bs; b += gridDim.x * (blockDim.x >> 5)) {
+        const int shot = w.bs_shot[b];
+        if (shot < 0) continue;
+        const int t = w.bs_t[b] + 1;
+        const int n = w.bs_nl[b];
+        ++ran;
+        const long long gb = dp->chunk_base + shot;
+        const uint32_t* s = dp->synd + gb * (long long)g.WM;
+        bool conv = false;
+        if (n <= kBsList) {
+            // H e^(t) xor s from the listed columns
+            uint32_t nz = 0;
+            for (int q = lane; q < g.WM; q += 32) {
+                uint32_t acc = __ldg(s + q);
+                for (int k = 0; k < n; ++k) acc ^= __ldg(g.hcol + (size_t)w.bs_list[(size_t)k * Bs + b] * g.WM + q);
+                nz |= acc;
+            }
+            conv = !__any_sync(FULLMASK, nz != 0u);
+        }
+        bool done = true;
+        if (conv) {
+            // outputs: e^ from the listed columns, A e^, status, iterations
+            uint32_t* corr = dp->out.corr + gb * g.WN;
+            for (int q = lane; q < g.WN; q += 32) {
+                uint32_t word = 0;
+                for (int k = 0; k < n; ++k) {
+                    const int j = w.bs_list[(size_t)k * Bs + b];
+                    if ((j >> 5) == q) word |= 1u << (j & 31);
+                }
+                corr[q] = word;
+            }
+            if (dp->out.obs != nullptr) {
+                for (int wq = 0; wq < g.WK; ++wq) {
+                    uint32_t acc = 0;
+                    for (int k = lane; k < n; k += 32)
+                        acc ^= __ldg(g.acol + (size_t)w.bs_list[(size_t)k * Bs + b] * g.WK + wq);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(FULLMASK, acc, o);
+                    if (lane == 0) dp->out.obs[gb * g.WK + wq] = acc;
+                }
+            }
+            if (lane == 0) {
+                dp->out.status[gb] = ST_SEED;
+                if (dp->out.iters != nullptr) dp->out.iters[gb] = (uint32_t)t;
+            }
+        } else if (n > kBsList || t >= cfg.initial_iters) {
+            // the seed BP fails (or e^ has more ones than the list holds): the
+            // per-candidate seed kernel decodes the shot again from E(0)
+            if (lane == 0) w.fail[atomicAdd(&w.ctr->n_fail, 1)] = shot;
+        } else {
+            done = false;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            int next = shot, tn = t;
+            if (done) {
+                const int k = atomicAdd(&w.ctr->bs_claim, 1);
+                next = k < nq ? (screened ? w.queue[k] : k) : -1;
+                tn = 0;
+            }
+            w.bs_shot[b] = next;
+            w.bs_t[b] = tn;
+            w.bs_nl[b] = 0;
+            active += next >= 0 ? 1 : 0;
+        }
+    }
+    if (lane == 0 && ran != 0ull) {
+        atomicAdd(&w.stats[0], ran);
+        atomicAdd(&w.stats[4], ran);
+    }
+    if (lane == 0 && active != 0) atomicAdd(&w.ctr->bs_active_next, active);
+    // the last block to finish decides whether another iteration runs
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&w.ctr->bs_done_blocks, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const int act = *((volatile int*)&w.ctr->bs_active_next);
+        w.ctr->bs_active_next = 0;
+        w.ctr->bs_done_blocks = 0;
+        w.ctr->bs_run = act > 0 ? 1 : 0;
+        if (use_cond) cudaGraphSetConditional(cond, act > 0 ? 1u : 0u);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// host side
+// ----------------------------------------------------------------------------
+int batch_slots_for(const DevGraph& g, long long budget)
+{
+    // per slot: the messages, the detector records, the list and small state
+    const long long per = (long long)g.Epad * g.msg_bytes + 8ll * g.M + 4ll * kBsList + 16;
+    long long bs = budget / (per > 0 ? per : 1);
+    bs = (bs / kBsChunk) * kBsChunk;
+    if (bs > 16384) bs = 16384;
+    return bs >= kBsChunk ? (int)bs : 0;
+}
+
+int batch_grid(int device)
+{
+    int sms = 0;
+    if (CUDA_FAILED(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device))) return 0;
+    return 8 * sms;
+}
+
+namespace {
+
+void* check_func(int prec)
+{
+    return prec == 0 ? (void*)k_bs_check<0> : prec == 1 ? (void*)k_bs_check<1> : (void*)k_bs_check<2>;
+}
+
+void* var_func(int dv, int prec)
+{
+    if (dv <= 3) return prec == 0 ? (void*)k_bs_var<3, 0> : prec == 1 ? (void*)k_bs_var<3, 1> : (void*)k_bs_var<3, 2>;
+    if (dv <= 6) return prec == 0 ? (void*)k_bs_var<6, 0> : prec == 1 ? (void*)k_bs_var<6, 1> : (void*)k_bs_var<6, 2>;
+    return prec == 0 ? (void*)k_bs_var<16, 0> : prec == 1 ? (void*)k_bs_var<16, 1> : (void*)k_bs_var<16, 2>;
+}
+
+// column degree bound of the generic engines (3, 6 or 16)
+int dv_of(const DevGraph& g) { return g.max_col_deg <= 3 ? 3 : g.max_col_deg <= 6 ? 6 : 16; }
+
+int grid_pass(const LaunchShape& ls, const Work& w)
+{
+    const int nch = w.bs_slots / kBsChunk;
+    int gr = ls.grid_bs > nch ? ls.grid_bs : nch;
+    return (gr / nch) * nch;                   // whole item groups per slot chunk
+}
+
+int grid_retire(const LaunchShape& ls, const Work& w)
+{
+    const int need = w.bs_slots / 8;           // one warp per slot, 8 warps per block
+    return need < ls.grid_bs ? need : ls.grid_bs;
+}
+
+int add_node(cudaGraph_t graph, cudaGraphNode_t* node, const cudaGraphNode_t* dep, void* func, int grid, int block,
+             void** args)
+{
+    cudaKernelNodeParams p{};
+    p.func = func;
+    p.gridDim = dim3((unsigned)grid);
+    p.blockDim = dim3((unsigned)block);
+    p.sharedMemBytes = 0;
+    p.kernelParams = args;
+    return !CUDA_FAILED(cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &p)) ? 0 : -2;
+}
+
+}  // namespace
+
+int add_batch_nodes(cudaGraph_t graph, cudaGraphNode_t dep, cudaGraphNode_t* last, const DevGraph& g0,
+                    const DecCfg& cfg0, const Work& w0, const LaunchShape& ls, int screened)
+{
+    DevGraph g = g0;
+    DecCfg cfg = cfg0;
+    Work w = w0;
+    cudaGraphConditionalHandle cond;
+    if (CUDA_FAILED(cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault))) return -2;
+    int use = 1;
+    cudaGraphNode_t nb, nw;
+    void* bargs[] = {&w, &screened, &cond, &use};
+    int rc = add_node(graph, &nb, dep ? &dep : nullptr, (void*)k_bs_begin, 1, 256, bargs);
+    cudaGraphNodeParams cp{};
+    if (!rc) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (CUDA_FAILED(cudaGraphAddNode(&nw, graph, &nb, nullptr, 1, &cp))) rc = -2;
+    }
+    if (!rc) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t nc, nv, nr;
+        void* pargs[] = {&g, &cfg, &w};
+        void* rargs[] = {&g, &cfg, &w, &screened, &cond, &use};
+        rc = add_node(body, &nc, nullptr, check_func(g.prec), grid_pass(ls, w), kBsChunk, pargs);
+        if (!rc) rc = add_node(body, &nv, &nc, var_func(dv_of(g), g.prec), grid_pass(ls, w), kBsChunk, pargs);
+        if (!rc) rc = add_node(body, &nr, &nv, (void*)k_bs_retire, grid_retire(ls, w), 256, rargs);
+    }
+    if (!rc) *last = nw;
+    return rc;
+}
+
+int launch_batch_direct(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls, int screened,
+                        cudaStream_t s, const LaunchHooks* hk, int* host_word)
+{
+    const cudaGraphConditionalHandle none{};
+    k_bs_begin<<<1, 256, 0, s>>>(w, screened, none, 0);
+    if (CUDA_FAILED(cudaGetLastError())) return -2;
+    const int gp = grid_pass(ls, w), gr = grid_retire(ls, w);
+    void* cf = check_func(g.prec);
+    void* vf = var_func(dv_of(g), g.prec);
+    DevGraph gg = g;
+    DecCfg cc = cfg;
+    Work ww = w;
+    int scr = screened, use = 0;
+    cudaGraphConditionalHandle h = none;
+    void* pargs[] = {&gg, &cc, &ww};
+    void* rargs[] = {&gg, &cc, &ww, &scr, &h, &use};
+    // kernels return at once when the batch has finished, so a few extra
+    // iterations between read-backs of the loop flag cost nothing
+    constexpr int kBetweenReads = 8;
+    for (;;) {
+        for (int k = 0; k < kBetweenReads; ++k) {
+            if (hk) hk->before(hk->ctx, 8);
+            if (CUDA_FAILED(cudaLaunchKernel(cf, dim3(gp), dim3(kBsChunk), pargs, 0, s))) return -2;
+            if (hk) { hk->after(hk->ctx, 8); hk->before(hk->ctx, 9); }
+            if (CUDA_FAILED(cudaLaunchKernel(vf, dim3(gp), dim3(kBsChunk), pargs, 0, s))) return -2;
+            if (hk) { hk->after(hk->ctx, 9); hk->before(hk->ctx, 10); }
+            if (CUDA_FAILED(cudaLaunchKernel((void*)k_bs_retire, dim3(gr), dim3(256), rargs, 0, s))) return -2;
+            if (hk) hk->after(hk->ctx, 10);
+        }
+        if (CUDA_FAILED(cudaMemcpyAsync(host_word, &w.ctr->bs_run, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+            CUDA_FAILED(cudaStreamSynchronize(s)))
+            return -2;
+        if (*host_word == 0) break;
+    }
+    return 0;
+}
+
+}  // namespace bsd

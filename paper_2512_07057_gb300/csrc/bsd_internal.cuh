@@ -103,6 +103,12 @@ struct Counters {
     int n_active;          // seed-store entries written by k_seed
     int err;
     int n_queue;           // shots the first-iteration screen passed on to the seed BP
+    // batched seed BP (bsd_batch.cu)
+    int bs_claim;          // queue entries handed to slots so far
+    int bs_run;            // the batch has active slots: another iteration runs
+    int bs_active_next;    // active slots after the current retirement (counted by its blocks)
+    int bs_done_blocks;    // blocks of the current retirement that have finished
+    int n_fail;            // shots passed on to the per-candidate seed kernel
     // followed by 3 * (max_rounds + 2) ints for the current pass:
     // claim_round[r], claim_select[r], work_count[r] (reset by k_pass_end)
 };
@@ -112,6 +118,15 @@ struct Work {
     long long A;           // active entries per beam pass
     int SB;                // words per slot bit record: sp[WM] mask[WN] vals[WN] ehat[WN]
     int* queue;            // [S] chunk-local shots the screen passed on to the seed BP
+    // batched seed BP over slots (bsd_batch.cu); bs_slots = 0: not used
+    int bs_slots;          // Bs, a multiple of kBsChunk
+    unsigned char* bsE;    // [Epad][Bs] messages in the storage format, shots contiguous
+    float2* bsR;           // [M][Bs] detector records (min1, min2) with the row's sign parity in bit 31
+    int* bs_shot;          // [Bs] chunk-local shot in the slot, -1 when empty
+    int* bs_t;             // [Bs] iterations the slot's shot has run
+    int* bs_nl;            // [Bs] columns with e^_j(t) = 1 found in the current iteration
+    int* bs_list;          // [kBsList][Bs] those columns
+    int* fail;             // [S] shots the batch passes on to the per-candidate seed kernel
     // seed store [S]
     unsigned char* seedE;  // [S][Epad] messages in the storage format
     uint32_t* seedBits;    // [S][SB]
@@ -136,9 +151,17 @@ struct Work {
     Counters* ctr;
     int* round_ctr;        // 3 * (max_rounds + 2) ints after ctr
     RunDesc* desc;
-    unsigned long long* stats;   // [4]: executed full BP iterations (seed, rounds), kernel launches, message
-                                 // updates of first-iteration screens; never reset by a chunk
+    unsigned long long* stats;   // [5]: executed full BP iterations (seed, rounds), kernel launches, message
+                                 // updates of first-iteration screens, seed iterations run by the batch
+                                 // (included in [0]); never reset by a chunk
 };
+
+// batched seed BP: slots per block of its passes, and the columns with
+// e^_j = 1 a slot can list in one iteration (a shot with more is passed on to
+// the per-candidate seed kernel)
+constexpr int kBsChunk = 256;
+constexpr int kBsList = 64;
+constexpr int kStats = 5;
 
 // true if e is an error; the error and the source line of the call are then
 // kept as the calling thread's most recent CUDA failure (bsd_last_cuda_error)
@@ -148,7 +171,8 @@ bool cuda_failed_at(cudaError_t e, const char* file, int line);
 // workspace layout for S seed entries and A window entries starting at base
 // (base may be null to size it); returns the bytes used.  The counters and the
 // run descriptor come first, in the first head_bytes(cfg) bytes.
-size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w);
+size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w,
+                   int bs_slots = 0);
 size_t work_head_bytes(const DecCfg& cfg);
 
 // host-side launch helpers (bsd_kernels.cu)
@@ -164,11 +188,14 @@ struct LaunchShape {
     size_t smem_bp;        // dynamic shared memory of the seed / round kernels
     size_t smem_select;
     int dv;                // engine id
+    int batch;             // the seed BP runs batched over slots (when the workspace has them)
+    int grid_bs;           // blocks of the batched passes (persistent)
 };
 
 // optional callbacks around every kernel launch; kinds 0 seed, 1 round,
 // 2 select, 3..6 the unrolled decoder's check / error / error adjoint / check
-// adjoint passes, 7 its other kernels
+// adjoint passes, 7 its other kernels, 8..10 the batched seed BP's check pass,
+// error-node pass and retirement
 constexpr int kProfKinds = BSD_PROFILE_KINDS;
 struct LaunchHooks {
     void (*before)(void* ctx, int kind);
@@ -191,6 +218,19 @@ int launch_chunk(const DevGraph& g, const DecCfg& cfg, const Work& w, const Laun
                  void* stream, const LaunchHooks* hooks, void* graph_exec, int* host_n_active);
 // build and instantiate the per-chunk graph (seed kernel + WHILE over beam passes)
 int build_graph(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls, void** graph_exec);
+
+// batched seed BP (bsd_batch.cu): slots that fit a byte budget (0: none)
+int batch_slots_for(const DevGraph& g, long long budget);
+// add its nodes after `dep` (begin, WHILE the batch has active slots {check
+// pass, error-node pass, retirement}); *last is the node that follows
+int add_batch_nodes(cudaGraph_t graph, cudaGraphNode_t dep, cudaGraphNode_t* last, const DevGraph& g,
+                    const DecCfg& cfg, const Work& w, const LaunchShape& ls, int screened);
+// the same kernels launched one by one, reading the batch's state back to the
+// host (into *host_word) every few iterations
+int launch_batch_direct(const DevGraph& g, const DecCfg& cfg, const Work& w, const LaunchShape& ls, int screened,
+                        cudaStream_t s, const LaunchHooks* hk, int* host_word);
+// grid of the batched passes for this device
+int batch_grid(int device);
 void destroy_graph(void* graph_exec);
 int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, const uint32_t* synd,
                   long long B, int T, float* llr, float* sum_llr, void* stream);

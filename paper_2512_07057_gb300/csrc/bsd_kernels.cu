@@ -36,52 +36,10 @@
 #include <cfloat>
 #include <cmath>
 
+#include "bsd_device.cuh"
 #include "bsd_internal.cuh"
 
 namespace bsd {
-
-#define FULLMASK 0xffffffffu
-
-// ----------------------------------------------------------------------------
-// message storage: float, binary16 or bfloat16; arithmetic is always float.
-// A stored value is the round-to-nearest-even conversion of the float result,
-// and a zero is stored as +0 (the sign rule treats -0 as positive anyway).
-// ----------------------------------------------------------------------------
-template <int P> struct Store;
-template <> struct Store<0> {
-    using T = float;
-    static __device__ __forceinline__ float ld(const T* p, int i) { return p[i]; }
-    static __device__ __forceinline__ void st(T* p, int i, float v) { p[i] = v; }
-    static __device__ __forceinline__ float2 ld2(const T* p, int i) { return *reinterpret_cast<const float2*>(p + i); }
-};
-template <> struct Store<1> {
-    using T = __half;
-    static __device__ __forceinline__ float ld(const T* p, int i) { return __half2float(p[i]); }
-    static __device__ __forceinline__ void st(T* p, int i, float v)
-    {
-        __half h = __float2half_rn(v);
-        if ((__half_as_ushort(h) & 0x7fffu) == 0) h = __ushort_as_half(0);
-        p[i] = h;
-    }
-    static __device__ __forceinline__ float2 ld2(const T* p, int i)
-    {
-        return __half22float2(*reinterpret_cast<const __half2*>(p + i));
-    }
-};
-template <> struct Store<2> {
-    using T = __nv_bfloat16;
-    static __device__ __forceinline__ float ld(const T* p, int i) { return __bfloat162float(p[i]); }
-    static __device__ __forceinline__ void st(T* p, int i, float v)
-    {
-        __nv_bfloat16 h = __float2bfloat16_rn(v);
-        if ((__bfloat16_as_ushort(h) & 0x7fffu) == 0) h = __ushort_as_bfloat16(0);
-        p[i] = h;
-    }
-    static __device__ __forceinline__ float2 ld2(const T* p, int i)
-    {
-        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + i));
-    }
-};
 
 // bytes and 16-byte vectors of one E snapshot (Epad is a multiple of 8)
 __host__ __device__ __forceinline__ size_t snap_bytes(const DevGraph& g) { return (size_t)g.Epad * (size_t)g.msg_bytes; }
@@ -112,7 +70,6 @@ __device__ __forceinline__ void group_copy16(const G& grp, void* dst, const void
     for (int q = grp.rank(); q < n16; q += grp.size()) d[q] = s[q];
 }
 
-enum : uint32_t { ST_SEED = 1u, ST_BEAM = 2u, ST_FAILED = 4u, ST_NEAR = 8u, ST_RERUN = 16u };
 
 // ----------------------------------------------------------------------------
 // candidate groups: the threads that process one BP candidate together.
@@ -879,6 +836,11 @@ __global__ void k_begin_chunk(Work w, int n_round_ints, const uint32_t* synd, Ou
         w.ctr->n_active = 0;
         w.ctr->n_queue = 0;
         w.ctr->err = 0;
+        w.ctr->bs_claim = 0;
+        w.ctr->bs_run = 0;
+        w.ctr->bs_active_next = 0;
+        w.ctr->bs_done_blocks = 0;
+        w.ctr->n_fail = 0;
         RunDesc d;
         d.synd = synd;
         d.out = out;
@@ -1135,7 +1097,11 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
     // chunk's counter, which a million one-iteration seeds would otherwise
     // hit a million times); a block candidate one at a time
     constexpr int kBatch = Eng::Grp::kBlock ? 1 : 4;
-    const int nq = screened ? *((volatile int*)&w.ctr->n_queue) : 0;
+    // the shots: every shot of the chunk (screened = 0), those the screen
+    // passed on (1), or those the batched seed BP passed on (2)
+    const int* list = screened == 2 ? w.fail : w.queue;
+    const int nq = screened == 2 ? *((volatile int*)&w.ctr->n_fail)
+                                 : screened ? *((volatile int*)&w.ctr->n_queue) : 0;
     int kcur = 0, kend = 0;                      // claimed slots [kcur, kend), the same in the whole group
     for (;;) {
         if (kcur >= kend) {
@@ -1146,7 +1112,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
         }
         const int k = kcur++;
         // after a screen, the shots it passed on; else every shot of the chunk
-        const int b = !screened ? k : (k < nq ? w.queue[k] : (int)dp->chunk_n);
+        const int b = !screened ? k : (k < nq ? list[k] : (int)dp->chunk_n);
         if (b >= dp->chunk_n) break;
         const long long gb = dp->chunk_base + b;
         const uint32_t* s = dp->synd + gb * g.WM;
@@ -1790,6 +1756,11 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, int group_warp
     ls->grid_seed = sms * bps_bp;
     ls->grid_round = sms * bps_bp;
     ls->grid_select = sms * bps_sel;
+    // the batched seed BP: generic engines with the scale alpha and one result
+    // (the shots it finishes need no snapshot; the others are decoded again by
+    // the per-candidate seed kernel)
+    ls->batch = (eng < 9 || eng >= kBlockEngine) && !weighted && cfg.num_results == 1 ? 1 : 0;
+    ls->grid_bs = batch_grid(device);
     return 0;
 }
 
@@ -1821,8 +1792,13 @@ static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, c
         launch_screen(g, cfg, w, ls, s);
         if (hk) hk->after(hk->ctx, 0);
     }
+    int seed_src = ls.screen;
+    if (ls.batch && w.bs_slots > 0) {
+        if (launch_batch_direct(g, cfg, w, ls, ls.screen, s, hk, host_n_active)) return -2;
+        seed_src = 2;
+    }
     if (hk) hk->before(hk->ctx, 0);
-    k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, ls.screen);
+    k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, seed_src);
     if (hk) hk->after(hk->ctx, 0);
     if (CUDA_FAILED(cudaGetLastError())) return -2;
     if (cfg.max_rounds == 0) return 0;
@@ -1886,16 +1862,19 @@ static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0,
     cudaGraph_t graph = nullptr;
     if (CUDA_FAILED(cudaGraphCreate(&graph, 0))) return -2;
     int rc = 0;
-    cudaGraphNode_t seed, scr;
-    int screened = ls.screen;
+    cudaGraphNode_t seed, scr, bs;
+    const bool batched = ls.batch && w.bs_slots > 0;
+    int screened = batched ? 2 : ls.screen;
     void* sargs[] = {&g, &cfg, &w, &screened};
     void* cargs[] = {&g, &cfg, &w};
     if (ls.screen)
         rc = add_kernel(graph, &scr, nullptr, screen_func(ls), ls.grid_screen, 32 * kScreenWarps, ls.smem_screen,
                         cargs);
+    // the batched seed BP, then the per-candidate seed kernel for the shots it passes on
+    if (!rc && batched) rc = add_batch_nodes(graph, ls.screen ? scr : nullptr, &bs, g, cfg, w, ls, ls.screen);
     if (!rc)
-        rc = add_kernel(graph, &seed, ls.screen ? &scr : nullptr, (void*)k_seed<Eng>, ls.grid_seed, threads,
-                        ls.smem_bp, sargs);
+        rc = add_kernel(graph, &seed, batched ? &bs : ls.screen ? &scr : nullptr, (void*)k_seed<Eng>, ls.grid_seed,
+                        threads, ls.smem_bp, sargs);
     // seed, then WHILE (a window of active shots left) { round 1, WHILE (the
     // next round has children) { round r, selection, round end }, pass end }:
     // a chunk runs exactly the passes and rounds it needs
@@ -1985,10 +1964,11 @@ static inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t work_head_bytes(const DecCfg& cfg)
 {
     return a256(sizeof(Counters) + sizeof(int) * 3 * (size_t)(cfg.max_rounds + 2)) + a256(sizeof(RunDesc)) +
-           a256(4 * sizeof(unsigned long long));
+           a256(kStats * sizeof(unsigned long long));
 }
 
-size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w)
+size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w,
+                   int bs_slots)
 {
     const size_t W2 = 2 * (size_t)cfg.w;
     const size_t SB = (size_t)g.WM + 3 * (size_t)g.WN;
@@ -2001,7 +1981,7 @@ size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long 
     };
     char* ctr = take(sizeof(Counters) + sizeof(int) * 3 * (size_t)(cfg.max_rounds + 2));
     char* desc = take(sizeof(RunDesc));
-    char* stats = take(4 * sizeof(unsigned long long));
+    char* stats = take(kStats * sizeof(unsigned long long));
     Work v{};
     v.S = S;
     v.A = A;
@@ -2030,6 +2010,18 @@ size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long 
     v.first_ok = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)A);
     v.near = (int*)take(sizeof(int) * (size_t)A);
     v.items = (int2*)take(sizeof(int2) * 2 * (size_t)A * W2);
+    // the batched seed BP's slots and the shots it passes on
+    v.bs_slots = bs_slots;
+    if (bs_slots > 0) {
+        const size_t Bs = (size_t)bs_slots;
+        v.bsE = (unsigned char*)take(Bs * (size_t)g.Epad * (size_t)g.msg_bytes);
+        v.bsR = (float2*)take(sizeof(float2) * Bs * (size_t)g.M);
+        v.bs_shot = (int*)take(sizeof(int) * Bs);
+        v.bs_t = (int*)take(sizeof(int) * Bs);
+        v.bs_nl = (int*)take(sizeof(int) * Bs);
+        v.bs_list = (int*)take(sizeof(int) * Bs * (size_t)kBsList);
+        v.fail = (int*)take(sizeof(int) * (size_t)S);
+    }
     if (w) *w = v;
     return off;
 }

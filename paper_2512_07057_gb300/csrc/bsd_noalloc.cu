@@ -101,7 +101,7 @@ extern "C" int bsd_decode_noalloc(const bsd_decoder* dec, const uint32_t* d_synd
         // the launch statistics in the array's head start at zero; each chunk
         // resets its own counters and run descriptor (k_begin_chunk), and
         // everything else is written before it is read
-        if (CUDA_FAILED(cudaMemsetAsync(w.stats, 0, 4 * sizeof(unsigned long long), s))) rc = BSD_ERR_CUDA;
+        if (CUDA_FAILED(cudaMemsetAsync(w.stats, 0, kStats * sizeof(unsigned long long), s))) rc = BSD_ERR_CUDA;
         for (long long b0 = 0; b0 < B && rc == BSD_OK; b0 += S) {
             const long long n = (B - b0) < S ? (B - b0) : S;
             if (launch_chunk(*g, *cfg, w, *ls, d_syndromes, b0, n, o, s, nullptr, nullptr, &g_nactive) != 0)

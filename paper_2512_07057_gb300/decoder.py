@@ -56,6 +56,7 @@ class BeamSearchDecoder:
         self.params = params
         self.h = B.bsd_create(self.M, self.N, self.K, ptr(hr), ptr(hc), ptr(ar), ptr(ac), ptr(pr), params, device)
         self.info = B.bsd_get_info(self.h)
+        self.info["batch"] = B.bsd_get_batch(self.h)
 
     def set_weights(self, weights) -> None:
         """Weighted min-sum: float32 [T, E] per-edge, per-iteration weights in
