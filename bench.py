@@ -417,65 +417,85 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
-def alu_roofline(prof, E: int, dev: int, traffic_case: str, shots: int = 0, msg_bytes: int = 4):
+def alu_roofline(prof, E: int, dev: int, traffic_case: str, shots: int = 0, msg_bytes: int = 4, M: int = 0):
     """Roofline of the dominant BP kernel from per-kernel event times.
 
-    Algorithmic lane operations of a launch = OPS_PER_UPDATE x (the full BP
-    iterations it executed x E + the message updates of first-iteration
-    screens, both counted on the device); the peak is the lane-operation
-    rate of the chip at its maximum SM clock."""
+    Per-candidate kernels (k_seed, k_round) keep their state on chip: their
+    roof is the lane-operation rate of the chip at its maximum SM clock, and
+    a launch does OPS_PER_UPDATE x (the full BP iterations it executed x E +
+    the message updates of first-iteration screens, counted on the device)
+    algorithmic operations.  The batched seed BP's passes (k_bs_check,
+    k_bs_var) stream the messages of many shots through device memory: their
+    roof is the measured HBM copy bandwidth, and a launch moves, per slot
+    iteration, msg_bytes x E (check pass: the messages read; error-node
+    pass: read and written, twice that) plus 8 x M bytes of detector records
+    (written by the check pass, read by the error-node pass)."""
     import torch
-    ms_kind = np.sum([pr["ms"] for pr in prof], axis=0)
-    launches = np.sum([pr["launches"] for pr in prof], axis=0)
+    kinds_ms = np.sum([pr["kinds"]["ms"] for pr in prof], axis=0)
+    kinds_ln = np.sum([pr["kinds"]["launches"] for pr in prof], axis=0)
     exec_iters = np.sum([pr["exec_iters"] for pr in prof], axis=0).astype(np.float64)
     # message updates of seed runs that ended in their first-iteration screen
     # (the columns next to flipped detectors; counted apart from full iterations)
     screen = float(sum(pr.get("screen_updates", 0) for pr in prof))
-    names = ("k_seed", "k_round", "k_select")
     pk, pk_kind = peaks()
     sm_mhz_max = float(pk.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak_tops = sms * LANES_PER_SM * sm_mhz_max * 1e6 / 1e12
-    # the selection kernel runs no BP, so its share is reported but it is never the roofline kernel
-    dom = int(np.argmax(ms_kind[:2]))
-    dom_iters = exec_iters[dom]
-    dom_updates_per_launch = (dom_iters * E + (screen if dom == 0 else 0.0)) / max(1, launches[dom])
-    dom_ms_per_launch = ms_kind[dom] / max(1, launches[dom])
-    achieved = OPS_PER_UPDATE * dom_updates_per_launch / (dom_ms_per_launch * 1e-3) / 1e12
-    roofline = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": alu_peak_tops,
-                "unit": "Tops/s", "frac": achieved / alu_peak_tops, "traffic": None,
-                "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz (sm_max_mhz {pk_kind})",
-                "ops_per_msg_update": OPS_PER_UPDATE,
-                "msg_updates_per_launch": dom_updates_per_launch, "launch_ms": dom_ms_per_launch,
-                "msg_updates_counted": "full BP iterations x E, plus the edges of first-iteration screens "
-                                       "(seed kernel)",
-                "screen_msg_updates_per_launch": (screen / max(1, launches[0])) if dom == 0 else 0.0,
-                "kernel_share": float(ms_kind[dom] / max(ms_kind.sum(), 1e-9)),
-                "measured_in": "second timed region: same steps, each kernel launched alone between CUDA events "
-                               "on the decode stream"}
-    # DRAM bytes per candidate-iteration from an ncu capture of a smaller case
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    batch_it = exec_iters[2] if len(exec_iters) > 2 else 0.0
+    # candidate kernels: kind, name, message updates of all their launches
+    cands = [(0, "k_seed", (exec_iters[0] - batch_it) * E + screen), (1, "k_round", exec_iters[1] * E),
+             (8, "k_bs_check", batch_it * E), (9, "k_bs_var", batch_it * E)]
+    dom_kind, name, updates = max(cands, key=lambda c: kinds_ms[c[0]])
+    launches = max(1, int(kinds_ln[dom_kind]))
+    ms_launch = float(kinds_ms[dom_kind]) / launches
+    upd_launch = updates / launches
+    ops_tops = OPS_PER_UPDATE * upd_launch / (ms_launch * 1e-3) / 1e12
+    share = float(kinds_ms[dom_kind] / max(kinds_ms[[0, 1, 2, 8, 9, 10]].sum(), 1e-9))
+    common = {"kernel": name, "msg_updates_per_launch": upd_launch, "launch_ms": ms_launch, "kernel_share": share,
+              "ops_per_msg_update": OPS_PER_UPDATE,
+              "measured_in": "second timed region: same steps, each kernel launched alone between CUDA events "
+                             "on the decode stream"}
+    if name.startswith("k_bs_"):
+        slot_iters_launch = batch_it / launches
+        per_slot = (2 if name == "k_bs_var" else 1) * msg_bytes * E + 8 * M
+        achieved = per_slot * slot_iters_launch / (ms_launch * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": None,
+                    "peak_source": f"measured copy bandwidth ({pk_kind})",
+                    "algorithmic_bytes_per_slot_iteration": per_slot,
+                    "slot_iterations_per_launch": slot_iters_launch,
+                    "alu_view": {"achieved_tops": ops_tops, "peak_tops": alu_peak_tops,
+                                 "frac": ops_tops / alu_peak_tops}, **common}
+    else:
+        roofline = {"bound": "alu", "achieved": ops_tops, "peak": alu_peak_tops, "unit": "Tops/s",
+                    "frac": ops_tops / alu_peak_tops, "traffic": None,
+                    "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz (sm_max_mhz {pk_kind})",
+                    "msg_updates_counted": "full BP iterations x E, plus the edges of first-iteration screens "
+                                           "(seed kernel)",
+                    "screen_msg_updates_per_launch": (screen / launches) if dom_kind == 0 else 0.0, **common}
+    # DRAM bytes per unit of work from an ncu capture of a smaller case
     # (profiles/), scaled to this run's average launch; null once the kernel
     # sources differ from the ones that were captured
-    tr = _traffic_record(names[dom], E, msg_bytes)
+    tr = _traffic_record(name, E, msg_bytes)
     if tr is not None:
         per, unit = tr
         if unit == "shot" and shots > 0:
             # the seed stage (screen and seed BP) moves its bytes per shot
-            roofline["traffic"] = per * shots / max(1, launches[dom])
+            roofline["traffic"] = per * shots / launches
             roofline["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum of the seed stage on " \
                                          f"a {traffic_case}, per shot, scaled by the shots of a launch"
         elif unit == "candidate_iteration":
-            roofline["traffic"] = per * (dom_iters / max(1, launches[dom]))
+            roofline["traffic"] = per * (updates / max(E, 1) / launches)
             roofline["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum on a {traffic_case}, " \
                                          "scaled by candidate-iterations"
     # measured DRAM throughput and L2 hit rate of one launch (ncu), against the measured copy bandwidth
-    mr = _memory_record(names[dom], E, msg_bytes)
+    mr = _memory_record(name, E, msg_bytes)
     if mr is not None:
-        hbm_peak = float(pk.get("hbm_gbs", 6800.0))
         roofline["dram_gbs"] = mr["dram_gbs"]
         roofline["l2_hit"] = mr["l2_hit"]
         roofline["dram_frac_of_peak"] = mr["dram_gbs"] / hbm_peak
-        roofline["dram_measured"] = {k: mr[k] for k in ("dram_bytes_per_launch", "launch_us_under_ncu", "case",
+        roofline["dram_measured"] = {k: mr[k] for k in ("dram_bytes_captured", "duration_us_captured", "case",
                                                        "record")}
     else:
         roofline["dram_gbs"] = roofline["l2_hit"] = roofline["dram_frac_of_peak"] = None
@@ -505,6 +525,7 @@ def timed_region(decs, step, flush, stream, dev, steps, world, rank, profiled: b
     for d in decs:
         d.profile(profiled)
         d.profile_read()                  # reset the device counters
+        d.profile_read_kinds()
     sampler = ClockSampler(dev) if (rank == 0 and sample_clocks) else None
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -525,7 +546,14 @@ def timed_region(decs, step, flush, stream, dev, steps, world, rank, profiled: b
     if world > 1:
         dist.barrier()
     clk = sampler.stop() if sampler else None
-    prof = [d.profile_read() for d in decs]
+    prof = []
+    for d in decs:
+        pr = d.profile_read()             # kinds 0-2 (reset by this read), iterations, launches
+        kinds = d.profile_read_kinds()    # the other kinds
+        kinds["ms"][:3] = pr["ms"]
+        kinds["launches"][:3] = pr["launches"]
+        pr["kinds"] = kinds
+        prof.append(pr)
     for d in decs:
         d.profile(False)
     return [s.elapsed_time(e) for s, e in zip(starts, ends)], wall, clk, prof
@@ -713,7 +741,7 @@ def precision_forms(work, dev, steps: int, warmup: int, world: int, rank: int, w
             ms_total = float(t.item())
         roofline, exec_iters = alu_roofline(prof, E, dev, "small case of the same DEM",
                                             shots=shots_per_step * steps,
-                                            msg_bytes=4 if prec == B.BSD_FP32 else 2)
+                                            msg_bytes=4 if prec == B.BSD_FP32 else 2, M=work[0][1].M)
         per_p = {}
         for (p, prob, sh), o in zip(work, outs):
             st = D.from_torch_words(o.status)
@@ -730,7 +758,8 @@ def precision_forms(work, dev, steps: int, warmup: int, world: int, rank: int, w
         forms[name] = {"value": world * shots_per_step * steps / steps_s, "unit": "syndromes/s",
                        "ms_per_step": ms_total / steps, "msg_bytes": 4 if prec == B.BSD_FP32 else 2,
                        "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / steps,
-                                                  "round": float(exec_iters[1]) / steps},
+                                                  "round": float(exec_iters[1]) / steps,
+                                                  "seed_batched": float(exec_iters[2]) / steps},
                        "roofline": roofline, "gpu_launches": int(sum(pr["kernel_launches"] for pr in prof_graph)),
                        "clocks": clocks, "per_p": per_p}
         if name == "fp16" and e2e_args is not None:
@@ -1104,7 +1133,7 @@ def synthetic_widths(prob, sh, dev, steps: int, warmup: int, world: int, rank: i
     # all three widths in one step (the headline of this workload)
     ms_total, clocks, prof_graph, prof = run_region(decs, outs)
     roofline, exec_iters = alu_roofline(prof, prob.n_edges, dev, "small case of the same DEM",
-                                        shots=len(decs) * sh.B * steps)
+                                        shots=len(decs) * sh.B * steps, M=prob.M)
     for preset, d, o, pr in zip(SYN_PRESETS, decs, outs, prof):
         st = D.from_torch_words(o.status)
         it = D.from_torch_words(o.iters).astype(np.int64)
@@ -1116,11 +1145,12 @@ def synthetic_widths(prob, sh, dev, steps: int, warmup: int, world: int, rank: i
     steps_s = ms_total * 1e-3
     res.update(value=world * len(decs) * sh.B * steps / steps_s, ms_per_step=ms_total / steps, clocks=clocks,
                roofline=roofline, gpu_launches=int(sum(pr["kernel_launches"] for pr in prof_graph)),
-               exec_bp_iters_per_step={"seed": float(exec_iters[0]) / steps, "round": float(exec_iters[1]) / steps})
+               exec_bp_iters_per_step={"seed": float(exec_iters[0]) / steps, "round": float(exec_iters[1]) / steps,
+                                       "seed_batched": float(exec_iters[2]) / steps})
     # each width timed alone, with its own roofline
     for preset, d, o in zip(SYN_PRESETS, decs, outs):
         ms_w, _, _, prof_w = run_region([d], [o])
-        rl, _ = alu_roofline(prof_w, prob.n_edges, dev, "small case of the same DEM", shots=sh.B * steps)
+        rl, _ = alu_roofline(prof_w, prob.n_edges, dev, "small case of the same DEM", shots=sh.B * steps, M=prob.M)
         res["per_width"][preset].update(value=world * sh.B * steps / (ms_w * 1e-3), ms_per_step=ms_w / steps,
                                         roofline=rl)
     if e2e_args is not None:
@@ -1546,7 +1576,7 @@ def _memory_record(kernel: str, edges: int, msg_bytes: int = 0):
             continue
         dram_b, dur = float(f["dram_bytes"]), float(f["duration_us"]) * 1e-6
         return {"dram_gbs": dram_b / dur / 1e9, "l2_hit": float(f["l2_hit_pct"]) / 100.0,
-                "dram_bytes_per_launch": dram_b, "launch_us_under_ncu": dur * 1e6, "case": f.get("case", ""),
+                "dram_bytes_captured": dram_b, "duration_us_captured": dur * 1e6, "case": f.get("case", ""),
                 "record": os.path.relpath(path, ROOT)}
     return None
 

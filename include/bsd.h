@@ -106,9 +106,11 @@ typedef struct {
     int32_t  batch_slots;      /* codes without the small engine's layout (detector error models),
                                   with the scale alpha and num_results = 1: the seed BP of many
                                   shots runs at once over this many slots, messages streamed
-                                  through device memory with the shots contiguous; 0 or -1 never,
-                                  else 256..65536 (rounded down to a multiple of 256, capped by a
-                                  quarter of the workspace); results do not depend on it */
+                                  through device memory with the shots contiguous; 0 the library
+                                  default (codes of at least 16384 edges: about 96 MiB of message
+                                  state; smaller codes: none), -1 never, else 256..65536 (rounded
+                                  down to a multiple of 256); at most a quarter of the workspace;
+                                  results do not depend on it */
 } bsd_params;
 
 /* Fill *out with the library defaults: beam8_230iters, ms_scale 1,

@@ -77,6 +77,11 @@ struct DeviceGuard {
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 inline int words_of(long long bits) { return (int)((bits + 31) / 32); }
 
+// default of the batched seed BP: codes with at least this many edges, and
+// about this much message state
+constexpr long long kBatchMinEdges = 16384;
+constexpr long long kBatchStateBytes = 96ll << 20;
+
 const char* kPresetNames[] = {"beam8_230iters", "beam32_340iters", "beam64_640iters", "beam64_32res_640iters"};
 // Table I: max_rounds, beam_width, initial_iters, iters_per_round, num_results
 const int kPresetVals[][5] = {{10, 8, 30, 20, 1}, {10, 32, 40, 30, 1}, {20, 64, 40, 30, 1}, {20, 64, 40, 30, 32}};
@@ -388,6 +393,26 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
             if (prec == BSD_FP32) std::memcpy(&lamEc_st[(size_t)j * 4], &v, 4);
         }
     }
+    // the columns ordered by degree, each column's (edge, row) pairs contiguous
+    // in the order of the column lists (the batched seed BP walks runs of
+    // columns of one degree)
+    std::vector<int> colperm, dstart(kMaxColDeg + 2, 0), dbase(kMaxColDeg + 2, 0);
+    std::vector<int2> colseq;
+    if (max_col <= kMaxColDeg) {
+        colperm.reserve(N);
+        colseq.reserve(E);
+        for (int d = 0; d <= kMaxColDeg; ++d) {
+            dstart[d] = (int)colperm.size();
+            dbase[d] = (int)colseq.size();
+            for (int j = 0; j < N; ++j) {
+                if (col_ptr[j + 1] - col_ptr[j] != d) continue;
+                colperm.push_back(j);
+                for (int k = col_ptr[j]; k < col_ptr[j + 1]; ++k) colseq.push_back(make_int2(col_edge[k], col_row[k]));
+            }
+        }
+        dstart[kMaxColDeg + 1] = (int)colperm.size();
+        dbase[kMaxColDeg + 1] = (int)colseq.size();
+    }
     std::vector<uint32_t> hcol((size_t)N * WM, 0u), acol((size_t)N * (WK > 0 ? WK : 1), 0u);
     for (int i = 0; i < M; ++i)
         for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e)
@@ -411,6 +436,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     gb += align256(sizeof(float) * Epad);
     gb += align256(sizeof(int2) * colER.size());
     gb += align256(lamEc_st.size());
+    gb += align256(sizeof(int) * colperm.size());
+    gb += align256(sizeof(int2) * colseq.size());
     if (CUDA_FAILED(cudaMalloc(&dec->graph_mem, gb))) { bsd_destroy(dec); return BSD_ERR_OOM; }
     dec->graph_bytes = gb;
     char* p = (char*)dec->graph_mem;
@@ -428,6 +455,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     float* d_D0 = carve<float>(p, Epad);
     int2* d_colER = colER.empty() ? nullptr : carve<int2>(p, colER.size());
     unsigned char* d_lamEc = carve<unsigned char>(p, lamEc_st.size());
+    int* d_colperm = colperm.empty() ? nullptr : carve<int>(p, colperm.size());
+    int2* d_colseq = colseq.empty() ? nullptr : carve<int2>(p, colseq.size());
     bool ok = !CUDA_FAILED(cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_row_col, H_col_idx, sizeof(int) * E, cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice)) &&
@@ -442,7 +471,11 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
               !CUDA_FAILED(cudaMemcpy(d_D0, D0.data(), sizeof(float) * Epad, cudaMemcpyHostToDevice)) &&
               (colER.empty() ||
                !CUDA_FAILED(cudaMemcpy(d_colER, colER.data(), sizeof(int2) * colER.size(), cudaMemcpyHostToDevice))) &&
-              !CUDA_FAILED(cudaMemcpy(d_lamEc, lamEc_st.data(), lamEc_st.size(), cudaMemcpyHostToDevice));
+              !CUDA_FAILED(cudaMemcpy(d_lamEc, lamEc_st.data(), lamEc_st.size(), cudaMemcpyHostToDevice)) &&
+              (colperm.empty() ||
+               !CUDA_FAILED(cudaMemcpy(d_colperm, colperm.data(), sizeof(int) * colperm.size(), cudaMemcpyHostToDevice))) &&
+              (colseq.empty() ||
+               !CUDA_FAILED(cudaMemcpy(d_colseq, colseq.data(), sizeof(int2) * colseq.size(), cudaMemcpyHostToDevice)));
     if (!ok) { bsd_destroy(dec); return BSD_ERR_CUDA; }
 
     DevGraph& g = dec->g;
@@ -455,6 +488,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.row_ptr = d_row_ptr; g.row_col = d_row_col; g.col_ptr = d_col_ptr; g.col_edge = d_col_edge; g.col_row = d_col_row;
     g.lam = d_lam; g.lamE = d_lamE; g.hcol = d_hcol; g.acol = d_acol; g.lamq = d_lamq; g.rs0 = d_rs0; g.D0 = d_D0;
     g.colER = d_colER; g.colK = colK; g.lamEc = d_lamEc;
+    g.colperm = d_colperm; g.colseq = d_colseq;
+    for (int d = 0; d < kMaxColDeg + 2; ++d) { g.dstart[d] = dstart[d]; g.dbase[d] = dbase[d]; }
 
     DecCfg& cfg = dec->cfg;
     cfg.max_rounds = params->max_rounds;
@@ -483,13 +518,19 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     const double win_b = 2.0 * W2 * ((double)msg_bytes * Epad + sizeof(uint32_t) * (double)SB + sizeof(SlotMeta)) +
                          12.0 + cfg.w + 8.0 + NR * (4.0 * WN + 12.0) + 4.0 + 2.0 * W2 * sizeof(int2);
     long long budget = params->workspace_bytes > 0 ? params->workspace_bytes : (4ll << 30);
-    // the batched seed BP's slots: the requested count (at most a quarter of
-    // the workspace)
+    // the batched seed BP's slots: the requested count, or by default for
+    // codes of at least kBatchMinEdges edges as many as kBatchStateBytes of
+    // messages hold (measured on GB300: on the 35k-edge synthetic DEM the
+    // batch decodes 1.7x faster than one candidate per block of warps, on the
+    // 6912-edge phenomenological DEM 1.7x slower, where the per-iteration
+    // launches dominate); at most a quarter of the workspace
     int bs_slots = 0;
-    if (dec->ls.batch && params->batch_slots > 0) {
+    const bool bs_default = params->batch_slots == 0 && E >= kBatchMinEdges;
+    if (dec->ls.batch && (params->batch_slots > 0 || bs_default)) {
         const long long cap = budget / 4;
         const int fit = batch_slots_for(g, cap);
-        const int want = params->batch_slots / kBsChunk * kBsChunk;
+        const int want = params->batch_slots > 0 ? params->batch_slots / kBsChunk * kBsChunk
+                                                 : batch_slots_for(g, kBatchStateBytes);
         bs_slots = want < fit ? want : fit;
         if (bs_slots > 0) {
             Work probe{};
@@ -504,8 +545,12 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     if (S > (1ll << 22)) S = 1ll << 22;
     if (S < A) S = A;
     if (A > (1ll << 22)) A = 1ll << 22;
+    // with the batched seed BP a chunk can hold far more shots than the seed
+    // store: only the shots it hands on need an entry, and they are decoded
+    // in windows of S
+    const long long S1 = bs_slots > 0 ? (1ll << 22) : 0;
     for (;;) {
-        const size_t wb = work_layout(g, cfg, S, A, nullptr, nullptr, bs_slots);
+        const size_t wb = work_layout(g, cfg, S, A, nullptr, nullptr, bs_slots, S1);
         if (cudaMalloc(&dec->work_mem, wb) == cudaSuccess) { dec->work_bytes = wb; break; }
         cudaGetLastError();
         dec->work_mem = nullptr;
@@ -514,7 +559,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
         A = A > 1 ? A / 2 : 1;
     }
     Work& w = dec->w;
-    work_layout(g, cfg, S, A, (char*)dec->work_mem, &w, bs_slots);
+    work_layout(g, cfg, S, A, (char*)dec->work_mem, &w, bs_slots, S1);
     dec->ctr_bytes = work_head_bytes(cfg);
     if (CUDA_FAILED(cudaMemset(dec->work_mem, 0, dec->ctr_bytes)) ||
         CUDA_FAILED(cudaMallocHost(&dec->h_nactive, sizeof(int)))) {
@@ -627,12 +672,29 @@ static void prof_collect(bsd_decoder* d)
     d->ev_used = 0;
 }
 
+// shots per chunk: the seed store, or with the batched seed BP the larger
+// chunk whose handed-on shots it decodes in windows of the seed store
+static long long chunk_of(const bsd_decoder* dec)
+{
+    return (dec->ls.batch && dec->w.bs_slots > 0) ? dec->w.S1 : dec->w.S;
+}
+
 static int decode_impl(bsd_decoder* dec, const uint32_t* d_synd, long long base, long long n, const Outputs& o,
                        cudaStream_t s)
 {
     LaunchHooks hk{prof_before, prof_after, dec};
     dec->prof_stream = s;
-    void* gx = dec->prof ? nullptr : (n <= dec->small_n && dec->graph_small ? dec->graph_small : dec->graph);
+    // a small chunk (at most S shots: no batched seed BP) runs the small-chunk
+    // graph, or its kernels one by one while timing is enabled
+    const bool small = dec->small_n > 0 && n <= dec->small_n && n <= dec->w.S;
+    if (dec->prof || (small ? !dec->graph_small : !dec->graph)) {
+        const LaunchShape ls = small ? small_shape(dec->ls, dec->cfg, dec->small_n) : dec->ls;
+        return launch_chunk(dec->g, dec->cfg, dec->w, ls, d_synd, base, n, o, s, dec->prof ? &hk : nullptr, nullptr,
+                            dec->h_nactive)
+                   ? BSD_ERR_CUDA
+                   : BSD_OK;
+    }
+    void* gx = small ? dec->graph_small : dec->graph;
     return launch_chunk(dec->g, dec->cfg, dec->w, dec->ls, d_synd, base, n, o, s, dec->prof ? &hk : nullptr, gx,
                         dec->h_nactive)
                ? BSD_ERR_CUDA
@@ -650,8 +712,9 @@ int bsd_decode(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, uint32_
     cudaStream_t s = (cudaStream_t)cuda_stream;
     dec->last_stream = s;
     Outputs o{d_corrections, dec->g.K > 0 ? d_obs_flips : nullptr, d_status, d_iters};
-    for (long long base = 0; base < B; base += dec->w.S) {
-        const long long n = (B - base) < dec->w.S ? (B - base) : dec->w.S;
+    const long long C = chunk_of(dec);
+    for (long long base = 0; base < B; base += C) {
+        const long long n = (B - base) < C ? (B - base) : C;
         const int rc = decode_impl(dec, d_syndromes, base, n, o, s);
         if (rc) return rc;
     }
@@ -669,7 +732,9 @@ int bsd_decode_host(bsd_decoder* dec, const uint32_t* h_syndromes, int64_t B, ui
     cudaStream_t s = (cudaStream_t)cuda_stream;
     dec->last_stream = s;
     const DevGraph& g = dec->g;
-    const long long C = dec->w.S;
+    // host chunks: the seed store, or for the batched seed BP up to 2^18 shots
+    const long long C = chunk_of(dec) > dec->w.S ? (chunk_of(dec) < (1ll << 18) ? chunk_of(dec) : (1ll << 18))
+                                                  : dec->w.S;
     const size_t need = align256(sizeof(uint32_t) * C * g.WM) + align256(sizeof(uint32_t) * C * g.WN) +
                         align256(sizeof(uint32_t) * C * (g.WK > 0 ? g.WK : 1)) + 2 * align256(sizeof(uint32_t) * C);
     if (dec->io_bytes < need) {

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(kBsChunk) k_bs_check(DevGraph g, DecCfg cfg, W
             m1 = L;
             m2 = L;
             const int rb = __ldg(g.row_ptr + i), re = __ldg(g.row_ptr + i + 1);
+#pragma unroll 4
             for (int e = rb; e < re; ++e) {
                 const float x = S::ld(E, (size_t)e * Bs + b);
                 const float a = fabsf(x);
@@ -135,90 +136,97 @@ __global__ void __launch_bounds__(kBsChunk) k_bs_check(DevGraph g, DecCfg cfg, W
     }
 }
 
-// Eq. 1 per edge, Eqs. 2-4 per (column, slot)
-template <int DV, int P>
-__global__ void __launch_bounds__(kBsChunk) k_bs_var(DevGraph g, DecCfg cfg, Work w)
+// Eq. 1 per edge, Eqs. 2-4 per (column, slot), for a run of columns of
+// degree D (positions [q0, q1) of the degree-sorted column order); every lane
+// of a warp holds the same column, so the degree is warp-uniform.  The next
+// column's (edge, row) pairs are loaded while the current one is computed.
+template <int D, int P>
+__device__ __forceinline__ void bs_var_run(const DevGraph& g, const DecCfg& cfg, const Work& w, int b, bool fresh,
+                                           int q0, int q1)
 {
-    if (!batch_running(w)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.stats[2], 1ull);
     using S = Store<P>;
     using T = typename S::T;
-    const BsRange rg = bs_range(w, g.N);
-    const int b = rg.b;
-    const int Bs = w.bs_slots;
-    const int shot = w.bs_shot[b];
-    if (shot < 0) return;
-    const bool fresh = w.bs_t[b] == 0;
     T* const E = reinterpret_cast<T*>(w.bsE);
+    const size_t Bs = (size_t)w.bs_slots;
     const float alpha = cfg.alpha, L = cfg.L;
-    for (int j = rg.lo; j < rg.hi; ++j) {
-        int kb = 0, deg = 0;
-        if constexpr (DV > 6) {
-            kb = __ldg(g.col_ptr + j);
-            deg = __ldg(g.col_ptr + j + 1) - kb;
+    const int2* seq = g.colseq + g.dbase[D] + (size_t)(q0 - g.dstart[D]) * D;
+    int2 er[D > 0 ? D : 1], nx[D > 0 ? D : 1];
+#pragma unroll
+    for (int k = 0; k < D; ++k) er[k] = __ldg(seq + k);
+    for (int q = q0; q < q1; ++q) {
+        seq += D;
+        if (q + 1 < q1) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) nx[k] = __ldg(seq + k);
         }
+        const int j = __ldg(g.colperm + q);
+        const float lj = __ldg(g.lam + j);
         // E(0) of a fresh slot: the same on every edge of the column
         const float x0 = fresh ? S::ld(reinterpret_cast<const T*>(g.lamEc), j) : 0.f;
-        float v[DV];
-        int ed[DV];
+        float v[D > 0 ? D : 1];
+        int ed[D > 0 ? D : 1];
 #pragma unroll
-        for (int k = 0; k < DV; ++k) {
-            int e = -1, r = 0;
-            if constexpr (DV <= 6) {
-                const int2 er = __ldg(g.colER + (size_t)k * g.Npad + j);
-                e = er.x;
-                r = er.y;
-                deg += (e >= 0) ? 1 : 0;
-            } else if (k < deg) {
-                e = __ldg(g.col_edge + kb + k);
-                r = __ldg(g.col_row + kb + k);
-            }
-            if (e >= 0) {
-                const float2 rec = w.bsR[(size_t)r * Bs + b];
-                const float xo = fresh ? x0 : S::ld(E, (size_t)e * Bs + b);
-                // the minimum over the row's other edges: min2 on an edge
-                // holding the minimum (a tie makes min2 = min1), min1 elsewhere
-                const float m = (fabsf(xo) == fabsf(rec.x)) ? rec.y : rec.x;
-                // sign: the row's parity (in m) without the edge's own sign
-                const float d = __fmul_rn(alpha, m);
-                v[k] = __uint_as_float(__float_as_uint(d) ^ (__float_as_uint(xo) & 0x80000000u));
-                ed[k] = e;
-            } else {
-                v[k] = INFINITY;
-                ed[k] = -1;
-            }
+        for (int k = 0; k < D; ++k) {
+            const float2 rec = w.bsR[(size_t)er[k].y * Bs + b];
+            const float xo = fresh ? x0 : S::ld(E, (size_t)er[k].x * Bs + b);
+            // the minimum over the row's other edges: min2 on an edge holding
+            // the minimum (a tie makes min2 = min1), min1 elsewhere
+            const float m = (fabsf(xo) == fabsf(rec.x)) ? rec.y : rec.x;
+            // sign: the row's parity (in m) without the edge's own sign
+            const float d = __fmul_rn(alpha, m);
+            v[k] = __uint_as_float(__float_as_uint(d) ^ (__float_as_uint(xo) & 0x80000000u));
+            ed[k] = er[k].x;
         }
-        // ascending order of value (the exchange network of the per-candidate engines)
+        // ascending order of value (an exchange network of D inputs)
 #pragma unroll
-        for (int a = 0; a < DV; ++a) {
+        for (int a = 0; a < D; ++a) {
 #pragma unroll
-            for (int k = 0; k + 1 < DV - a; ++k) {
+            for (int k = 0; k + 1 < D - a; ++k) {
                 if (v[k] > v[k + 1]) {
                     const float tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv;
                     const int te = ed[k]; ed[k] = ed[k + 1]; ed[k + 1] = te;
                 }
             }
         }
-        const float lj = __ldg(g.lam + j);
 #pragma unroll
-        for (int k = 0; k < DV; ++k) {                        // Eq. 2: leave d_i out
-            if (k < deg) {
-                float acc = lj;
+        for (int k = 0; k < D; ++k) {                         // Eq. 2: leave d_i out
+            float acc = lj;
 #pragma unroll
-                for (int k2 = 0; k2 < DV; ++k2)
-                    if (k2 != k && k2 < deg) acc = __fadd_rn(acc, v[k2]);
-                S::st(E, (size_t)ed[k] * Bs + b, fminf(fmaxf(acc, -L), L));
-            }
+            for (int k2 = 0; k2 < D; ++k2)
+                if (k2 != k) acc = __fadd_rn(acc, v[k2]);
+            S::st(E, (size_t)ed[k] * Bs + b, fminf(fmaxf(acc, -L), L));
         }
         float post = lj;                                      // Eq. 3
 #pragma unroll
-        for (int k = 0; k < DV; ++k)
-            if (k < deg) post = __fadd_rn(post, v[k]);
+        for (int k = 0; k < D; ++k) post = __fadd_rn(post, v[k]);
         if (post <= 0.f) {                                    // Eq. 4
-            const int q = atomicAdd(&w.bs_nl[b], 1);
-            if (q < kBsList) w.bs_list[(size_t)q * Bs + b] = j;
+            const int qn = atomicAdd(&w.bs_nl[b], 1);
+            if (qn < kBsList) w.bs_list[(size_t)qn * Bs + b] = j;
         }
+#pragma unroll
+        for (int k = 0; k < D; ++k) er[k] = nx[k];
     }
+}
+
+template <int DV, int P>
+__global__ void __launch_bounds__(kBsChunk) k_bs_var(DevGraph g, DecCfg cfg, Work w)
+{
+    if (!batch_running(w)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.stats[2], 1ull);
+    const BsRange rg = bs_range(w, g.N);
+    const int b = rg.b;
+    const int shot = w.bs_shot[b];
+    if (shot < 0) return;
+    const bool fresh = w.bs_t[b] == 0;
+    // the block's positions of the degree-sorted order, run by run of one degree
+#define BS_RUN(DD)                                                                  \
+    if constexpr (DD <= DV) {                                                       \
+        const int q0 = max(rg.lo, g.dstart[DD]), q1 = min(rg.hi, g.dstart[DD + 1]); \
+        if (q0 < q1) bs_var_run<DD, P>(g, cfg, w, b, fresh, q0, q1);                \
+    }
+    BS_RUN(0) BS_RUN(1) BS_RUN(2) BS_RUN(3) BS_RUN(4) BS_RUN(5) BS_RUN(6) BS_RUN(7) BS_RUN(8)
+    BS_RUN(9) BS_RUN(10) BS_RUN(11) BS_RUN(12) BS_RUN(13) BS_RUN(14) BS_RUN(15) BS_RUN(16)
+#undef BS_RUN
 }
 
 // stopping rule, outputs of converged shots, hand-off of the others, refill
@@ -350,6 +358,10 @@ int batch_grid(int device)
 
 namespace {
 
+// items per thread of the check pass (rows) and the error-node pass (columns)
+constexpr int kRowsPerThread = 2;
+constexpr int kColsPerThread = 8;
+
 void* check_func(int prec)
 {
     return prec == 0 ? (void*)k_bs_check<0> : prec == 1 ? (void*)k_bs_check<1> : (void*)k_bs_check<2>;
@@ -365,11 +377,13 @@ void* var_func(int dv, int prec)
 // column degree bound of the generic engines (3, 6 or 16)
 int dv_of(const DevGraph& g) { return g.max_col_deg <= 3 ? 3 : g.max_col_deg <= 6 ? 6 : 16; }
 
-int grid_pass(const LaunchShape& ls, const Work& w)
+// blocks of a pass: every slot chunk times groups of about `per` items
+// (rows or columns), enough blocks to keep every SM busy
+int grid_pass(const Work& w, int items, int per)
 {
     const int nch = w.bs_slots / kBsChunk;
-    int gr = ls.grid_bs > nch ? ls.grid_bs : nch;
-    return (gr / nch) * nch;                   // whole item groups per slot chunk
+    const int groups = (items + per - 1) / per;
+    return nch * (groups > 0 ? groups : 1);
 }
 
 int grid_retire(const LaunchShape& ls, const Work& w)
@@ -417,8 +431,10 @@ int add_batch_nodes(cudaGraph_t graph, cudaGraphNode_t dep, cudaGraphNode_t* las
         cudaGraphNode_t nc, nv, nr;
         void* pargs[] = {&g, &cfg, &w};
         void* rargs[] = {&g, &cfg, &w, &screened, &cond, &use};
-        rc = add_node(body, &nc, nullptr, check_func(g.prec), grid_pass(ls, w), kBsChunk, pargs);
-        if (!rc) rc = add_node(body, &nv, &nc, var_func(dv_of(g), g.prec), grid_pass(ls, w), kBsChunk, pargs);
+        rc = add_node(body, &nc, nullptr, check_func(g.prec), grid_pass(w, g.M, kRowsPerThread), kBsChunk, pargs);
+        if (!rc)
+            rc = add_node(body, &nv, &nc, var_func(dv_of(g), g.prec), grid_pass(w, g.N, kColsPerThread), kBsChunk,
+                          pargs);
         if (!rc) rc = add_node(body, &nr, &nv, (void*)k_bs_retire, grid_retire(ls, w), 256, rargs);
     }
     if (!rc) *last = nw;
@@ -431,7 +447,8 @@ int launch_batch_direct(const DevGraph& g, const DecCfg& cfg, const Work& w, con
     const cudaGraphConditionalHandle none{};
     k_bs_begin<<<1, 256, 0, s>>>(w, screened, none, 0);
     if (CUDA_FAILED(cudaGetLastError())) return -2;
-    const int gp = grid_pass(ls, w), gr = grid_retire(ls, w);
+    const int gc = grid_pass(w, g.M, kRowsPerThread), gv = grid_pass(w, g.N, kColsPerThread);
+    const int gr = grid_retire(ls, w);
     void* cf = check_func(g.prec);
     void* vf = var_func(dv_of(g), g.prec);
     DevGraph gg = g;
@@ -447,9 +464,9 @@ int launch_batch_direct(const DevGraph& g, const DecCfg& cfg, const Work& w, con
     for (;;) {
         for (int k = 0; k < kBetweenReads; ++k) {
             if (hk) hk->before(hk->ctx, 8);
-            if (CUDA_FAILED(cudaLaunchKernel(cf, dim3(gp), dim3(kBsChunk), pargs, 0, s))) return -2;
+            if (CUDA_FAILED(cudaLaunchKernel(cf, dim3(gc), dim3(kBsChunk), pargs, 0, s))) return -2;
             if (hk) { hk->after(hk->ctx, 8); hk->before(hk->ctx, 9); }
-            if (CUDA_FAILED(cudaLaunchKernel(vf, dim3(gp), dim3(kBsChunk), pargs, 0, s))) return -2;
+            if (CUDA_FAILED(cudaLaunchKernel(vf, dim3(gv), dim3(kBsChunk), pargs, 0, s))) return -2;
             if (hk) { hk->after(hk->ctx, 9); hk->before(hk->ctx, 10); }
             if (CUDA_FAILED(cudaLaunchKernel((void*)k_bs_retire, dim3(gr), dim3(256), rargs, 0, s))) return -2;
             if (hk) hk->after(hk->ctx, 10);

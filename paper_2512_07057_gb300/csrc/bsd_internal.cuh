@@ -33,6 +33,7 @@
 
 namespace bsd {
 
+constexpr int kMaxColDeg = 16;   // the generic engines' largest column degree bound
 constexpr int kMaxBeam = 64;
 constexpr int kMaxResults = 64;
 constexpr double kFixScale = 65536.0;   // fixed-point grid 2^-16 for scores and weights
@@ -61,6 +62,14 @@ struct DevGraph {
     const int2* colER;     // [colK][Npad] (edge, row) of edge k of column j, (-1, -1) past its degree
     int colK;              // 3 or 6 (the generic engines' degree bound), 0 when colER is absent
     const void* lamEc;     // [Npad] E(0) of column j (clamp(Lambda_j)) in the storage format
+    // the columns ordered by degree (batched seed BP): colperm[q] is the
+    // column at position q, the columns of degree d hold positions
+    // [dstart[d], dstart[d + 1]), and the (edge, row) pairs of the column at
+    // position q of degree d are colseq[dbase[d] + (q - dstart[d]) * d + k]
+    const int* colperm;    // [N]
+    const int2* colseq;    // [E]
+    int dstart[kMaxColDeg + 2];
+    int dbase[kMaxColDeg + 2];
 };
 
 struct DecCfg {
@@ -95,6 +104,7 @@ struct RunDesc {
     long long chunk_n;     // shots in the chunk
     int pass;              // current beam pass
     int round;             // current beam round of the pass (graph launches read it from here)
+    int win_base;          // batched seed BP: first entry of the fail list in the current window
 };
 
 // per-chunk counters (reset by k_begin_chunk)
@@ -115,9 +125,11 @@ struct Counters {
 
 struct Work {
     long long S;           // shots per chunk = seed-store entries
+    long long S1;          // with the batched seed BP: shots per chunk (>= S); the shots it hands on are
+                           // decoded from the seed on in windows of S
     long long A;           // active entries per beam pass
     int SB;                // words per slot bit record: sp[WM] mask[WN] vals[WN] ehat[WN]
-    int* queue;            // [S] chunk-local shots the screen passed on to the seed BP
+    int* queue;            // [S1] chunk-local shots the screen passed on to the seed BP
     // batched seed BP over slots (bsd_batch.cu); bs_slots = 0: not used
     int bs_slots;          // Bs, a multiple of kBsChunk
     unsigned char* bsE;    // [Epad][Bs] messages in the storage format, shots contiguous
@@ -126,7 +138,7 @@ struct Work {
     int* bs_t;             // [Bs] iterations the slot's shot has run
     int* bs_nl;            // [Bs] columns with e^_j(t) = 1 found in the current iteration
     int* bs_list;          // [kBsList][Bs] those columns
-    int* fail;             // [S] shots the batch passes on to the per-candidate seed kernel
+    int* fail;             // [S1] shots the batch passes on to the per-candidate seed kernel
     // seed store [S]
     unsigned char* seedE;  // [S][Epad] messages in the storage format
     uint32_t* seedBits;    // [S][SB]
@@ -172,7 +184,7 @@ bool cuda_failed_at(cudaError_t e, const char* file, int line);
 // (base may be null to size it); returns the bytes used.  The counters and the
 // run descriptor come first, in the first head_bytes(cfg) bytes.
 size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w,
-                   int bs_slots = 0);
+                   int bs_slots = 0, long long S1 = 0);
 size_t work_head_bytes(const DecCfg& cfg);
 
 // host-side launch helpers (bsd_kernels.cu)

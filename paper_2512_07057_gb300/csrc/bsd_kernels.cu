@@ -848,6 +848,7 @@ __global__ void k_begin_chunk(Work w, int n_round_ints, const uint32_t* synd, Ou
         d.chunk_n = n;
         d.pass = 0;
         d.round = 1;
+        d.win_base = 0;
         *w.desc = d;
     }
 }
@@ -894,6 +895,45 @@ __global__ void k_round_end(Work w, int max_rounds, cudaGraphConditionalHandle c
         const int more = (r < max_rounds && *((volatile int*)(w.round_ctr + 3 * (r + 1) + 2)) > 0) ? 1 : 0;
         w.desc->round = r + 1;
         cudaGraphSetConditional(cond, (unsigned)more);
+    }
+}
+
+// batched seed BP: the shots it hands on are decoded from the seed on in
+// windows of at most S shots (the seed store); graph only: enter the loop
+// over windows if there is any
+__global__ void k_win_gate(Work w, cudaGraphConditionalHandle cond)
+{
+    count_launch(w);
+    if (threadIdx.x == 0) {
+        w.desc->win_base = 0;
+        cudaGraphSetConditional(cond, *((volatile int*)&w.ctr->n_fail) > 0 ? 1u : 0u);
+    }
+}
+
+// start of a window: the per-window counters and early-abort keys start
+// afresh, as at the start of a chunk (base < 0: keep the window base)
+__global__ void k_win_begin(Work w, int n_round_ints, int base)
+{
+    count_launch(w);
+    for (int q = threadIdx.x; q < n_round_ints; q += blockDim.x) w.round_ctr[q] = 0;
+    for (long long q = threadIdx.x; q < w.A; q += blockDim.x) w.first_ok[q] = 0ull;
+    if (threadIdx.x == 0) {
+        w.ctr->claim_seed = 0;
+        w.ctr->n_active = 0;
+        w.desc->pass = 0;
+        w.desc->round = 1;
+        if (base >= 0) w.desc->win_base = base;
+    }
+}
+
+// end of a window: graph only, another window if the fail list goes on
+__global__ void k_win_end(Work w, cudaGraphConditionalHandle cond)
+{
+    count_launch(w);
+    if (threadIdx.x == 0) {
+        const long long nb = (long long)w.desc->win_base + w.S;
+        w.desc->win_base = (int)(nb < 0x7fffffffll ? nb : 0x7fffffffll);
+        cudaGraphSetConditional(cond, nb < (long long)*((volatile int*)&w.ctr->n_fail) ? 1u : 0u);
     }
 }
 
@@ -1099,9 +1139,14 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
     constexpr int kBatch = Eng::Grp::kBlock ? 1 : 4;
     // the shots: every shot of the chunk (screened = 0), those the screen
     // passed on (1), or those the batched seed BP passed on (2)
-    const int* list = screened == 2 ? w.fail : w.queue;
-    const int nq = screened == 2 ? *((volatile int*)&w.ctr->n_fail)
-                                 : screened ? *((volatile int*)&w.ctr->n_queue) : 0;
+    const int wb = screened == 2 ? *((volatile int*)&w.desc->win_base) : 0;
+    const int* list = screened == 2 ? w.fail + wb : w.queue;
+    int nq = screened ? *((volatile int*)&w.ctr->n_queue) : 0;
+    if (screened == 2) {
+        // the current window of the fail list: at most S shots (the seed store)
+        const long long left = (long long)*((volatile int*)&w.ctr->n_fail) - wb;
+        nq = (int)(left < w.S ? (left > 0 ? left : 0) : w.S);
+    }
     int kcur = 0, kend = 0;                      // claimed slots [kcur, kend), the same in the whole group
     for (;;) {
         if (kcur >= kend) {
@@ -1792,32 +1837,44 @@ static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, c
         launch_screen(g, cfg, w, ls, s);
         if (hk) hk->after(hk->ctx, 0);
     }
-    int seed_src = ls.screen;
-    if (ls.batch && w.bs_slots > 0) {
-        if (launch_batch_direct(g, cfg, w, ls, ls.screen, s, hk, host_n_active)) return -2;
-        seed_src = 2;
-    }
-    if (hk) hk->before(hk->ctx, 0);
-    k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, seed_src);
-    if (hk) hk->after(hk->ctx, 0);
-    if (CUDA_FAILED(cudaGetLastError())) return -2;
-    if (cfg.max_rounds == 0) return 0;
-    // without a graph: read the number of active entries back, then run
-    // exactly the passes it needs
-    if (CUDA_FAILED(cudaMemcpyAsync(host_n_active, &w.ctr->n_active, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+    // the seed kernel on its shots, then exactly the beam passes they need
+    // (without a graph the number of active entries is read back)
+    auto seed_and_passes = [&](int seed_src) -> int {
+        if (hk) hk->before(hk->ctx, 0);
+        k_seed<Eng><<<ls.grid_seed, threads, ls.smem_bp, s>>>(g, cfg, w, seed_src);
+        if (hk) hk->after(hk->ctx, 0);
+        if (CUDA_FAILED(cudaGetLastError())) return -2;
+        if (cfg.max_rounds == 0) return 0;
+        if (CUDA_FAILED(cudaMemcpyAsync(host_n_active, &w.ctr->n_active, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+            CUDA_FAILED(cudaStreamSynchronize(s)))
+            return -2;
+        const long long passes = (*host_n_active + w.A - 1) / w.A;
+        for (long long p = 0; p < passes; ++p) {
+            for (int r = 1; r <= cfg.max_rounds; ++r) {
+                if (hk) hk->before(hk->ctx, 1);
+                k_round<Eng><<<ls.grid_round, threads, ls.smem_bp, s>>>(g, cfg, w, r);
+                if (hk) { hk->after(hk->ctx, 1); hk->before(hk->ctx, 2); }
+                k_select<<<ls.grid_select, 32 * ls.select_warps, ls.smem_select, s>>>(g, cfg, w, r);
+                if (hk) hk->after(hk->ctx, 2);
+            }
+            k_pass_end<<<1, 128, 0, s>>>(w, nri, cudaGraphConditionalHandle{}, 0);
+            if (CUDA_FAILED(cudaGetLastError())) return -2;
+        }
+        return 0;
+    };
+    if (!(ls.batch && w.bs_slots > 0)) return seed_and_passes(ls.screen);
+    // batched seed BP over the chunk, then the shots it handed on in windows
+    // of at most S (the seed store)
+    if (launch_batch_direct(g, cfg, w, ls, ls.screen, s, hk, host_n_active)) return -2;
+    if (CUDA_FAILED(cudaMemcpyAsync(host_n_active, &w.ctr->n_fail, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
         CUDA_FAILED(cudaStreamSynchronize(s)))
         return -2;
-    const long long passes = (*host_n_active + w.A - 1) / w.A;
-    for (long long p = 0; p < passes; ++p) {
-        for (int r = 1; r <= cfg.max_rounds; ++r) {
-            if (hk) hk->before(hk->ctx, 1);
-            k_round<Eng><<<ls.grid_round, threads, ls.smem_bp, s>>>(g, cfg, w, r);
-            if (hk) { hk->after(hk->ctx, 1); hk->before(hk->ctx, 2); }
-            k_select<<<ls.grid_select, 32 * ls.select_warps, ls.smem_select, s>>>(g, cfg, w, r);
-            if (hk) hk->after(hk->ctx, 2);
-        }
-        k_pass_end<<<1, 128, 0, s>>>(w, nri, cudaGraphConditionalHandle{}, 0);
+    const long long n_fail = *host_n_active;
+    for (long long wb = 0; wb < n_fail; wb += w.S) {
+        k_win_begin<<<1, 128, 0, s>>>(w, nri, (int)wb);
         if (CUDA_FAILED(cudaGetLastError())) return -2;
+        const int rc = seed_and_passes(2);
+        if (rc) return rc;
     }
     return 0;
 }
@@ -1850,6 +1907,67 @@ static int add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cudaGraphN
     return !CUDA_FAILED(cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &p)) ? 0 : -2;
 }
 
+// WHILE (a window of active shots left) { round 1, WHILE (the next round has
+// children) { round r, selection, round end }, pass end }, after `dep` in
+// `graph`: a chunk runs exactly the passes and rounds it needs
+template <class Eng>
+static int add_beam_nodes(cudaGraph_t graph, cudaGraphNode_t dep, cudaGraphNode_t* last, DevGraph& g, DecCfg& cfg,
+                          Work& w, const LaunchShape& ls)
+{
+    const int threads = 32 * ls.warps_per_block;
+    int nri = 3 * (cfg.max_rounds + 2);
+    int rc = 0;
+    cudaGraphConditionalHandle cpass, cround;
+    cudaGraphNode_t gate, wpass, rbegin, wround, pend;
+    cudaGraphNodeParams cp{};
+    if (CUDA_FAILED(cudaGraphConditionalHandleCreate(&cpass, graph, 0, cudaGraphCondAssignDefault))) rc = -2;
+    if (!rc) {
+        void* gargs[] = {&w, &cpass};
+        rc = add_kernel(graph, &gate, &dep, (void*)k_pass_gate, 1, 32, 0, gargs);
+    }
+    if (!rc) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cpass;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (CUDA_FAILED(cudaGraphAddNode(&wpass, graph, &gate, nullptr, 1, &cp))) rc = -2;
+    }
+    cudaGraph_t body = rc ? nullptr : cp.conditional.phGraph_out[0];
+    if (!rc && CUDA_FAILED(cudaGraphConditionalHandleCreate(&cround, body, 0, 0))) rc = -2;
+    if (!rc) {
+        void* bargs[] = {&w, &cround};
+        rc = add_kernel(body, &rbegin, nullptr, (void*)k_rounds_begin, 1, 32, 0, bargs);
+    }
+    cudaGraphNodeParams cr{};
+    if (!rc) {
+        cr.type = cudaGraphNodeTypeConditional;
+        cr.conditional.handle = cround;
+        cr.conditional.type = cudaGraphCondTypeWhile;
+        cr.conditional.size = 1;
+        if (CUDA_FAILED(cudaGraphAddNode(&wround, body, &rbegin, nullptr, 1, &cr))) rc = -2;
+    }
+    if (!rc) {
+        // kernel parameters are copied when a node is added; round 0 means
+        // "read the round counter"
+        cudaGraph_t rbody = cr.conditional.phGraph_out[0];
+        cudaGraphNode_t nr, ns, ne;
+        int r0 = 0, maxr = cfg.max_rounds;
+        void* rargs[] = {&g, &cfg, &w, &r0};
+        rc = add_kernel(rbody, &nr, nullptr, (void*)k_round<Eng>, ls.grid_round, threads, ls.smem_bp, rargs);
+        if (!rc) rc = add_kernel(rbody, &ns, &nr, (void*)k_select, ls.grid_select, 32 * ls.select_warps,
+                                    ls.smem_select, rargs);
+        void* eargs[] = {&w, &maxr, &cround};
+        if (!rc) rc = add_kernel(rbody, &ne, &ns, (void*)k_round_end, 1, 32, 0, eargs);
+    }
+    if (!rc) {
+        int use = 1;
+        void* pargs[] = {&w, &nri, &cpass, &use};
+        rc = add_kernel(body, &pend, &wround, (void*)k_pass_end, 1, 128, 0, pargs);
+    }
+    if (!rc) *last = wpass;
+    return rc;
+}
+
 template <class Eng>
 static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0, const LaunchShape& ls,
                          cudaGraphExec_t* out)
@@ -1862,7 +1980,7 @@ static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0,
     cudaGraph_t graph = nullptr;
     if (CUDA_FAILED(cudaGraphCreate(&graph, 0))) return -2;
     int rc = 0;
-    cudaGraphNode_t seed, scr, bs;
+    cudaGraphNode_t seed, scr, last;
     const bool batched = ls.batch && w.bs_slots > 0;
     int screened = batched ? 2 : ls.screen;
     void* sargs[] = {&g, &cfg, &w, &screened};
@@ -1870,61 +1988,45 @@ static int build_graph_t(const DevGraph& g0, const DecCfg& cfg0, const Work& w0,
     if (ls.screen)
         rc = add_kernel(graph, &scr, nullptr, screen_func(ls), ls.grid_screen, 32 * kScreenWarps, ls.smem_screen,
                         cargs);
-    // the batched seed BP, then the per-candidate seed kernel for the shots it passes on
-    if (!rc && batched) rc = add_batch_nodes(graph, ls.screen ? scr : nullptr, &bs, g, cfg, w, ls, ls.screen);
-    if (!rc)
-        rc = add_kernel(graph, &seed, batched ? &bs : ls.screen ? &scr : nullptr, (void*)k_seed<Eng>, ls.grid_seed,
-                        threads, ls.smem_bp, sargs);
-    // seed, then WHILE (a window of active shots left) { round 1, WHILE (the
-    // next round has children) { round r, selection, round end }, pass end }:
-    // a chunk runs exactly the passes and rounds it needs
-    if (!rc && cfg.max_rounds > 0) {
-        cudaGraphConditionalHandle cpass, cround;
-        cudaGraphNode_t gate, wpass, rbegin, wround, pend;
-        cudaGraphNodeParams cp{};
-        if (CUDA_FAILED(cudaGraphConditionalHandleCreate(&cpass, graph, 0, cudaGraphCondAssignDefault))) rc = -2;
+    if (!batched) {
+        // seed, then the beam passes
+        if (!rc)
+            rc = add_kernel(graph, &seed, ls.screen ? &scr : nullptr, (void*)k_seed<Eng>, ls.grid_seed, threads,
+                            ls.smem_bp, sargs);
+        if (!rc && cfg.max_rounds > 0) rc = add_beam_nodes<Eng>(graph, seed, &last, g, cfg, w, ls);
+    } else {
+        // the batched seed BP over the chunk, then WHILE (shots handed on
+        // remain) { window start, the seed kernel on at most S of them, the
+        // beam passes, window end }
+        cudaGraphNode_t bs, wgate, wwin;
+        cudaGraphConditionalHandle cwin;
+        if (!rc) rc = add_batch_nodes(graph, ls.screen ? scr : nullptr, &bs, g, cfg, w, ls, ls.screen);
+        if (!rc && CUDA_FAILED(cudaGraphConditionalHandleCreate(&cwin, graph, 0, cudaGraphCondAssignDefault)))
+            rc = -2;
         if (!rc) {
-            void* gargs[] = {&w, &cpass};
-            rc = add_kernel(graph, &gate, &seed, (void*)k_pass_gate, 1, 32, 0, gargs);
+            void* gargs[] = {&w, &cwin};
+            rc = add_kernel(graph, &wgate, &bs, (void*)k_win_gate, 1, 32, 0, gargs);
         }
+        cudaGraphNodeParams cp{};
         if (!rc) {
             cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = cpass;
+            cp.conditional.handle = cwin;
             cp.conditional.type = cudaGraphCondTypeWhile;
             cp.conditional.size = 1;
-            if (CUDA_FAILED(cudaGraphAddNode(&wpass, graph, &gate, nullptr, 1, &cp))) rc = -2;
-        }
-        cudaGraph_t body = rc ? nullptr : cp.conditional.phGraph_out[0];
-        if (!rc && CUDA_FAILED(cudaGraphConditionalHandleCreate(&cround, body, 0, 0))) rc = -2;
-        if (!rc) {
-            void* bargs[] = {&w, &cround};
-            rc = add_kernel(body, &rbegin, nullptr, (void*)k_rounds_begin, 1, 32, 0, bargs);
-        }
-        cudaGraphNodeParams cr{};
-        if (!rc) {
-            cr.type = cudaGraphNodeTypeConditional;
-            cr.conditional.handle = cround;
-            cr.conditional.type = cudaGraphCondTypeWhile;
-            cr.conditional.size = 1;
-            if (CUDA_FAILED(cudaGraphAddNode(&wround, body, &rbegin, nullptr, 1, &cr))) rc = -2;
+            if (CUDA_FAILED(cudaGraphAddNode(&wwin, graph, &wgate, nullptr, 1, &cp))) rc = -2;
         }
         if (!rc) {
-            // kernel parameters are copied when a node is added; round 0 means
-            // "read the round counter"
-            cudaGraph_t rbody = cr.conditional.phGraph_out[0];
-            cudaGraphNode_t nr, ns, ne;
-            int r0 = 0, maxr = cfg.max_rounds;
-            void* rargs[] = {&g, &cfg, &w, &r0};
-            rc = add_kernel(rbody, &nr, nullptr, (void*)k_round<Eng>, ls.grid_round, threads, ls.smem_bp, rargs);
-            if (!rc) rc = add_kernel(rbody, &ns, &nr, (void*)k_select, ls.grid_select, 32 * ls.select_warps,
-                                        ls.smem_select, rargs);
-            void* eargs[] = {&w, &maxr, &cround};
-            if (!rc) rc = add_kernel(rbody, &ne, &ns, (void*)k_round_end, 1, 32, 0, eargs);
-        }
-        if (!rc) {
-            int use = 1;
-            void* pargs[] = {&w, &nri, &cpass, &use};
-            rc = add_kernel(body, &pend, &wround, (void*)k_pass_end, 1, 128, 0, pargs);
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            cudaGraphNode_t wbeg, wend;
+            int keep = -1;
+            void* bargs[] = {&w, &nri, &keep};
+            rc = add_kernel(body, &wbeg, nullptr, (void*)k_win_begin, 1, 128, 0, bargs);
+            if (!rc)
+                rc = add_kernel(body, &seed, &wbeg, (void*)k_seed<Eng>, ls.grid_seed, threads, ls.smem_bp, sargs);
+            cudaGraphNode_t tail = seed;
+            if (!rc && cfg.max_rounds > 0) rc = add_beam_nodes<Eng>(body, seed, &tail, g, cfg, w, ls);
+            void* eargs[] = {&w, &cwin};
+            if (!rc) rc = add_kernel(body, &wend, &tail, (void*)k_win_end, 1, 32, 0, eargs);
         }
     }
     cudaGraphExec_t gx = nullptr;
@@ -1968,8 +2070,9 @@ size_t work_head_bytes(const DecCfg& cfg)
 }
 
 size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long A, char* base, Work* w,
-                   int bs_slots)
+                   int bs_slots, long long S1)
 {
+    if (bs_slots <= 0 || S1 < S) S1 = S;
     const size_t W2 = 2 * (size_t)cfg.w;
     const size_t SB = (size_t)g.WM + 3 * (size_t)g.WN;
     const size_t NR = (size_t)cfg.num_results;
@@ -1984,6 +2087,7 @@ size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long 
     char* stats = take(kStats * sizeof(unsigned long long));
     Work v{};
     v.S = S;
+    v.S1 = S1;
     v.A = A;
     v.SB = (int)SB;
     v.ctr = reinterpret_cast<Counters*>(ctr);
@@ -1994,7 +2098,7 @@ size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long 
     v.seedBits = (uint32_t*)take(sizeof(uint32_t) * (size_t)S * SB);
     v.seedMeta = (SlotMeta*)take(sizeof(SlotMeta) * (size_t)S);
     v.seed_shot = (int*)take(sizeof(int) * (size_t)S);
-    v.queue = (int*)take(sizeof(int) * (size_t)S);
+    v.queue = (int*)take(sizeof(int) * (size_t)S1);
     v.slotE = (unsigned char*)take(2 * (size_t)A * W2 * snap_bytes(g));
     v.slotBits = (uint32_t*)take(sizeof(uint32_t) * 2 * (size_t)A * W2 * SB);
     v.slotMeta = (SlotMeta*)take(sizeof(SlotMeta) * 2 * (size_t)A * W2);
@@ -2020,7 +2124,7 @@ size_t work_layout(const DevGraph& g, const DecCfg& cfg, long long S, long long 
         v.bs_t = (int*)take(sizeof(int) * Bs);
         v.bs_nl = (int*)take(sizeof(int) * Bs);
         v.bs_list = (int*)take(sizeof(int) * Bs * (size_t)kBsList);
-        v.fail = (int*)take(sizeof(int) * (size_t)S);
+        v.fail = (int*)take(sizeof(int) * (size_t)S1);
     }
     if (w) *w = v;
     return off;

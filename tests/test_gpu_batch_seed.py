@@ -131,6 +131,19 @@ def test_high_degree_columns_and_negative_priors():
     _same(on, _oracle(prob, params, shots.syndromes), shots.B)
 
 
+def test_default_slots_follow_the_code_size():
+    """By default the batch is used for codes of at least 16384 edges (the
+    synthetic DEM), not for smaller ones (the phenomenological DEM)."""
+    syn = D.BeamSearchDecoder(W.synthetic_dem(), D.make_params("beam32_340iters", ms_scale=0.625,
+                                                               workspace_bytes=2 << 30))
+    assert syn.info["batch"]["active"] and syn.info["batch"]["slots"] >= 256
+    syn.close()
+    phen = D.BeamSearchDecoder(W.bb_phenomenological(12, 6, 12, 2e-3, 2e-3),
+                               D.make_params("beam32_340iters", ms_scale=0.625))
+    assert not phen.info["batch"]["active"] and phen.info["batch"]["slots"] == 0
+    phen.close()
+
+
 def test_batch_is_off_where_it_does_not_apply():
     """num_results > 1 (a converged seed joins results and the search goes
     on), weighted min-sum and the small engine of the BB codes keep the
