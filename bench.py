@@ -203,6 +203,17 @@ def make_workload(rank: int, shots: int, ps=PS):
     return out
 
 
+def wilson(k: int, n: int, z: float = 1.96) -> tuple[float, float]:
+    """95% Wilson score interval of a binomial proportion k / n."""
+    if n <= 0:
+        return 0.0, 1.0
+    p = k / n
+    d = 1 + z * z / n
+    c = (p + z * z / (2 * n)) / d
+    h = z * np.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / d
+    return float(max(0.0, c - h)), float(min(1.0, c + h))
+
+
 def ler_of(prob, shots, obs, status):
     from paper_2512_07057_gb300 import workloads as W
     o = W.unpack_bits(obs[:, :(prob.K + 31) // 32], prob.K)
@@ -899,7 +910,7 @@ def run_unrolled(args, rank: int, world: int, local_rank: int):
     def step(i):
         s_t, e_t = batches[i]
         opt.zero_grad(set_to_none=True)
-        loss = G.unrolled_loss(w, tr, s_t, e_t)
+        loss = G.unrolled_loss(w, tr, s_t, e_t)[0]
         loss.backward()
         opt.step()
         return loss
@@ -1008,7 +1019,7 @@ def _unrolled_e2e(tr, w, opt, prob, Bn, args, dev):
         s_t = host[i][0].to(f"cuda:{dev}", non_blocking=True)
         e_t = host[i][1].to(f"cuda:{dev}", non_blocking=True)
         opt.zero_grad(set_to_none=True)
-        loss = G.unrolled_loss(w, tr, s_t, e_t)
+        loss = G.unrolled_loss(w, tr, s_t, e_t)[0]
         loss.backward()
         opt.step()
         return float(loss.detach())            # device -> host read of the step's loss
@@ -1037,11 +1048,19 @@ def _judge_weights(prob, args, dev):
     wl, hist = G.train_weights(prob, T=UNR_T, ckpt_every=UNR_K, batch=UNR_B, steps=args.train_steps, lr=UNR_LR,
                                init=ALPHA, tag="unrolled_judge_train", device=dev)
     train_s = time.perf_counter() - t0
+    # objectives that weight the late iterations (the plain decoder reads its
+    # hard decision at the last one): the last term alone, and c_t = t / T
+    variants = {"learned": wl}
+    for vname, c in (("learned_last_iteration", np.eye(UNR_T)[-1]),
+                     ("learned_linear_in_t", np.arange(1, UNR_T + 1) / UNR_T)):
+        variants[vname], _ = G.train_weights(prob, T=UNR_T, ckpt_every=UNR_K, batch=UNR_B, steps=args.train_steps,
+                                             lr=UNR_LR, init=ALPHA, tag="unrolled_judge_train", device=dev,
+                                             iter_weights=c)
     # the loss on one fixed held-out batch, with the initial and the learned weights
     tr = G.UnrolledTrainer(prob, UNR_B, UNR_T, UNR_K, device=dev)
     vs, ve, _ = G.batch_tensors(prob, UNR_B, W.shot_seed("unrolled_judge_validation", 0), dev)
     val = {}
-    for wname, wts in (("scale_0.625", np.full_like(wl, ALPHA)), ("learned", wl)):
+    for wname, wts in (("scale_0.625", np.full_like(wl, ALPHA)), *variants.items()):
         lv = tr.forward(torch.from_numpy(wts).to(f"cuda:{dev}"), vs, ve).cpu().numpy()
         val[wname] = {"loss": float(lv[0]), "loss_last_iteration": float(lv[-1])}
     tr.close()
@@ -1054,13 +1073,20 @@ def _judge_weights(prob, args, dev):
                          ("beam64_640iters", D.make_params(PHEN_PRESET, ms_scale=ALPHA))):
         dec = D.BeamSearchDecoder(prob, params, device=dev)
         res = {}
-        for wname, wts in (("scale_0.625", None), ("learned", wl)):
+        for wname, wts in (("scale_0.625", None), *variants.items()):
             dec.set_weights(wts)
             o = dec.decode(synd)
             torch.cuda.synchronize(dev)
             st = D.from_torch_words(o.status)
             fails = int(round(ler_of(prob, sh, D.from_torch_words(o.obs_flips), st & 7) * sh.B))
-            res[wname] = {"ler": fails / sh.B, "failures": fails, "not_converged": int(((st & 7) == 4).sum())}
+            lo, hi = wilson(fails, sh.B)
+            res[wname] = {"ler": fails / sh.B, "failures": fails, "wilson95": [lo, hi],
+                          "not_converged": int(((st & 7) == 4).sum())}
+        # a change is significant when the Wilson intervals do not overlap
+        base = res["scale_0.625"]["wilson95"]
+        for wname in variants:
+            iv = res[wname]["wilson95"]
+            res[wname]["differs_from_scale"] = bool(iv[1] < base[0] or iv[0] > base[1])
         dec.close()
         out[name] = res
     return out

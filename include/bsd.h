@@ -315,9 +315,13 @@ int bsd_unrolled_forward(const bsd_decoder *dec, const uint32_t *d_syndromes, co
                          int32_t T, int32_t ckpt_every, const float *d_weights, float *d_loss, float *d_llr,
                          void *d_work, int64_t work_bytes, void *cuda_stream);
 
-/*   d_grad_loss     device, float [1]: the derivative of the caller's objective
- *                   with respect to the loss (1 for the loss itself)
- *   d_grad_weights  device, float [T][E]: overwritten with d_grad_loss * dloss/dw
+/*   d_grad_loss     device, float [T + 1]: the derivative of the caller's
+ *                   objective with respect to the entries of the forward's
+ *                   loss vector -- [0] the total, [t] the term of iteration t
+ *                   ({1, 0, ..., 0} for the loss itself; {0, c_1, ..., c_T}
+ *                   for an objective that weights iteration t by c_t)
+ *   d_grad_weights  device, float [T][E]: overwritten with the derivative of
+ *                   that objective with respect to the weights
  * Asynchronous on cuda_stream; same errors as the forward.  Weight gradients
  * are sums over the batch taken in a fixed order: the result is deterministic. */
 int bsd_unrolled_backward(const bsd_decoder *dec, int64_t B, int32_t T, int32_t ckpt_every, const float *d_weights,

@@ -104,12 +104,14 @@ def _initial(tab: Tables, B: int, L: float):
 
 
 def unrolled_loss(tab: Tables, s_bits: np.ndarray, e_bits: np.ndarray, weights: torch.Tensor,
-                  llr_clamp: float = 1e4, record: bool = False):
+                  llr_clamp: float = 1e4, record: bool = False, iter_weights=None):
     """Loss of the unrolled decoder on B shots.
 
     s_bits: uint8 [B, M] syndromes; e_bits: uint8 [B, N] true errors;
-    weights: float64 [T, E] (may require grad).  Returns (loss, per-iteration
-    losses [T], posteriors [T, B, N] if record else None)."""
+    weights: float64 [T, E] (may require grad); iter_weights: optional [T]
+    factors c_t of the per-iteration terms (the loss is sum_t c_t L_t; all
+    ones by default).  Returns (loss, per-iteration losses [T], posteriors
+    [T, B, N] if record else None)."""
     L = float(llr_clamp)
     s = torch.as_tensor(np.asarray(s_bits, np.uint8), dtype=torch.float64)
     y = torch.as_tensor(np.asarray(e_bits, np.uint8), dtype=torch.float64)
@@ -122,17 +124,17 @@ def unrolled_loss(tab: Tables, s_bits: np.ndarray, e_bits: np.ndarray, weights: 
         post, Em, _ = _error_pass(tab, D, L)
         # BCE between sigmoid(-Lam(t)) and the true error, averaged over shots and nodes
         lt = (y * torch.nn.functional.softplus(post) + (1.0 - y) * torch.nn.functional.softplus(-post)).mean()
-        total = total + lt
+        total = total + (lt if iter_weights is None else float(iter_weights[t]) * lt)
         per_t.append(lt)
         if record:
             traj.append(post.detach())
     return total, torch.stack(per_t), (torch.stack(traj) if record else None)
 
 
-def unrolled_grad(tab: Tables, s_bits, e_bits, weights: np.ndarray, llr_clamp: float = 1e4):
+def unrolled_grad(tab: Tables, s_bits, e_bits, weights: np.ndarray, llr_clamp: float = 1e4, iter_weights=None):
     """(loss, dloss/dweights [T, E], per-iteration losses, posteriors) in float64."""
     w = torch.tensor(np.asarray(weights, np.float64), requires_grad=True)
-    loss, per_t, traj = unrolled_loss(tab, s_bits, e_bits, w, llr_clamp, record=True)
+    loss, per_t, traj = unrolled_loss(tab, s_bits, e_bits, w, llr_clamp, record=True, iter_weights=iter_weights)
     loss.backward()
     return float(loss.detach()), w.grad.numpy().copy(), per_t.detach().numpy(), traj.numpy()
 

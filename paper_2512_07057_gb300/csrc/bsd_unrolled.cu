@@ -314,11 +314,13 @@ __global__ void k_u_loss_total(int T, float* __restrict__ out)
 template <int CAP>
 __global__ void __launch_bounds__(kThreads) k_u_bvar(UArgs a, const float* __restrict__ gEin,
                                                      const float* __restrict__ Et, const float* __restrict__ lamT,
-                                                     const float* __restrict__ gout, double scale,
+                                                     const float* __restrict__ gout, double scale, int t,
                                                      float* __restrict__ gD)
 {
     const long long b = (long long)blockIdx.x * kTile + 4 * threadIdx.x;
-    const float gs = (float)((double)__ldg(gout) * scale);
+    // the objective's derivative with respect to the term of iteration t:
+    // through the total ([0]) and through the term itself ([t])
+    const float gs = (float)(((double)__ldg(gout) + (double)__ldg(gout + t)) * scale);
     for (int j = blockIdx.y; j < a.N; j += gridDim.y) {
         const int kb = __ldg(a.col_ptr + j), deg = __ldg(a.col_ptr + j + 1) - kb;
         const float4 post = ld4(lamT, j, a.Bp, b);
@@ -627,9 +629,11 @@ int bsd_unrolled_backward(const bsd_decoder* dec, int64_t B, int32_t T, int32_t 
             const float* gEin = (t == T) ? nullptr : u.gE[cur];
             {
                 Timed tm(hk, kKindBVar);
-                if (cap_c == 4) k_u_bvar<4><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, u.gD);
-                else if (cap_c == 8) k_u_bvar<8><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, u.gD);
-                else k_u_bvar<0><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, u.gD);
+                if (cap_c == 4)
+                    k_u_bvar<4><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, t, u.gD);
+                else if (cap_c == 8)
+                    k_u_bvar<8><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, t, u.gD);
+                else k_u_bvar<0><<<gcol, kThreads, 0, s>>>(a, gEin, Et, lamT, d_grad_loss, scale, t, u.gD);
             }
             const float* Eprev = (t == t0 + 1) ? u.ck + (size_t)c * EB : u.seg + (size_t)(t - t0 - 2) * EB;
             float* gEout = (t > 1) ? u.gE[cur ^ 1] : nullptr;

@@ -1,11 +1,11 @@
 """Differentiable unrolled weighted min-sum on the GPU.
 
 T flooding iterations of Eqs. 1-3 with a weight w[t][e] per edge and
-iteration in place of the min-sum scale, and the loss
-    loss = sum_{t=1..T} mean_{b,j} BCE(sigmoid(-Lambda_j(t)), e_j),
-computed by bsd_unrolled_forward; its gradient with respect to the weights by
-the hand-written adjoint bsd_unrolled_backward (checkpoints every k
-iterations, segments recomputed).  UnrolledLoss exposes the pair as a
+iteration in place of the min-sum scale, and the loss terms
+    L_t = mean_{b,j} BCE(sigmoid(-Lambda_j(t)), e_j),  loss = sum_t L_t,
+computed by bsd_unrolled_forward; the gradient of an objective sum_t c_t L_t
+with respect to the weights by the hand-written adjoint bsd_unrolled_backward
+(checkpoints every k iterations, segments recomputed).  UnrolledLoss exposes the pair as a
 torch.autograd.Function; train_weights fits the weights with Adam, and the
 decoder takes the result through BeamSearchDecoder.set_weights.
 """
@@ -67,9 +67,15 @@ class UnrolledTrainer:
         return self.loss
 
     def backward(self, weights, grad_loss):
-        """grad_loss: float32 CUDA tensor with one element; returns float32 [T, E]."""
+        """grad_loss: float32 CUDA tensor, the objective's derivative with respect
+        to the loss vector [T + 1] of the forward ([0] the total, [t] the term of
+        iteration t); one element stands for [g, 0, ..., 0].  Returns float32 [T, E]."""
         import torch
-        g = grad_loss.reshape(1).to(torch.float32).contiguous()
+        g = grad_loss.reshape(-1).to(torch.float32)
+        if g.numel() == 1:
+            g = torch.cat([g, torch.zeros(self.T, dtype=torch.float32, device=g.device)])
+        assert g.numel() == self.T + 1
+        g = g.contiguous()
         out = torch.empty((self.T, self.n_edges), dtype=torch.float32, device=weights.device)
         B.bsd_unrolled_backward(self.dec.h, self.B, self.T, self.k, _p(weights), _p(g), _p(out), _p(self.work),
                                 self.work.numel(), self._stream())
@@ -83,7 +89,8 @@ def _autograd_function():
     import torch
 
     class UnrolledLoss(torch.autograd.Function):
-        """loss = UnrolledLoss.apply(weights, trainer, syndromes, errors)."""
+        """losses = UnrolledLoss.apply(weights, trainer, syndromes, errors): the
+        loss vector [T + 1] ([0] the total, [t] the term of iteration t)."""
 
         @staticmethod
         def forward(ctx, weights, trainer, syndromes, errors):
@@ -92,7 +99,7 @@ def _autograd_function():
             ctx.trainer = trainer
             ctx.generation = trainer.generation
             ctx.save_for_backward(w)
-            return loss[0].clone()
+            return loss.clone()
 
         @staticmethod
         def backward(ctx, grad_out):
@@ -108,7 +115,8 @@ _FN = None
 
 
 def unrolled_loss(weights, trainer: UnrolledTrainer, syndromes, errors):
-    """Differentiable loss of the unrolled decoder (torch.autograd)."""
+    """Differentiable loss vector of the unrolled decoder (torch.autograd):
+    [0] the total over iterations, [t] the term of iteration t."""
     global _FN
     if _FN is None:
         _FN = _autograd_function()
@@ -122,19 +130,25 @@ def batch_tensors(prob, batch: int, seed, device: int = 0):
 
 
 def train_weights(prob, T: int = 20, ckpt_every: int = 5, batch: int = 4096, steps: int = 300, lr: float = 1e-2,
-                  init: float = 0.625, tag: str = "unrolled_train", device: int = 0, log_every: int = 0):
+                  init: float = 0.625, tag: str = "unrolled_train", device: int = 0, log_every: int = 0,
+                  iter_weights=None):
     """Adam on the per-edge, per-iteration weights; a fresh seeded batch every
-    step.  Returns (weights float32 [T, E] as numpy, losses per step)."""
+    step.  The objective is sum_t c_t L_t over the per-iteration loss terms,
+    c = iter_weights (default all ones: the total loss).  Returns (weights
+    float32 [T, E] as numpy, objective per step)."""
     import torch
     tr = UnrolledTrainer(prob, batch, T, ckpt_every, device)
     w = torch.full((T, prob.n_edges), float(init), dtype=torch.float32, device=f"cuda:{device}",
                    requires_grad=True)
+    c = torch.ones(T, dtype=torch.float32, device=f"cuda:{device}") if iter_weights is None else \
+        torch.as_tensor(np.asarray(iter_weights, np.float32), device=f"cuda:{device}")
+    assert c.numel() == T
     opt = torch.optim.Adam([w], lr=lr)
     hist = []
     for step in range(steps):
         s, e, _ = batch_tensors(prob, batch, W.shot_seed(tag, step), device)
         opt.zero_grad(set_to_none=True)
-        loss = unrolled_loss(w, tr, s, e)
+        loss = (unrolled_loss(w, tr, s, e)[1:] * c).sum()
         loss.backward()
         opt.step()
         hist.append(float(loss.detach()))

@@ -184,3 +184,26 @@ def test_full_size_phenomenological_sampled(prec):
     else:
         exp, _ = _expected(prob, params, shots.syndromes[idx], prec)
     _check(sub, exp, prob.K)
+
+
+def test_full_size_synthetic_dem_fp16_sampled():
+    """The 936 x 8800 synthetic DEM with binary16 message storage at 10^6
+    shots, autotuned, with near-tie re-runs: the batched seed BP stores its
+    messages in 16 bits too.  1000 sampled shots equal the oracle's 16-bit
+    run (or, on shots it flags, the single-precision run), bit for bit."""
+    prob = W.synthetic_dem()
+    shots = W.sample_shots(prob, 1_000_000, "synthetic_dem")
+    params = D.make_params("beam32_340iters", ms_scale=0.625, msg_precision=B.BSD_FP16, workspace_bytes=32 << 30)
+    dec = D.BeamSearchDecoder(prob, params)
+    assert dec.info["batch"]["active"]
+    s = D.to_torch_words(shots.syndromes)
+    dec.autotune(s[:16384].contiguous())
+    out = dec.decode(s)
+    torch.cuda.synchronize()
+    gpu = {k: D.from_torch_words(getattr(out, a)).copy()
+           for k, a in (("corrections", "corrections"), ("obs", "obs_flips"), ("status", "status"), ("iters", "iters"))}
+    dec.close()
+    idx = np.sort(np.random.default_rng(4).choice(shots.B, size=1000, replace=False))
+    sub = {k: v[idx] for k, v in gpu.items()}
+    exp, _ = _expected(prob, params, shots.syndromes[idx], B.BSD_FP16)
+    _check(sub, exp, prob.K)

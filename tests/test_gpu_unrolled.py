@@ -95,7 +95,7 @@ def test_autograd_function_and_upstream_gradient():
     tr = G.UnrolledTrainer(prob, Bn, T, 2)
     s_t, e_t, _ = G.batch_tensors(prob, Bn, "unrolled_autograd")
     w = torch.from_numpy(_weights(prob, T, 1)).cuda().requires_grad_(True)
-    loss = G.unrolled_loss(w, tr, s_t, e_t)
+    loss = G.unrolled_loss(w, tr, s_t, e_t)[0]
     (3.0 * loss).backward()
     direct = tr.backward(w.detach(), torch.full((1,), 3.0, device="cuda"))
     torch.cuda.synchronize()
@@ -104,7 +104,33 @@ def test_autograd_function_and_upstream_gradient():
     loss1 = G.unrolled_loss(w, tr, s_t, e_t)
     G.unrolled_loss(w, tr, s_t, e_t)
     with pytest.raises(RuntimeError):
-        loss1.backward()
+        loss1[0].backward()
+    tr.close()
+
+
+def test_iteration_weighted_objective_matches_fp64():
+    """An objective sum_t c_t L_t (here c_t = t / T, weighting the late
+    iterations): the adjoint's weight gradient equals the float64 autograd
+    gradient of the same objective, and the autograd function gives the same
+    through the loss vector."""
+    prob = _irregular()
+    T, Bn = 6, 300
+    w = _weights(prob, T, 5)
+    c = np.arange(1, T + 1, dtype=np.float64) / T
+    s_t, e_t, sh = G.batch_tensors(prob, Bn, "unrolled_iter_weights")
+    tr = G.UnrolledTrainer(prob, Bn, T, 2)
+    wt = torch.from_numpy(w).cuda()
+    tr.forward(wt, s_t, e_t)
+    g = torch.cat([torch.zeros(1), torch.from_numpy(c.astype(np.float32))]).cuda()
+    grad = tr.backward(wt, g).cpu().numpy()
+    s, e = W.unpack_bits(sh.syndromes, prob.M), W.unpack_bits(sh.errors, prob.N)
+    _, rg, _, _ = U.unrolled_grad(U.Tables(prob), s, e, w.astype(np.float64), iter_weights=c)
+    bar = 1e-4 * np.abs(rg).max() + 1e-3 * np.abs(rg)
+    assert not (np.abs(grad - rg) > bar).any()
+    wa = wt.clone().requires_grad_(True)
+    (G.unrolled_loss(wa, tr, s_t, e_t)[1:] * torch.from_numpy(c.astype(np.float32)).cuda()).sum().backward()
+    torch.cuda.synchronize()
+    assert torch.allclose(wa.grad, torch.from_numpy(grad).cuda(), rtol=1e-6, atol=1e-12)
     tr.close()
 
 

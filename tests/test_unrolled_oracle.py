@@ -149,3 +149,24 @@ def test_loss_is_bce_of_posteriors():
     bce = -(e * np.log(q) + (1 - e) * np.log(1 - q))
     np.testing.assert_allclose(per_t, bce.mean(axis=(1, 2)), rtol=1e-12)
     assert abs(loss - per_t.sum()) < 1e-12
+
+
+def test_iteration_weighted_objective_is_linear_in_the_terms():
+    """sum_t c_t L_t: with c = the t-th unit vector the objective is the t-th
+    term, and the gradients of the T unit objectives add up to the gradient
+    of the plain total (c = all ones)."""
+    prob = W.bb72_code_capacity(0.05)
+    sh = W.sample_shots(prob, 20, "iter_weights_ref", keep_errors=True)
+    s, e = W.unpack_bits(sh.syndromes, prob.M), W.unpack_bits(sh.errors, prob.N)
+    T = 4
+    w = np.random.default_rng(2).uniform(0.5, 1.0, size=(T, prob.n_edges))
+    tab = U.Tables(prob)
+    total, g_all, per_t, _ = U.unrolled_grad(tab, s, e, w)
+    acc = np.zeros_like(g_all)
+    for t in range(T):
+        c = np.zeros(T)
+        c[t] = 1.0
+        lt, gt, _, _ = U.unrolled_grad(tab, s, e, w, iter_weights=c)
+        assert abs(lt - per_t[t]) <= 1e-15 * max(1.0, abs(lt))
+        acc += gt
+    np.testing.assert_allclose(acc, g_all, rtol=1e-10, atol=1e-15)
