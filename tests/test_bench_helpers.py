@@ -9,6 +9,8 @@ used, so the benchmark line reports null traffic instead of a stale figure.
 """
 import os
 
+import numpy as np
+
 import pytest
 
 import bench
@@ -102,3 +104,43 @@ def test_ops_per_update_is_the_algorithmic_count():
     of the outgoing magnitude, one add into the posterior, one extrinsic
     subtraction."""
     assert bench.OPS_PER_UPDATE == 2 + 1 + 1 + 1 + 1
+
+
+def _prof(kind_ms, kind_ln, exec_iters, screen=0):
+    ms = np.zeros(11)
+    ln = np.zeros(11, np.int64)
+    for k, v in kind_ms.items():
+        ms[k] = v
+    for k, v in kind_ln.items():
+        ln[k] = v
+    return {"kinds": {"ms": ms, "launches": ln}, "exec_iters": np.array(exec_iters, np.uint64),
+            "screen_updates": screen}
+
+
+def test_roofline_picks_the_dominant_kernel_and_its_bound(monkeypatch):
+    """The per-candidate round kernel is measured against the lane-operation
+    peak (6 operations per message update), the batched error-node pass
+    against HBM with its algorithmic bytes per slot iteration."""
+    import types
+    fake_torch = types.SimpleNamespace(cuda=types.SimpleNamespace(
+        get_device_properties=lambda dev: types.SimpleNamespace(multi_processor_count=152)))
+    monkeypatch.setitem(__import__("sys").modules, "torch", fake_torch)
+    monkeypatch.setattr(bench, "peaks", lambda: ({"hbm_gbs": 6000.0, "sm_max_mhz": 2000.0}, "measured"))
+    monkeypatch.setattr(bench, "_traffic_record", lambda *a, **k: None)
+    monkeypatch.setattr(bench, "_memory_record", lambda *a, **k: None)
+    E, M = 432, 72
+    # k_round: 10 launches, 2 ms in all, 1e6 candidate-iterations
+    r, _ = bench.alu_roofline([_prof({0: 0.5, 1: 2.0, 2: 0.1}, {0: 1, 1: 10, 2: 10}, [1000, 10**6, 0])], E, 0, "case",
+                              M=M)
+    peak = 152 * 128 * 2000e6 / 1e12
+    assert r["kernel"] == "k_round" and r["bound"] == "alu" and abs(r["peak"] - peak) < 1e-9
+    assert abs(r["achieved"] - 6 * (1e6 * E / 10) / (0.2e-3) / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / peak) < 1e-12
+    # k_bs_var dominant: 4 launches of 8 ms in all, 2048 slot iterations, 2-byte messages
+    E2, M2 = 35110, 936
+    r, _ = bench.alu_roofline([_prof({0: 1.0, 1: 0.2, 8: 3.0, 9: 8.0, 10: 1.0}, {0: 1, 1: 2, 8: 4, 9: 4, 10: 4},
+                                     [3000, 50, 2048])], E2, 0, "case", msg_bytes=2, M=M2)
+    assert r["kernel"] == "k_bs_var" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    per_slot = 2 * 2 * E2 + 8 * M2
+    assert abs(r["achieved"] - per_slot * (2048 / 4) / 2e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12 and np.isfinite(r["alu_view"]["frac"])
