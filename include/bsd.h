@@ -107,8 +107,8 @@ typedef struct {
                                   with the scale alpha and num_results = 1: the seed BP of many
                                   shots runs at once over this many slots, messages streamed
                                   through device memory with the shots contiguous; 0 the library
-                                  default (codes of at least 16384 edges: about 96 MiB of message
-                                  state; smaller codes: none), -1 never, else 256..65536 (rounded
+                                  default (codes of at least 16384 edges: 2048 slots; smaller
+                                  codes: none), -1 never, else 256..65536 (rounded
                                   down to a multiple of 256); at most a quarter of the workspace;
                                   results do not depend on it */
 } bsd_params;

@@ -78,9 +78,9 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 inline int words_of(long long bits) { return (int)((bits + 31) / 32); }
 
 // default of the batched seed BP: codes with at least this many edges, and
-// about this much message state
+// this many slots
 constexpr long long kBatchMinEdges = 16384;
-constexpr long long kBatchStateBytes = 96ll << 20;
+constexpr int kBatchDefaultSlots = 2048;
 
 const char* kPresetNames[] = {"beam8_230iters", "beam32_340iters", "beam64_640iters", "beam64_32res_640iters"};
 // Table I: max_rounds, beam_width, initial_iters, iters_per_round, num_results
@@ -519,18 +519,18 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
                          12.0 + cfg.w + 8.0 + NR * (4.0 * WN + 12.0) + 4.0 + 2.0 * W2 * sizeof(int2);
     long long budget = params->workspace_bytes > 0 ? params->workspace_bytes : (4ll << 30);
     // the batched seed BP's slots: the requested count, or by default for
-    // codes of at least kBatchMinEdges edges as many as kBatchStateBytes of
-    // messages hold (measured on GB300: on the 35k-edge synthetic DEM the
-    // batch decodes 1.7x faster than one candidate per block of warps, on the
-    // 6912-edge phenomenological DEM 1.7x slower, where the per-iteration
-    // launches dominate); at most a quarter of the workspace
+    // codes of at least kBatchMinEdges edges kBatchDefaultSlots (measured on
+    // GB300: on the 35k-edge synthetic DEM the batch decodes 1.8x faster than
+    // one candidate per block of warps in single precision, on the 6912-edge
+    // phenomenological DEM 1.6x slower, where the per-iteration launches
+    // dominate); at most a quarter of the workspace
     int bs_slots = 0;
     const bool bs_default = params->batch_slots == 0 && E >= kBatchMinEdges;
     if (dec->ls.batch && (params->batch_slots > 0 || bs_default)) {
         const long long cap = budget / 4;
         const int fit = batch_slots_for(g, cap);
         const int want = params->batch_slots > 0 ? params->batch_slots / kBsChunk * kBsChunk
-                                                 : batch_slots_for(g, kBatchStateBytes);
+                                                 : kBatchDefaultSlots;
         bs_slots = want < fit ? want : fit;
         if (bs_slots > 0) {
             Work probe{};

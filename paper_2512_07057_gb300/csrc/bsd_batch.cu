@@ -49,6 +49,14 @@ struct BsRange {
     int lo, hi;       // items [lo, hi)
 };
 
+// the error-node pass gives each thread two adjacent slots (b, b + 1): one
+// 8-byte (FP32) or 4-byte (16-bit) load moves the message of an edge for
+// both, one 16-byte load their detector records, and the graph-table loads
+// serve both (more bytes in flight per instruction for a pass that waits on
+// memory); the check pass keeps one slot per thread (more warps in flight)
+constexpr int kBsThreads = kBsChunk / 2;
+
+template <int SPT>
 __device__ __forceinline__ BsRange bs_range(const Work& w, int items)
 {
     const int nch = w.bs_slots / kBsChunk;
@@ -56,7 +64,7 @@ __device__ __forceinline__ BsRange bs_range(const Work& w, int items)
     const int c = blockIdx.x % nch, grp = blockIdx.x / nch;
     const int per = (items + groups - 1) / groups;
     BsRange r;
-    r.b = c * kBsChunk + threadIdx.x;
+    r.b = c * kBsChunk + SPT * threadIdx.x;
     r.lo = grp * per;
     r.hi = min(items, r.lo + per);
     return r;
@@ -96,7 +104,7 @@ __global__ void __launch_bounds__(kBsChunk) k_bs_check(DevGraph g, DecCfg cfg, W
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.stats[2], 1ull);
     using S = Store<P>;
     using T = typename S::T;
-    const BsRange rg = bs_range(w, g.M);
+    const BsRange rg = bs_range<1>(w, g.M);
     const int b = rg.b;
     const int Bs = w.bs_slots;
     const int shot = w.bs_shot[b];
@@ -137,12 +145,14 @@ __global__ void __launch_bounds__(kBsChunk) k_bs_check(DevGraph g, DecCfg cfg, W
 }
 
 // Eq. 1 per edge, Eqs. 2-4 per (column, slot), for a run of columns of
-// degree D (positions [q0, q1) of the degree-sorted column order); every lane
-// of a warp holds the same column, so the degree is warp-uniform.  The next
-// column's (edge, row) pairs are loaded while the current one is computed.
+// degree D (positions [q0, q1) of the degree-sorted column order) and the
+// thread's two slots; every lane of a warp holds the same column, so the
+// degree is warp-uniform.  The next column's (edge, row) pairs are loaded
+// while the current one is computed.  A slot without a shot computes values
+// no one reads and lists nothing.
 template <int D, int P>
-__device__ __forceinline__ void bs_var_run(const DevGraph& g, const DecCfg& cfg, const Work& w, int b, bool fresh,
-                                           int q0, int q1)
+__device__ __forceinline__ void bs_var_run(const DevGraph& g, const DecCfg& cfg, const Work& w, int b, bool act0,
+                                           bool act1, bool fresh0, bool fresh1, int q0, int q1)
 {
     using S = Store<P>;
     using T = typename S::T;
@@ -162,46 +172,67 @@ __device__ __forceinline__ void bs_var_run(const DevGraph& g, const DecCfg& cfg,
         const int j = __ldg(g.colperm + q);
         const float lj = __ldg(g.lam + j);
         // E(0) of a fresh slot: the same on every edge of the column
-        const float x0 = fresh ? S::ld(reinterpret_cast<const T*>(g.lamEc), j) : 0.f;
-        float v[D > 0 ? D : 1];
-        int ed[D > 0 ? D : 1];
+        const float x0 = (fresh0 || fresh1) ? S::ld(reinterpret_cast<const T*>(g.lamEc), j) : 0.f;
+        float v0[D > 0 ? D : 1], v1[D > 0 ? D : 1];
+        int e0[D > 0 ? D : 1], e1[D > 0 ? D : 1];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            const float2 rec = w.bsR[(size_t)er[k].y * Bs + b];
-            const float xo = fresh ? x0 : S::ld(E, (size_t)er[k].x * Bs + b);
+            const float4 rec = *reinterpret_cast<const float4*>(w.bsR + (size_t)er[k].y * Bs + b);
+            float2 xo = S::ld2(E, (size_t)er[k].x * Bs + b);
+            if (fresh0) xo.x = x0;
+            if (fresh1) xo.y = x0;
             // the minimum over the row's other edges: min2 on an edge holding
-            // the minimum (a tie makes min2 = min1), min1 elsewhere
-            const float m = (fabsf(xo) == fabsf(rec.x)) ? rec.y : rec.x;
-            // sign: the row's parity (in m) without the edge's own sign
-            const float d = __fmul_rn(alpha, m);
-            v[k] = __uint_as_float(__float_as_uint(d) ^ (__float_as_uint(xo) & 0x80000000u));
-            ed[k] = er[k].x;
+            // the minimum (a tie makes min2 = min1), min1 elsewhere; sign: the
+            // row's parity (in the record) without the edge's own sign
+            const float m0 = (fabsf(xo.x) == fabsf(rec.x)) ? rec.y : rec.x;
+            const float m1 = (fabsf(xo.y) == fabsf(rec.z)) ? rec.w : rec.z;
+            const float d0 = __fmul_rn(alpha, m0), d1 = __fmul_rn(alpha, m1);
+            v0[k] = __uint_as_float(__float_as_uint(d0) ^ (__float_as_uint(xo.x) & 0x80000000u));
+            v1[k] = __uint_as_float(__float_as_uint(d1) ^ (__float_as_uint(xo.y) & 0x80000000u));
+            e0[k] = er[k].x;
+            e1[k] = er[k].x;
         }
-        // ascending order of value (an exchange network of D inputs)
+        // ascending order of value (an exchange network of D inputs per slot)
 #pragma unroll
         for (int a = 0; a < D; ++a) {
 #pragma unroll
             for (int k = 0; k + 1 < D - a; ++k) {
-                if (v[k] > v[k + 1]) {
-                    const float tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv;
-                    const int te = ed[k]; ed[k] = ed[k + 1]; ed[k + 1] = te;
+                if (v0[k] > v0[k + 1]) {
+                    const float tv = v0[k]; v0[k] = v0[k + 1]; v0[k + 1] = tv;
+                    const int te = e0[k]; e0[k] = e0[k + 1]; e0[k + 1] = te;
+                }
+                if (v1[k] > v1[k + 1]) {
+                    const float tv = v1[k]; v1[k] = v1[k + 1]; v1[k + 1] = tv;
+                    const int te = e1[k]; e1[k] = e1[k + 1]; e1[k + 1] = te;
                 }
             }
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) {                         // Eq. 2: leave d_i out
-            float acc = lj;
+            float acc0 = lj, acc1 = lj;
 #pragma unroll
-            for (int k2 = 0; k2 < D; ++k2)
-                if (k2 != k) acc = __fadd_rn(acc, v[k2]);
-            S::st(E, (size_t)ed[k] * Bs + b, fminf(fmaxf(acc, -L), L));
+            for (int k2 = 0; k2 < D; ++k2) {
+                if (k2 != k) {
+                    acc0 = __fadd_rn(acc0, v0[k2]);
+                    acc1 = __fadd_rn(acc1, v1[k2]);
+                }
+            }
+            S::st(E, (size_t)e0[k] * Bs + b, fminf(fmaxf(acc0, -L), L));
+            S::st(E, (size_t)e1[k] * Bs + b + 1, fminf(fmaxf(acc1, -L), L));
         }
-        float post = lj;                                      // Eq. 3
+        float p0 = lj, p1 = lj;                               // Eq. 3
 #pragma unroll
-        for (int k = 0; k < D; ++k) post = __fadd_rn(post, v[k]);
-        if (post <= 0.f) {                                    // Eq. 4
+        for (int k = 0; k < D; ++k) {
+            p0 = __fadd_rn(p0, v0[k]);
+            p1 = __fadd_rn(p1, v1[k]);
+        }
+        if (act0 && p0 <= 0.f) {                              // Eq. 4
             const int qn = atomicAdd(&w.bs_nl[b], 1);
             if (qn < kBsList) w.bs_list[(size_t)qn * Bs + b] = j;
+        }
+        if (act1 && p1 <= 0.f) {
+            const int qn = atomicAdd(&w.bs_nl[b + 1], 1);
+            if (qn < kBsList) w.bs_list[(size_t)qn * Bs + b + 1] = j;
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) er[k] = nx[k];
@@ -209,20 +240,22 @@ __device__ __forceinline__ void bs_var_run(const DevGraph& g, const DecCfg& cfg,
 }
 
 template <int DV, int P>
-__global__ void __launch_bounds__(kBsChunk) k_bs_var(DevGraph g, DecCfg cfg, Work w)
+__global__ void __launch_bounds__(kBsThreads) k_bs_var(DevGraph g, DecCfg cfg, Work w)
 {
     if (!batch_running(w)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.stats[2], 1ull);
-    const BsRange rg = bs_range(w, g.N);
+    const BsRange rg = bs_range<2>(w, g.N);
     const int b = rg.b;
-    const int shot = w.bs_shot[b];
-    if (shot < 0) return;
-    const bool fresh = w.bs_t[b] == 0;
+    const int2 shot = *reinterpret_cast<const int2*>(w.bs_shot + b);
+    if (shot.x < 0 && shot.y < 0) return;
+    const int2 tt = *reinterpret_cast<const int2*>(w.bs_t + b);
+    const bool act0 = shot.x >= 0, act1 = shot.y >= 0;
+    const bool fresh0 = tt.x == 0, fresh1 = tt.y == 0;
     // the block's positions of the degree-sorted order, run by run of one degree
 #define BS_RUN(DD)                                                                  \
     if constexpr (DD <= DV) {                                                       \
         const int q0 = max(rg.lo, g.dstart[DD]), q1 = min(rg.hi, g.dstart[DD + 1]); \
-        if (q0 < q1) bs_var_run<DD, P>(g, cfg, w, b, fresh, q0, q1);                \
+        if (q0 < q1) bs_var_run<DD, P>(g, cfg, w, b, act0, act1, fresh0, fresh1, q0, q1); \
     }
     BS_RUN(0) BS_RUN(1) BS_RUN(2) BS_RUN(3) BS_RUN(4) BS_RUN(5) BS_RUN(6) BS_RUN(7) BS_RUN(8)
     BS_RUN(9) BS_RUN(10) BS_RUN(11) BS_RUN(12) BS_RUN(13) BS_RUN(14) BS_RUN(15) BS_RUN(16)
@@ -433,7 +466,7 @@ int add_batch_nodes(cudaGraph_t graph, cudaGraphNode_t dep, cudaGraphNode_t* las
         void* rargs[] = {&g, &cfg, &w, &screened, &cond, &use};
         rc = add_node(body, &nc, nullptr, check_func(g.prec), grid_pass(w, g.M, kRowsPerThread), kBsChunk, pargs);
         if (!rc)
-            rc = add_node(body, &nv, &nc, var_func(dv_of(g), g.prec), grid_pass(w, g.N, kColsPerThread), kBsChunk,
+            rc = add_node(body, &nv, &nc, var_func(dv_of(g), g.prec), grid_pass(w, g.N, kColsPerThread), kBsThreads,
                           pargs);
         if (!rc) rc = add_node(body, &nr, &nv, (void*)k_bs_retire, grid_retire(ls, w), 256, rargs);
     }
@@ -466,7 +499,7 @@ int launch_batch_direct(const DevGraph& g, const DecCfg& cfg, const Work& w, con
             if (hk) hk->before(hk->ctx, 8);
             if (CUDA_FAILED(cudaLaunchKernel(cf, dim3(gc), dim3(kBsChunk), pargs, 0, s))) return -2;
             if (hk) { hk->after(hk->ctx, 8); hk->before(hk->ctx, 9); }
-            if (CUDA_FAILED(cudaLaunchKernel(vf, dim3(gv), dim3(kBsChunk), pargs, 0, s))) return -2;
+            if (CUDA_FAILED(cudaLaunchKernel(vf, dim3(gv), dim3(kBsThreads), pargs, 0, s))) return -2;
             if (hk) { hk->after(hk->ctx, 9); hk->before(hk->ctx, 10); }
             if (CUDA_FAILED(cudaLaunchKernel((void*)k_bs_retire, dim3(gr), dim3(256), rargs, 0, s))) return -2;
             if (hk) hk->after(hk->ctx, 10);

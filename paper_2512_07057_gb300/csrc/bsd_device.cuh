@@ -21,7 +21,11 @@ template <> struct Store<0> {
     using T = float;
     static __device__ __forceinline__ float ld(const T* p, size_t i) { return p[i]; }
     static __device__ __forceinline__ void st(T* p, size_t i, float v) { p[i] = v; }
-    static __device__ __forceinline__ float2 ld2(const T* p, int i) { return *reinterpret_cast<const float2*>(p + i); }
+    static __device__ __forceinline__ float2 ld2(const T* p, size_t i) { return *reinterpret_cast<const float2*>(p + i); }
+    static __device__ __forceinline__ void st2(T* p, size_t i, float a, float b)
+    {
+        *reinterpret_cast<float2*>(p + i) = make_float2(a, b);
+    }
 };
 template <> struct Store<1> {
     using T = __half;
@@ -32,9 +36,16 @@ template <> struct Store<1> {
         if ((__half_as_ushort(h) & 0x7fffu) == 0) h = __ushort_as_half(0);
         p[i] = h;
     }
-    static __device__ __forceinline__ float2 ld2(const T* p, int i)
+    static __device__ __forceinline__ float2 ld2(const T* p, size_t i)
     {
         return __half22float2(*reinterpret_cast<const __half2*>(p + i));
+    }
+    static __device__ __forceinline__ void st2(T* p, size_t i, float a, float b)
+    {
+        __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+        if ((__half_as_ushort(ha) & 0x7fffu) == 0) ha = __ushort_as_half(0);
+        if ((__half_as_ushort(hb) & 0x7fffu) == 0) hb = __ushort_as_half(0);
+        *reinterpret_cast<__half2*>(p + i) = __halves2half2(ha, hb);
     }
 };
 template <> struct Store<2> {
@@ -46,9 +57,16 @@ template <> struct Store<2> {
         if ((__bfloat16_as_ushort(h) & 0x7fffu) == 0) h = __ushort_as_bfloat16(0);
         p[i] = h;
     }
-    static __device__ __forceinline__ float2 ld2(const T* p, int i)
+    static __device__ __forceinline__ float2 ld2(const T* p, size_t i)
     {
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + i));
+    }
+    static __device__ __forceinline__ void st2(T* p, size_t i, float a, float b)
+    {
+        __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+        if ((__bfloat16_as_ushort(ha) & 0x7fffu) == 0) ha = __ushort_as_bfloat16(0);
+        if ((__bfloat16_as_ushort(hb) & 0x7fffu) == 0) hb = __ushort_as_bfloat16(0);
+        *reinterpret_cast<__nv_bfloat162*>(p + i) = __halves2bfloat162(ha, hb);
     }
 };
 
