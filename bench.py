@@ -428,6 +428,16 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+KIND_NAMES = {0: "k_seed", 1: "k_round", 2: "k_select", 8: "k_bs_check", 9: "k_bs_var", 10: "k_bs_retire",
+              11: "k_screen"}
+
+
+def kernel_ms(pr, steps: int) -> dict:
+    """Event-timed milliseconds per step of each decoding kernel kind that ran."""
+    ms = pr["kinds"]["ms"]
+    return {n: float(ms[k]) / steps for k, n in KIND_NAMES.items() if k < len(ms) and (k < 3 or ms[k] > 0)}
+
+
 def alu_roofline(prof, E: int, dev: int, traffic_case: str, shots: int = 0, msg_bytes: int = 4, M: int = 0):
     """Roofline of the dominant BP kernel from per-kernel event times.
 
@@ -455,14 +465,14 @@ def alu_roofline(prof, E: int, dev: int, traffic_case: str, shots: int = 0, msg_
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     batch_it = exec_iters[2] if len(exec_iters) > 2 else 0.0
     # candidate kernels: kind, name, message updates of all their launches
-    cands = [(0, "k_seed", (exec_iters[0] - batch_it) * E + screen), (1, "k_round", exec_iters[1] * E),
-             (8, "k_bs_check", batch_it * E), (9, "k_bs_var", batch_it * E)]
+    cands = [(0, "k_seed", (exec_iters[0] - batch_it) * E), (1, "k_round", exec_iters[1] * E),
+             (8, "k_bs_check", batch_it * E), (9, "k_bs_var", batch_it * E), (11, "k_screen", screen)]
     dom_kind, name, updates = max(cands, key=lambda c: kinds_ms[c[0]])
     launches = max(1, int(kinds_ln[dom_kind]))
     ms_launch = float(kinds_ms[dom_kind]) / launches
     upd_launch = updates / launches
     ops_tops = OPS_PER_UPDATE * upd_launch / (ms_launch * 1e-3) / 1e12
-    share = float(kinds_ms[dom_kind] / max(kinds_ms[[0, 1, 2, 8, 9, 10]].sum(), 1e-9))
+    share = float(kinds_ms[dom_kind] / max(kinds_ms[[0, 1, 2, 8, 9, 10, 11]].sum(), 1e-9))
     common = {"kernel": name, "msg_updates_per_launch": upd_launch, "launch_ms": ms_launch, "kernel_share": share,
               "ops_per_msg_update": OPS_PER_UPDATE,
               "measured_in": "second timed region: same steps, each kernel launched alone between CUDA events "
@@ -482,9 +492,8 @@ def alu_roofline(prof, E: int, dev: int, traffic_case: str, shots: int = 0, msg_
         roofline = {"bound": "alu", "achieved": ops_tops, "peak": alu_peak_tops, "unit": "Tops/s",
                     "frac": ops_tops / alu_peak_tops, "traffic": None,
                     "peak_source": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz (sm_max_mhz {pk_kind})",
-                    "msg_updates_counted": "full BP iterations x E, plus the edges of first-iteration screens "
-                                           "(seed kernel)",
-                    "screen_msg_updates_per_launch": (screen / launches) if dom_kind == 0 else 0.0, **common}
+                    "msg_updates_counted": "full BP iterations x E (k_seed, k_round) or the edges the "
+                                           "first-iteration screens formed (k_screen)", **common}
     # DRAM bytes per unit of work from an ncu capture of a smaller case
     # (profiles/), scaled to this run's average launch; null once the kernel
     # sources differ from the ones that were captured
@@ -634,9 +643,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         per_p[str(p)] = {"ler": ler_of(prob, sh, obs, st), "seed_converged": float((st == 1).mean()),
                          "beam_converged": float((st == 2).mean()), "failed": float((st == 4).mean()),
                          "mean_alg_iters": float(it.mean())}
-    names = ("k_seed", "k_round", "k_select")
     for (p, _, _), pr in zip(work, prof):
-        per_p[str(p)]["kernel_ms_per_step"] = {n: float(x) / args.steps for n, x in zip(names, pr["ms"])}
+        per_p[str(p)]["kernel_ms_per_step"] = kernel_ms(pr, args.steps)
     roofline, exec_iters = alu_roofline(prof, E, dev, "16000-shot case")
     pk, _ = peaks()
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
@@ -1167,7 +1175,7 @@ def synthetic_widths(prob, sh, dev, steps: int, warmup: int, world: int, rank: i
             "ler": ler_of(prob, sh, D.from_torch_words(o.obs_flips), st & 7),
             "seed_converged": float(((st & 7) == 1).mean()), "beam_converged": float(((st & 7) == 2).mean()),
             "failed": float(((st & 7) == 4).mean()), "mean_alg_iters": float(it.mean()),
-            "kernel_ms_per_step": {n: float(x) / steps for n, x in zip(("k_seed", "k_round", "k_select"), pr["ms"])}}
+            "kernel_ms_per_step": kernel_ms(pr, steps)}
     steps_s = ms_total * 1e-3
     res.update(value=world * len(decs) * sh.B * steps / steps_s, ms_per_step=ms_total / steps, clocks=clocks,
                roofline=roofline, gpu_launches=int(sum(pr["kernel_launches"] for pr in prof_graph)),
@@ -1494,8 +1502,7 @@ def run_num_results(args, rank: int, world: int, local_rank: int):
                              "seed_converged": float(((st & 7) == 1).mean()),
                              "beam_converged": float(((st & 7) == 2).mean()),
                              "failed": float(((st & 7) == 4).mean()), "mean_alg_iters": float(it.mean()),
-                             "kernel_ms_per_step": {n: float(x) / args.steps
-                                                    for n, x in zip(("k_seed", "k_round", "k_select"), pr["ms"])}}
+                             "kernel_ms_per_step": kernel_ms(pr, args.steps)}
         forms[preset] = {"value": world * sum(sh.B for _, _, sh in work) * args.steps / (ms_total * 1e-3),
                          "unit": "syndromes/s", "ms_per_step": ms_total / args.steps, "roofline": roofline,
                          "exec_bp_iters_per_step": {"seed": float(exec_iters[0]) / args.steps,

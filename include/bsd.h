@@ -251,13 +251,13 @@ int bsd_profile_enable(bsd_decoder *dec, int enable);
 int bsd_profile_read(bsd_decoder *dec, double ms[3], int64_t launches[3], uint64_t exec_iters[3],
                      uint64_t *kernel_launches, uint64_t *screen_updates);
 
-/* Kernel kinds timed while timing is enabled: 0..2 as above (0 also the
- * first-iteration screen), then the unrolled decoder's passes
- * (bsd_unrolled_forward / _backward): 3 check pass, 4 error-node pass,
- * 5 error-node adjoint, 6 check adjoint, 7 its other kernels (bit planes,
- * initial messages, loss and gradient reductions), then the batched seed BP:
- * 8 its check pass, 9 its error-node pass, 10 its stopping test and refill. */
-#define BSD_PROFILE_KINDS 11
+/* Kernel kinds timed while timing is enabled: 0..2 as above, then the
+ * unrolled decoder's passes (bsd_unrolled_forward / _backward): 3 check pass,
+ * 4 error-node pass, 5 error-node adjoint, 6 check adjoint, 7 its other
+ * kernels (bit planes, initial messages, loss and gradient reductions), then
+ * the batched seed BP: 8 its check pass, 9 its error-node pass, 10 its
+ * stopping test and refill, and 11 the first-iteration screen of seed runs. */
+#define BSD_PROFILE_KINDS 12
 
 /* Synchronise the stream of the last timed launch, then return and reset the
  * summed event-timed milliseconds and launch counts of every kind. */

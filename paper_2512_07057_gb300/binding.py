@@ -36,7 +36,7 @@ EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode"
            "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_autotune", "bsd_get_shape", "bsd_dem_parse",
            "bsd_dem_sizes", "bsd_dem_fill", "bsd_dem_free",
            "bsd_error_string", "bsd_last_cuda_error", "bsd_destroy")
-BSD_PROFILE_KINDS = 11
+BSD_PROFILE_KINDS = 12
 BSD_DEM_MERGE = 1
 BSD_ERR_SCRATCH = -7
 
@@ -230,7 +230,8 @@ def bsd_profile_read(dec) -> dict:
 
 def bsd_profile_read_kinds(dec) -> dict:
     """Event-timed ms and launches of every kernel kind (0 seed, 1 round, 2 select,
-    3..6 unrolled check / error / error adjoint / check adjoint, 7 other unrolled)."""
+    3..6 unrolled check / error / error adjoint / check adjoint, 7 other unrolled,
+    8..10 batched seed check / error / retirement, 11 first-iteration screen)."""
     import numpy as np
     ms = np.zeros(BSD_PROFILE_KINDS, np.float64)
     ln = np.zeros(BSD_PROFILE_KINDS, np.int64)

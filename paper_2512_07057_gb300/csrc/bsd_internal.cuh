@@ -207,7 +207,7 @@ struct LaunchShape {
 // optional callbacks around every kernel launch; kinds 0 seed, 1 round,
 // 2 select, 3..6 the unrolled decoder's check / error / error adjoint / check
 // adjoint passes, 7 its other kernels, 8..10 the batched seed BP's check pass,
-// error-node pass and retirement
+// error-node pass and retirement, 11 the first-iteration screen
 constexpr int kProfKinds = BSD_PROFILE_KINDS;
 struct LaunchHooks {
     void (*before)(void* ctx, int kind);

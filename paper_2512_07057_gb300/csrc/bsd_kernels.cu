@@ -1833,9 +1833,9 @@ static int launch_chunk_t(const DevGraph& g, const DecCfg& cfg, const Work& w, c
     if (CUDA_FAILED(cudaGetLastError())) return -2;
     if (gx != nullptr) return !CUDA_FAILED(cudaGraphLaunch(gx, s)) ? 0 : -2;
     if (ls.screen) {
-        if (hk) hk->before(hk->ctx, 0);
+        if (hk) hk->before(hk->ctx, 11);
         launch_screen(g, cfg, w, ls, s);
-        if (hk) hk->after(hk->ctx, 0);
+        if (hk) hk->after(hk->ctx, 11);
     }
     // the seed kernel on its shots, then exactly the beam passes they need
     // (without a graph the number of active entries is read back)

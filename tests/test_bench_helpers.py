@@ -107,8 +107,8 @@ def test_ops_per_update_is_the_algorithmic_count():
 
 
 def _prof(kind_ms, kind_ln, exec_iters, screen=0):
-    ms = np.zeros(11)
-    ln = np.zeros(11, np.int64)
+    ms = np.zeros(12)
+    ln = np.zeros(12, np.int64)
     for k, v in kind_ms.items():
         ms[k] = v
     for k, v in kind_ln.items():
