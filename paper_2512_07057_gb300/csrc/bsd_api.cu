@@ -393,6 +393,24 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
             if (prec == BSD_FP32) std::memcpy(&lamEc_st[(size_t)j * 4], &v, 4);
         }
     }
+    // the first-iteration screen's column table: per column the check message
+    // of E(0) on each of its edges (D0, before the syndrome sign) and the edge's
+    // row, padded to the engines' degree bound with (+inf, -1)
+    const int rdk = max_col <= 3 ? 4 : max_col <= 6 ? 6 : max_col <= kMaxColDeg ? kMaxColDeg : 0;
+    std::vector<float> colRD((size_t)Npad * rdk * 2, 0.f);
+    for (int j = 0; j < Npad && rdk > 0; ++j) {
+        const int deg = j < N ? col_ptr[j + 1] - col_ptr[j] : 0;
+        for (int k = 0; k < rdk; ++k) {
+            float d = INFINITY;
+            int r = -1;
+            if (k < deg) {
+                d = D0[col_edge[col_ptr[j] + k]];
+                r = col_row[col_ptr[j] + k];
+            }
+            colRD[((size_t)j * rdk + k) * 2] = d;
+            std::memcpy(&colRD[((size_t)j * rdk + k) * 2 + 1], &r, 4);
+        }
+    }
     // the columns ordered by degree, each column's (edge, row) pairs contiguous
     // in the order of the column lists (the batched seed BP walks runs of
     // columns of one degree)
@@ -438,6 +456,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     gb += align256(lamEc_st.size());
     gb += align256(sizeof(int) * colperm.size());
     gb += align256(sizeof(int2) * colseq.size());
+    gb += align256(sizeof(float) * colRD.size());
     if (CUDA_FAILED(cudaMalloc(&dec->graph_mem, gb))) { bsd_destroy(dec); return BSD_ERR_OOM; }
     dec->graph_bytes = gb;
     char* p = (char*)dec->graph_mem;
@@ -457,6 +476,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     unsigned char* d_lamEc = carve<unsigned char>(p, lamEc_st.size());
     int* d_colperm = colperm.empty() ? nullptr : carve<int>(p, colperm.size());
     int2* d_colseq = colseq.empty() ? nullptr : carve<int2>(p, colseq.size());
+    float* d_colRD = colRD.empty() ? nullptr : carve<float>(p, colRD.size());
     bool ok = !CUDA_FAILED(cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_row_col, H_col_idx, sizeof(int) * E, cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice)) &&
@@ -475,7 +495,9 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
               (colperm.empty() ||
                !CUDA_FAILED(cudaMemcpy(d_colperm, colperm.data(), sizeof(int) * colperm.size(), cudaMemcpyHostToDevice))) &&
               (colseq.empty() ||
-               !CUDA_FAILED(cudaMemcpy(d_colseq, colseq.data(), sizeof(int2) * colseq.size(), cudaMemcpyHostToDevice)));
+               !CUDA_FAILED(cudaMemcpy(d_colseq, colseq.data(), sizeof(int2) * colseq.size(), cudaMemcpyHostToDevice))) &&
+              (colRD.empty() ||
+               !CUDA_FAILED(cudaMemcpy(d_colRD, colRD.data(), sizeof(float) * colRD.size(), cudaMemcpyHostToDevice)));
     if (!ok) { bsd_destroy(dec); return BSD_ERR_CUDA; }
 
     DevGraph& g = dec->g;
@@ -489,6 +511,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.lam = d_lam; g.lamE = d_lamE; g.hcol = d_hcol; g.acol = d_acol; g.lamq = d_lamq; g.rs0 = d_rs0; g.D0 = d_D0;
     g.colER = d_colER; g.colK = colK; g.lamEc = d_lamEc;
     g.colperm = d_colperm; g.colseq = d_colseq;
+    g.colRD = reinterpret_cast<const float4*>(d_colRD); g.colRDk = rdk;
     for (int d = 0; d < kMaxColDeg + 2; ++d) { g.dstart[d] = dstart[d]; g.dbase[d] = dbase[d]; }
 
     DecCfg& cfg = dec->cfg;

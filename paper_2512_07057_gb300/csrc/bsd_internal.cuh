@@ -68,6 +68,11 @@ struct DevGraph {
     // position q of degree d are colseq[dbase[d] + (q - dstart[d]) * d + k]
     const int* colperm;    // [N]
     const int2* colseq;    // [E]
+    // first-iteration screen: per column j its colRDk (D0 of the edge, row)
+    // pairs, rows ascending, padded with (+inf, -1); colRDk = 4, 6 or 16 for
+    // the degree bounds 3, 6 and 16 (two pairs per float4)
+    const float4* colRD;   // [Npad][colRDk / 2]
+    int colRDk;
     int dstart[kMaxColDeg + 2];
     int dbase[kMaxColDeg + 2];
 };

@@ -946,7 +946,9 @@ __global__ void k_win_end(Work w, cudaGraphConditionalHandle cond)
 // column none of whose detectors is flipped has Lambda_j(1) > 0, e^_j(1) = 0.
 // One warp per shot forms e^(1) from the columns next to flipped detectors
 // (each once), by the operations and in the order of the seed BP's first
-// iteration (bp_iterate with the E(0) records), and tests H e^(1) = s.  A shot
+// iteration (its check messages are the create-time table D0 of E(0) with the
+// syndrome sign, the values bp_iterate forms from the E(0) records; the sums
+// of Eq. 3 in ascending order), and tests H e^(1) = s.  A shot
 // that converges (or has s = 0) is finalised here: its seed BP would stop at
 // t = 1 with this e^, and a converged seed with one result reads neither E(1)
 // nor sum_LLR.  The others go to the seed BP through the queue.  The state of
@@ -1046,56 +1048,48 @@ __global__ void k_screen(DevGraph g, DecCfg cfg, Work w)
                     const int j = __ldg(g.row_col + e0);
                     const uint32_t bit = 1u << (j & 31);
                     if (atomicOr(&seen[j >> 5], bit) & bit) continue;   // another flipped detector has it
-                    // D_{i'->j}(1) on the column's edges from the E(0) records
-                    // with the syndrome bit folded into the sign parity
-                    int kb = 0, deg = 0;
-                    if constexpr (DV > 6) {
-                        kb = __ldg(g.col_ptr + j);
-                        deg = __ldg(g.col_ptr + j + 1) - kb;
-                    }
-                    float v[DV];
+                    // D_{i'->j}(1) on the column's edges: the check message of
+                    // E(0) on the edge (the same for every shot: E(0) > 0 on
+                    // every edge, so it is alpha times the row's minimum over the
+                    // other edges, positive) with the syndrome bit of its row as
+                    // the sign; two (message, row) pairs per 16-byte load, padding
+                    // (+inf, -1) past the column's degree
+                    constexpr int KD = DV == 3 ? 4 : DV;
+                    const float4* cr = g.colRD + (size_t)j * (KD / 2);
+                    float v[KD];
+                    int rr[KD];
+                    int deg = 0;
 #pragma unroll
-                    for (int k = 0; k < DV; ++k) {
-                        int e = -1, r = 0;
-                        if constexpr (DV <= 6) {
-                            const int2 er = __ldg(g.colER + (size_t)k * g.Npad + j);
-                            e = er.x;
-                            r = er.y;
-                            deg += (e >= 0) ? 1 : 0;
-                        } else if (k < deg) {
-                            e = __ldg(g.col_edge + kb + k);
-                            r = __ldg(g.col_row + kb + k);
-                        }
-                        if (e >= 0) {
-                            const float4 s4 = __ldg(g.rs0 + r);
-                            const uint32_t si = (sp[r >> 5] >> (r & 31)) & 1u;
-                            const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
-                            const uint32_t sg = __float_as_uint(s4.w) ^ si;   // E(0) > 0 on every edge
-                            const float d = __fmul_rn(alpha, m);
-                            v[k] = sg ? -d : d;
-                        } else {
-                            v[k] = INFINITY;
+                    for (int h = 0; h < KD / 2; ++h) {
+                        const float4 q = __ldg(cr + h);
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int r = __float_as_int(u ? q.w : q.y);
+                            const float d = u ? q.z : q.x;
+                            const int rs = r >= 0 ? r : 0;
+                            const uint32_t si = (r >= 0) ? (sp[rs >> 5] >> (rs & 31)) & 1u : 0u;
+                            v[2 * h + u] = __uint_as_float(__float_as_uint(d) ^ (si << 31));
+                            rr[2 * h + u] = r;
+                            deg += (r >= 0) ? 1 : 0;
                         }
                     }
 #pragma unroll
-                    for (int a = 0; a < DV; ++a) {
+                    for (int a = 0; a < KD; ++a) {
 #pragma unroll
-                        for (int k = 0; k + 1 < DV - a; ++k) {
+                        for (int k = 0; k + 1 < KD - a; ++k) {
                             if (v[k] > v[k + 1]) { const float tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv; }
                         }
                     }
                     float post = __ldg(g.lam + j);               // Eq. 3 in ascending order
 #pragma unroll
-                    for (int k = 0; k < DV; ++k)
+                    for (int k = 0; k < KD; ++k)
                         if (k < deg) post = __fadd_rn(post, v[k]);
                     upd += (unsigned long long)deg;
                     if (post <= 0.f) {                            // Eq. 4
                         atomicOr(&eh[j >> 5], bit);
-                        for (int k = 0; k < deg; ++k) {
-                            const int r = DV <= 6 ? __ldg(g.colER + (size_t)k * g.Npad + j).y
-                                                  : __ldg(g.col_row + kb + k);
-                            atomicXor(&par[r >> 5], 1u << (r & 31));
-                        }
+#pragma unroll
+                        for (int k = 0; k < KD; ++k)
+                            if (rr[k] >= 0) atomicXor(&par[rr[k] >> 5], 1u << (rr[k] & 31));
                     }
                 }
                 __syncwarp();
@@ -1787,7 +1781,12 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, int group_warp
         if (!weighted && g.all_lam_pos && cfg.num_results == 1 && ls->smem_screen <= (size_t)max_optin) {
             void* kf = gkind == 0 ? (void*)k_screen<3> : gkind == 1 ? (void*)k_screen<6> : (void*)k_screen<16>;
             int bps_scr = 0;
+            // a screen warp's state is a few KB of bit sets and lists: prefer the
+            // shared-memory carveout that lets the register file, not the
+            // carveout, bound the resident blocks
             if (CUDA_FAILED(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) ||
+                CUDA_FAILED(cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                 cudaSharedmemCarveoutMaxShared)) ||
                 CUDA_FAILED(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_scr, kf, 32 * kScreenWarps,
                                                                           ls->smem_screen)))
                 return -2;
