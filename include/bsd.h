@@ -226,6 +226,28 @@ int bsd_get_info(const bsd_decoder *dec, int32_t *M, int32_t *N, int32_t *K, int
  * launch shape uses them.  Any pointer may be NULL. */
 int bsd_get_batch(const bsd_decoder *dec, int32_t *slots, int32_t *active);
 
+/* Where the single-warp engine keeps a candidate's messages in shared memory
+ * (a layout choice of this library; the paper's Eqs. 1-3 do not depend on
+ * it).  For codes with every row of degree 6 and every column of degree 3
+ * (the bivariate bicycle codes) the pair h of row i is at word plane[h] + 2 i
+ * with plane[h] = h (64 ceil(M / 32) + 12), and the error-node pass reads the
+ * k-th edge of column j at col_word[3 j + k].
+ * The rows' edge orders and the columns' k orders are searched so that both
+ * passes touch 32 distinct banks per access; bsd_create builds the same
+ * placement for codes of at most 160 columns and 96 rows.  Host only; nothing
+ * is allocated on a device.
+ *   M, N, H_row_ptr, H_col_idx  host, H in CSR as for bsd_create
+ *   plane      host int32[3]: out, the plane bases
+ *   edge_word  host int32[E]: out, the word of CSR edge e (E = H_row_ptr[M])
+ *   col_word   host int32[3 N]: out
+ *   extent     host int32: out, the words spanned
+ *   excess     host int32: out, the error-pass bank loads above three that
+ *              remain (0: every access conflict-free)
+ * Errors: BSD_ERR_INVALID_ARG (null pointer, bad CSR), BSD_ERR_UNSUPPORTED
+ * (another degree structure). */
+int bsd_small_layout(int32_t M, int32_t N, const int32_t *H_row_ptr, const int32_t *H_col_idx, int32_t *plane,
+                     int32_t *edge_word, int32_t *col_word, int32_t *extent, int32_t *excess);
+
 /* Opt-in timing of this library's kernels (not part of the method): while
  * enabled, every kernel launch made by bsd_decode / bsd_decode_host is
  * bracketed by two CUDA events recorded on the decode stream.  Enabling costs

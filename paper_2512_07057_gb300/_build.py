@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbsd.so")
-SOURCES = ["bsd_kernels.cu", "bsd_batch.cu", "bsd_api.cu", "bsd_noalloc.cu", "bsd_unrolled.cu", "bsd_dem.cpp"]
+SOURCES = ["bsd_kernels.cu", "bsd_batch.cu", "bsd_api.cu", "bsd_noalloc.cu", "bsd_unrolled.cu", "bsd_dem.cpp",
+           "bsd_layout.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -31,7 +31,7 @@ BSD_STATUS_FAILED = 4
 
 # every symbol include/bsd.h declares
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
-           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_get_batch", "bsd_profile_enable", "bsd_profile_read",
+           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_get_batch", "bsd_small_layout", "bsd_profile_enable", "bsd_profile_read",
            "bsd_decode_noalloc", "bsd_set_weights", "bsd_unrolled_workspace", "bsd_unrolled_forward",
            "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_autotune", "bsd_get_shape", "bsd_dem_parse",
            "bsd_dem_sizes", "bsd_dem_fill", "bsd_dem_free",
@@ -85,6 +85,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_sync_error.argtypes = [P]
     lib.bsd_get_info.argtypes = [P] + [C.POINTER(C.c_int32)] * 4 + [C.POINTER(C.c_int64)] * 2
     lib.bsd_get_batch.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.bsd_small_layout.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.bsd_decode_noalloc.argtypes = [P, P, C.c_int64, P, P, P, P, P]
     lib.bsd_profile_enable.argtypes = [P, C.c_int]
     lib.bsd_set_weights.argtypes = [P, P, C.c_int32]
@@ -185,6 +186,23 @@ def bsd_get_batch(dec) -> dict:
     sl, ac = C.c_int32(), C.c_int32()
     check(load().bsd_get_batch(dec, C.byref(sl), C.byref(ac)), "bsd_get_batch")
     return dict(slots=sl.value, active=bool(ac.value))
+
+
+def bsd_small_layout(M: int, N: int, row_ptr, col_idx) -> dict:
+    """The single-warp engine's shared-memory placement of H's messages (host
+    only): plane bases, the word of every CSR edge, the word of the k-th edge
+    of every column ([N][3]), the words spanned and the bank loads above three
+    left in the error-node pass."""
+    import numpy as np
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    plane = np.zeros(3, np.int32)
+    ew = np.zeros(int(rp[-1]), np.int32)
+    cw = np.zeros(3 * int(N), np.int32)
+    ext, exc = C.c_int32(), C.c_int32()
+    check(load().bsd_small_layout(int(M), int(N), rp.ctypes.data, ci.ctypes.data, plane.ctypes.data, ew.ctypes.data,
+                                  cw.ctypes.data, C.byref(ext), C.byref(exc)), "bsd_small_layout")
+    return dict(plane=plane, edge_word=ew, col_word=cw.reshape(int(N), 3), extent=ext.value, excess=exc.value)
 
 
 def bsd_set_weights(dec, h_weights, T: int) -> None:

@@ -53,7 +53,11 @@ struct bsd_decoder {
     bsd_decoder* twin = nullptr;
     void* rr_mem = nullptr;                  // flagged list, count, gathered syndromes, re-run outputs
     long long rr_cap = 0;                    // capacity of the flagged list
-    float* weights_mem = nullptr;            // [wT][Epad] weights of weighted min-sum (bsd_set_weights)
+    float* weights_mem = nullptr;            // [wT][Epad] weights of weighted min-sum (bsd_set_weights),
+                                             // then the same at the single-warp engine's words
+    int small_excess = -1;                   // single-warp placement: bank loads above three left (-1: none)
+    int small_extent = 0;                    // words it spans
+    std::vector<int> small_addr;             // its word of every CSR edge
     void* graph_small = nullptr;             // the same graph with grids sized for chunks of <= small_n shots
     int small_n = 0;
 };
@@ -288,7 +292,13 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
 
     // ---- host tables
     const int WM = words_of(M), WN = words_of(N), WK = words_of(K);
-    const int Epad = (int)((E + 7) / 8 * 8), Npad = (N + 3) / 4 * 4;
+    // the single-warp engine's placement of the messages, for the codes it
+    // can run (at most 5 words of columns, 3 of rows); Epad covers it
+    SmallLayout sl;
+    const bool has_sl = N <= 32 * kSmallMaxCpl && M <= 32 * kSmallMaxRpl && small_layout(M, N, H_row_ptr, H_col_idx, &sl);
+    int Epad = (int)((E + 7) / 8 * 8);
+    if (has_sl) Epad = std::max(Epad, (sl.extent + 7) / 8 * 8);
+    const int Npad = (N + 3) / 4 * 4;
     const int prec = params->msg_precision;
     const int msg_bytes = prec == BSD_FP32 ? 4 : 2;
     std::vector<int> col_ptr(N + 1, 0), col_edge(E), col_row(E);
@@ -375,6 +385,17 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
             D0[e] = d;
         }
     }
+    // D0 and E(0) at the single-warp engine's words
+    std::vector<float> sD0;
+    std::vector<unsigned char> slamE_st;
+    if (has_sl) {
+        sD0.assign(Epad, 0.f);
+        slamE_st.assign((size_t)Epad * msg_bytes, 0);
+        for (long long e = 0; e < E; ++e) {
+            sD0[sl.addr[e]] = D0[e];
+            std::memcpy(&slamE_st[(size_t)sl.addr[e] * msg_bytes], &lamE_st[(size_t)e * msg_bytes], msg_bytes);
+        }
+    }
     // the generic engines' column table: (edge, row) of the k-th edge of column
     // j at [k][j], (-1, -1) past the column's degree, for degree bounds 3 and 6
     const int colK = max_col <= 3 ? 3 : max_col <= 6 ? 6 : 0;
@@ -457,6 +478,11 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     gb += align256(sizeof(int) * colperm.size());
     gb += align256(sizeof(int2) * colseq.size());
     gb += align256(sizeof(float) * colRD.size());
+    if (has_sl) {
+        gb += align256(sizeof(uint32_t) * sl.col.size());
+        gb += align256(sizeof(float) * sD0.size());
+        gb += align256(slamE_st.size());
+    }
     if (CUDA_FAILED(cudaMalloc(&dec->graph_mem, gb))) { bsd_destroy(dec); return BSD_ERR_OOM; }
     dec->graph_bytes = gb;
     char* p = (char*)dec->graph_mem;
@@ -477,6 +503,9 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     int* d_colperm = colperm.empty() ? nullptr : carve<int>(p, colperm.size());
     int2* d_colseq = colseq.empty() ? nullptr : carve<int2>(p, colseq.size());
     float* d_colRD = colRD.empty() ? nullptr : carve<float>(p, colRD.size());
+    uint32_t* d_scol = has_sl ? carve<uint32_t>(p, sl.col.size()) : nullptr;
+    float* d_sD0 = has_sl ? carve<float>(p, sD0.size()) : nullptr;
+    unsigned char* d_slamE = has_sl ? carve<unsigned char>(p, slamE_st.size()) : nullptr;
     bool ok = !CUDA_FAILED(cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_row_col, H_col_idx, sizeof(int) * E, cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice)) &&
@@ -497,7 +526,11 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
               (colseq.empty() ||
                !CUDA_FAILED(cudaMemcpy(d_colseq, colseq.data(), sizeof(int2) * colseq.size(), cudaMemcpyHostToDevice))) &&
               (colRD.empty() ||
-               !CUDA_FAILED(cudaMemcpy(d_colRD, colRD.data(), sizeof(float) * colRD.size(), cudaMemcpyHostToDevice)));
+               !CUDA_FAILED(cudaMemcpy(d_colRD, colRD.data(), sizeof(float) * colRD.size(), cudaMemcpyHostToDevice))) &&
+              (!has_sl ||
+               (!CUDA_FAILED(cudaMemcpy(d_scol, sl.col.data(), sizeof(uint32_t) * sl.col.size(), cudaMemcpyHostToDevice)) &&
+                !CUDA_FAILED(cudaMemcpy(d_sD0, sD0.data(), sizeof(float) * sD0.size(), cudaMemcpyHostToDevice)) &&
+                !CUDA_FAILED(cudaMemcpy(d_slamE, slamE_st.data(), slamE_st.size(), cudaMemcpyHostToDevice))));
     if (!ok) { bsd_destroy(dec); return BSD_ERR_CUDA; }
 
     DevGraph& g = dec->g;
@@ -513,6 +546,12 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.colperm = d_colperm; g.colseq = d_colseq;
     g.colRD = reinterpret_cast<const float4*>(d_colRD); g.colRDk = rdk;
     for (int d = 0; d < kMaxColDeg + 2; ++d) { g.dstart[d] = dstart[d]; g.dbase[d] = dbase[d]; }
+    g.scol = d_scol; g.sD0 = d_sD0; g.slamE = d_slamE;
+    if (has_sl) {
+        dec->small_excess = sl.excess;
+        dec->small_extent = sl.extent;
+        dec->small_addr = sl.addr;
+    }
 
     DecCfg& cfg = dec->cfg;
     cfg.max_rounds = params->max_rounds;
@@ -527,6 +566,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     const float tg = params->tie_guard_rel;
     cfg.tie_guard = tg > 0.f ? (double)tg : (tg == 0.f && prec == BSD_FP16) ? 1e-3 : (tg == 0.f && prec == BSD_BF16) ? 1e-2 : 0.0;
     cfg.weights = nullptr;         // the scale alpha until bsd_set_weights
+    cfg.sweights = nullptr;
     cfg.wT = 0;
 
     rc = configure_kernels(g, cfg, device, params->group_warps, 0, &dec->ls);
@@ -922,10 +962,17 @@ int bsd_set_weights(bsd_decoder* dec, const float* h_weights, int32_t T)
     // work already queued on the decoder's stream uses the current kernels and weights
     if (CUDA_FAILED(cudaStreamSynchronize(dec->last_stream))) return BSD_ERR_CUDA;
     float* d_w = nullptr;
+    // [T][Epad] in the CSR edge order, then (for codes the single-warp engine
+    // can run) [T][Epad] at that engine's words
+    const bool two = dec->g.scol != nullptr;
     if (T > 0) {
-        std::vector<float> hw((size_t)T * Epad, 0.f);
-        for (size_t t = 0; t < (size_t)T; ++t)
+        std::vector<float> hw((size_t)T * Epad * (two ? 2 : 1), 0.f);
+        for (size_t t = 0; t < (size_t)T; ++t) {
             std::memcpy(hw.data() + t * Epad, h_weights + t * E, sizeof(float) * E);
+            if (two)
+                for (size_t e = 0; e < E; ++e)
+                    hw[((size_t)T + t) * Epad + (size_t)dec->small_addr[e]] = h_weights[t * E + e];
+        }
         if (CUDA_FAILED(cudaMalloc(&d_w, sizeof(float) * hw.size()))) return BSD_ERR_OOM;
         if (CUDA_FAILED(cudaMemcpy(d_w, hw.data(), sizeof(float) * hw.size(), cudaMemcpyHostToDevice))) {
             cudaFree(d_w);
@@ -934,6 +981,7 @@ int bsd_set_weights(bsd_decoder* dec, const float* h_weights, int32_t T)
     }
     DecCfg cfg = dec->cfg;
     cfg.weights = d_w;
+    cfg.sweights = (d_w && two) ? d_w + (size_t)T * Epad : nullptr;
     cfg.wT = T;
     DevGraph g = dec->g;
     LaunchShape ls{};

@@ -55,6 +55,8 @@ struct BsRange {
 // serve both (more bytes in flight per instruction for a pass that waits on
 // memory); the check pass keeps one slot per thread (more warps in flight)
 constexpr int kBsThreads = kBsChunk / 2;
+// messages of a row the check pass loads before it reduces them
+constexpr int kBsRowBatch = 8;
 
 template <int SPT>
 __device__ __forceinline__ BsRange bs_range(const Work& w, int items)
@@ -125,18 +127,30 @@ __global__ void __launch_bounds__(kBsChunk) k_bs_check(DevGraph g, DecCfg cfg, W
             m2 = r.y;
             nb ^= __float_as_uint(r.w) & 1u;
         } else {
-            // branch-free running pair of smallest magnitudes, capped at L_MAX (R3)
+            // branch-free running pair of smallest magnitudes, capped at L_MAX
+            // (R3), eight messages in flight per thread: past the row's end a
+            // lane takes +L_MAX, which changes neither minimum nor the parity
             m1 = L;
             m2 = L;
             const int rb = __ldg(g.row_ptr + i), re = __ldg(g.row_ptr + i + 1);
-#pragma unroll 4
-            for (int e = rb; e < re; ++e) {
-                const float x = S::ld(E, (size_t)e * Bs + b);
-                const float a = fabsf(x);
-                m2 = fminf(m2, fmaxf(m1, a));
-                m1 = fminf(m1, a);
-                nb ^= (x < 0.f) ? 1u : 0u;
+            const T* Eb = E + b;
+            uint32_t sg = 0u;
+            for (int e = rb; e < re; e += kBsRowBatch) {
+                float x[kBsRowBatch];
+#pragma unroll
+                for (int u = 0; u < kBsRowBatch; ++u)
+                    x[u] = (e + u < re) ? S::ld(Eb, (size_t)(e + u) * Bs) : L;
+#pragma unroll
+                for (int u = 0; u < kBsRowBatch; ++u) {
+                    const float a = fabsf(x[u]);
+                    m2 = fminf(m2, fmaxf(m1, a));
+                    m1 = fminf(m1, a);
+                    sg ^= __float_as_uint(x[u]);
+                }
             }
+            // a stored message is never -0 (a clamped sum that starts at
+            // Lambda_j), so its sign bit is exactly x < 0
+            nb ^= sg >> 31;
         }
         const uint32_t sb = nb << 31;
         w.bsR[(size_t)i * Bs + b] = make_float2(__uint_as_float(__float_as_uint(m1) | sb),

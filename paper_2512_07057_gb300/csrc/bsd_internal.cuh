@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "bsd.h"
 
@@ -35,6 +36,8 @@ namespace bsd {
 
 constexpr int kMaxColDeg = 16;   // the generic engines' largest column degree bound
 constexpr int kMaxBeam = 64;
+constexpr int kSmallMaxCpl = 5;   // the single-warp engine's largest code: 5 words of columns
+constexpr int kSmallMaxRpl = 3;   // and 3 of rows
 constexpr int kMaxResults = 64;
 constexpr double kFixScale = 65536.0;   // fixed-point grid 2^-16 for scores and weights
 
@@ -75,6 +78,15 @@ struct DevGraph {
     int colRDk;
     int dstart[kMaxColDeg + 2];
     int dbase[kMaxColDeg + 2];
+    // the single-warp engine's shared-memory placement of a candidate's
+    // messages (codes with every row of degree 6 and every column of degree
+    // 3; bsd_layout.cu): the pair h of row i at word h small_plane_stride(M)
+    // + 2 i, and scol[3 j + k] = (word << 16) | row for the k-th edge of
+    // column j; sD0 and slamE hold D0 and E(0) at those words (Epad covers
+    // the placement)
+    const uint32_t* scol;  // [3 N], null when the code has no such placement
+    const float* sD0;      // [Epad]
+    const void* slamE;     // [Epad] in the storage format
 };
 
 struct DecCfg {
@@ -82,8 +94,27 @@ struct DecCfg {
     float alpha, L;        // L: L_MAX as the storage format holds it
     double tie_guard;      // near-tie margin (0: no flags)
     const float* weights;  // optional [wT][Epad]: w_{e,t} in place of alpha (weighted engines only)
+    const float* sweights; // the same weights at the single-warp engine's words (when DevGraph::scol is set)
     int wT;                // iteration t of a BP call uses row min(t, wT) - 1
 };
+
+// the single-warp engine's placement of a code's messages (bsd_layout.cu):
+// plane bases A[0..2], the word of every CSR edge, the per-(column, k) table,
+// the words spanned and the bank loads above three the search left (0: both
+// passes conflict-free); false when the code is not of row degree 6 and
+// column degree 3
+struct SmallLayout {
+    int A[4];
+    std::vector<int> addr;
+    std::vector<uint32_t> col;
+    int extent;
+    int excess;
+};
+bool small_layout(int M, int N, const int* row_ptr, const int* col_idx, SmallLayout* out);
+// the placement's plane stride for codes of M rows (the engine holds
+// ceil(M / 32) rows per lane); every plane spans 2 M <= 64 ceil(M / 32) words
+__host__ __device__ constexpr int small_plane_stride_rpl(int rpl) { return 64 * rpl + 12; }
+inline int small_plane_stride(int M) { return small_plane_stride_rpl((M + 31) / 32); }
 
 struct SlotMeta {
     long long S;           // sum over U of q(|sum_LLR_j|), q = round(x * 2^16)

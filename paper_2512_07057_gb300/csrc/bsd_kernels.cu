@@ -455,6 +455,14 @@ struct GenericEngine {
     static constexpr bool kPriorSetsSums = true;  // ... nor cleared sums: their first iteration sets them
     G grp;
     __device__ void load_graph(const DevGraph&) {}
+    // E(0) in this engine's message layout (the CSR edge order)
+    static __device__ const void* prior_E(const DevGraph& g) { return g.lamE; }
+    // the sentinel +L_MAX on every message of the newly fixed node j
+    __device__ void fix_node(const DevGraph& g, const WarpState& st, int j, float L) const
+    {
+        for (int q = __ldg(g.col_ptr + j) + grp.rank(); q < __ldg(g.col_ptr + j + 1); q += grp.size())
+            Store<P>::st(reinterpret_cast<typename Store<P>::T*>(st.E), __ldg(g.col_edge + q), L);
+    }
     __device__ void clear_sums(const DevGraph& g, const WarpState& st)
     {
         for (int j = grp.rank(); j < g.N; j += grp.size()) st.sumllr[j] = 0.f;
@@ -477,15 +485,19 @@ struct GenericEngine {
 };
 
 // SmallEngine: codes with every column of degree exactly 3, every row of
-// degree exactly RD (row i's edges at RD*i .. RD*i+RD-1), N <= 32*CPL,
-// M <= 32*RPL and fewer than 65536 edges -- the bivariate bicycle codes.
-// Each lane keeps its columns' edge and row indices, priors, sum_LLR and
-// mask bits in registers for the warp's lifetime.  The detector pass writes
-// D_{i->j} itself for every edge (row-contiguous vector stores), so the
+// degree exactly RD = 6, N <= 32*CPL, M <= 32*RPL and fewer than 65536 edges
+// -- the bivariate bicycle codes.  A candidate's messages E and D sit at the
+// words of the code's placement (bsd_layout.cu): the pair h of row i at
+// h kPlane + 2 i, so the detector pass moves 32 consecutive pairs per access,
+// and the error pass gathers and scatters through a per-(column, k) word
+// table chosen to put the 32 lanes in 32 distinct banks.  Each lane keeps its
+// columns' words and rows, sum_LLR and mask bits in registers for the warp's
+// lifetime.  The detector pass writes D_{i->j} itself for every edge, so the
 // error-node pass gathers one 4-byte message per edge; the ascending-order
 // sums of three messages are formed from min / max / median directly.  Every
 // value it produces is the one GenericEngine produces (same operations, same
-// order).
+// order; the placement only permutes where a row's edges and a column's
+// edges are kept, and neither pass depends on that order).
 template <int CPL, int RPL, int RD, int P, bool W = false>
 struct SmallEngine {
     using Grp = WarpGroup;
@@ -496,7 +508,9 @@ struct SmallEngine {
     static constexpr bool kPriorSetsSums = false;
     WarpGroup grp;
     using S = Store<P>;
-    uint32_t ci[CPL][3];   // (CSR edge id << 16) | row, for column lane + 32 c
+    static_assert(RD == 6, "the placement holds rows of degree 6");
+    static constexpr int kPlane = small_plane_stride_rpl(RPL);   // words between a row's pairs
+    uint32_t ci[CPL][3];   // (word << 16) | row of the k-th edge of column lane + 32 c
     float sum[CPL];
     uint32_t mb;           // bit c: column lane + 32 c is masked or beyond N
 
@@ -508,13 +522,17 @@ struct SmallEngine {
             const int j = lane + 32 * c;
             ci[c][0] = ci[c][1] = ci[c][2] = 0u;
             if (j < g.N) {
-                const int kb = __ldg(g.col_ptr + j);
 #pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    ci[c][k] = ((uint32_t)__ldg(g.col_edge + kb + k) << 16) | (uint32_t)__ldg(g.col_row + kb + k);
-
+                for (int k = 0; k < 3; ++k) ci[c][k] = __ldg(g.scol + 3 * j + k);
             }
         }
+    }
+    static __device__ const void* prior_E(const DevGraph& g) { return g.slamE; }
+    __device__ void fix_node(const DevGraph& g, const WarpState& st, int j, float L) const
+    {
+        const int lane = threadIdx.x & 31;
+        if (lane < 3)
+            Store<P>::st(reinterpret_cast<typename Store<P>::T*>(st.E), __ldg(g.scol + 3 * j + lane) >> 16, L);
     }
     __device__ void clear_sums(const DevGraph&, const WarpState&)
     {
@@ -547,7 +565,7 @@ struct SmallEngine {
             if (ab.key != nullptr && lane == 0) ab_key = *((volatile const unsigned long long*)ab.key);
             if (lane < RPL) st.par[lane] = spw;           // the code's M bits fill RPL words
             // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
-            const float* wt = W ? cfg.weights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
+            const float* wt = W ? cfg.sweights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
             // ---- detector pass (Eq. 1); a run from E(0) takes its first check
             // messages from the table D0, flipping the sign where s_i = 1
             if (!W && from_prior && t == 1) {
@@ -556,13 +574,13 @@ struct SmallEngine {
                     const int i = lane + 32 * r;
                     if (i < g.M) {
                         const uint32_t sb = ((st.sp[i >> 5] >> (i & 31)) & 1u) << 31;
-                        const float2* src = reinterpret_cast<const float2*>(g.D0 + RD * i);
-                        float2* dr = reinterpret_cast<float2*>(st.D + RD * i);
 #pragma unroll
                         for (int h = 0; h < RD / 2; ++h) {
-                            const float2 v = __ldg(src + h);
-                            dr[h] = make_float2(__uint_as_float(__float_as_uint(v.x) ^ sb),
-                                                __uint_as_float(__float_as_uint(v.y) ^ sb));
+                            const int wd = h * kPlane + 2 * i;
+                            const float2 v = __ldg(reinterpret_cast<const float2*>(g.sD0 + wd));
+                            *reinterpret_cast<float2*>(st.D + wd) =
+                                make_float2(__uint_as_float(__float_as_uint(v.x) ^ sb),
+                                            __uint_as_float(__float_as_uint(v.y) ^ sb));
                         }
                     }
                 }
@@ -571,11 +589,10 @@ struct SmallEngine {
             for (int r = 0; r < ((!W && from_prior && t == 1) ? 0 : RPL); ++r) {
                 const int i = lane + 32 * r;
                 if (i < g.M) {
-                    const int eb = RD * i;
                     float x[RD];
 #pragma unroll
                     for (int h = 0; h < RD / 2; ++h) {
-                        const float2 x2 = S::ld2(E, eb + 2 * h);
+                        const float2 x2 = S::ld2(E, h * kPlane + 2 * i);
                         x[2 * h] = x2.x;
                         x[2 * h + 1] = x2.y;
                     }
@@ -617,12 +634,12 @@ struct SmallEngine {
                     const float m1s = __uint_as_float(__float_as_uint(m1) | nb);
                     const float m2s = __uint_as_float(__float_as_uint(m2) | nb);
                     const float d1 = W ? m1s : __fmul_rn(alpha, m1s), d2 = W ? m2s : __fmul_rn(alpha, m2s);
-                    float2* dr = reinterpret_cast<float2*>(st.D + RD * i);
 #pragma unroll
                     for (int h = 0; h < RD / 2; ++h) {
+                        const int wd = h * kPlane + 2 * i;
                         float dd[2];
                         float2 w2 = make_float2(alpha, alpha);
-                        if (W) w2 = __ldg(reinterpret_cast<const float2*>(wt + eb + 2 * h));
+                        if (W) w2 = __ldg(reinterpret_cast<const float2*>(wt + wd));
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             const int k = 2 * h + u;
@@ -630,7 +647,7 @@ struct SmallEngine {
                             const float d = W ? __fmul_rn(u ? w2.y : w2.x, sel) : sel;
                             dd[u] = __uint_as_float(__float_as_uint(d) ^ (__float_as_uint(x[k]) & 0x80000000u));
                         }
-                        dr[h] = make_float2(dd[0], dd[1]);
+                        *reinterpret_cast<float2*>(st.D + wd) = make_float2(dd[0], dd[1]);
                     }
                 }
             }
@@ -1170,7 +1187,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
             grp.sync();
             continue;
         }
-        if (!Eng::kPriorStart) group_copy16(grp, st.E, g.lamE, snap_vec16(g));
+        if (!Eng::kPriorStart) group_copy16(grp, st.E, Eng::prior_E(g), snap_vec16(g));
         if (!Eng::kPriorSetsSums) eng.clear_sums(g, st);
         grp.sync();
         int succ = 0;
@@ -1265,8 +1282,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_round(Dev
         group_copy16(grp, st.E, par.E, snap_vec16(g));
         eng.clear_sums(g, st);
         grp.sync();
-        for (int q = __ldg(g.col_ptr + pos) + grp.rank(); q < __ldg(g.col_ptr + pos + 1); q += grp.size())
-            Store<Eng::kPrec>::st(reinterpret_cast<typename Store<Eng::kPrec>::T*>(st.E), __ldg(g.col_edge + q), cfg.L);
+        eng.fix_node(g, st, pos, cfg.L);
         grp.sync();
         // with num_results = 1, only the first success in visit order matters:
         // a child stops once a lower-index sibling of this round has succeeded
@@ -1612,7 +1628,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_bp_llr(De
     for (long long b = (long long)blockIdx.x * grp.per_block() + grp.index(); b < B; b += nw) {
         for (int q = grp.rank(); q < g.WM; q += grp.size()) st.sp[q] = synd[b * g.WM + q];
         for (int q = grp.rank(); q < g.WN; q += grp.size()) { st.mask[q] = 0u; st.vals[q] = 0u; }
-        if (!Eng::kPriorStart) group_copy16(grp, st.E, g.lamE, snap_vec16(g));
+        if (!Eng::kPriorStart) group_copy16(grp, st.E, Eng::prior_E(g), snap_vec16(g));
         if (!Eng::kPriorSetsSums) eng.clear_sums(g, st);
         grp.sync();
         int succ;
@@ -1688,9 +1704,11 @@ static int occupancy(int threads, size_t smem_bp, int* bps)
     return 0;
 }
 
-// can the small engine run this code? (column degree 3, row degree 6 laid out at 6 i)
+// can the small engine run this code? (column degree 3, row degree 6, with
+// the placement of its messages built)
 static bool small_fits(const DevGraph& g, int cpl, int rpl)
 {
+    if (g.scol == nullptr) return false;
     if (g.max_col_deg != 3 || g.max_row_deg != 6 || g.E != 3 * g.N || g.E != 6 * g.M) return false;
     if (g.E >= 65536 || g.M >= 65536) return false;
     return g.WN == cpl && (g.M + 31) / 32 == rpl;
