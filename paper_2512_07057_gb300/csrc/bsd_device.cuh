@@ -70,6 +70,14 @@ template <> struct Store<2> {
     }
 };
 
+// the smallest of three floats (an exact operation; no operand is NaN here)
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 enum : uint32_t { ST_SEED = 1u, ST_BEAM = 2u, ST_FAILED = 4u, ST_NEAR = 8u, ST_RERUN = 16u };
 
 }  // namespace bsd

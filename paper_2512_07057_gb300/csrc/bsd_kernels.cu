@@ -607,17 +607,12 @@ struct SmallEngine {
                         lo[h] = fminf(fabsf(x[2 * h]), fabsf(x[2 * h + 1]));
                         hi[h] = fmaxf(fabsf(x[2 * h]), fabsf(x[2 * h + 1]));
                     }
-                    float m1 = fminf(lo[0], lo[1]), m2 = fmaxf(lo[0], lo[1]);
-#pragma unroll
-                    for (int h = 2; h < RD / 2; ++h) {
-                        m2 = fminf(m2, fmaxf(m1, lo[h]));
-                        m1 = fminf(m1, lo[h]);
-                    }
-                    float hm = hi[0];
-#pragma unroll
-                    for (int h = 1; h < RD / 2; ++h) hm = fminf(hm, hi[h]);
-                    m2 = fminf(fminf(m2, hm), L);
-                    m1 = fminf(m1, L);
+                    // (three pairs: t <= u the pair minima lo0, lo1 in order;
+                    // the runner-up among the lo is min(u, max(t, lo2)); the
+                    // caps at L_MAX folded into three-input minima)
+                    const float t = fminf(lo[0], lo[1]), u = fmaxf(lo[0], lo[1]);
+                    const float m1 = fmin3(t, lo[2], L);
+                    const float m2 = fminf(fmin3(u, fmaxf(t, lo[2]), hi[0]), fmin3(hi[1], hi[2], L));
                     // sign parity in bit 31: a stored message is never -0 (it is
                     // a clamped sum of terms that starts at Lambda_j or the
                     // sentinel), so its sign bit is exactly x < 0
