@@ -203,6 +203,37 @@ int bsd_decode_noalloc(const bsd_decoder *dec, const uint32_t *d_syndromes, int6
                        uint32_t *d_corrections, uint32_t *d_obs_flips,
                        uint32_t *d_status, uint32_t *d_iters, void *cuda_stream);
 
+/* Single-syndrome request loop (low-latency decoding).  bsd_serve_start
+ * keeps one candidate group of the decoder's kernels resident on its device,
+ * polling a mailbox in host-mapped memory; bsd_serve_decode posts one
+ * syndrome and waits for the answer.  A syndrome whose first BP run ends the
+ * search (Alg. 3: it converges, with num_results = 1, or max_rounds = 0) is
+ * answered by the loop itself -- the same kernels, operations and order as
+ * bsd_decode, so the outputs are identical -- with no launch and no stream
+ * wait; any other is decoded by the regular path (bsd_decode_host on a stream
+ * of the loop's own), so every answer equals bsd_decode's.
+ *   idle_ms     the loop leaves after this many milliseconds without a
+ *               request (1..60000) and bsd_serve_decode starts it again;
+ *               every wait of the loop is bounded by it or by the stop flag
+ *   h_syndrome  host, WM words; h_correction host, WN words; h_obs_flips
+ *               host, WK words (NULL allowed when K = 0); h_status host, one
+ *               word; h_iters host, one word or NULL -- as bsd_decode_host
+ *               for B = 1
+ * bsd_serve_start runs one regular decode first, so the regular path's
+ * buffers exist before the loop is resident, then allocates the mailbox
+ * (pinned, mapped) and two streams; a decoder already serving returns
+ * BSD_OK.  bsd_serve_decode returns BSD_ERR_INVALID_ARG when the decoder is
+ * not serving, BSD_ERR_TIMEOUT when no answer comes within 2 s.
+ * bsd_serve_stop ends the loop and frees what start allocated (BSD_OK when
+ * not serving); bsd_destroy, bsd_set_weights and bsd_autotune call it.
+ * While serving, the decoder's other calls may run on other streams; one
+ * that allocates device memory (a first decode of a larger batch) may wait
+ * for the loop's idle limit.  Calls on one decoder are not thread-safe. */
+int bsd_serve_start(bsd_decoder *dec, int32_t idle_ms);
+int bsd_serve_decode(bsd_decoder *dec, const uint32_t *h_syndrome, uint32_t *h_correction,
+                     uint32_t *h_obs_flips, uint32_t *h_status, uint32_t *h_iters);
+int bsd_serve_stop(bsd_decoder *dec);
+
 /* Plain min-sum BP (App. A, Eqs. 1-3) from E(0) = Lambda for exactly T
  * iterations per syndrome, with no stopping rule; writes the posterior LLRs
  * Lambda_j(T) (device, B x N floats) and, if d_sum_llr is not NULL, the sums

@@ -31,7 +31,8 @@ BSD_STATUS_FAILED = 4
 
 # every symbol include/bsd.h declares
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
-           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_get_batch", "bsd_small_layout", "bsd_profile_enable", "bsd_profile_read",
+           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_get_batch", "bsd_small_layout", "bsd_serve_start", "bsd_serve_decode",
+           "bsd_serve_stop", "bsd_profile_enable", "bsd_profile_read",
            "bsd_decode_noalloc", "bsd_set_weights", "bsd_unrolled_workspace", "bsd_unrolled_forward",
            "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_autotune", "bsd_get_shape", "bsd_dem_parse",
            "bsd_dem_sizes", "bsd_dem_fill", "bsd_dem_free",
@@ -81,6 +82,9 @@ def load(path: str | None = None) -> C.CDLL:
                                C.POINTER(P)]
     lib.bsd_decode.argtypes = [P, P, C.c_int64, P, P, P, P, P]
     lib.bsd_decode_host.argtypes = [P, P, C.c_int64, P, P, P, P, P]
+    lib.bsd_serve_start.argtypes = [P, C.c_int32]
+    lib.bsd_serve_decode.argtypes = [P, P, P, P, P, P]
+    lib.bsd_serve_stop.argtypes = [P]
     lib.bsd_bp_llr.argtypes = [P, P, C.c_int64, C.c_int32, P, P, P]
     lib.bsd_sync_error.argtypes = [P]
     lib.bsd_get_info.argtypes = [P] + [C.POINTER(C.c_int32)] * 4 + [C.POINTER(C.c_int64)] * 2
@@ -163,6 +167,19 @@ def bsd_decode_noalloc(dec, d_syndromes, B, d_corrections, d_obs_flips, d_status
 def bsd_decode_host(dec, h_syndromes, B, h_corrections, h_obs_flips, h_status, h_iters, stream) -> None:
     check(load().bsd_decode_host(dec, h_syndromes, int(B), h_corrections, h_obs_flips, h_status, h_iters, stream),
           "bsd_decode_host")
+
+
+def bsd_serve_start(dec, idle_ms: int) -> None:
+    check(load().bsd_serve_start(dec, int(idle_ms)), "bsd_serve_start")
+
+
+def bsd_serve_decode(dec, h_syndrome, h_correction, h_obs_flips, h_status, h_iters) -> None:
+    """One syndrome through the request loop; host addresses as bsd_decode_host with B = 1."""
+    check(load().bsd_serve_decode(dec, h_syndrome, h_correction, h_obs_flips, h_status, h_iters), "bsd_serve_decode")
+
+
+def bsd_serve_stop(dec) -> None:
+    check(load().bsd_serve_stop(dec), "bsd_serve_stop")
 
 
 def bsd_bp_llr(dec, d_syndromes, B, T, d_llr, d_sum_llr, stream) -> None:

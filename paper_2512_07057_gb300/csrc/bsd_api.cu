@@ -9,6 +9,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -58,6 +59,13 @@ struct bsd_decoder {
     int small_excess = -1;                   // single-warp placement: bank loads above three left (-1: none)
     int small_extent = 0;                    // words it spans
     std::vector<int> small_addr;             // its word of every CSR edge
+    // the single-syndrome request loop (bsd_serve_*)
+    ServeBox* serve_h = nullptr;             // mailbox, host-mapped (null when not serving)
+    ServeBox* serve_d = nullptr;             // its device address
+    cudaStream_t serve_stream = nullptr;     // the loop's stream
+    cudaStream_t serve_fb = nullptr;         // the regular path for answers left to the beam search
+    uint32_t serve_seq = 0;                  // number of the latest request
+    unsigned long long serve_idle_ns = 0;
     void* graph_small = nullptr;             // the same graph with grids sized for chunks of <= small_n shots
     int small_n = 0;
 };
@@ -235,6 +243,7 @@ int bsd_params_preset(const char* name, bsd_params* out)
 void bsd_destroy(bsd_decoder* dec)
 {
     if (!dec) return;
+    bsd_serve_stop(dec);
     {
         DeviceGuard dg(dec->device);
         if (dec->graph_mem) cudaFree(dec->graph_mem);
@@ -890,6 +899,7 @@ int bsd_autotune(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, void*
                  bsd_shape_timing* report, int32_t report_cap, int32_t* n_report)
 {
     if (!dec || !d_syndromes || B < 1 || report_cap < 0 || (report_cap > 0 && !report)) return BSD_ERR_INVALID_ARG;
+    if (dec->serve_h && bsd_serve_stop(dec) != BSD_OK) return BSD_ERR_CUDA;   // it runs the current kernels
     DeviceGuard dg(dec->device);
     if (!dg.ok) return BSD_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -953,6 +963,7 @@ int bsd_autotune(bsd_decoder* dec, const uint32_t* d_syndromes, int64_t B, void*
 int bsd_set_weights(bsd_decoder* dec, const float* h_weights, int32_t T)
 {
     if (!dec || T < 0 || (T > 0 && !h_weights)) return BSD_ERR_INVALID_ARG;
+    if (dec->serve_h && bsd_serve_stop(dec) != BSD_OK) return BSD_ERR_CUDA;   // it runs the current kernels
     if (T > 0 && dec->g.prec != BSD_FP32) return BSD_ERR_UNSUPPORTED;
     const size_t E = (size_t)dec->g.E, Epad = (size_t)dec->g.Epad;
     for (size_t k = 0; k < (size_t)T * E; ++k)
@@ -1104,6 +1115,138 @@ int bsd_get_batch(const bsd_decoder* dec, int32_t* slots, int32_t* active)
     if (slots) *slots = dec->w.bs_slots;
     if (active) *active = (dec->ls.batch && dec->w.bs_slots > 0) ? 1 : 0;
     return BSD_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// single-syndrome request loop
+// ----------------------------------------------------------------------------
+namespace {
+
+constexpr double kServeWaitSeconds = 2.0;     // the host's bound on one answer
+
+// the decoder's streams are the caller's or the legacy stream once the
+// loop's own are gone (later calls synchronise dec->last_stream)
+void serve_drop_streams(bsd_decoder* dec)
+{
+    if (dec->last_stream == dec->serve_stream || dec->last_stream == dec->serve_fb) dec->last_stream = nullptr;
+    if (dec->serve_stream) cudaStreamDestroy(dec->serve_stream);
+    if (dec->serve_fb) cudaStreamDestroy(dec->serve_fb);
+    dec->serve_stream = dec->serve_fb = nullptr;
+}
+
+int serve_launch(bsd_decoder* dec)
+{
+    ServeBox* b = dec->serve_h;
+    __atomic_store_n(&b->stop, 0u, __ATOMIC_RELAXED);
+    __atomic_store_n(&b->state, 0u, __ATOMIC_RELAXED);
+    // answer whatever came after the last answered request
+    const uint32_t last = __atomic_load_n(&b->done, __ATOMIC_ACQUIRE);
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    return launch_serve(dec->g, dec->cfg, dec->ls, dec->serve_d, last, dec->serve_idle_ns, dec->serve_stream)
+               ? BSD_ERR_CUDA
+               : BSD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bsd_serve_start(bsd_decoder* dec, int32_t idle_ms)
+{
+    if (!dec || idle_ms < 1 || idle_ms > 60000) return BSD_ERR_INVALID_ARG;
+    if (dec->serve_h) return BSD_OK;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    const DevGraph& g = dec->g;
+    if (CUDA_FAILED(cudaStreamCreateWithFlags(&dec->serve_fb, cudaStreamNonBlocking))) return BSD_ERR_CUDA;
+    // one regular decode first: every buffer the regular path allocates on
+    // first use exists before the loop is resident (an allocation may wait
+    // for the whole device)
+    std::vector<uint32_t> zs(g.WM, 0u), zc(g.WN), zo(g.WK > 0 ? g.WK : 1), zst(1), zit(1);
+    int rc = bsd_decode_host(dec, zs.data(), 1, zc.data(), g.K > 0 ? zo.data() : nullptr, zst.data(), zit.data(),
+                             dec->serve_fb);
+    if (rc == BSD_OK && CUDA_FAILED(cudaStreamSynchronize(dec->serve_fb))) rc = BSD_ERR_CUDA;
+    const size_t bytes = sizeof(ServeBox) + sizeof(uint32_t) * (size_t)(g.WM + g.WN + (g.WK > 0 ? g.WK : 1));
+    void* h = nullptr;
+    void* d = nullptr;
+    if (rc == BSD_OK && CUDA_FAILED(cudaHostAlloc(&h, bytes, cudaHostAllocMapped))) rc = BSD_ERR_OOM;
+    if (rc == BSD_OK) {
+        std::memset(h, 0, bytes);
+        if (CUDA_FAILED(cudaHostGetDevicePointer(&d, h, 0)) ||
+            CUDA_FAILED(cudaStreamCreateWithFlags(&dec->serve_stream, cudaStreamNonBlocking)))
+            rc = BSD_ERR_CUDA;
+    }
+    if (rc == BSD_OK) {
+        dec->serve_h = (ServeBox*)h;
+        dec->serve_d = (ServeBox*)d;
+        dec->serve_seq = 0;
+        dec->serve_idle_ns = (unsigned long long)idle_ms * 1000000ull;
+        rc = serve_launch(dec);
+        if (rc == BSD_OK) return BSD_OK;
+        dec->serve_h = dec->serve_d = nullptr;
+    }
+    serve_drop_streams(dec);
+    if (h) cudaFreeHost(h);
+    return rc;
+}
+
+int bsd_serve_decode(bsd_decoder* dec, const uint32_t* h_syndrome, uint32_t* h_correction, uint32_t* h_obs_flips,
+                     uint32_t* h_status, uint32_t* h_iters)
+{
+    if (!dec || !dec->serve_h || !h_syndrome || !h_correction || !h_status || (dec->g.K > 0 && !h_obs_flips))
+        return BSD_ERR_INVALID_ARG;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    const DevGraph& g = dec->g;
+    ServeBox* b = dec->serve_h;
+    uint32_t* words = reinterpret_cast<uint32_t*>(b + 1);
+    // a loop that left after its idle limit runs again
+    if (__atomic_load_n(&b->state, __ATOMIC_ACQUIRE) >= 2u) {
+        if (CUDA_FAILED(cudaStreamSynchronize(dec->serve_stream))) return BSD_ERR_CUDA;
+        if (serve_launch(dec) != BSD_OK) return BSD_ERR_CUDA;
+    }
+    std::memcpy(words, h_syndrome, sizeof(uint32_t) * (size_t)g.WM);
+    uint32_t seq = dec->serve_seq + 1;
+    if (seq == 0u) seq = 1u;                      // 0 is the mailbox's initial number
+    dec->serve_seq = seq;
+    __atomic_store_n(&b->req, seq, __ATOMIC_RELEASE);
+    const auto t0 = std::chrono::steady_clock::now();
+    while (__atomic_load_n(&b->done, __ATOMIC_ACQUIRE) != seq) {
+        if (__atomic_load_n(&b->state, __ATOMIC_ACQUIRE) >= 2u) {
+            // the loop reached its idle limit before it saw this request
+            if (CUDA_FAILED(cudaStreamSynchronize(dec->serve_stream))) return BSD_ERR_CUDA;
+            if (__atomic_load_n(&b->done, __ATOMIC_ACQUIRE) == seq) break;
+            if (serve_launch(dec) != BSD_OK) return BSD_ERR_CUDA;
+        }
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > kServeWaitSeconds)
+            return BSD_ERR_TIMEOUT;
+    }
+    const uint32_t status = __atomic_load_n(&b->status, __ATOMIC_ACQUIRE);
+    if (status == 0u)                             // the beam search decides: the regular path
+        return bsd_decode_host(dec, h_syndrome, 1, h_correction, h_obs_flips, h_status, h_iters, dec->serve_fb);
+    std::memcpy(h_correction, words + g.WM, sizeof(uint32_t) * (size_t)g.WN);
+    if (g.K > 0) std::memcpy(h_obs_flips, words + g.WM + g.WN, sizeof(uint32_t) * (size_t)g.WK);
+    *h_status = status;
+    if (h_iters) *h_iters = __atomic_load_n(&b->iters, __ATOMIC_RELAXED);
+    return BSD_OK;
+}
+
+int bsd_serve_stop(bsd_decoder* dec)
+{
+    if (!dec) return BSD_ERR_INVALID_ARG;
+    if (!dec->serve_h) return BSD_OK;
+    DeviceGuard dg(dec->device);
+    if (!dg.ok) return BSD_ERR_CUDA;
+    __atomic_store_n(&dec->serve_h->stop, 1u, __ATOMIC_RELEASE);
+    // the loop reads the stop flag on every poll and leaves within one answer
+    int rc = CUDA_FAILED(cudaStreamSynchronize(dec->serve_stream)) ? BSD_ERR_CUDA : BSD_OK;
+    if (CUDA_FAILED(cudaStreamSynchronize(dec->serve_fb))) rc = BSD_ERR_CUDA;
+    serve_drop_streams(dec);
+    cudaFreeHost(dec->serve_h);
+    dec->serve_h = dec->serve_d = nullptr;
+    return rc;
 }
 
 }  // extern "C"

@@ -280,6 +280,19 @@ int launch_batch_direct(const DevGraph& g, const DecCfg& cfg, const Work& w, con
 // grid of the batched passes for this device
 int batch_grid(int device);
 void destroy_graph(void* graph_exec);
+// the mailbox of the single-syndrome request loop, in host-mapped memory;
+// the syndrome [WM], correction [WN] and observable flips [WK] words follow it
+struct ServeBox {
+    uint32_t req;          // host: number of the latest request (its syndrome written first)
+    uint32_t stop;         // host: nonzero ends the loop
+    uint32_t done;         // device: number of the last answered request (outputs written first)
+    uint32_t state;        // device: 1 looping, 2 left after the idle limit, 3 left on stop
+    uint32_t status;       // device: the answer's status, 0 when the beam search must decide
+    uint32_t iters;        // device: the answer's BP iterations
+    uint32_t pad[2];
+};
+int launch_serve(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, ServeBox* box, uint32_t last,
+                 unsigned long long idle_ns, void* stream);
 int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, const uint32_t* synd,
                   long long B, int T, float* llr, float* sum_llr, void* stream);
 // single-precision re-runs of near-tie shots

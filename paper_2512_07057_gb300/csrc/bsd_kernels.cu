@@ -2149,6 +2149,122 @@ static void launch_llr_t(const DevGraph& g, const DecCfg& cfg, const LaunchShape
     k_bp_llr<Eng><<<blocks, 32 * ls.warps_per_block, ls.smem_bp, s>>>(g, cfg, synd, B, T, llr, sum_llr);
 }
 
+// ----------------------------------------------------------------------------
+// request loop for single syndromes (low-latency mode): one candidate group
+// stays resident and answers requests posted in host-mapped memory, so a
+// syndrome whose seed BP ends the search (Alg. 3: the first BP run converges,
+// with one result) costs no launch and no host-side stream wait
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v)
+{
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The loop answers a request (ServeBox::req != the last answered number) by
+// the seed BP of its syndrome -- the same engine, operations and order as
+// k_seed, so the outputs are identical -- and writes e^, A e^, status and
+// iterations, or status 0 when the beam search must decide (the host then
+// takes the regular path).  Every wait is bounded: the loop leaves when the
+// host sets ServeBox::stop or when no request comes for idle_ns.
+template <class Eng>
+__global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_serve(DevGraph g, DecCfg cfg, ServeBox* box,
+                                                                           uint32_t last, unsigned long long idle_ns)
+{
+    extern __shared__ __align__(16) char smem[];
+    Eng eng;
+    eng.grp = Eng::Grp::make(smem + warp_smem_bytes(g));
+    const auto& grp = eng.grp;
+    const WarpState st = carve(smem, g);
+    eng.load_graph(g);
+    volatile uint32_t* const synd = reinterpret_cast<volatile uint32_t*>(box + 1);
+    uint32_t* const obuf = reinterpret_cast<uint32_t*>(box + 1) + g.WM;
+    const Outputs out{obuf, g.K > 0 ? obuf + g.WN : nullptr, &box->status, &box->iters};
+    if (grp.rank() == 0) st_release_sys(&box->state, 1u);
+    for (;;) {
+        int what = 0;                             // 1 request, 2 stop, 3 idle
+        if (grp.rank() == 0) {
+            const unsigned long long t0 = global_ns();
+            for (;;) {
+                if (ld_acquire_sys(&box->stop) != 0u) { what = 2; break; }
+                const uint32_t r = ld_acquire_sys(&box->req);
+                if (r != last) { last = r; what = 1; break; }
+                if (global_ns() - t0 > idle_ns) { what = 3; break; }
+            }
+        }
+        what = grp.bcast(what);
+        if (what != 1) {
+            if (grp.rank() == 0) st_release_sys(&box->state, what == 2 ? 3u : 2u);
+            return;
+        }
+        uint32_t nz = 0;
+        for (int q = grp.rank(); q < g.WM; q += grp.size()) {
+            const uint32_t x = synd[q];
+            st.sp[q] = x;
+            nz |= x;
+        }
+        for (int q = grp.rank(); q < g.WN; q += grp.size()) { st.mask[q] = 0u; st.vals[q] = 0u; st.ehat[q] = 0u; }
+        grp.sync();
+        if (!grp.any(nz != 0u) && cfg.num_results == 1 && g.all_lam_pos) {
+            // s = 0 with every Lambda_j > 0: the seed converges at t = 1 with e^ = 0
+            finalize_shot<typename Eng::Grp, true>(g, out, 0, st.ehat, ST_SEED, 1ull, grp);
+        } else {
+            if (!Eng::kPriorStart) group_copy16(grp, st.E, Eng::prior_E(g), snap_vec16(g));
+            if (!Eng::kPriorSetsSums) eng.clear_sums(g, st);
+            grp.sync();
+            int succ = 0;
+            const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr, true);
+            grp.sync();
+            if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0)
+                finalize_shot<typename Eng::Grp, true>(g, out, 0, st.ehat, succ ? ST_SEED : ST_FAILED,
+                                                       (unsigned long long)it, grp);
+            else if (grp.rank() == 0)
+                box->status = 0u;
+        }
+        __threadfence_system();
+        grp.sync();
+        if (grp.rank() == 0) st_release_sys(&box->done, last);
+    }
+}
+
+template <class Eng>
+static int launch_serve_t(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, ServeBox* box,
+                          uint32_t last, unsigned long long idle_ns, cudaStream_t s)
+{
+    const bool block = ls.group_warps >= 2;
+    const size_t smem = block ? ls.smem_bp : warp_smem_bytes(g);
+    if (CUDA_FAILED(cudaFuncSetAttribute(k_serve<Eng>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return -2;
+    k_serve<Eng><<<1, 32 * (block ? ls.group_warps : 1), smem, s>>>(g, cfg, box, last, idle_ns);
+    return CUDA_FAILED(cudaGetLastError()) ? -2 : 0;
+}
+
+int launch_serve(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, ServeBox* box, uint32_t last,
+                 unsigned long long idle_ns, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (ls.dv) {
+#define X(id, E) \
+    case id: return launch_serve_t<E>(g, cfg, ls, box, last, idle_ns, s);
+        BSD_ENGINES(X)
+#undef X
+        default: return -5;
+    }
+}
+
 int launch_bp_llr(const DevGraph& g, const DecCfg& cfg, const LaunchShape& ls, const uint32_t* synd, long long B,
                   int T, float* llr, float* sum_llr, void* stream)
 {

@@ -171,6 +171,28 @@ class BeamSearchDecoder:
         B.bsd_decode_host(self.h, C.c_void_p(synd_ptr), nb, C.c_void_p(corr_ptr), C.c_void_p(obs_ptr),
                           C.c_void_p(status_ptr), C.c_void_p(iters_ptr) if iters_ptr else None, self._stream(stream))
 
+    # ---- single-syndrome request loop (low latency)
+    def serve_start(self, idle_ms: int = 1000) -> None:
+        """Keep a request loop resident on the device (bsd_serve_start)."""
+        B.bsd_serve_start(self.h, int(idle_ms))
+        W = _words
+        self._sv = dict(synd=np.zeros(W(self.M), np.uint32), corr=np.zeros(W(self.N), np.uint32),
+                        obs=np.zeros(max(W(self.K), 1), np.uint32), status=np.zeros(1, np.uint32),
+                        iters=np.zeros(1, np.uint32))
+        self._svp = {k: v.ctypes.data_as(C.c_void_p) for k, v in self._sv.items()}
+
+    def serve_decode(self, syndrome: np.ndarray) -> dict:
+        """One syndrome (ceil(M/32) words) through the request loop; the same
+        outputs as decode_host for B = 1."""
+        sv, p = self._sv, self._svp
+        sv["synd"][:] = np.asarray(syndrome, np.uint32).reshape(-1)
+        B.bsd_serve_decode(self.h, p["synd"], p["corr"], p["obs"], p["status"], p["iters"])
+        return dict(corrections=sv["corr"].copy(), obs=sv["obs"].copy(), status=int(sv["status"][0]),
+                    iters=int(sv["iters"][0]))
+
+    def serve_stop(self) -> None:
+        B.bsd_serve_stop(self.h)
+
     def bp_llr(self, syndromes, T: int, stream=None):
         """Plain BP for exactly T iterations: (Lambda_j(T), sum_t Lambda_j(t)) as float32 [B, N]."""
         import torch

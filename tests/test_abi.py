@@ -146,3 +146,11 @@ def test_decoder_rejects_mis_sized_tensors_before_any_launch(bad, call, monkeypa
             dec.decode(synd, out)
         else:
             dec.decode_noalloc(synd, out)
+
+
+def test_request_loop_entry_points_reject_null_arguments():
+    """bsd_serve_*: argument checks come before any device work."""
+    lib = B.load()
+    assert lib.bsd_serve_start(None, 100) == B.BSD_ERR_INVALID_ARG
+    assert lib.bsd_serve_decode(None, None, None, None, None, None) == B.BSD_ERR_INVALID_ARG
+    assert lib.bsd_serve_stop(None) == B.BSD_ERR_INVALID_ARG
