@@ -1188,6 +1188,29 @@ def synthetic_widths(prob, sh, dev, steps: int, warmup: int, world: int, rank: i
         rl, _ = alu_roofline(prof_w, prob.n_edges, dev, "small case of the same DEM", shots=sh.B * steps, M=prob.M)
         res["per_width"][preset].update(value=world * sh.B * steps / (ms_w * 1e-3), ms_per_step=ms_w / steps,
                                         roofline=rl)
+    # binary16 message storage at w = 32, timed alone beside the single-
+    # precision decoder of the same width: the batch streams its messages, so
+    # half the bytes per message is where 16-bit storage can pay
+    from paper_2512_07057_gb300 import binding as BB
+    d16 = D.BeamSearchDecoder(prob, D.make_params("beam32_340iters", ms_scale=ALPHA, msg_precision=BB.BSD_FP16,
+                                                  workspace_bytes=int(workspace_gb * (1 << 30))), device=dev)
+    o16 = d16.alloc_outputs(sh.B)
+    res["launch_shapes"]["beam32_340iters_fp16"] = autotune(d16, synd, 16384)
+    ms16, _, _, prof16 = run_region([d16], [o16])
+    rl16, _ = alu_roofline(prof16, prob.n_edges, dev, "small case of the same DEM", shots=sh.B * steps,
+                           msg_bytes=2, M=prob.M)
+    st16 = D.from_torch_words(o16.status)
+    ref32 = outs[SYN_PRESETS.index("beam32_340iters")]
+    same = (D.from_torch_words(o16.corrections) == D.from_torch_words(ref32.corrections)).all(axis=1)
+    fp32_ms = res["per_width"]["beam32_340iters"]["ms_per_step"]
+    res["fp16_beam32"] = {
+        "value": world * sh.B * steps / (ms16 * 1e-3), "ms_per_step": ms16 / steps, "msg_bytes": 2,
+        "speedup_vs_fp32_same_width": fp32_ms / (ms16 / steps),
+        "ler": ler_of(prob, sh, D.from_torch_words(o16.obs_flips), st16 & 7),
+        "near_tie_rerun_fraction": float(((st16 & BB.BSD_STATUS_FP32_RERUN) != 0).mean()),
+        "corrections_equal_to_fp32_fraction": float(same.mean()),
+        "kernel_ms_per_step": kernel_ms(prof16[0], steps), "roofline": rl16}
+    d16.close()
     if e2e_args is not None:
         res["e2e"] = e2e_host(decs, [(w, prob, sh) for w in SYN_PRESETS], e2e_args, dev)
     for d in decs:
@@ -1237,7 +1260,7 @@ def run_synthetic(args, rank: int, world: int, local_rank: int):
                    "launch_shapes": res["launch_shapes"]},
         "exec_bp_iters_per_step": res["exec_bp_iters_per_step"],
         "roofline": res["roofline"], "gpu_launches": res["gpu_launches"],
-        "per_width": res["per_width"], "clocks": res["clocks"],
+        "per_width": res["per_width"], "clocks": res["clocks"], "fp16_beam32": res["fp16_beam32"],
     }
     if "e2e" in res:
         line["e2e"] = res["e2e"]
