@@ -2203,6 +2203,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_serve(Dev
                 const uint32_t r = ld_acquire_sys(&box->req);
                 if (r != last) { last = r; what = 1; break; }
                 if (global_ns() - t0 > idle_ns) { what = 3; break; }
+                __nanosleep(32);                  // each poll crosses to host memory
             }
         }
         what = grp.bcast(what);
