@@ -406,6 +406,28 @@ def random_ldpc(M: int, N: int, col_weight: int, p: float, seed: int, K: int = 2
                    priors=np.full(N, float(p)), meta={"kind": "random_ldpc"})
 
 
+def random_regular_36(M: int, p: float, seed: int, K: int = 2) -> Problem:
+    """Random code with every row of degree 6 and every column of degree 3
+    (N = 2 M): a random pairing of the rows' six edge slots with the columns'
+    three, drawn again until no column meets a row twice."""
+    N = 2 * M
+    rng = np.random.default_rng(np.random.SeedSequence([ROOT_SEED, 11, M, seed]))
+    while True:
+        slots = np.repeat(np.arange(M), 6)
+        rng.shuffle(slots)
+        cols = slots.reshape(N, 3)
+        if all(len(set(c.tolist())) == 3 for c in cols):
+            break
+    H = np.zeros((M, N), dtype=np.uint8)
+    for j in range(N):
+        H[cols[j], j] = 1
+    A = (rng.random((K, N)) < 0.2).astype(np.uint8)
+    hr, hc = dense_to_csr(H)
+    ar, ac = dense_to_csr(A)
+    return Problem(name=f"regular36_{M}x{N}_s{seed}", M=M, N=N, K=K, H_row_ptr=hr, H_col_idx=hc,
+                   A_row_ptr=ar, A_col_idx=ac, priors=np.full(N, float(p)), meta={"kind": "random_regular_36"})
+
+
 def problem_from_dense(H: np.ndarray, A: np.ndarray, priors, name: str = "dense") -> Problem:
     H = np.asarray(H, np.uint8)
     A = np.asarray(A, np.uint8).reshape(-1, H.shape[1])

@@ -15,6 +15,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
+from paper_2512_07057_gb300 import binding as B  # noqa: E402
 from paper_2512_07057_gb300 import decoder as D  # noqa: E402
 from paper_2512_07057_gb300 import workloads as W  # noqa: E402
 from parity_f64 import check_against_f64  # noqa: E402
@@ -173,6 +174,19 @@ def test_irregular_random_codes(seed):
     shots = W.sample_shots(prob, 3_000, f"rand_{seed}")
     params = D.make_params(max_rounds=6, beam_width=4, initial_iters=12, iters_per_round=7,
                            num_results=1 + 2 * (seed % 2), ms_scale=0.75)
+    _check_workload(prob, params, shots, check_f64=False)
+
+
+@pytest.mark.parametrize("M,seed", [(48, 2), (80, 5)])
+def test_random_regular_codes_on_the_single_warp_engine(M, seed):
+    """Random codes of row degree 6 and column degree 3 run on the single-warp
+    engine; unlike the BB codes, their message placement keeps some bank
+    conflicts (the search does not reach zero), so the column orders come
+    partly from the fallback order.  Bit-exact against the oracle."""
+    prob = W.random_regular_36(M, 0.05, seed)
+    assert B.bsd_small_layout(prob.M, prob.N, prob.H_row_ptr, prob.H_col_idx)["excess"] > 0
+    shots = W.sample_shots(prob, 3_000, f"reg36_{M}")
+    params = D.make_params(max_rounds=6, beam_width=8, initial_iters=20, iters_per_round=10, ms_scale=0.625)
     _check_workload(prob, params, shots, check_f64=False)
 
 

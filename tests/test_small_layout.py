@@ -78,3 +78,30 @@ def test_bad_csr_is_rejected():
     with pytest.raises(B.BsdError) as ei:
         B.bsd_small_layout(p.M, p.N, p.H_row_ptr, ci)
     assert ei.value.code == B.BSD_ERR_INVALID_ARG
+
+
+
+@pytest.mark.parametrize("M,seed", [(36, 1), (48, 2), (64, 3), (72, 4), (80, 5)])
+def test_placement_of_random_regular_codes_is_valid(M, seed):
+    """Whatever bank loads the search leaves, the placement is a bijection
+    onto the rows' pairs and every column takes k = 0, 1, 2 once; where no
+    bank of a column group holds more than three edges, the error pass is
+    conflict-free."""
+    prob = W.random_regular_36(M, 0.05, seed)
+    rp, ci = prob.H_row_ptr, prob.H_col_idx
+    lay = B.bsd_small_layout(prob.M, prob.N, rp, ci)
+    plane, ew, cw = lay["plane"], lay["edge_word"], lay["col_word"]
+    assert len(set(ew.tolist())) == int(rp[-1])
+    for i in range(prob.M):
+        assert set(ew[rp[i]:rp[i + 1]].tolist()) == {int(plane[h]) + 2 * i + u for h in range(3) for u in range(2)}
+    cols = [[] for _ in range(prob.N)]
+    for i in range(prob.M):
+        for e in range(rp[i], rp[i + 1]):
+            cols[ci[e]].append(int(ew[e]))
+    for j in range(prob.N):
+        assert sorted(cw[j].tolist()) == sorted(cols[j])
+    if lay["excess"] == 0:
+        for c in range((prob.N + 31) // 32):
+            for k in range(3):
+                words = cw[32 * c:32 * c + 32, k]
+                assert len(set((words % 32).tolist())) == len(words)
