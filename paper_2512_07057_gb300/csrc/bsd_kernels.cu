@@ -2,9 +2,10 @@
 //
 // One warp owns one BP candidate (the seed path of a shot, or one child of a
 // beam round) and keeps its whole state in shared memory: the edge messages
-// E_{j->i}, a compact per-detector record (min1, min2, argmin edge, sign
-// parity) standing in for the detector-to-error messages D_{i->j}, sum_LLR,
-// and the bit vectors s', mask, vals, e^ and the running syndrome parity.
+// E_{j->i}, a compact 8-byte per-detector record (min1, min2 with the sign
+// parity in both sign bits) standing in for the detector-to-error messages
+// D_{i->j} (the single-warp engine keeps D per edge instead), sum_LLR, and
+// the bit vectors s', mask, vals, e^ and the running syndrome parity.
 //
 // Kernels (all persistent: warps claim work with one atomic per item and
 // exit when the item counter runs out, so uneven iteration counts balance):
@@ -156,7 +157,7 @@ __host__ __device__ inline size_t warp_smem_bytes(const DevGraph& g)
 
 struct WarpState {
     void* E;           // [Epad] E_{j->i} in the storage format, CSR edge order
-    float4* rs;        // [M]    (min1, min2, argmin edge id, s'_i xor parity of negatives)
+    float2* rs;        // [M]    (min1, min2), s'_i xor the parity of the negative messages in both sign bits
     float* D;          // [Epad] D_{i->j} per CSR edge (same storage as rs)
     float* sumllr;     // [Npad]
     uint32_t* sp;      // [WM] s' = s with the columns of nodes fixed to 1 folded in
@@ -171,7 +172,7 @@ __device__ inline WarpState carve(char* base, const DevGraph& g)
     WarpState s;
     char* p = base;
     s.E = p;                                 p += align16((size_t)g.msg_bytes * (size_t)g.Epad);
-    s.rs = reinterpret_cast<float4*>(p);
+    s.rs = reinterpret_cast<float2*>(p);
     s.D = reinterpret_cast<float*>(p);       p += det_region_bytes(g);
     s.sumllr = reinterpret_cast<float*>(p);  p += align16(sizeof(float) * (size_t)g.Npad);
     uint32_t* b = reinterpret_cast<uint32_t*>(p);
@@ -226,27 +227,31 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
         if (prior) {
             for (int i = grp.rank(); i < g.M; i += grp.size()) {
                 const float4 r = __ldg(g.rs0 + i);
-                const uint32_t si = (st.sp[i >> 5] >> (i & 31)) & 1u;
-                st.rs[i] = make_float4(r.x, r.y, r.z, __uint_as_float(__float_as_uint(r.w) ^ si));
+                const uint32_t sb = (((st.sp[i >> 5] >> (i & 31)) ^ __float_as_uint(r.w)) & 1u) << 31;
+                st.rs[i] = make_float2(__uint_as_float(__float_as_uint(r.x) | sb),
+                                       __uint_as_float(__float_as_uint(r.y) | sb));
             }
         }
-        // ---- detector pass (Eq. 1): min1, min2, argmin and sign parity per row
+        // ---- detector pass (Eq. 1): min1, min2 and the sign parity per row
+        // (8-byte records: the error pass tells the edge holding the minimum
+        // by its magnitude -- where the minimum is attained twice, min2 =
+        // min1, so this equals the lowest-index argmin rule)
         for (int i = prior ? g.M : grp.rank(); i < g.M; i += grp.size()) {
             const int rb = __ldg(g.row_ptr + i), re = __ldg(g.row_ptr + i + 1);
             float m1 = L, m2 = L;
-            int id = -1;
-            uint32_t neg = (st.sp[i >> 5] >> (i & 31)) & 1u;
-            // branch-free: the runner-up is min(m2, max(m1, a)); the argmin
-            // moves only on a strictly smaller value (first index on ties)
+            uint32_t sg = ((st.sp[i >> 5] >> (i & 31)) & 1u) << 31;
+            // branch-free: the runner-up is min(m2, max(m1, a)); a stored
+            // message is never -0 (a clamped sum that starts at Lambda_j), so
+            // its sign bit is exactly x < 0
             for (int e = rb; e < re; ++e) {
                 const float x = S::ld(E, e);
                 const float a = fabsf(x);
                 m2 = fminf(m2, fmaxf(m1, a));
-                id = (a < m1) ? e : id;
                 m1 = fminf(m1, a);
-                neg ^= (x < 0.f) ? 1u : 0u;
+                sg ^= __float_as_uint(x);
             }
-            st.rs[i] = make_float4(m1, m2, __int_as_float(id), __uint_as_float(neg));
+            sg &= 0x80000000u;
+            st.rs[i] = make_float2(__uint_as_float(__float_as_uint(m1) | sg), __uint_as_float(__float_as_uint(m2) | sg));
         }
         grp.sync();
 
@@ -261,8 +266,8 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
                 kb = __ldg(g.col_ptr + j);
                 deg = __ldg(g.col_ptr + j + 1) - kb;
             }
-            // E(0) is the same on every edge of a column: one load for its sign
-            const bool x0neg = prior && S::ld(reinterpret_cast<const T*>(g.lamEc), j) < 0.f;
+            // E(0) is the same on every edge of a column: one load
+            const float x0 = prior ? S::ld(reinterpret_cast<const T*>(g.lamEc), j) : 0.f;
 #pragma unroll
             for (int k = 0; k < DV; ++k) {
                 int e = -1, r = 0;
@@ -276,12 +281,15 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
                     r = __ldg(g.col_row + kb + k);
                 }
                 if (e >= 0) {
-                    const float4 s4 = st.rs[r];
-                    const bool xneg = prior ? x0neg : (S::ld(E, e) < 0.f);
-                    const float m = (e == __float_as_int(s4.z)) ? s4.y : s4.x;
-                    const uint32_t sg = __float_as_uint(s4.w) ^ (xneg ? 1u : 0u);
+                    const float2 r2 = st.rs[r];
+                    const float x = prior ? x0 : S::ld(E, e);
+                    // the minimum over the row's other edges: min2 on an edge
+                    // holding the minimum, min1 elsewhere; sign: the row's
+                    // parity without the edge's own sign
+                    const float m = (fabsf(x) == fabsf(r2.x)) ? fabsf(r2.y) : fabsf(r2.x);
+                    const uint32_t sg = (__float_as_uint(r2.x) ^ __float_as_uint(x)) & 0x80000000u;
                     const float d = __fmul_rn(W ? __ldg(wt + e) : alpha, m);
-                    v[k] = sg ? -d : d;
+                    v[k] = __uint_as_float(__float_as_uint(d) ^ sg);
                     ed[k] = e;
                 } else {
                     v[k] = INFINITY;
@@ -1728,7 +1736,7 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, int group_warp
         CUDA_FAILED(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)))
         return -2;
     // per-candidate state with the generic engine's detector records
-    g.det_bytes = (int)align16(sizeof(float4) * (size_t)g.M);
+    g.det_bytes = (int)align16(sizeof(float2) * (size_t)g.M);
     const size_t generic_bytes = warp_smem_bytes(g);
     // automatic choice: the small engine where it fits; otherwise a warp per
     // candidate while eight or more candidates fit on an SM, a block of 8
@@ -1744,7 +1752,7 @@ int configure_kernels(DevGraph& g, const DecCfg& cfg, int device, int group_warp
         const int kind = skind >= 0 ? skind : gkind;
         eng = weighted ? kWeightedEngine + kind : 3 * kind + g.prec;
         // the small engine keeps D per edge in float; the generic one a record per detector
-        const size_t recs = sizeof(float4) * (size_t)g.M, msgs = sizeof(float) * (size_t)g.Epad;
+        const size_t recs = sizeof(float2) * (size_t)g.M, msgs = sizeof(float) * (size_t)g.Epad;
         g.det_bytes = (int)align16(kind >= 3 && msgs > recs ? msgs : recs);
         const size_t per_warp = warp_smem_bytes(g);
         if (per_warp > (size_t)max_optin) return -5;
