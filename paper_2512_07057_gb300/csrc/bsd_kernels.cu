@@ -243,12 +243,19 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
             // branch-free: the runner-up is min(m2, max(m1, a)); a stored
             // message is never -0 (a clamped sum that starts at Lambda_j), so
             // its sign bit is exactly x < 0
-            for (int e = rb; e < re; ++e) {
-                const float x = S::ld(E, e);
-                const float a = fabsf(x);
-                m2 = fminf(m2, fmaxf(m1, a));
-                m1 = fminf(m1, a);
-                sg ^= __float_as_uint(x);
+            // (four messages per step; past the row's end a lane takes
+            // +L_MAX, which changes neither minimum nor the parity)
+            for (int e = rb; e < re; e += 4) {
+                float x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = (e + u < re) ? S::ld(E, e + u) : L;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float a = fabsf(x[u]);
+                    m2 = fminf(m2, fmaxf(m1, a));
+                    m1 = fminf(m1, a);
+                    sg ^= __float_as_uint(x[u]);
+                }
             }
             sg &= 0x80000000u;
             st.rs[i] = make_float2(__uint_as_float(__float_as_uint(m1) | sg), __uint_as_float(__float_as_uint(m2) | sg));
@@ -996,7 +1003,6 @@ __global__ void k_screen(DevGraph g, DecCfg cfg, Work w)
     const RunDesc* dp = w.desc;
     const long long n = dp->chunk_n;
     const long long nw = (long long)gridDim.x * kScreenWarps;
-    const float alpha = cfg.alpha;
     unsigned long long upd = 0;                  // message updates formed (lane)
     for (long long b = (long long)blockIdx.x * kScreenWarps + (threadIdx.x >> 5); b < n; b += nw) {
         const long long gb = dp->chunk_base + b;
