@@ -653,7 +653,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     value = world * shots_per_step * args.steps / steps_total_s
     msg_alg = alg_iters_step * E * world / (steps_total_s / args.steps)
     msg_exec = float(exec_iters.sum()) * E * world / steps_total_s
-    # the survey's streaming model: 14.7 B per update if every iteration moved its state through HBM
+    # a streaming model for context: 14.7 B per update if every iteration moved its state through HBM
     # (context only: the state of this code stays on chip; the measured figure is the roofline's dram_gbs)
     stream_bytes = 2 * 4 * E + 2 * (2 * 4 + 4) * 72 + 8 * 144
     line = {
