@@ -59,6 +59,7 @@ struct bsd_decoder {
     int small_excess = -1;                   // single-warp placement: bank loads above three left (-1: none)
     int small_extent = 0;                    // words it spans
     std::vector<int> small_addr;             // its word of every CSR edge
+    std::vector<int> generic_pos;            // the generic engines' word of every CSR edge (empty: CSR order)
     // the single-syndrome request loop (bsd_serve_*)
     ServeBox* serve_h = nullptr;             // mailbox, host-mapped (null when not serving)
     ServeBox* serve_d = nullptr;             // its device address
@@ -409,9 +410,26 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     // j at [k][j], (-1, -1) past the column's degree, for degree bounds 3 and 6
     const int colK = max_col <= 3 ? 3 : max_col <= 6 ? 6 : 0;
     std::vector<int2> colER((size_t)colK * Npad, make_int2(-1, -1));
-    for (int j = 0; j < N && colK > 0; ++j)
-        for (int k = 0; k < col_ptr[j + 1] - col_ptr[j]; ++k)
-            colER[(size_t)k * Npad + j] = make_int2(col_edge[col_ptr[j] + k], col_row[col_ptr[j] + k]);
+    // the generic engines keep a candidate's messages at the words of their
+    // own placement (bsd_layout.cu: each row's edges permuted inside the row's
+    // window, each column's edges in the k slots of a colouring), so that the
+    // 32 lanes of an error-pass access meet distinct banks where possible
+    GenericLayout gl;
+    const bool has_gl = colK > 0 && generic_layout(M, N, H_row_ptr, H_col_idx, colK, &gl);
+    if (has_gl) {
+        std::vector<int> erow(E);
+        for (int i = 0; i < M; ++i)
+            for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e) erow[e] = i;
+        for (int k = 0; k < colK; ++k)
+            for (int j = 0; j < N; ++j) {
+                const int e = gl.kedge[(size_t)k * N + j];
+                if (e >= 0) colER[(size_t)k * Npad + j] = make_int2(gl.pos[e], erow[e]);
+            }
+    } else {
+        for (int j = 0; j < N && colK > 0; ++j)
+            for (int k = 0; k < col_ptr[j + 1] - col_ptr[j]; ++k)
+                colER[(size_t)k * Npad + j] = make_int2(col_edge[col_ptr[j] + k], col_row[col_ptr[j] + k]);
+    }
     // E(0) of column j in the storage format (every edge of the column holds it)
     std::vector<unsigned char> lamEc_st((size_t)Npad * msg_bytes, 0);
     for (int j = 0; j < N; ++j) {
@@ -556,6 +574,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.colRD = reinterpret_cast<const float4*>(d_colRD); g.colRDk = rdk;
     for (int d = 0; d < kMaxColDeg + 2; ++d) { g.dstart[d] = dstart[d]; g.dbase[d] = dbase[d]; }
     g.scol = d_scol; g.sD0 = d_sD0; g.slamE = d_slamE;
+    if (has_gl) dec->generic_pos = gl.pos;
     if (has_sl) {
         dec->small_excess = sl.excess;
         dec->small_extent = sl.extent;
@@ -973,13 +992,18 @@ int bsd_set_weights(bsd_decoder* dec, const float* h_weights, int32_t T)
     // work already queued on the decoder's stream uses the current kernels and weights
     if (CUDA_FAILED(cudaStreamSynchronize(dec->last_stream))) return BSD_ERR_CUDA;
     float* d_w = nullptr;
-    // [T][Epad] in the CSR edge order, then (for codes the single-warp engine
-    // can run) [T][Epad] at that engine's words
+    // [T][Epad] at the generic engines' words, then (for codes the
+    // single-warp engine can run) [T][Epad] at that engine's words
     const bool two = dec->g.scol != nullptr;
+    const bool gperm = !dec->generic_pos.empty();
     if (T > 0) {
         std::vector<float> hw((size_t)T * Epad * (two ? 2 : 1), 0.f);
         for (size_t t = 0; t < (size_t)T; ++t) {
-            std::memcpy(hw.data() + t * Epad, h_weights + t * E, sizeof(float) * E);
+            if (gperm) {
+                for (size_t e = 0; e < E; ++e) hw[t * Epad + (size_t)dec->generic_pos[e]] = h_weights[t * E + e];
+            } else {
+                std::memcpy(hw.data() + t * Epad, h_weights + t * E, sizeof(float) * E);
+            }
             if (two)
                 for (size_t e = 0; e < E; ++e)
                     hw[((size_t)T + t) * Epad + (size_t)dec->small_addr[e]] = h_weights[t * E + e];

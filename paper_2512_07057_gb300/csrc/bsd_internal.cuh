@@ -13,7 +13,8 @@
 //   lamq[N]               Lambda_j on the 2^-16 fixed-point grid (weights)
 //   rs0[M]                the detector records of E(0) (a seed run's first check pass, up to the syndrome)
 //   D0[Epad]              the check messages of E(0) with the scale alpha, before the syndrome sign
-//   colER[colK][Npad]     (edge, row) of the k-th edge of column j, (-1, -1) past its degree
+//   colER[colK][Npad]     (word, row) of the edge in slot k of column j at the
+//                         generic engines' placement, (-1, -1) for an empty slot
 //   lamEc[Npad]           clamp(Lambda_j) in the storage format (E(0) of every edge of column j)
 //
 // Workspace (one decoder):
@@ -62,7 +63,7 @@ struct DevGraph {
     const long long* lamq;
     const float4* rs0;     // [M] detector records of E(0): (min1, min2, argmin edge, parity of negatives)
     const float* D0;       // [Epad] check messages of E(0) with scale alpha, before the syndrome sign
-    const int2* colER;     // [colK][Npad] (edge, row) of edge k of column j, (-1, -1) past its degree
+    const int2* colER;     // [colK][Npad] (word, row) of the edge in slot k of column j, (-1, -1): empty
     int colK;              // 3 or 6 (the generic engines' degree bound), 0 when colER is absent
     const void* lamEc;     // [Npad] E(0) of column j (clamp(Lambda_j)) in the storage format
     // the columns ordered by degree (batched seed BP): colperm[q] is the
@@ -111,6 +112,19 @@ struct SmallLayout {
     int excess;
 };
 bool small_layout(int M, int N, const int* row_ptr, const int* col_idx, SmallLayout* out);
+// the generic engines' placement of a candidate's messages for column degree
+// bounds up to 6 (bsd_layout.cu): pos[e] = the word of CSR edge e inside its
+// row's storage window [row_ptr[i], row_ptr[i + 1]); kedge[k * N + j] = the
+// CSR edge in slot k of column j (-1: a hole); excess = bank loads above each
+// column group's largest degree left by the search; false for codes beyond
+// kGenericLayoutMaxEdges edges or with a column above colK
+struct GenericLayout {
+    std::vector<int> pos;
+    std::vector<int> kedge;
+    int excess;
+};
+constexpr int kGenericLayoutMaxEdges = 1 << 20;
+bool generic_layout(int M, int N, const int* row_ptr, const int* col_idx, int colK, GenericLayout* out);
 // the placement's plane stride for codes of M rows (the engine holds
 // ceil(M / 32) rows per lane); every plane spans 2 M <= 64 ceil(M / 32) words
 __host__ __device__ constexpr int small_plane_stride_rpl(int rpl) { return 64 * rpl + 12; }

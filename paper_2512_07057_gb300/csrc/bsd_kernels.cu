@@ -317,10 +317,18 @@ __device__ int bp_iterate(const G& grp, const DevGraph& g, const DecCfg& cfg, co
             return deg;
         };
         auto flip_rows = [&](int j, int deg) {                 // s' xor H e^: the rows of column j
-            for (int k = 0; k < deg; ++k) {
-                const int r = DV <= 6 ? __ldg(g.colER + (size_t)k * g.Npad + j).y
-                                      : __ldg(g.col_row + __ldg(g.col_ptr + j) + k);
-                atomicXor(&st.par[r >> 5], 1u << (r & 31));
+            if constexpr (DV <= 6) {
+                // the column's slots of the padded table (a slot may be a hole)
+#pragma unroll
+                for (int k = 0; k < DV; ++k) {
+                    const int r = __ldg(g.colER + (size_t)k * g.Npad + j).y;
+                    if (r >= 0) atomicXor(&st.par[r >> 5], 1u << (r & 31));
+                }
+            } else {
+                for (int k = 0; k < deg; ++k) {
+                    const int r = __ldg(g.col_row + __ldg(g.col_ptr + j) + k);
+                    atomicXor(&st.par[r >> 5], 1u << (r & 31));
+                }
             }
         };
 
@@ -472,11 +480,21 @@ struct GenericEngine {
     __device__ void load_graph(const DevGraph&) {}
     // E(0) in this engine's message layout (the CSR edge order)
     static __device__ const void* prior_E(const DevGraph& g) { return g.lamE; }
-    // the sentinel +L_MAX on every message of the newly fixed node j
+    // the sentinel +L_MAX on every message of the newly fixed node j (at the
+    // words of the padded column table for degree bounds up to 6, which may
+    // have holes; at the CSR edges for the column lists)
     __device__ void fix_node(const DevGraph& g, const WarpState& st, int j, float L) const
     {
-        for (int q = __ldg(g.col_ptr + j) + grp.rank(); q < __ldg(g.col_ptr + j + 1); q += grp.size())
-            Store<P>::st(reinterpret_cast<typename Store<P>::T*>(st.E), __ldg(g.col_edge + q), L);
+        typename Store<P>::T* const E = reinterpret_cast<typename Store<P>::T*>(st.E);
+        if constexpr (DV <= 6) {
+            for (int k = grp.rank(); k < DV; k += grp.size()) {
+                const int e = __ldg(g.colER + (size_t)k * g.Npad + j).x;
+                if (e >= 0) Store<P>::st(E, e, L);
+            }
+        } else {
+            for (int q = __ldg(g.col_ptr + j) + grp.rank(); q < __ldg(g.col_ptr + j + 1); q += grp.size())
+                Store<P>::st(E, __ldg(g.col_edge + q), L);
+        }
     }
     __device__ void clear_sums(const DevGraph& g, const WarpState& st)
     {

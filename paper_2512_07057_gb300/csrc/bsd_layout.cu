@@ -1,5 +1,18 @@
-// bsd_layout.cu -- where the single-warp engine keeps each edge's messages in
-// shared memory (host code, run once when a decoder is created).
+// bsd_layout.cu -- where the BP engines keep each edge's messages in shared
+// memory (host code, run once when a decoder is created).
+//
+// Generic engines (column degree bound 3 or 6; generic_layout): a row's
+// edges occupy the row's window [row_ptr[i], row_ptr[i + 1]) in any order
+// (the detector pass reduces the window with order-independent operations),
+// and a column's edges may take any k slots of the padded column table (the
+// error pass sorts its inputs).  A local search over swaps within rows
+// spreads each group of 32 columns over the banks (at most the group's
+// largest column degree per bank), and a colouring of the group's
+// (column, bank) multigraph then gives each k slot distinct banks; where the
+// search leaves a bank above that, each edge takes the free slot whose bank
+// is least loaded.  Columns may keep holes in their slots.
+//
+// Single-warp engine (small_layout):
 //
 // The single-warp engine (codes with every row of degree 6 and every column of
 // degree 3) runs two passes per BP iteration over a candidate's messages in
@@ -223,6 +236,176 @@ bool small_layout(int M, int N, const int* row_ptr, const int* col_idx, SmallLay
             const int e = ids[x], j = col_idx[e];
             out->col[(size_t)j * kColDeg + colour[x]] = ((uint32_t)out->addr[e] << 16) | (uint32_t)erow[e];
         }
+    }
+    return true;
+}
+
+}  // namespace bsd
+
+namespace bsd {
+
+namespace {
+
+constexpr int kMaxColour = 16;
+constexpr int kPatience = 4;
+
+// proper colouring with `ncol` colours of the edges of one column group whose
+// banks each hold at most ncol of its edges and whose columns have at most
+// ncol edges (Koenig's theorem; alternating paths, as colour_group)
+void colour_group_n(const std::vector<int>& eu, const std::vector<int>& ev, int ncol, std::vector<int>* colour)
+{
+    const int n = (int)eu.size();
+    colour->assign(n, -1);
+    int atU[32][kMaxColour], atV[32][kMaxColour];
+    for (int a = 0; a < 32; ++a)
+        for (int c = 0; c < kMaxColour; ++c) atU[a][c] = atV[a][c] = -1;
+    for (int i = 0; i < n; ++i) {
+        const int u = eu[i], v = ev[i];
+        int a = -1, b = -1;
+        for (int c = 0; c < ncol && a < 0; ++c)
+            if (atU[u][c] < 0) a = c;
+        for (int c = 0; c < ncol && b < 0; ++c)
+            if (atV[v][c] < 0) b = c;
+        if (atV[v][a] >= 0) {
+            std::vector<int> path;
+            int x = v, side = 1, c = a;
+            while ((int)path.size() <= n) {
+                const int e = side ? atV[x][c] : atU[x][c];
+                if (e < 0) break;
+                path.push_back(e);
+                x = side ? eu[e] : ev[e];
+                side ^= 1;
+                c = (c == a) ? b : a;
+            }
+            for (int e : path) {
+                atU[eu[e]][(*colour)[e]] = -1;
+                atV[ev[e]][(*colour)[e]] = -1;
+            }
+            for (int e : path) {
+                const int ce = (*colour)[e] == a ? b : a;
+                (*colour)[e] = ce;
+                atU[eu[e]][ce] = e;
+                atV[ev[e]][ce] = e;
+            }
+        }
+        (*colour)[i] = a;
+        atU[u][a] = i;
+        atV[v][a] = i;
+    }
+}
+
+}  // namespace
+
+bool generic_layout(int M, int N, const int* row_ptr, const int* col_idx, int colK, GenericLayout* out)
+{
+    if (M < 1 || N < 1 || colK < 1 || colK > kMaxColour) return false;
+    const int E = row_ptr[M];
+    if (E > kGenericLayoutMaxEdges) return false;
+    std::vector<int> cdeg(N, 0);
+    for (int e = 0; e < E; ++e) cdeg[col_idx[e]]++;
+    for (int j = 0; j < N; ++j)
+        if (cdeg[j] > colK) return false;
+    const int NG = (N + 31) / 32;
+    std::vector<int> cap(NG, 0);                  // the largest column degree of each group
+    for (int j = 0; j < N; ++j) cap[j >> 5] = std::max(cap[j >> 5], cdeg[j]);
+    // position of every CSR edge inside its row's storage window: start from
+    // the CSR order and swap within rows while the bank loads above each
+    // group's cap fall
+    std::vector<int> pos(E);
+    for (int e = 0; e < E; ++e) pos[e] = e;
+    std::vector<int> cnt((size_t)NG * 32, 0);
+    for (int e = 0; e < E; ++e) cnt[(size_t)(col_idx[e] >> 5) * 32 + (pos[e] & 31)]++;
+    auto over = [&](int g, int b) { return std::max(0, cnt[(size_t)g * 32 + b] - cap[g]); };
+    int ex = 0;
+    for (int g = 0; g < NG; ++g)
+        for (int b = 0; b < 32; ++b) ex += over(g, b);
+    Rng rng{0x243f6a8885a308d3ull};
+    std::vector<int> order(M);
+    for (int i = 0; i < M; ++i) order[i] = i;
+    // a bounded effort: at most ~5e7 swap trials, and kPatience sweeps
+    // without a lower load end the search
+    double per_sweep = 1.0;
+    for (int i = 0; i < M; ++i) {
+        const double d = row_ptr[i + 1] - row_ptr[i];
+        per_sweep += d * (d - 1) / 2;
+    }
+    const int max_sweeps = (int)std::min<double>(kSweeps, 5e7 / per_sweep);
+    int best = ex, stale = 0;
+    for (int sw = 0; sw < max_sweeps && ex > 0 && stale < kPatience; ++sw) {
+        if (ex < best) { best = ex; stale = 0; } else if (sw > 0) { ++stale; }
+        for (int i = M - 1; i > 0; --i) std::swap(order[i], order[rng.below((uint32_t)i + 1)]);
+        for (int i : order) {
+            for (int a = row_ptr[i]; a < row_ptr[i + 1]; ++a) {
+                for (int b = a + 1; b < row_ptr[i + 1]; ++b) {
+                    const int ga = col_idx[a] >> 5, gb = col_idx[b] >> 5;
+                    if (ga == gb) continue;
+                    const int ba = pos[a] & 31, bb = pos[b] & 31;
+                    const int before = over(ga, ba) + over(gb, bb) + over(ga, bb) + over(gb, ba);
+                    cnt[(size_t)ga * 32 + ba]--; cnt[(size_t)gb * 32 + bb]--;
+                    cnt[(size_t)ga * 32 + bb]++; cnt[(size_t)gb * 32 + ba]++;
+                    const int after = over(ga, ba) + over(gb, bb) + over(ga, bb) + over(gb, ba);
+                    if (after < before || (after == before && rng.below(4) == 0)) {
+                        std::swap(pos[a], pos[b]);
+                        ex += after - before;
+                    } else {
+                        cnt[(size_t)ga * 32 + ba]++; cnt[(size_t)gb * 32 + bb]++;
+                        cnt[(size_t)ga * 32 + bb]--; cnt[(size_t)gb * 32 + ba]--;
+                    }
+                }
+            }
+        }
+    }
+    out->pos = pos;
+    out->excess = ex;
+    // the k slot of every column's edges: a proper colouring per group where
+    // the loads allow one (holes where a column has fewer edges than colours),
+    // else the column lists' order
+    std::vector<std::vector<int>> cedges(N);
+    for (int e = 0; e < E; ++e) cedges[col_idx[e]].push_back(e);
+    out->kedge.assign((size_t)colK * N, -1);
+    for (int g = 0; g < NG; ++g) {
+        std::vector<int> ids, eu, ev, colour;
+        for (int j = 32 * g; j < std::min(N, 32 * g + 32); ++j)
+            for (int e : cedges[j]) {
+                ids.push_back(e);
+                eu.push_back(j - 32 * g);
+                ev.push_back(pos[e] & 31);
+            }
+        int vdeg[32] = {0};
+        for (int v : ev) vdeg[v]++;
+        bool proper = cap[g] > 0 && *std::max_element(vdeg, vdeg + 32) <= cap[g];
+        if (proper) colour_group_n(eu, ev, cap[g], &colour);
+        // every column's edges take distinct slots below colK
+        if (proper) {
+            std::vector<int> seen((size_t)32 * kMaxColour, 0);
+            for (size_t x = 0; x < ids.size() && proper; ++x) {
+                const int c = colour[x];
+                if (c < 0 || c >= colK || seen[(size_t)eu[x] * kMaxColour + c]++) proper = false;
+            }
+        }
+        if (!proper) {
+            // greedy: each edge takes the free slot of its column whose bank
+            // is least loaded so far
+            colour.assign(ids.size(), 0);
+            std::vector<int> load((size_t)colK * 32, 0);
+            for (size_t x = 0; x < ids.size();) {
+                size_t y = x;
+                while (y < ids.size() && eu[y] == eu[x]) ++y;
+                uint32_t used = 0;
+                for (size_t z = x; z < y; ++z) {
+                    int bestk = -1;
+                    for (int k = 0; k < colK; ++k) {
+                        if ((used >> k) & 1u) continue;
+                        if (bestk < 0 || load[(size_t)k * 32 + ev[z]] < load[(size_t)bestk * 32 + ev[z]]) bestk = k;
+                    }
+                    colour[z] = bestk;
+                    used |= 1u << bestk;
+                    load[(size_t)bestk * 32 + ev[z]]++;
+                }
+                x = y;
+            }
+        }
+        for (size_t x = 0; x < ids.size(); ++x) out->kedge[(size_t)colour[x] * N + col_idx[ids[x]]] = ids[x];
     }
     return true;
 }
