@@ -279,6 +279,25 @@ int bsd_get_batch(const bsd_decoder *dec, int32_t *slots, int32_t *active);
 int bsd_small_layout(int32_t M, int32_t N, const int32_t *H_row_ptr, const int32_t *H_col_idx, int32_t *plane,
                      int32_t *edge_word, int32_t *col_word, int32_t *extent, int32_t *excess);
 
+/* Where the generic engines keep a candidate's messages (a layout choice of
+ * this library, for codes with every column of degree at most 6): each row's
+ * edges permuted inside the row's storage window, each column's edges in the
+ * k slots of the padded column table (colK = 3 for a largest column degree of
+ * 3 or less, else 6), chosen so that the 32 lanes of an error-pass access
+ * meet distinct banks where possible.  bsd_create builds the same placement.
+ * Host only; nothing is allocated on a device.
+ *   M, N, H_row_ptr, H_col_idx  host, H in CSR as for bsd_create
+ *   edge_word  host int32[E]: out, the element of CSR edge e
+ *   slot_edge  host int32[colK * N]: out, the CSR edge in slot k of column j
+ *              at [k * N + j], -1 for an empty slot
+ *   colK       host int32: out, 3 or 6
+ *   excess     host int32: out, the bank loads above each 32-column group's
+ *              largest degree that the search leaves
+ * Errors: BSD_ERR_INVALID_ARG (null pointer, bad CSR), BSD_ERR_UNSUPPORTED
+ * (a column of degree above 6, or more than 2^20 edges). */
+int bsd_generic_layout(int32_t M, int32_t N, const int32_t *H_row_ptr, const int32_t *H_col_idx,
+                       int32_t *edge_word, int32_t *slot_edge, int32_t *colK, int32_t *excess);
+
 /* Opt-in timing of this library's kernels (not part of the method): while
  * enabled, every kernel launch made by bsd_decode / bsd_decode_host is
  * bracketed by two CUDA events recorded on the decode stream.  Enabling costs

@@ -31,7 +31,7 @@ BSD_STATUS_FAILED = 4
 
 # every symbol include/bsd.h declares
 EXPORTS = ("bsd_params_default", "bsd_params_preset", "bsd_create", "bsd_decode", "bsd_decode_host",
-           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_get_batch", "bsd_small_layout", "bsd_serve_start", "bsd_serve_decode",
+           "bsd_bp_llr", "bsd_sync_error", "bsd_get_info", "bsd_get_batch", "bsd_small_layout", "bsd_generic_layout", "bsd_serve_start", "bsd_serve_decode",
            "bsd_serve_stop", "bsd_profile_enable", "bsd_profile_read",
            "bsd_decode_noalloc", "bsd_set_weights", "bsd_unrolled_workspace", "bsd_unrolled_forward",
            "bsd_unrolled_backward", "bsd_profile_read_kinds", "bsd_autotune", "bsd_get_shape", "bsd_dem_parse",
@@ -90,6 +90,8 @@ def load(path: str | None = None) -> C.CDLL:
     lib.bsd_get_info.argtypes = [P] + [C.POINTER(C.c_int32)] * 4 + [C.POINTER(C.c_int64)] * 2
     lib.bsd_get_batch.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.bsd_small_layout.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.bsd_generic_layout.argtypes = [C.c_int32, C.c_int32, P, P, P, P, C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32)]
     lib.bsd_decode_noalloc.argtypes = [P, P, C.c_int64, P, P, P, P, P]
     lib.bsd_profile_enable.argtypes = [P, C.c_int]
     lib.bsd_set_weights.argtypes = [P, P, C.c_int32]
@@ -220,6 +222,23 @@ def bsd_small_layout(M: int, N: int, row_ptr, col_idx) -> dict:
     check(load().bsd_small_layout(int(M), int(N), rp.ctypes.data, ci.ctypes.data, plane.ctypes.data, ew.ctypes.data,
                                   cw.ctypes.data, C.byref(ext), C.byref(exc)), "bsd_small_layout")
     return dict(plane=plane, edge_word=ew, col_word=cw.reshape(int(N), 3), extent=ext.value, excess=exc.value)
+
+
+def bsd_generic_layout(M: int, N: int, row_ptr, col_idx) -> dict:
+    """The generic engines' placement of H's messages (host only): the
+    element of every CSR edge, the CSR edge in every (k, column) slot
+    ([colK][N], -1 empty), colK and the bank loads above the groups' largest
+    degrees left by the search."""
+    import numpy as np
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    ew = np.zeros(int(rp[-1]), np.int32)
+    se = np.zeros(6 * int(N), np.int32)
+    ck, exc = C.c_int32(), C.c_int32()
+    check(load().bsd_generic_layout(int(M), int(N), rp.ctypes.data, ci.ctypes.data, ew.ctypes.data, se.ctypes.data,
+                                    C.byref(ck), C.byref(exc)), "bsd_generic_layout")
+    return dict(edge_word=ew, slot_edge=se[:ck.value * int(N)].reshape(ck.value, int(N)), colK=ck.value,
+                excess=exc.value)
 
 
 def bsd_set_weights(dec, h_weights, T: int) -> None:

@@ -435,3 +435,31 @@ extern "C" int bsd_small_layout(int32_t M, int32_t N, const int32_t* H_row_ptr, 
     *excess = sl.excess;
     return BSD_OK;
 }
+
+extern "C" int bsd_generic_layout(int32_t M, int32_t N, const int32_t* H_row_ptr, const int32_t* H_col_idx,
+                                  int32_t* edge_word, int32_t* slot_edge, int32_t* colK, int32_t* excess)
+{
+    if (M < 1 || N < 1 || !H_row_ptr || !H_col_idx || !edge_word || !slot_edge || !colK || !excess)
+        return BSD_ERR_INVALID_ARG;
+    if (H_row_ptr[0] != 0) return BSD_ERR_INVALID_ARG;
+    for (int i = 0; i < M; ++i) {
+        if (H_row_ptr[i + 1] < H_row_ptr[i]) return BSD_ERR_INVALID_ARG;
+        for (int e = H_row_ptr[i]; e < H_row_ptr[i + 1]; ++e) {
+            if (H_col_idx[e] < 0 || H_col_idx[e] >= N) return BSD_ERR_INVALID_ARG;
+            if (e > H_row_ptr[i] && H_col_idx[e] <= H_col_idx[e - 1]) return BSD_ERR_INVALID_ARG;
+        }
+    }
+    const int E = H_row_ptr[M];
+    std::vector<int> cdeg(N, 0);
+    for (int e = 0; e < E; ++e) cdeg[H_col_idx[e]]++;
+    const int max_col = N > 0 ? *std::max_element(cdeg.begin(), cdeg.end()) : 0;
+    if (max_col > 6) return BSD_ERR_UNSUPPORTED;
+    const int K = max_col <= 3 ? 3 : 6;
+    bsd::GenericLayout gl;
+    if (!bsd::generic_layout(M, N, H_row_ptr, H_col_idx, K, &gl)) return BSD_ERR_UNSUPPORTED;
+    for (int e = 0; e < E; ++e) edge_word[e] = gl.pos[e];
+    for (size_t q = 0; q < gl.kedge.size(); ++q) slot_edge[q] = gl.kedge[q];
+    *colK = K;
+    *excess = gl.excess;
+    return BSD_OK;
+}

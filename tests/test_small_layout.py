@@ -105,3 +105,87 @@ def test_placement_of_random_regular_codes_is_valid(M, seed):
             for k in range(3):
                 words = cw[32 * c:32 * c + 32, k]
                 assert len(set((words % 32).tolist())) == len(words)
+
+
+# ----------------------------------------------------------------------------
+# the generic engines' placement (bsd_generic_layout)
+# ----------------------------------------------------------------------------
+def _check_generic(prob, lay):
+    rp, ci = prob.H_row_ptr, prob.H_col_idx
+    ew, se = lay["edge_word"], lay["slot_edge"]
+    # each row's edges fill exactly the row's window
+    for i in range(prob.M):
+        assert sorted(ew[rp[i]:rp[i + 1]].tolist()) == list(range(int(rp[i]), int(rp[i + 1])))
+    # every edge sits in exactly one slot, of its own column
+    seen = np.zeros(int(rp[-1]), np.int64)
+    for k in range(lay["colK"]):
+        for j in range(prob.N):
+            e = int(se[k, j])
+            if e >= 0:
+                assert ci[e] == j
+                seen[e] += 1
+    assert (seen == 1).all()
+
+
+def _wavefronts(prob, word_of, slot_edge):
+    """Bank-conflict wavefronts of the error pass's message accesses: per
+    (32-column group, slot), the busiest bank's count."""
+    tot = 0
+    for c in range((prob.N + 31) // 32):
+        for k in range(slot_edge.shape[0]):
+            banks = [word_of(int(slot_edge[k, j])) % 32 for j in range(32 * c, min(prob.N, 32 * c + 32))
+                     if slot_edge[k, j] >= 0]
+            if banks:
+                tot += max(np.bincount(banks))
+    return tot
+
+
+@pytest.mark.parametrize("name", ["phenomenological", "synthetic"])
+def test_generic_placement_of_the_dems(name):
+    prob = W.bb_phenomenological(12, 6, 12, 3e-3, 3e-3) if name == "phenomenological" else W.synthetic_dem()
+    lay = B.bsd_generic_layout(prob.M, prob.N, prob.H_row_ptr, prob.H_col_idx)
+    _check_generic(prob, lay)
+    # the CSR order, slots in the column lists' order, for comparison
+    rp, ci = prob.H_row_ptr, prob.H_col_idx
+    csr = -np.ones_like(lay["slot_edge"])
+    fill = np.zeros(prob.N, np.int64)
+    for e in range(int(rp[-1])):
+        j = ci[e]
+        csr[fill[j], j] = e
+        fill[j] += 1
+    before = _wavefronts(prob, lambda e: e, csr)
+    after = _wavefronts(prob, lambda e: int(lay["edge_word"][e]), lay["slot_edge"])
+    assert after < 0.4 * before
+    if name == "synthetic":
+        # conflict-free: one wavefront per (group, slot) that has an edge
+        assert lay["excess"] == 0
+        ideal = sum(1 for c in range((prob.N + 31) // 32) for k in range(lay["colK"])
+                    if (lay["slot_edge"][k, 32 * c:32 * c + 32] >= 0).any())
+        assert after == ideal
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_generic_placement_of_random_codes_is_valid(seed):
+    """Columns of degree 0 to 6 (holes in the slots), rows of any degree
+    including 1."""
+    rng = np.random.default_rng(100 + seed)
+    M, N = 30 + 7 * seed, 150 + 40 * seed
+    H = np.zeros((M, N), np.uint8)
+    for j in range(N):
+        d = int(rng.integers(0, 7 if seed % 2 else 4))
+        if d:
+            H[rng.choice(M, size=d, replace=False), j] = 1
+    prob = W.problem_from_dense(H, np.zeros((1, N), np.uint8), np.full(N, 0.05), name=f"gen_{seed}")
+    lay = B.bsd_generic_layout(prob.M, prob.N, prob.H_row_ptr, prob.H_col_idx)
+    assert lay["colK"] == (6 if seed % 2 else 3)
+    _check_generic(prob, lay)
+
+
+def test_generic_placement_rejects_higher_degrees():
+    rng = np.random.default_rng(7)
+    H = (rng.random((40, 60)) < 0.05).astype(np.uint8)
+    H[:8, 0] = 1                                   # a column of degree 8
+    prob = W.problem_from_dense(H, np.zeros((1, 60), np.uint8), np.full(60, 0.05))
+    with pytest.raises(B.BsdError) as ei:
+        B.bsd_generic_layout(prob.M, prob.N, prob.H_row_ptr, prob.H_col_idx)
+    assert ei.value.code == B.BSD_ERR_UNSUPPORTED
