@@ -590,13 +590,11 @@ struct SmallEngine {
         uint32_t sb[RPL];
 #pragma unroll
         for (int r = 0; r < RPL; ++r) sb[r] = (lane + 32 * r < g.M) ? ((st.sp[r] >> lane) & 1u) << 31 : 0u;
-        const uint32_t spw = lane < RPL ? st.sp[lane] : 0u;
         int iters = 0;
         int ok = 0;
         for (int t = 1; t <= max_iters; ++t) {
             unsigned long long ab_key = 0ull;
             if (ab.key != nullptr && lane == 0) ab_key = *((volatile const unsigned long long*)ab.key);
-            if (lane < RPL) st.par[lane] = spw;           // the code's M bits fill RPL words
             // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
             const float* wt = W ? cfg.sweights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
             // ---- detector pass (Eq. 1); a run from E(0) takes its first check
@@ -680,7 +678,12 @@ struct SmallEngine {
                 }
             }
             __syncwarp();
-            // ---- error-node pass (Eqs. 2-4)
+            // ---- error-node pass (Eqs. 2-4); hx: the XOR of the columns of H
+            // of the lane's columns with e^_j = 1, reduced over the warp into
+            // H e^ after the pass (the code's M bits fill RPL words)
+            uint32_t hx[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) hx[q] = 0u;
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
                 // every column is computed; a masked column or one beyond N
@@ -718,22 +721,23 @@ struct SmallEngine {
                 sum[c] = __fadd_rn(sum[c], post);           // unused for masked columns
                 if (kPostOut && t == max_iters && inr) post_out[lane + 32 * c] = post;
                 const uint32_t ebit = (act && post <= 0.f) ? 1u : 0u;                // Eq. 4
-                if (ebit) {
+                // column j of H, read only where e^_j = 1 (predicated, no branch)
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const int r = (int)(ci[c][k] & 0xffffu);
-                        atomicXor(&st.par[r >> 5], 1u << (r & 31));
-                    }
+                for (int q = 0; q < RPL; ++q) {
+                    uint32_t h = 0u;
+                    if (ebit) h = __ldg(g.hcol + (size_t)(lane + 32 * c) * RPL + q);
+                    hx[q] ^= h;
                 }
                 const uint32_t bal = __ballot_sync(FULLMASK, ebit);
                 if (lane == 0) st.ehat[c] = bal;
             }
+            // stopping rule: H e^ = s' word by word (every lane gets the same
+            // reductions, so the decision needs no vote)
+            uint32_t nz = 0u;
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) nz |= __reduce_xor_sync(FULLMASK, hx[q]) ^ st.sp[q];
             __syncwarp();
-            uint32_t nz = 0;
-            if (lane < RPL) nz = st.par[lane];
-            // (a lane reads and, next iteration, resets only its own word of
-            // par; the other lanes' atomics come after the detector pass sync)
-            ok = !__any_sync(FULLMASK, nz != 0u);
+            ok = (nz == 0u);
             iters = t;
             if (ok && stop) break;
             if (ab.key != nullptr && __any_sync(FULLMASK, lane == 0 && ab.hit(ab_key))) { ok = 0; break; }
