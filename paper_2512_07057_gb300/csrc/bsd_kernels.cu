@@ -500,7 +500,9 @@ struct GenericEngine {
     {
         for (int j = grp.rank(); j < g.N; j += grp.size()) st.sumllr[j] = 0.f;
     }
-    template <bool kPostOut = false>
+    // (kAtomicStop selects the small engine's form of the stopping rule; the
+    // generic engines have one form)
+    template <bool kPostOut = false, bool kAtomicStop = false>
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
                        int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
     {
@@ -524,8 +526,14 @@ struct GenericEngine {
 // h kPlane + 2 i, so the detector pass moves 32 consecutive pairs per access,
 // and the error pass gathers and scatters through a per-(column, k) word
 // table chosen to put the 32 lanes in 32 distinct banks.  Each lane keeps its
-// columns' words and rows, sum_LLR and mask bits in registers for the warp's
-// lifetime.  The detector pass writes D_{i->j} itself for every edge, so the
+// columns' words, sum_LLR and mask bits in registers for the warp's lifetime.
+// The stopping rule forms H e^ from the columns of H of the lane's columns
+// with e^_j = 1 and three warp XOR reductions, with no shared-memory atomics
+// (kAtomicStop: XOR of the set columns' rows into shared words instead, which
+// the seed kernel uses: most of its runs stop after one or two iterations,
+// where the reductions' latency is not hidden).  The warp's e^ words stay in
+// registers and are written once, after the last iteration.
+// The detector pass writes D_{i->j} itself for every edge, so the
 // error-node pass gathers one 4-byte message per edge; the ascending-order
 // sums of three messages are formed from min / max / median directly.  Every
 // value it produces is the one GenericEngine produces (same operations, same
@@ -572,7 +580,7 @@ struct SmallEngine {
 #pragma unroll
         for (int c = 0; c < CPL; ++c) sum[c] = 0.f;
     }
-    template <bool kPostOut = false>
+    template <bool kPostOut = false, bool kAtomicStop = false>
     __device__ int run(const DevGraph& g, const DecCfg& cfg, const WarpState& st, int max_iters, bool stop,
                        int* success, float* post_out, bool from_prior = false, const AbortCheck& ab = AbortCheck{})
     {
@@ -590,11 +598,16 @@ struct SmallEngine {
         uint32_t sb[RPL];
 #pragma unroll
         for (int r = 0; r < RPL; ++r) sb[r] = (lane + 32 * r < g.M) ? ((st.sp[r] >> lane) & 1u) << 31 : 0u;
+        const uint32_t spw = lane < RPL ? st.sp[lane] : 0u;
         int iters = 0;
         int ok = 0;
+        uint32_t bal[CPL];     // e^ words of the last iteration (the same in every lane)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) bal[c] = 0u;
         for (int t = 1; t <= max_iters; ++t) {
             unsigned long long ab_key = 0ull;
             if (ab.key != nullptr && lane == 0) ab_key = *((volatile const unsigned long long*)ab.key);
+            if (kAtomicStop && lane < RPL) st.par[lane] = spw;
             // weighted min-sum: row min(t, wT) - 1 of the weights in place of alpha
             const float* wt = W ? cfg.sweights + (size_t)((t < cfg.wT ? t : cfg.wT) - 1) * (size_t)g.Epad : nullptr;
             // ---- detector pass (Eq. 1); a run from E(0) takes its first check
@@ -721,27 +734,47 @@ struct SmallEngine {
                 sum[c] = __fadd_rn(sum[c], post);           // unused for masked columns
                 if (kPostOut && t == max_iters && inr) post_out[lane + 32 * c] = post;
                 const uint32_t ebit = (act && post <= 0.f) ? 1u : 0u;                // Eq. 4
-                // column j of H, read only where e^_j = 1 (predicated, no branch)
+                if (kAtomicStop) {
+                    if (ebit) {
 #pragma unroll
-                for (int q = 0; q < RPL; ++q) {
-                    uint32_t h = 0u;
-                    if (ebit) h = __ldg(g.hcol + (size_t)(lane + 32 * c) * RPL + q);
-                    hx[q] ^= h;
+                        for (int k = 0; k < 3; ++k) {
+                            const int r = (int)(ci[c][k] & 0xffffu);
+                            atomicXor(&st.par[r >> 5], 1u << (r & 31));
+                        }
+                    }
+                } else {
+                    // column j of H, read only where e^_j = 1 (predicated, no branch)
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) {
+                        uint32_t h = 0u;
+                        if (ebit) h = __ldg(g.hcol + (size_t)(lane + 32 * c) * RPL + q);
+                        hx[q] ^= h;
+                    }
                 }
-                const uint32_t bal = __ballot_sync(FULLMASK, ebit);
-                if (lane == 0) st.ehat[c] = bal;
+                bal[c] = __ballot_sync(FULLMASK, ebit);
             }
             // stopping rule: H e^ = s' word by word (every lane gets the same
             // reductions, so the decision needs no vote)
-            uint32_t nz = 0u;
+            if (kAtomicStop) {
+                __syncwarp();
+                uint32_t nz = 0;
+                if (lane < RPL) nz = st.par[lane];
+                ok = !__any_sync(FULLMASK, nz != 0u);
+            } else {
+                uint32_t nz = 0u;
 #pragma unroll
-            for (int q = 0; q < RPL; ++q) nz |= __reduce_xor_sync(FULLMASK, hx[q]) ^ st.sp[q];
-            __syncwarp();
-            ok = (nz == 0u);
+                for (int q = 0; q < RPL; ++q) nz |= __reduce_xor_sync(FULLMASK, hx[q]) ^ st.sp[q];
+                __syncwarp();
+                ok = (nz == 0u);
+            }
             iters = t;
             if (ok && stop) break;
             if (ab.key != nullptr && __any_sync(FULLMASK, lane == 0 && ab.hit(ab_key))) { ok = 0; break; }
         }
+        // e^ of the last iteration run
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+            if (lane == c && iters > 0) st.ehat[c] = bal[c];
         *success = ok;
         return iters;
     }
@@ -1222,7 +1255,7 @@ __global__ void __launch_bounds__(Eng::kMaxThreads, Eng::kMinBlocks) k_seed(DevG
         if (!Eng::kPriorSetsSums) eng.clear_sums(g, st);
         grp.sync();
         int succ = 0;
-        const int it = eng.run(g, cfg, st, cfg.initial_iters, true, &succ, nullptr, true);
+        const int it = eng.template run<false, true>(g, cfg, st, cfg.initial_iters, true, &succ, nullptr, true);
         if (grp.rank() == 0) seed_iters += (unsigned long long)it;
         grp.sync();
         if ((succ && cfg.num_results == 1) || cfg.max_rounds == 0) {
