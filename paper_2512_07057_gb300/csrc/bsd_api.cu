@@ -505,10 +505,20 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     gb += align256(sizeof(int) * colperm.size());
     gb += align256(sizeof(int2) * colseq.size());
     gb += align256(sizeof(float) * colRD.size());
+    // the single-warp engine's per-column record: Lambda_j and column j of H in one 16-byte load
+    std::vector<uint32_t> slamh;
+    if (has_sl) {
+        slamh.assign((size_t)4 * 32 * WN, 0u);
+        for (int j = 0; j < N; ++j) {
+            std::memcpy(&slamh[(size_t)4 * j], &lam[j], sizeof(float));
+            for (int q = 0; q < WM && q < 3; ++q) slamh[(size_t)4 * j + 1 + q] = hcol[(size_t)j * WM + q];
+        }
+    }
     if (has_sl) {
         gb += align256(sizeof(uint32_t) * sl.col.size());
         gb += align256(sizeof(float) * sD0.size());
         gb += align256(slamE_st.size());
+        gb += align256(sizeof(uint32_t) * slamh.size());
     }
     if (CUDA_FAILED(cudaMalloc(&dec->graph_mem, gb))) { bsd_destroy(dec); return BSD_ERR_OOM; }
     dec->graph_bytes = gb;
@@ -533,6 +543,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     uint32_t* d_scol = has_sl ? carve<uint32_t>(p, sl.col.size()) : nullptr;
     float* d_sD0 = has_sl ? carve<float>(p, sD0.size()) : nullptr;
     unsigned char* d_slamE = has_sl ? carve<unsigned char>(p, slamE_st.size()) : nullptr;
+    uint32_t* d_slamh = has_sl ? carve<uint32_t>(p, slamh.size()) : nullptr;
     bool ok = !CUDA_FAILED(cudaMemcpy(d_row_ptr, H_row_ptr, sizeof(int) * (M + 1), cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_row_col, H_col_idx, sizeof(int) * E, cudaMemcpyHostToDevice)) &&
               !CUDA_FAILED(cudaMemcpy(d_col_ptr, col_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice)) &&
@@ -557,7 +568,8 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
               (!has_sl ||
                (!CUDA_FAILED(cudaMemcpy(d_scol, sl.col.data(), sizeof(uint32_t) * sl.col.size(), cudaMemcpyHostToDevice)) &&
                 !CUDA_FAILED(cudaMemcpy(d_sD0, sD0.data(), sizeof(float) * sD0.size(), cudaMemcpyHostToDevice)) &&
-                !CUDA_FAILED(cudaMemcpy(d_slamE, slamE_st.data(), slamE_st.size(), cudaMemcpyHostToDevice))));
+                !CUDA_FAILED(cudaMemcpy(d_slamE, slamE_st.data(), slamE_st.size(), cudaMemcpyHostToDevice)) &&
+                !CUDA_FAILED(cudaMemcpy(d_slamh, slamh.data(), sizeof(uint32_t) * slamh.size(), cudaMemcpyHostToDevice))));
     if (!ok) { bsd_destroy(dec); return BSD_ERR_CUDA; }
 
     DevGraph& g = dec->g;
@@ -573,7 +585,7 @@ int bsd_create(int32_t M, int32_t N, int32_t K, const int32_t* H_row_ptr, const 
     g.colperm = d_colperm; g.colseq = d_colseq;
     g.colRD = reinterpret_cast<const float4*>(d_colRD); g.colRDk = rdk;
     for (int d = 0; d < kMaxColDeg + 2; ++d) { g.dstart[d] = dstart[d]; g.dbase[d] = dbase[d]; }
-    g.scol = d_scol; g.sD0 = d_sD0; g.slamE = d_slamE;
+    g.scol = d_scol; g.sD0 = d_sD0; g.slamE = d_slamE; g.slamh = reinterpret_cast<const uint4*>(d_slamh);
     if (has_gl) dec->generic_pos = gl.pos;
     if (has_sl) {
         dec->small_excess = sl.excess;

@@ -88,6 +88,8 @@ struct DevGraph {
     const uint32_t* scol;  // [3 N], null when the code has no such placement
     const float* sD0;      // [Epad]
     const void* slamE;     // [Epad] in the storage format
+    const uint4* slamh;    // [32 WN] with the placement: per column slot j the bits of Lambda_j and the
+                           // (at most 3) words of column j of H; zero past N
 };
 
 struct DecCfg {

@@ -550,6 +550,7 @@ struct SmallEngine {
     WarpGroup grp;
     using S = Store<P>;
     static_assert(RD == 6, "the placement holds rows of degree 6");
+    static_assert(RPL <= 3, "the per-column record holds at most three words of a column of H");
     static constexpr int kPlane = small_plane_stride_rpl(RPL);   // words between a row's pairs
     uint32_t ci[CPL][3];   // (word << 16) | row of the k-th edge of column lane + 32 c
     float sum[CPL];
@@ -710,7 +711,9 @@ struct SmallEngine {
                     ed[k] = (int)(ci[c][k] >> 16);
                     v[k] = st.D[ed[k]];
                 }
-                const float l = inr ? __ldg(g.lam + lane + 32 * c) : 0.f;
+                // Lambda_j and column j of H in one 16-byte record (zero past N)
+                const uint4 lh = __ldg(g.slamh + lane + 32 * c);
+                const float l = __uint_as_float(lh.x);
                 // Eq. 2: each message leaves its own detector out; the other two
                 // are added in ascending order.  Messages are stored unclamped:
                 // the detector pass reads min(|E|, L_MAX) and the sign, which is
@@ -743,13 +746,11 @@ struct SmallEngine {
                         }
                     }
                 } else {
-                    // column j of H, read only where e^_j = 1 (predicated, no branch)
+                    // column j of H where e^_j = 1
+                    const uint32_t em = 0u - ebit;
+                    const uint32_t hw[3] = {lh.y, lh.z, lh.w};
 #pragma unroll
-                    for (int q = 0; q < RPL; ++q) {
-                        uint32_t h = 0u;
-                        if (ebit) h = __ldg(g.hcol + (size_t)(lane + 32 * c) * RPL + q);
-                        hx[q] ^= h;
-                    }
+                    for (int q = 0; q < RPL; ++q) hx[q] ^= hw[q] & em;
                 }
                 bal[c] = __ballot_sync(FULLMASK, ebit);
             }
